@@ -1,0 +1,234 @@
+/*
+ * Plain CPU oracle for all-pairs identity-by-state (IBS) counts.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may link, load or
+ * call this file; it exists so that tests, the smoke check and the CPU-baseline
+ * leg of the benchmark can compare the GPU library against an obviously
+ * correct reading of the paper.  It shares no code, header or table with the
+ * CUDA library.
+ *
+ * Source of the definition: "Second-generation PLINK" (Chang et al.),
+ * section "Improvements in PLINK 1.9 / Bitwise parallelism", the per-marker
+ * identity-by-state loop of PLINK 1.07:
+ *   for every sample pair (i, j), for every marker k:
+ *     1. if i_k or j_k is a missing call, skip the marker;
+ *     2. if i_k equals j_k, count IBS2;
+ *     3. otherwise, if both bits of the 2-bit codes differ, count IBS0;
+ *     4. otherwise count IBS1.
+ * The count of markers that were not skipped is N (= IBS0 + IBS1 + IBS2).
+ *
+ * Genotype codes are the PLINK 1 binary 2-bit values ("Bitwise parallelism":
+ * packed 2-bit elements, 4 per byte), read as the integer
+ * (byte >> 2*(s % 4)) & 3 for sample s:
+ *   0 = homozygous A1, 1 = missing, 2 = heterozygous, 3 = homozygous A2.
+ * The input buffer is variant-major: row k holds ceil(n/4) bytes, sample s in
+ * byte s/4.  Bits of a row's last byte that belong to no sample are ignored.
+ *
+ * Derived distance (the paper prints IBS similarity; its complement is used):
+ *   dist = (IBS1 + 2*IBS0) / (2*N) in IEEE double, one rounded division,
+ *   and NaN when N == 0.
+ *
+ * The pair loop is deliberately the plain definition: one byte per genotype,
+ * one comparison per marker, no blocking.  Threads split the rows i only; each
+ * output element is produced by exactly the same sequence of operations
+ * whatever the thread count.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <unistd.h>
+
+#define ORACLE_MISSING 1
+
+/* Unpack a variant-major packed matrix into one byte per genotype, sample-major:
+ * G[s * m + k] = code of sample s at marker k. */
+int oracle_unpack(const uint8_t* packed, int64_t n, int64_t m, uint8_t* G) {
+  if (n <= 0 || m <= 0 || !packed || !G) return 1;
+  const int64_t row_bytes = (n + 3) / 4;
+  for (int64_t k = 0; k < m; ++k) {
+    const uint8_t* row = packed + k * row_bytes;
+    for (int64_t s = 0; s < n; ++s) {
+      const uint8_t byte = row[s / 4];
+      const int shift = (int)(2 * (s % 4));
+      G[s * m + k] = (uint8_t)((byte >> shift) & 3u);
+    }
+  }
+  return 0;
+}
+
+/* Unpack selected samples over a window of markers [var_begin, var_begin +
+ * var_len) of a variant-major packed matrix with n samples:
+ * G[r * var_len + k] = code of sample sel[r] at marker var_begin + k. */
+int oracle_unpack_subset(const uint8_t* packed, int64_t n, int64_t m,
+                         const int64_t* sel, int64_t n_sel,
+                         int64_t var_begin, int64_t var_len, uint8_t* G) {
+  if (!packed || !sel || !G || n <= 0 || m <= 0 || n_sel <= 0 || var_len <= 0) return 1;
+  if (var_begin < 0 || var_begin + var_len > m) return 1;
+  const int64_t row_bytes = (n + 3) / 4;
+  for (int64_t r = 0; r < n_sel; ++r) {
+    const int64_t s = sel[r];
+    if (s < 0 || s >= n) return 1;
+    for (int64_t k = 0; k < var_len; ++k) {
+      const uint8_t byte = packed[(var_begin + k) * row_bytes + s / 4];
+      G[r * var_len + k] = (uint8_t)((byte >> (2 * (s % 4))) & 3u);
+    }
+  }
+  return 0;
+}
+
+/* The per-marker rule for one pair of unpacked genotype rows. */
+static void oracle_pair(const uint8_t* gi, const uint8_t* gj, int64_t m, int32_t out[4]) {
+  int64_t ibs0 = 0, ibs1 = 0, ibs2 = 0, nn = 0;
+  for (int64_t k = 0; k < m; ++k) {
+    const uint8_t a = gi[k];
+    const uint8_t b = gj[k];
+    if (a == ORACLE_MISSING || b == ORACLE_MISSING) continue; /* step 1 */
+    nn += 1;
+    if (a == b) {
+      ibs2 += 1;                       /* step 2 */
+    } else if ((a ^ b) == 3) {
+      ibs0 += 1;                       /* step 3: both bits differ */
+    } else {
+      ibs1 += 1;                       /* step 4 */
+    }
+  }
+  out[0] = (int32_t)ibs0;
+  out[1] = (int32_t)ibs1;
+  out[2] = (int32_t)ibs2;
+  out[3] = (int32_t)nn;
+}
+
+static double oracle_dist(const int32_t c[4]) {
+  if (c[3] == 0) return NAN;
+  return (double)(c[1] + 2 * (int64_t)c[0]) / (2.0 * (double)c[3]);
+}
+
+typedef struct {
+  const uint8_t* GA;      /* rows side, sample-major [*][m] */
+  const uint8_t* GB;      /* columns side, sample-major [*][m] */
+  int64_t m;
+  const int64_t* rows;    /* row indices into GA */
+  int64_t n_rows;
+  const int64_t* cols;    /* column indices into GB */
+  int64_t n_cols;
+  int32_t* out_counts;    /* [n_rows][n_cols][4] */
+  double* out_dist;       /* [n_rows][n_cols] or NULL */
+  int64_t next;           /* next row to take (guarded by lock) */
+  pthread_mutex_t lock;
+} oracle_job;
+
+static void* oracle_worker(void* arg) {
+  oracle_job* job = (oracle_job*)arg;
+  for (;;) {
+    pthread_mutex_lock(&job->lock);
+    const int64_t r = job->next++;
+    pthread_mutex_unlock(&job->lock);
+    if (r >= job->n_rows) break;
+    const uint8_t* gi = job->GA + job->rows[r] * job->m;
+    for (int64_t c = 0; c < job->n_cols; ++c) {
+      const uint8_t* gj = job->GB + job->cols[c] * job->m;
+      int32_t* o = job->out_counts + (r * job->n_cols + c) * 4;
+      oracle_pair(gi, gj, job->m, o);
+      if (job->out_dist) job->out_dist[r * job->n_cols + c] = oracle_dist(o);
+    }
+  }
+  return NULL;
+}
+
+/* Counts for every (row, column) combination of two lists of samples, which
+ * may come from two different unpacked matrices with the same markers (a query
+ * set against a panel) or from the same one (the all-pairs matrix).
+ * threads <= 0 means one thread per online core.  Returns the thread count
+ * used, or -1 on bad arguments. */
+int oracle_ibs_block(const uint8_t* GA, const uint8_t* GB, int64_t m,
+                     const int64_t* rows, int64_t n_rows,
+                     const int64_t* cols, int64_t n_cols,
+                     int32_t* out_counts, double* out_dist, int threads) {
+  if (!GA || !GB || !rows || !cols || !out_counts || m <= 0 || n_rows < 0 || n_cols < 0) return -1;
+  if (threads <= 0) {
+    long c = sysconf(_SC_NPROCESSORS_ONLN);
+    threads = c > 0 ? (int)c : 1;
+  }
+  if (threads > 1024) threads = 1024;
+  if (n_rows < threads) threads = n_rows > 0 ? (int)n_rows : 1;
+  oracle_job job;
+  job.GA = GA; job.GB = GB; job.m = m;
+  job.rows = rows; job.n_rows = n_rows; job.cols = cols; job.n_cols = n_cols;
+  job.out_counts = out_counts; job.out_dist = out_dist; job.next = 0;
+  pthread_mutex_init(&job.lock, NULL);
+  if (threads == 1) {
+    oracle_worker(&job);
+  } else {
+    pthread_t* tids = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)threads);
+    int started = 0;
+    for (int t = 0; t < threads; ++t) {
+      if (pthread_create(&tids[t], NULL, oracle_worker, &job) == 0) started++;
+      else break;
+    }
+    if (started == 0) oracle_worker(&job);
+    for (int t = 0; t < started; ++t) pthread_join(tids[t], NULL);
+    free(tids);
+    if (started > 0) threads = started; else threads = 1;
+  }
+  pthread_mutex_destroy(&job.lock);
+  return threads;
+}
+
+/* Full upper triangle including the diagonal, row-major over i <= j:
+ * pair (i, j) sits at index i*n - i*(i-1)/2 + (j - i).  Rows are handed to
+ * threads one at a time; row i visits j = i .. n-1 in order. */
+typedef struct {
+  const uint8_t* G;
+  int64_t n, m;
+  int32_t* out_counts;
+  double* out_dist;
+  int64_t next;
+  pthread_mutex_t lock;
+} oracle_tri_job;
+
+static void* oracle_tri_worker(void* arg) {
+  oracle_tri_job* job = (oracle_tri_job*)arg;
+  for (;;) {
+    pthread_mutex_lock(&job->lock);
+    const int64_t i = job->next++;
+    pthread_mutex_unlock(&job->lock);
+    if (i >= job->n) break;
+    const int64_t base = i * job->n - i * (i - 1) / 2;
+    const uint8_t* gi = job->G + i * job->m;
+    for (int64_t j = i; j < job->n; ++j) {
+      int32_t* o = job->out_counts + (base + j - i) * 4;
+      oracle_pair(gi, job->G + j * job->m, job->m, o);
+      if (job->out_dist) job->out_dist[base + j - i] = oracle_dist(o);
+    }
+  }
+  return NULL;
+}
+
+int oracle_ibs_triangle(const uint8_t* G, int64_t n, int64_t m,
+                        int32_t* out_counts, double* out_dist, int threads) {
+  if (!G || n <= 0 || m <= 0 || !out_counts) return -1;
+  if (threads <= 0) {
+    long c = sysconf(_SC_NPROCESSORS_ONLN);
+    threads = c > 0 ? (int)c : 1;
+  }
+  if (threads > 1024) threads = 1024;
+  if (n < threads) threads = (int)n;
+  oracle_tri_job job;
+  job.G = G; job.n = n; job.m = m; job.out_counts = out_counts; job.out_dist = out_dist; job.next = 0;
+  pthread_mutex_init(&job.lock, NULL);
+  int started = 0;
+  if (threads > 1) {
+    pthread_t* tids = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)threads);
+    for (int t = 0; t < threads; ++t) {
+      if (pthread_create(&tids[t], NULL, oracle_tri_worker, &job) == 0) started++;
+      else break;
+    }
+    for (int t = 0; t < started; ++t) pthread_join(tids[t], NULL);
+    free(tids);
+  }
+  if (started == 0) { oracle_tri_worker(&job); started = 1; }
+  pthread_mutex_destroy(&job.lock);
+  return started;
+}

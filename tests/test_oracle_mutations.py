@@ -1,0 +1,46 @@
+"""Planted mistakes in the oracle must fail its pins.
+
+Each case copies ``oracle/ibs_oracle.c``, plants one plausible mistake (a
+wrong condition, a wrong bit order, a dropped factor, a swapped output, a
+skipped diagonal), builds it with gcc into a temporary library and runs the
+pin tests against it through IBS_ORACLE_LIB.  The pins pass on the real
+oracle and must fail on every mutant.  All of this runs on the CPU.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "ibs_oracle.c")
+
+MUTATIONS = {
+    "ibs0_condition": ("} else if ((a ^ b) == 3) {", "} else if ((a ^ b) == 2) {"),
+    "bit_order": ("const int shift = (int)(2 * (s % 4));", "const int shift = (int)(6 - 2 * (s % 4));"),
+    "missing_code": ("#define ORACLE_MISSING 1", "#define ORACLE_MISSING 2"),
+    "dist_dropped_factor": ("return (double)(c[1] + 2 * (int64_t)c[0]) / (2.0 * (double)c[3]);",
+                            "return (double)(c[1] + (int64_t)c[0]) / (2.0 * (double)c[3]);"),
+    "swapped_outputs": ("out[0] = (int32_t)ibs0;\n  out[1] = (int32_t)ibs1;",
+                        "out[0] = (int32_t)ibs1;\n  out[1] = (int32_t)ibs0;"),
+    "skip_needs_both_missing": ("if (a == ORACLE_MISSING || b == ORACLE_MISSING) continue;",
+                                "if (a == ORACLE_MISSING && b == ORACLE_MISSING) continue;"),
+    "no_diagonal": ("for (int64_t j = i; j < job->n; ++j) {", "for (int64_t j = i + 1; j < job->n; ++j) {"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_fails_pins(name, tmp_path):
+    old, new = MUTATIONS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    mutant = tmp_path / "mutant.c"
+    mutant.write_text(src.replace(old, new))
+    lib = tmp_path / "libmutant.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_POSIX_C_SOURCE=200809L", "-shared", "-fPIC", "-pthread",
+                           str(mutant), "-o", str(lib), "-lm"])
+    env = dict(os.environ, IBS_ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"mutant {name} passed every pin:\n{r.stdout[-2000:]}"
