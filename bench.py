@@ -1,0 +1,419 @@
+#!/usr/bin/env python3
+"""All-pairs IBS benchmark: sample-pair x variant comparisons per second.
+
+Default workload: the plain IBS matrix of n = 4,096 samples x m = 100,000
+variants (MAF ~ U(0.01, 0.5), 2% missing i.i.d. plus 0.5% of variants at 30%
+missing), synthetic, on one GB300.  One step = one ibs_compute call (bit-plane
+transpose + triangular pair-count kernel with the fused epilogue) over inputs
+already resident in HBM; L2 is flushed (256 MiB write) between steps outside
+the timed events.  `e2e` repeats the step through the same C ABI with the
+packed input in pinned host memory and the counts and distances copied back
+each step.  `roofline` compares the pair-count kernel, timed with CUDA events
+on its own stream inside the library, with the integer-pipe ceiling derived
+from a live microbenchmark of POPC / LOP3 / IADD3 throughput.  `cpu_baseline`
+times the CPU oracle on a bounded row sample of the same workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload plain|structured|batch|serve]
+
+With N > 1 (torchrun, one rank per GPU) every rank runs its own copy of the
+workload (replicas; weak scaling) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sample-pair×variant comparisons/s; served p50/p99 latency vs plain GPU path"
+UNIT = "comparisons/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clk_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for ln in open(self.path):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) == len(self.FIELDS):
+                rows.append(parts)
+        os.unlink(self.path)
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[0]) for r in rows if num(r[0]) is not None]
+        smax = [num(r[1]) for r in rows if num(r[1]) is not None]
+        power = [num(r[2]) for r in rows if num(r[2]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        loaded = [s for s in sm if smax and s > 0.3 * max(smax)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# integer-pipe roofline
+
+def int_pipe_roofline(probe: dict, sm_mhz: float | None) -> dict:
+    """Best comparisons per clock per SM over the two exact instruction mixes
+    the pair loop can issue, from the measured per-SM pipe rates.
+
+    Per pair and 32-marker word: plain = 3 POPC + 4 LOP3 + 1.5 IADD3;
+    carry-save over 3 words = 2 POPC + 6 LOP3 + 2 adds.  LOP3 and the adds
+    share the ALU pipe; POPC has its own.  Time per pair-word is the larger of
+    the POPC time and the ALU time."""
+    r_popc, r_lop, r_add = probe["popc_per_clk_sm"], probe["lop3_per_clk_sm"], probe["iadd3_per_clk_sm"]
+    r_alu = min(r_lop, r_add)
+    mixes = {"plain": (3.0, 4.0 + 1.5), "csa3": (2.0, 6.0 + 2.0)}
+    best = {}
+    for name, (popc, alu) in mixes.items():
+        t = max(popc / r_popc, alu / r_alu)
+        best[name] = 32.0 / t
+    comps_clk_sm = max(best.values())
+    mhz = sm_mhz or probe["sm_mhz"]
+    return {"comps_per_clk_sm": comps_clk_sm, "by_mix": best, "sm_mhz": mhz,
+            "peak": comps_clk_sm * probe["sms"] * mhz * 1e6}
+
+
+def hbm_peak_gbs() -> float:
+    """Measured copy bandwidth of the GB300s; 6.8 TB/s fallback when absent."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except Exception:
+        return 6800.0
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("ibs_pairs.cu", "ibs_device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1410_4803_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(name: str):
+    """DRAM bytes per launch of the pair kernel from the committed ncu summary,
+    or None when the summary is missing or the kernel source changed since."""
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_hash = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", text)
+    m_bytes = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_hash or not m_bytes or m_hash.group(1) != kernel_source_hash():
+        return None
+    return float(m_bytes.group(1))
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline
+
+def oracle_rate(packed, n, m, target_s: float, threads: int = 0):
+    """Time the oracle on a row sample sized to about target_s seconds.
+    Returns (comparisons/s, threads, sample description, seconds)."""
+    import numpy as np
+    import oracle
+    G = oracle.unpack(packed, n, m)
+    cores = os.cpu_count() or 1
+    rows0 = np.arange(min(n, cores), dtype=np.int64)
+    t = time.perf_counter()
+    oracle.ibs_block(G, G, rows=rows0, threads=threads)
+    dt0 = time.perf_counter() - t
+    per_row = dt0 / rows0.size * min(cores, rows0.size)  # seconds per row-wave
+    R = int(max(rows0.size, min(n, rows0.size * target_s / max(dt0, 1e-6))))
+    rows = np.linspace(0, n - 1, R).astype(np.int64)
+    t = time.perf_counter()
+    _, _ = oracle.ibs_block(G, G, rows=rows, threads=threads)
+    dt = time.perf_counter() - t
+    comps = R * (n - 1) * m
+    used = threads if threads > 0 else cores
+    del per_row
+    return comps / dt, used, f"{R} rows x all {n} columns x {m} variants", dt
+
+
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def reduce_max(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def make_workload(name: str):
+    from paper_1410_4803_gb300 import synth
+    if name == "plain":
+        return synth.plain_config2()
+    if name == "structured":
+        return synth.structured_config3()
+    raise ValueError(name)
+
+
+def run_plain(args, rank, world, local):
+    import numpy as np
+    import torch
+    from paper_1410_4803_gb300 import ibs
+
+    torch.cuda.set_device(local)
+    w = make_workload(args.workload)
+    n, m = w.n, w.m
+    comps = n * (n - 1) // 2 * m
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    packed = torch.from_numpy(w.packed).to(dev)
+    P = n * (n + 1) // 2
+    counts = torch.empty((P, 4), dtype=torch.int32, device=dev)
+    dist_t = torch.empty(P, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    ctx = ibs.ibs_init(local, flags=ibs.IBS_TIMING)
+    probe = ibs.ibs_probe_int_pipes(ctx)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.zero_()
+            ibs.ibs_compute(ctx, packed, n, m, counts, dist_t, stream)
+        ibs.ibs_synchronize(ctx, stream)
+        ibs.ibs_kernel_times(ctx)  # drop warm-up records
+        launches_per_step = ibs.ibs_last_launch_info(ctx)["launches"]
+
+        clk = ClockSampler(local)
+        clk.start()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        t_wall = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            ibs.ibs_compute(ctx, packed, n, m, counts, dist_t, stream)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        wall = time.perf_counter() - t_wall
+        clocks = clk.stop()
+        ibs.ibs_synchronize(ctx, stream)
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+        kt = ibs.ibs_kernel_times(ctx)
+
+        # end to end through the same API: pinned host input, results copied back
+        h_packed = torch.from_numpy(w.packed).pin_memory()
+        h_counts = torch.empty((P, 4), dtype=torch.int32).pin_memory()
+        h_dist = torch.empty(P, dtype=torch.float64).pin_memory()
+        d_in = torch.empty_like(packed)
+        for _ in range(2):
+            d_in.copy_(h_packed, non_blocking=True)
+            ibs.ibs_compute(ctx, d_in, n, m, counts, dist_t, stream)
+            h_counts.copy_(counts, non_blocking=True)
+            h_dist.copy_(dist_t, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.zero_()
+            e2e_ev[i][0].record(stream)
+            d_in.copy_(h_packed, non_blocking=True)
+            ibs.ibs_compute(ctx, d_in, n, m, counts, dist_t, stream)
+            h_counts.copy_(counts, non_blocking=True)
+            h_dist.copy_(dist_t, non_blocking=True)
+            e2e_ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        ibs.ibs_synchronize(ctx, stream)
+        ibs.ibs_kernel_times(ctx)
+        e2e_ms = [a.elapsed_time(b) for a, b in e2e_ev]
+
+    # spot check of the last result against the oracle on a few rows (rank 0)
+    total_ms = reduce_max(sum(step_ms), world)
+    e2e_total = reduce_max(sum(e2e_ms), world)
+    ms_per_step = total_ms / args.steps
+    pairs_ms = kt["pairs_ms"] / max(1, kt["calls"])
+    planes_ms = kt["planes_ms"] / max(1, kt["calls"])
+    roof = int_pipe_roofline(probe, clocks.get("sm_mhz"))
+    achieved = comps / (pairs_ms * 1e-3)
+    mode = "plain" if os.environ.get("IBS_PAIR_MODE", "1") == "0" else "csa3"
+    # transpose: read the 2-bit input once, write 16 bytes per (padded) sample-word of planes
+    words = (m + 31) // 32
+    n_blocks, n_chunks = (n + 63) // 64, (words + 11) // 12
+    transpose_bytes = m * ((n + 3) // 4) + n_blocks * n_chunks * 12 * 64 * 16
+    ibs.ibs_shutdown(ctx)
+
+    if rank != 0:
+        return None
+    line = {
+        "metric": METRIC,
+        "value": world * comps / (total_ms / args.steps * 1e-3),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": w.name + " (MAF U(0.01,0.5), 2% missing + 0.5% of variants at 30%), seed 1"
+                   if args.workload == "plain" else w.name,
+                   "n_samples": n, "n_variants": m, "pairs_incl_diagonal": P,
+                   "comparisons_per_step": comps,
+                   "l2": "flushed between steps (256 MiB write, outside the step events)",
+                   "parallelism": f"replicas x{world}", "kernel_mode": mode},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": roof["peak"], "unit": UNIT,
+                     "frac": achieved / roof["peak"],
+                     "traffic": profiled_traffic(f"pair_kernel_{args.workload}.md"),
+                     "kernel": "tri_kernel (pair counts)", "kernel_ms": pairs_ms,
+                     "peak_basis": f"{roof['comps_per_clk_sm']:.1f} comparisons/clk/SM x {probe['sms']} SMs x "
+                                   f"{roof['sm_mhz']:.0f} MHz (median SM clock in the timed region); pipe rates "
+                                   f"measured live: POPC {probe['popc_per_clk_sm']:.2f}, LOP3 "
+                                   f"{probe['lop3_per_clk_sm']:.2f}, IADD3 {probe['iadd3_per_clk_sm']:.2f} /clk/SM"},
+        "transpose": {"kernel_ms": planes_ms, "bytes": transpose_bytes,
+                      "achieved_gbs": transpose_bytes / (planes_ms * 1e-3) / 1e9,
+                      "peak_gbs": hbm_peak_gbs(), "frac": transpose_bytes / (planes_ms * 1e-3) / 1e9 / hbm_peak_gbs()},
+        "e2e": {"value": world * comps / (e2e_total / args.steps * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": int(w.packed.nbytes), "d2h_bytes_per_step": int(P * 16 + P * 8)},
+        "gpu_launches": int(launches_per_step * args.steps),
+        "clocks": clocks,
+        "wall_s_timed_region": wall,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        rate, cores, sample, dt = oracle_rate(w.packed, n, m, target_s=args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": sample + f" ({dt:.1f} s)"}
+    return line
+
+
+def run_reference(args, rank, world, local):
+    """The oracle arm: the CPU oracle as it stands, on this machine's host cores,
+    each step a bounded row sample of the same workload."""
+    if rank != 0:
+        return None
+    w = make_workload(args.workload)
+    n, m = w.n, w.m
+    import numpy as np
+    import oracle
+    G = oracle.unpack(w.packed, n, m)
+    cores = os.cpu_count() or 1
+    # size a step at about args.ref_step_seconds
+    rows = np.arange(min(n, cores), dtype=np.int64)
+    t = time.perf_counter()
+    oracle.ibs_block(G, G, rows=rows)
+    dt0 = time.perf_counter() - t
+    R = int(max(rows.size, min(n, rows.size * args.ref_step_seconds / max(dt0, 1e-6))))
+    sel = np.linspace(0, n - 1, R).astype(np.int64)
+    for _ in range(args.warmup):
+        oracle.ibs_block(G, G, rows=sel[: max(1, R // 4)])
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        oracle.ibs_block(G, G, rows=sel)
+        times.append(time.perf_counter() - t)
+    comps = R * (n - 1) * m
+    value = comps / statistics.mean(times)
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(times) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": w.name, "n_samples": n, "n_variants": m,
+                   "sample_per_step": f"{R} rows x all {n} columns x {m} variants"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{R} rows x all {n} columns x {m} variants per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="plain", choices=["plain", "structured"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-step-seconds", type=float, default=4.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    rank, world, local = dist_env()
+    if world > 1 and args.impl == "ours":
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if args.impl == "reference":
+        line = run_reference(args, rank, world, local)
+    else:
+        line = run_plain(args, rank, world, local)
+    if line is not None:
+        print(json.dumps(line))
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,199 @@
+/*
+ * libibs: all-pairs identity-by-state (IBS) counts over PLINK 1 binary
+ * genotype matrices on one GB300 GPU (sm_103a).
+ *
+ * The operation (paper "Second-generation PLINK", section "Improvements in
+ * PLINK 1.9 / Bitwise parallelism"): for every sample pair (i, j) and every
+ * marker k, skip k when either call is missing; otherwise count IBS2 when the
+ * 2-bit codes are equal, IBS0 when both bits differ and IBS1 otherwise.
+ * N = IBS0 + IBS1 + IBS2 is the number of jointly non-missing markers.  The
+ * paper's replacement evaluates the same counts with XOR, a missing-call mask
+ * and a population count over blocks of markers; this library does that on
+ * sample-major bit planes with LOP3 and POPC in registers.
+ *
+ * Input layout (every entry point): a variant-major packed matrix, row k =
+ * ceil(n/4) bytes, sample s in bits 2*(s%4) (low) and 2*(s%4)+1 (high) of
+ * byte s/4, code = (byte >> 2*(s%4)) & 3 with 0 = hom A1, 1 = missing,
+ * 2 = het, 3 = hom A2 (the .bed payload without its 3-byte magic header).
+ * Padding bits of a row's last byte are ignored.
+ *
+ * Outputs: counts are int32 quadruples {IBS0, IBS1, IBS2, N}; the distance is
+ * (IBS1 + 2*IBS0) / (2*N) in IEEE double (NaN when N == 0), the complement of
+ * the IBS similarity printed by the paper's `--distance ibs`.  The all-pairs
+ * layout is the upper triangle including the diagonal, row-major over i <= j:
+ * pair (i, j) is element i*n - i*(i-1)/2 + (j - i) of P = n*(n+1)/2; with
+ * IBS_OUT_SQUARE it is the full [n][n] matrix (both halves written).
+ *
+ * Conventions.  Every call returns an ibs_status and never throws; on a
+ * non-OK return the outputs are undefined and ibs_last_error() (thread-local)
+ * says why.  All input and output buffers are caller-owned; the library owns
+ * its context, its bit-plane workspace, work lists, the resident panel and
+ * the serving engine, all freed by ibs_shutdown.  Work is enqueued on the
+ * caller's CUDA stream (a cudaStream_t passed as void*, NULL = legacy default
+ * stream) and the call returns after enqueue unless stated otherwise.  There
+ * is no CPU fallback: without a usable sm_103a device the calls fail with
+ * IBS_ECUDA.
+ */
+#ifndef IBS_H_
+#define IBS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ibs_ctx ibs_ctx; /* opaque, library-owned */
+
+typedef enum {
+  IBS_OK = 0,
+  IBS_EINVAL = 1,     /* bad argument: null pointer, size out of range, misaligned output */
+  IBS_ENOMEM = 2,     /* device allocation failed or the workspace limit would be exceeded */
+  IBS_ECUDA = 3,      /* a CUDA runtime call failed (message in ibs_last_error) */
+  IBS_ETIMEOUT = 4,   /* a bounded device-side wait or ibs_wait timed out */
+  IBS_EBUSY = 5,      /* admission refused: no slot or not enough free device memory yet */
+  IBS_ECANCELLED = 6, /* the request was cancelled by ibs_shutdown */
+  IBS_ESTATE = 7      /* call not valid in the context's current state */
+} ibs_status;
+
+/* ibs_config.flags */
+#define IBS_OUT_SQUARE 0x1 /* write the full [n][n] matrix instead of the upper triangle */
+#define IBS_NO_DIST 0x2    /* do not compute distances (out_dist may be NULL anyway) */
+#define IBS_KERNEL_PLAIN 0x10 /* pair loop variant: one POPC per count and 32-marker word */
+#define IBS_KERNEL_CSA 0x20   /* pair loop variant: carry-save reduction of 3 words before POPC */
+#define IBS_TIMING 0x40       /* record CUDA events around each kernel of ibs_compute (ibs_kernel_times) */
+
+typedef struct {
+  int device;                      /* CUDA device ordinal */
+  size_t workspace_bytes;          /* upper bound for library-owned device memory; 0 = no bound */
+  int flags;                       /* IBS_OUT_SQUARE, IBS_NO_DIST */
+  const char* autotune_cache_path; /* JSON file for the batched-launch tuner; NULL = in-memory only */
+} ibs_config;
+
+/* Create a context on cfg->device (NULL cfg = device 0, defaults).  Allocates
+ * only the small control block; workspaces grow on demand up to
+ * cfg->workspace_bytes. */
+ibs_status ibs_init(const ibs_config* cfg, ibs_ctx** out_ctx);
+
+/* Plain all-pairs IBS of one cohort (paper: the IBS matrix of
+ * "Bitwise parallelism"; "Performance comparisons", IBS matrix rows).
+ *   packed      DEVICE uint8 [n_variants][ceil(n_samples/4)], read-only.
+ *   n_samples   1 .. 2^31-1; n_variants 1 .. 2^31-1.
+ *   out_counts  DEVICE int32 [P][4] (P = n(n+1)/2, or n*n with IBS_OUT_SQUARE), 16-byte aligned.
+ *   out_dist    DEVICE double [P] (8-byte aligned) or NULL.
+ *   stream      cudaStream_t or NULL.
+ * Transposes the matrix into library-owned sample-major bit planes, then runs
+ * the triangular pair-count kernel with the fused count/distance epilogue. */
+ibs_status ibs_compute(ibs_ctx* ctx, const uint8_t* packed, int64_t n_samples, int64_t n_variants,
+                       int32_t* out_counts, double* out_dist, void* stream);
+
+/* Wait for all work enqueued on `stream` and report device-side errors of
+ * this context's kernels since the last call: IBS_ETIMEOUT when a bounded
+ * device wait expired (the kernel stopped early; outputs undefined), IBS_EINVAL
+ * when a batched subset held an out-of-range sample index (that sample was
+ * treated as all-missing).  Clears the device status word. */
+ibs_status ibs_synchronize(ibs_ctx* ctx, void* stream);
+
+/* One cohort subset of a pool for ibs_compute_batch: samples sample_idx[0..n)
+ * (DEVICE int64, each in [0, pool_n), may be in any order; output row r is
+ * sample_idx[r]) over the variant window [var_begin, var_begin + var_len). */
+typedef struct {
+  const int64_t* sample_idx; /* DEVICE */
+  int64_t n;
+  int64_t var_begin;
+  int64_t var_len;
+  int32_t* out_counts;       /* DEVICE int32 [n(n+1)/2][4] (upper triangle) */
+  double* out_dist;          /* DEVICE double [n(n+1)/2] or NULL */
+} ibs_subset;
+
+/* Batched all-pairs IBS of many subsets of one pool (paper "Multicore and
+ * cluster parallelism": independent pieces of sample x sample matrices).  All
+ * subsets' bit planes are built by one gather-transpose launch and all their
+ * pair tiles run in ONE persistent launch that takes (subset, tile) work items
+ * from a device work list, longest first.  The launch sequence is captured
+ * into a CUDA graph per batch shape and replayed; tile splitting is chosen by
+ * the autotuner.  pool_packed is DEVICE [pool_m][ceil(pool_n/4)].  Results are
+ * bit-identical to ibs_compute on each subset alone. */
+ibs_status ibs_compute_batch(ibs_ctx* ctx, const uint8_t* pool_packed, int64_t pool_n, int64_t pool_m,
+                             const ibs_subset* subsets, int n_subsets, void* stream);
+
+/* Serving.  ibs_panel_load copies a reference panel (DEVICE or HOST packed
+ * [n_variants][ceil(n_panel/4)]) into library-owned resident bit planes and
+ * starts the serving engine: a host thread that admits requests by free
+ * device memory and slot count and advances all admitted requests together,
+ * one panel chunk per step (continuous batching).  Blocks until the planes
+ * are built.  Replaces any previous panel (pending requests are cancelled). */
+ibs_status ibs_panel_load(ibs_ctx* ctx, const uint8_t* panel_packed, int64_t n_panel, int64_t n_variants);
+
+/* Submit q query samples (HOST or DEVICE packed [n_variants][ceil(q/4)],
+ * copied before return) for counts against every panel sample plus the k
+ * nearest panel samples by distance.  Non-blocking; returns a request id.
+ *   out_counts    HOST or DEVICE int32 [q][n_panel][4], or NULL.
+ *   out_topk_idx  HOST or DEVICE int32 [q][k]; out_topk_dist double [q][k].
+ * Output buffers must be device memory or pinned (page-locked) host memory.
+ * Ranking: ascending distance, ties by ascending panel index, N == 0 (NaN)
+ * last, padded with (-1, NaN) when k > n_panel.  1 <= q <= 4096, 0 <= k <= 64.
+ * Returns IBS_EBUSY when the request can never fit the memory budget.
+ * Thread-safe. */
+ibs_status ibs_query(ibs_ctx* ctx, const uint8_t* query_packed, int64_t n_query, int k,
+                     int32_t* out_counts, int32_t* out_topk_idx, double* out_topk_dist, uint64_t* req_id);
+
+/* The unbatched serving path, for comparison with the engine: one request,
+ * one launch sequence (query transpose, all query x panel tiles, top-k, copies
+ * back) on a private stream, returning when the outputs are written.  Same
+ * arguments and results as ibs_query + ibs_wait.  Output buffers must be
+ * device memory or pinned host memory (as for ibs_query). */
+ibs_status ibs_query_sync(ibs_ctx* ctx, const uint8_t* query_packed, int64_t n_query, int k, int32_t* out_counts,
+                          int32_t* out_topk_idx, double* out_topk_dist);
+
+/* Wait until request req_id has written its outputs (timeout_ms < 0 = no
+ * limit).  Returns IBS_OK, IBS_ETIMEOUT, IBS_ECANCELLED or the request's
+ * error.  A request id can be waited on successfully once.  Thread-safe. */
+ibs_status ibs_wait(ibs_ctx* ctx, uint64_t req_id, int64_t timeout_ms);
+
+/* Non-blocking completion check: IBS_OK when done, IBS_EBUSY while pending. */
+ibs_status ibs_poll(ibs_ctx* ctx, uint64_t req_id);
+
+/* Serving-engine counters: completed requests, steps run, peak in-flight query rows. */
+typedef struct {
+  uint64_t requests_done;
+  uint64_t steps;
+  uint64_t peak_rows;
+  uint64_t rejected;
+} ibs_serve_stats;
+ibs_status ibs_serve_stats_get(ibs_ctx* ctx, ibs_serve_stats* out);
+
+/* Stop the engine, fail pending requests with IBS_ECANCELLED, free all
+ * library-owned memory and the context.  Idempotent for NULL. */
+ibs_status ibs_shutdown(ibs_ctx* ctx);
+
+/* Thread-local message for the last non-OK status returned on this thread. */
+const char* ibs_last_error(void);
+
+/* Measure the sustained per-SM throughput of the integer instructions the pair
+ * loop issues (POPC, LOP3, IADD3) with an all-SM microbenchmark on the
+ * context's device: out[0..2] = operations per clock per SM for POPC, LOP3,
+ * IADD3; out[3] = SM clock in MHz seen during the run; out[4] = SM count.
+ * Synchronous.  Used to derive the integer-pipe roofline. */
+ibs_status ibs_probe_int_pipes(ibs_ctx* ctx, double out[5]);
+
+/* The largest cached batched-launch plan: out[0] = kernel mode (0 plain,
+ * 1 carry-save), out[1] = split policy, out[2] = work items, out[3] = grid. */
+ibs_status ibs_batch_plan_info(ibs_ctx* ctx, int64_t out[4]);
+
+/* With IBS_TIMING: wait for the recorded events and return the summed device
+ * time in ms of each kernel of all ibs_compute calls since the last query:
+ * out[0] = bit-plane transpose, out[1] = pair-count kernel, out[2] = split-K
+ * finalisation, out[3] = number of calls.  Resets the sums. */
+ibs_status ibs_kernel_times(ibs_ctx* ctx, double out[4]);
+
+/* Counters of the last ibs_compute / ibs_compute_batch on this context:
+ * out[0] = kernel launches enqueued, out[1] = pair tiles, out[2] = K splits. */
+ibs_status ibs_last_launch_info(ibs_ctx* ctx, int64_t out[3]);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IBS_H_ */

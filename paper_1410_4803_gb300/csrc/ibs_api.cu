@@ -1,0 +1,667 @@
+// libibs C ABI: context, validation, workspaces, the plain all-pairs path and
+// the batched persistent path (work list, CUDA graph, autotuner).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <fstream>
+#include <sstream>
+
+#include "ibs_ctx.h"
+#include "ibs_device.cuh"
+
+namespace ibs {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+ibs_status fail(ibs_status st, const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+void clear_error() { g_last_error.clear(); }
+
+const char* last_error_cstr() { return g_last_error.c_str(); }
+
+bool reserve_bytes(ibs_ctx* ctx, size_t bytes) {
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (ctx->ws_limit && ctx->owned_bytes + bytes > ctx->ws_limit) return false;
+  ctx->owned_bytes += bytes;
+  return true;
+}
+
+void release_bytes(ibs_ctx* ctx, size_t bytes) {
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ctx->owned_bytes = bytes > ctx->owned_bytes ? 0 : ctx->owned_bytes - bytes;
+}
+
+ibs_status ensure_buf(ibs_ctx* ctx, DevBuf& b, size_t need) {
+  if (need == 0) need = 16;
+  if (b.cap >= need) return IBS_OK;
+  if (b.p) {
+    cudaFree(b.p);  // synchronises the device, so no launch still uses it
+    release_bytes(ctx, b.cap);
+    b.p = nullptr;
+    b.cap = 0;
+  }
+  if (!reserve_bytes(ctx, need))
+    return fail(IBS_ENOMEM, "workspace limit %zu bytes would be exceeded (need %zu more)", ctx->ws_limit, need);
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, need);
+  if (e != cudaSuccess) {
+    release_bytes(ctx, need);
+    cudaGetLastError();
+    return fail(IBS_ENOMEM, "cudaMalloc(%zu) failed: %s", need, cudaGetErrorString(e));
+  }
+  b.p = p;
+  b.cap = need;
+  return IBS_OK;
+}
+
+void free_buf(ibs_ctx* ctx, DevBuf& b) {
+  if (b.p) {
+    cudaFree(b.p);
+    release_bytes(ctx, b.cap);
+  }
+  b.p = nullptr;
+  b.cap = 0;
+}
+
+int pick_mode(const ibs_ctx* ctx) { return ctx->default_mode; }
+
+}  // namespace ibs
+
+using namespace ibs;
+
+namespace {
+
+constexpr int kFlagPlain = 0x10;  // force the plain kernel (one POPC per count and word)
+constexpr int kFlagCsa = 0x20;    // force the carry-save kernel
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+ibs_status check_ctx(ibs_ctx* ctx) {
+  if (!ctx) return fail(IBS_EINVAL, "context is NULL");
+  return IBS_OK;
+}
+
+int mode_for(const ibs_ctx* ctx) {
+  if (ctx->flags & kFlagPlain) return 0;
+  if (ctx->flags & kFlagCsa) return 1;
+  return ctx->default_mode;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ibs_last_error(void) { return ibs::last_error_cstr(); }
+
+ibs_status ibs_init(const ibs_config* cfg, ibs_ctx** out_ctx) {
+  clear_error();
+  if (!out_ctx) return fail(IBS_EINVAL, "out_ctx is NULL");
+  *out_ctx = nullptr;
+  ibs_config c{};
+  if (cfg) c = *cfg;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(IBS_ECUDA, "no CUDA device available (%s)", cudaGetErrorString(e));
+  }
+  if (c.device < 0 || c.device >= ndev) return fail(IBS_EINVAL, "device %d out of range [0, %d)", c.device, ndev);
+  DeviceGuard g(c.device);
+  cudaDeviceProp prop;
+  IBS_CUDA_TRY(cudaGetDeviceProperties(&prop, c.device));
+  if (prop.major != 10 || prop.minor != 3)
+    return fail(IBS_ECUDA, "device %d is sm_%d%d; this library is built for sm_103a only", c.device, prop.major,
+                prop.minor);
+  auto* ctx = new ibs_ctx();
+  ctx->device = c.device;
+  ctx->flags = c.flags;
+  ctx->ws_limit = c.workspace_bytes;
+  if (c.autotune_cache_path) ctx->tune_path = c.autotune_cache_path;
+  ctx->num_sms = prop.multiProcessorCount;
+  ctx->cc_major = prop.major;
+  ctx->cc_minor = prop.minor;
+  const char* env = getenv("IBS_PAIR_MODE");
+  if (env && (env[0] == '0' || env[0] == '1')) ctx->default_mode = env[0] - '0';
+  e = cudaHostAlloc(reinterpret_cast<void**>(&ctx->status_host), sizeof(int), cudaHostAllocMapped);
+  if (e != cudaSuccess) {
+    delete ctx;
+    return fail(IBS_ECUDA, "cudaHostAlloc(status) failed: %s", cudaGetErrorString(e));
+  }
+  *ctx->status_host = 0;
+  e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&ctx->status_dev), ctx->status_host, 0);
+  if (e != cudaSuccess) {
+    cudaFreeHost(ctx->status_host);
+    delete ctx;
+    return fail(IBS_ECUDA, "cudaHostGetDevicePointer failed: %s", cudaGetErrorString(e));
+  }
+  // Load the autotune cache.
+  if (!ctx->tune_path.empty()) {
+    std::ifstream f(ctx->tune_path);
+    std::string line;
+    while (std::getline(f, line)) {
+      char key[512];
+      TuneEntry t;
+      if (sscanf(line.c_str(), "{\"key\": \"%511[^\"]\", \"mode\": %d, \"split\": %d, \"ms\": %lf}", key, &t.mode,
+                 &t.split_policy, &t.ms) == 4)
+        ctx->tune[key] = t;
+    }
+  }
+  *out_ctx = ctx;
+  return IBS_OK;
+}
+
+ibs_status ibs_compute(ibs_ctx* ctx, const uint8_t* packed, int64_t n, int64_t m, int32_t* out_counts,
+                       double* out_dist, void* stream) {
+  clear_error();
+  if (ibs_status s = check_ctx(ctx)) return s;
+  if (!packed || !out_counts) return fail(IBS_EINVAL, "packed and out_counts must be non-NULL");
+  if (n < 1 || n > 2147483647LL) return fail(IBS_EINVAL, "n_samples %lld out of range [1, 2^31)", (long long)n);
+  if (m < 1 || m > 2147483647LL) return fail(IBS_EINVAL, "n_variants %lld out of range [1, 2^31)", (long long)m);
+  if (reinterpret_cast<uintptr_t>(out_counts) % 16) return fail(IBS_EINVAL, "out_counts must be 16-byte aligned");
+  if (out_dist && reinterpret_cast<uintptr_t>(out_dist) % 8) return fail(IBS_EINVAL, "out_dist must be 8-byte aligned");
+  DeviceGuard g(ctx->device);
+  if (!is_device_ptr(packed) || !is_device_ptr(out_counts) || (out_dist && !is_device_ptr(out_dist)))
+    return fail(IBS_EINVAL, "packed, out_counts and out_dist must be device memory");
+  if (ctx->flags & IBS_NO_DIST) out_dist = nullptr;
+  const bool square = (ctx->flags & IBS_OUT_SQUARE) != 0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const PlaneGeom geo = PlaneGeom::make(n, m);
+  if (ibs_status s = ensure_buf(ctx, ctx->planes, geo.bytes())) return s;
+  const int64_t tiles = geo.n_blocks * (geo.n_blocks + 1) / 2;
+  const int splits = tri_splits_for(tiles, geo.n_chunks, ctx->num_sms);
+  const int64_t P = n * (n + 1) / 2;
+  if (splits > 1) {
+    if (ibs_status s = ensure_buf(ctx, ctx->partial, (size_t)P * 16)) return s;
+    IBS_CUDA_TRY(cudaMemsetAsync(ctx->partial.p, 0, (size_t)P * 16, st));
+  }
+  BedSource src;
+  src.packed = packed;
+  src.row_bytes = (n + 3) / 4;
+  src.n_src = n;
+  const bool timing = (ctx->flags & IBS_TIMING) != 0;
+  ibs_ctx::TimingRec rec;
+  if (timing) {
+    if (!ctx->timing_free.empty()) {
+      rec = ctx->timing_free.back();
+      ctx->timing_free.pop_back();
+    } else {
+      for (auto& e : rec.ev) IBS_CUDA_TRY(cudaEventCreate(&e));
+    }
+    rec.n = splits > 1 ? 4 : 3;
+    IBS_CUDA_TRY(cudaEventRecord(rec.ev[0], st));
+  }
+  IBS_CUDA_TRY(launch_planes(src, n, m, geo, static_cast<uint32_t*>(ctx->planes.p), ctx->status_dev, st));
+  if (timing) IBS_CUDA_TRY(cudaEventRecord(rec.ev[1], st));
+  IBS_CUDA_TRY(launch_tri(mode_for(ctx), static_cast<const uint32_t*>(ctx->planes.p), geo, splits, out_counts,
+                          out_dist, static_cast<int32_t*>(ctx->partial.p), square, ctx->status_dev, ctx->num_sms, st));
+  if (timing) IBS_CUDA_TRY(cudaEventRecord(rec.ev[2], st));
+  if (splits > 1)
+    IBS_CUDA_TRY(launch_finalize(static_cast<const int32_t*>(ctx->partial.p), n, out_counts, out_dist, square, st));
+  if (timing) {
+    if (splits > 1) IBS_CUDA_TRY(cudaEventRecord(rec.ev[3], st));
+    ctx->timing_used.push_back(rec);
+  }
+  ctx->last_info[0] = splits > 1 ? 3 : 2;
+  ctx->last_info[1] = tiles;
+  ctx->last_info[2] = splits;
+  return IBS_OK;
+}
+
+ibs_status ibs_synchronize(ibs_ctx* ctx, void* stream) {
+  clear_error();
+  if (ibs_status s = check_ctx(ctx)) return s;
+  DeviceGuard g(ctx->device);
+  IBS_CUDA_TRY(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  const int st = __atomic_exchange_n(ctx->status_host, 0, __ATOMIC_SEQ_CST);
+  if (st == kDevTimeout) return fail(IBS_ETIMEOUT, "a bounded device wait timed out");
+  if (st == IBS_EINVAL) return fail(IBS_EINVAL, "a sample index was out of range (treated as missing)");
+  if (st != 0) return fail((ibs_status)st, "device status %d", st);
+  return IBS_OK;
+}
+
+ibs_status ibs_kernel_times(ibs_ctx* ctx, double out[4]) {
+  clear_error();
+  if (ibs_status s = check_ctx(ctx)) return s;
+  if (!out) return fail(IBS_EINVAL, "out is NULL");
+  DeviceGuard g(ctx->device);
+  for (int i = 0; i < 4; ++i) out[i] = 0;
+  for (auto& r : ctx->timing_used) {
+    IBS_CUDA_TRY(cudaEventSynchronize(r.ev[r.n - 1]));
+    float ms = 0;
+    IBS_CUDA_TRY(cudaEventElapsedTime(&ms, r.ev[0], r.ev[1]));
+    out[0] += ms;
+    IBS_CUDA_TRY(cudaEventElapsedTime(&ms, r.ev[1], r.ev[2]));
+    out[1] += ms;
+    if (r.n == 4) {
+      IBS_CUDA_TRY(cudaEventElapsedTime(&ms, r.ev[2], r.ev[3]));
+      out[2] += ms;
+    }
+    out[3] += 1;
+    ctx->timing_free.push_back(r);
+  }
+  ctx->timing_used.clear();
+  return IBS_OK;
+}
+
+ibs_status ibs_last_launch_info(ibs_ctx* ctx, int64_t out[3]) {
+  clear_error();
+  if (ibs_status s = check_ctx(ctx)) return s;
+  if (!out) return fail(IBS_EINVAL, "out is NULL");
+  for (int i = 0; i < 3; ++i) out[i] = ctx->last_info[i];
+  return IBS_OK;
+}
+
+ibs_status ibs_probe_int_pipes(ibs_ctx* ctx, double out[5]) {
+  clear_error();
+  if (ibs_status s = check_ctx(ctx)) return s;
+  if (!out) return fail(IBS_EINVAL, "out is NULL");
+  DeviceGuard g(ctx->device);
+  IBS_CUDA_TRY(probe_int_pipes(ctx->device, out));
+  return IBS_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched path.
+namespace {
+
+struct SubsetShape {
+  int64_t n, m;
+  PlaneGeom g;
+};
+
+// Build the work list for a batch: every (subset, tile) item, K-split for
+// subsets whose tiles would be too large relative to one CTA's fair share
+// (split_policy 1), sorted by descending cost (longest processing time first).
+void build_items(const std::vector<SubsetShape>& shapes, int split_policy, int grid, std::vector<WorkItem>& items,
+                 std::vector<int>& subset_split, int64_t& tiles_total) {
+  items.clear();
+  subset_split.assign(shapes.size(), 1);
+  double total = 0;
+  tiles_total = 0;
+  for (const auto& s : shapes) {
+    const int64_t T = s.g.n_blocks;
+    total += (double)(T * (T + 1) / 2) * (double)s.g.n_chunks;
+    tiles_total += T * (T + 1) / 2;
+  }
+  const double share = total / std::max(1, grid);
+  for (size_t k = 0; k < shapes.size(); ++k) {
+    const auto& s = shapes[k];
+    if (split_policy == 1) {
+      const double item = (double)s.g.n_chunks;
+      // aim for items no larger than a quarter of a CTA's fair share
+      int pieces = (int)std::ceil(item / std::max(1.0, share / 4.0));
+      pieces = std::max(1, std::min<int>(pieces, (int)std::min<int64_t>(s.g.n_chunks, 64)));
+      subset_split[k] = pieces;
+    }
+  }
+  for (size_t k = 0; k < shapes.size(); ++k) {
+    const auto& s = shapes[k];
+    const int64_t T = s.g.n_blocks;
+    const int pieces = subset_split[k];
+    for (int64_t I = 0; I < T; ++I)
+      for (int64_t J = I; J < T; ++J)
+        for (int p = 0; p < pieces; ++p) {
+          WorkItem w;
+          w.subset = (int32_t)k;
+          w.I = (int32_t)I;
+          w.J = (int32_t)J;
+          w.c0 = (int32_t)(s.g.n_chunks * p / pieces);
+          w.c1 = (int32_t)(s.g.n_chunks * (p + 1) / pieces);
+          w.split = pieces > 1 ? 1 : 0;
+          items.push_back(w);
+        }
+  }
+  std::stable_sort(items.begin(), items.end(), [](const WorkItem& a, const WorkItem& b) {
+    const int64_t ca = (int64_t)(a.c1 - a.c0) * (a.I == a.J ? 1 : 2);
+    const int64_t cb = (int64_t)(b.c1 - b.c0) * (b.I == b.J ? 1 : 2);
+    return ca > cb;
+  });
+}
+
+std::string tune_key(const ibs_ctx* ctx, const std::vector<SubsetShape>& shapes) {
+  // bucket: subsets count, log2 of total pair-words, log2 of the largest subset's n
+  double total = 0;
+  int64_t nmax = 0;
+  for (const auto& s : shapes) {
+    total += (double)s.n * (double)s.n * 0.5 * (double)s.m;
+    nmax = std::max(nmax, s.n);
+  }
+  std::ostringstream o;
+  o << "sms" << ctx->num_sms << "_s" << shapes.size() << "_w" << (int)std::log2(std::max(1.0, total)) << "_n"
+    << (int)std::log2((double)std::max<int64_t>(1, nmax));
+  return o.str();
+}
+
+ibs_status plan_build(ibs_ctx* ctx, BatchPlan& plan, const std::vector<SubsetShape>& shapes, int mode,
+                      int split_policy) {
+  plan.mode = mode;
+  plan.split_policy = split_policy;
+  plan.grid = ctx->num_sms * pair_kernel_ctas_per_sm(mode);
+  std::vector<WorkItem> items;
+  std::vector<int> split;
+  build_items(shapes, split_policy, plan.grid, items, split, plan.tiles);
+  plan.n_items = (int64_t)items.size();
+  if (plan.grid > plan.n_items) plan.grid = (int)std::max<int64_t>(1, plan.n_items);
+  // planes and partial offsets
+  size_t pb = 0, qb = 0;
+  plan.plane_offsets.resize(shapes.size());
+  plan.partial_offsets.assign(shapes.size(), -1);
+  std::vector<int32_t> split_ids;
+  plan.max_split_pairs = 0;
+  for (size_t k = 0; k < shapes.size(); ++k) {
+    plan.plane_offsets[k] = (int64_t)pb;
+    pb += (shapes[k].g.bytes() + 255) / 256 * 256;
+    if (split[k] > 1) {
+      const int64_t P = shapes[k].n * (shapes[k].n + 1) / 2;
+      plan.partial_offsets[k] = (int64_t)qb;
+      qb += ((size_t)P * 16 + 255) / 256 * 256;
+      split_ids.push_back((int32_t)k);
+      plan.max_split_pairs = std::max(plan.max_split_pairs, P);
+    }
+  }
+  plan.n_split = (int)split_ids.size();
+  plan.total_ctas = 0;
+  for (const auto& s : shapes) plan.total_ctas += s.g.n_chunks * ((s.g.n_blocks + 1) / 2);
+  if (ibs_status s = ensure_buf(ctx, plan.planes, pb)) return s;
+  if (ibs_status s = ensure_buf(ctx, plan.partial, qb)) return s;
+  if (ibs_status s = ensure_buf(ctx, plan.subsets, sizeof(SubsetDev) * shapes.size())) return s;
+  if (ibs_status s = ensure_buf(ctx, plan.jobs, sizeof(PlaneJob) * shapes.size())) return s;
+  if (ibs_status s = ensure_buf(ctx, plan.items, sizeof(WorkItem) * std::max<size_t>(1, items.size()))) return s;
+  if (ibs_status s = ensure_buf(ctx, plan.split_ids, sizeof(int32_t) * std::max<size_t>(1, split_ids.size())))
+    return s;
+  if (ibs_status s = ensure_buf(ctx, plan.counter, 256)) return s;
+  IBS_CUDA_TRY(cudaMemcpy(plan.items.p, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice));
+  if (!split_ids.empty())
+    IBS_CUDA_TRY(cudaMemcpy(plan.split_ids.p, split_ids.data(), sizeof(int32_t) * split_ids.size(),
+                            cudaMemcpyHostToDevice));
+  return IBS_OK;
+}
+
+// Upload the per-call descriptors (pointers may change between calls of one shape).
+ibs_status plan_upload(ibs_ctx* ctx, BatchPlan& plan, const uint8_t* pool, int64_t pool_n,
+                       const ibs_subset* subs, const std::vector<SubsetShape>& shapes, cudaStream_t st) {
+  const size_t k = shapes.size();
+  std::vector<SubsetDev> sd(k);
+  std::vector<PlaneJob> jobs(k);
+  int64_t cta = 0;
+  for (size_t i = 0; i < k; ++i) {
+    uint32_t* planes = reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(plan.planes.p) + plan.plane_offsets[i]);
+    sd[i].planes = planes;
+    sd[i].n = shapes[i].n;
+    sd[i].n_blocks = shapes[i].g.n_blocks;
+    sd[i].n_chunks = shapes[i].g.n_chunks;
+    sd[i].out_counts = subs[i].out_counts;
+    sd[i].out_dist = (ctx->flags & IBS_NO_DIST) ? nullptr : subs[i].out_dist;
+    sd[i].partial = plan.partial_offsets[i] >= 0
+                        ? reinterpret_cast<int32_t*>(static_cast<uint8_t*>(plan.partial.p) + plan.partial_offsets[i])
+                        : nullptr;
+    sd[i].pad = 0;
+    jobs[i].src.packed = pool;
+    jobs[i].src.row_bytes = (pool_n + 3) / 4;
+    jobs[i].src.var_begin = subs[i].var_begin;
+    jobs[i].src.sel = subs[i].sample_idx;
+    jobs[i].src.n_src = pool_n;
+    jobs[i].m = shapes[i].m;
+    jobs[i].n = shapes[i].n;
+    jobs[i].planes = planes;
+    jobs[i].n_blocks = shapes[i].g.n_blocks;
+    jobs[i].n_chunks = shapes[i].g.n_chunks;
+    jobs[i].groups = (shapes[i].g.n_blocks + 1) / 2;
+    jobs[i].cta_begin = cta;
+    cta += shapes[i].g.n_chunks * jobs[i].groups;
+  }
+  // Pageable sources: the copy is staged before return, so the vectors may go.
+  IBS_CUDA_TRY(cudaMemcpyAsync(plan.subsets.p, sd.data(), sizeof(SubsetDev) * k, cudaMemcpyHostToDevice, st));
+  IBS_CUDA_TRY(cudaMemcpyAsync(plan.jobs.p, jobs.data(), sizeof(PlaneJob) * k, cudaMemcpyHostToDevice, st));
+  return IBS_OK;
+}
+
+// Enqueue the batch's launches (also used under stream capture).
+ibs_status plan_enqueue(ibs_ctx* ctx, BatchPlan& plan, int n_subsets, cudaStream_t st) {
+  IBS_CUDA_TRY(cudaMemsetAsync(plan.counter.p, 0, sizeof(int), st));
+  if (plan.n_split > 0) IBS_CUDA_TRY(cudaMemsetAsync(plan.partial.p, 0, plan.partial.cap, st));
+  IBS_CUDA_TRY(launch_planes_batch(static_cast<const PlaneJob*>(plan.jobs.p), n_subsets, plan.total_ctas,
+                                   ctx->status_dev, st));
+  IBS_CUDA_TRY(launch_batch(plan.mode, static_cast<const SubsetDev*>(plan.subsets.p),
+                            static_cast<const WorkItem*>(plan.items.p), plan.n_items,
+                            static_cast<int*>(plan.counter.p), ctx->status_dev, plan.grid, st));
+  if (plan.n_split > 0)
+    IBS_CUDA_TRY(launch_finalize_batch(static_cast<const SubsetDev*>(plan.subsets.p),
+                                       static_cast<const int32_t*>(plan.split_ids.p), plan.n_split,
+                                       plan.max_split_pairs, st));
+  return IBS_OK;
+}
+
+void plan_free(ibs_ctx* ctx, BatchPlan& plan) {
+  if (plan.exec) cudaGraphExecDestroy(plan.exec);
+  if (plan.graph) cudaGraphDestroy(plan.graph);
+  plan.exec = nullptr;
+  plan.graph = nullptr;
+  for (DevBuf* b : {&plan.planes, &plan.partial, &plan.subsets, &plan.jobs, &plan.items, &plan.split_ids,
+                    &plan.counter})
+    free_buf(ctx, *b);
+}
+
+void save_tune(const ibs_ctx* ctx) {
+  if (ctx->tune_path.empty()) return;
+  std::ofstream f(ctx->tune_path, std::ios::trunc);
+  for (const auto& kv : ctx->tune)
+    f << "{\"key\": \"" << kv.first << "\", \"mode\": " << kv.second.mode << ", \"split\": " << kv.second.split_policy
+      << ", \"ms\": " << kv.second.ms << "}\n";
+}
+
+}  // namespace
+
+extern "C" ibs_status ibs_compute_batch(ibs_ctx* ctx, const uint8_t* pool, int64_t pool_n, int64_t pool_m,
+                                        const ibs_subset* subs, int n_subsets, void* stream) {
+  clear_error();
+  if (ibs_status s = check_ctx(ctx)) return s;
+  if (!pool || !subs || n_subsets < 1) return fail(IBS_EINVAL, "pool, subsets must be non-NULL and n_subsets >= 1");
+  if (pool_n < 1 || pool_n > 2147483647LL || pool_m < 1 || pool_m > 2147483647LL)
+    return fail(IBS_EINVAL, "pool size out of range");
+  if (ctx->flags & IBS_OUT_SQUARE) return fail(IBS_EINVAL, "IBS_OUT_SQUARE is not supported by the batched path");
+  DeviceGuard g(ctx->device);
+  if (!is_device_ptr(pool)) return fail(IBS_EINVAL, "pool_packed must be device memory");
+  std::vector<SubsetShape> shapes(n_subsets);
+  std::vector<int64_t> key = {pool_n, pool_m, n_subsets};
+  for (int i = 0; i < n_subsets; ++i) {
+    const ibs_subset& s = subs[i];
+    if (!s.sample_idx || !s.out_counts) return fail(IBS_EINVAL, "subset %d: NULL sample_idx or out_counts", i);
+    if (s.n < 1 || s.n > pool_n) return fail(IBS_EINVAL, "subset %d: n=%lld out of range", i, (long long)s.n);
+    if (s.var_len < 1 || s.var_begin < 0 || s.var_begin + s.var_len > pool_m)
+      return fail(IBS_EINVAL, "subset %d: variant window out of range", i);
+    if (reinterpret_cast<uintptr_t>(s.out_counts) % 16) return fail(IBS_EINVAL, "subset %d: out_counts not 16-byte aligned", i);
+    if (s.out_dist && reinterpret_cast<uintptr_t>(s.out_dist) % 8) return fail(IBS_EINVAL, "subset %d: out_dist not 8-byte aligned", i);
+    if (reinterpret_cast<uintptr_t>(s.sample_idx) % 8) return fail(IBS_EINVAL, "subset %d: sample_idx not 8-byte aligned", i);
+    shapes[i].n = s.n;
+    shapes[i].m = s.var_len;
+    shapes[i].g = PlaneGeom::make(s.n, s.var_len);
+    key.push_back(s.n);
+    key.push_back(s.var_len);
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int forced = (ctx->flags & kFlagPlain) ? 0 : ((ctx->flags & kFlagCsa) ? 1 : -1);
+  key.push_back(forced);
+
+  auto it = ctx->plans.find(key);
+  if (it == ctx->plans.end()) {
+    // Choose mode and split policy: cached tuning result, or measure the candidates now.
+    const std::string tk = tune_key(ctx, shapes);
+    int mode = forced >= 0 ? forced : ctx->default_mode, policy = 0;
+    auto te = ctx->tune.find(tk);
+    if (te != ctx->tune.end()) {
+      if (forced < 0) mode = te->second.mode;
+      policy = te->second.split_policy;
+    } else if (!getenv("IBS_NO_AUTOTUNE")) {
+      double best = 1e30;
+      for (int cm = 0; cm < 2; ++cm) {
+        if (forced >= 0 && cm != forced) continue;
+        for (int cp = 0; cp < 2; ++cp) {
+          BatchPlan trial;
+          if (ibs_status s = plan_build(ctx, trial, shapes, cm, cp)) {
+            plan_free(ctx, trial);
+            return s;
+          }
+          ibs_status s = plan_upload(ctx, trial, pool, pool_n, subs, shapes, st);
+          cudaEvent_t e0, e1;
+          cudaEventCreate(&e0);
+          cudaEventCreate(&e1);
+          if (!s) s = plan_enqueue(ctx, trial, n_subsets, st);  // warm-up
+          cudaEventRecord(e0, st);
+          if (!s) s = plan_enqueue(ctx, trial, n_subsets, st);
+          cudaEventRecord(e1, st);
+          cudaError_t ce = cudaEventSynchronize(e1);
+          float ms = 0;
+          cudaEventElapsedTime(&ms, e0, e1);
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          plan_free(ctx, trial);
+          if (s) return s;
+          if (ce != cudaSuccess) return fail(IBS_ECUDA, "autotune run failed: %s", cudaGetErrorString(ce));
+          if (ms < best) {
+            best = ms;
+            mode = cm;
+            policy = cp;
+          }
+        }
+      }
+      TuneEntry t;
+      t.mode = mode;
+      t.split_policy = policy;
+      t.ms = best;
+      ctx->tune[tk] = t;
+      save_tune(ctx);
+    }
+    auto plan = std::make_unique<BatchPlan>();
+    plan->shape_key = key;
+    if (ibs_status s = plan_build(ctx, *plan, shapes, mode, policy)) {
+      plan_free(ctx, *plan);
+      return s;
+    }
+    // Capture the launch sequence once on a private stream.
+    cudaStream_t cs;
+    IBS_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    ibs_status s = IBS_OK;
+    cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (ce == cudaSuccess) {
+      s = plan_enqueue(ctx, *plan, n_subsets, cs);
+      cudaGraph_t graph = nullptr;
+      ce = cudaStreamEndCapture(cs, &graph);
+      if (!s && ce == cudaSuccess) {
+        plan->graph = graph;
+        ce = cudaGraphInstantiate(&plan->exec, graph, 0);
+      }
+    }
+    cudaStreamDestroy(cs);
+    if (s || ce != cudaSuccess) {
+      plan_free(ctx, *plan);
+      if (s) return s;
+      return fail(IBS_ECUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+    }
+    it = ctx->plans.emplace(key, std::move(plan)).first;
+  }
+  BatchPlan& plan = *it->second;
+  if (ibs_status s = plan_upload(ctx, plan, pool, pool_n, subs, shapes, st)) return s;
+  IBS_CUDA_TRY(cudaGraphLaunch(plan.exec, st));
+  ctx->last_info[0] = 3 + (plan.n_split > 0 ? 1 : 0);
+  ctx->last_info[1] = plan.tiles;
+  ctx->last_info[2] = plan.split_policy;
+  return IBS_OK;
+}
+
+extern "C" ibs_status ibs_batch_plan_info(ibs_ctx* ctx, int64_t out[4]) {
+  clear_error();
+  if (ibs_status s = check_ctx(ctx)) return s;
+  if (!out) return fail(IBS_EINVAL, "out is NULL");
+  if (ctx->plans.empty()) return fail(IBS_ESTATE, "no batch plan yet");
+  // the most recently created plan is not tracked separately; report the largest
+  const BatchPlan* best = nullptr;
+  for (const auto& kv : ctx->plans)
+    if (!best || kv.second->n_items > best->n_items) best = kv.second.get();
+  out[0] = best->mode;
+  out[1] = best->split_policy;
+  out[2] = best->n_items;
+  out[3] = best->grid;
+  return IBS_OK;
+}
+
+extern "C" ibs_status ibs_shutdown(ibs_ctx* ctx) {
+  clear_error();
+  if (!ctx) return IBS_OK;
+  {
+    DeviceGuard g(ctx->device);
+    serve_stop(ctx);
+    cudaDeviceSynchronize();
+    for (auto& kv : ctx->plans) plan_free(ctx, *kv.second);
+    ctx->plans.clear();
+    free_buf(ctx, ctx->planes);
+    free_buf(ctx, ctx->partial);
+    for (auto* v : {&ctx->timing_used, &ctx->timing_free})
+      for (auto& r : *v)
+        for (auto& e : r.ev)
+          if (e) cudaEventDestroy(e);
+    if (ctx->status_host) cudaFreeHost(ctx->status_host);
+  }
+  delete ctx;
+  return IBS_OK;
+}
+
+// Serving entry points forward to the engine (ibs_serve.cu).
+extern "C" ibs_status ibs_panel_load(ibs_ctx* ctx, const uint8_t* panel, int64_t n_panel, int64_t m) {
+  clear_error();
+  if (ibs_status s = check_ctx(ctx)) return s;
+  return serve_panel_load(ctx, panel, n_panel, m);
+}
+
+extern "C" ibs_status ibs_query(ibs_ctx* ctx, const uint8_t* q, int64_t nq, int k, int32_t* oc, int32_t* oi,
+                                double* od, uint64_t* id) {
+  clear_error();
+  if (ibs_status s = check_ctx(ctx)) return s;
+  return serve_query(ctx, q, nq, k, oc, oi, od, id);
+}
+
+extern "C" ibs_status ibs_query_sync(ibs_ctx* ctx, const uint8_t* q, int64_t nq, int k, int32_t* oc, int32_t* oi,
+                                     double* od) {
+  clear_error();
+  if (ibs_status s = check_ctx(ctx)) return s;
+  return serve_query_sync(ctx, q, nq, k, oc, oi, od);
+}
+
+extern "C" ibs_status ibs_wait(ibs_ctx* ctx, uint64_t id, int64_t timeout_ms) {
+  clear_error();
+  if (ibs_status s = check_ctx(ctx)) return s;
+  return serve_wait(ctx, id, timeout_ms);
+}
+
+extern "C" ibs_status ibs_poll(ibs_ctx* ctx, uint64_t id) {
+  clear_error();
+  if (ibs_status s = check_ctx(ctx)) return s;
+  return serve_poll(ctx, id);
+}
+
+extern "C" ibs_status ibs_serve_stats_get(ibs_ctx* ctx, ibs_serve_stats* out) {
+  clear_error();
+  if (ibs_status s = check_ctx(ctx)) return s;
+  if (!out) return fail(IBS_EINVAL, "out is NULL");
+  return serve_stats(ctx, out);
+}

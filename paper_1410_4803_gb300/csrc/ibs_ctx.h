@@ -1,0 +1,123 @@
+// Library context and host utilities shared by ibs_api.cu and ibs_serve.cu.
+#pragma once
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/ibs.h"
+#include "ibs_internal.h"
+
+namespace ibs {
+
+ibs_status fail(ibs_status st, const char* fmt, ...);
+void clear_error();
+
+#define IBS_CUDA_TRY(call)                                                                        \
+  do {                                                                                            \
+    cudaError_t _e = (call);                                                                      \
+    if (_e != cudaSuccess) return ::ibs::fail(IBS_ECUDA, "%s failed: %s", #call, cudaGetErrorString(_e)); \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int d) {
+    cudaGetDevice(&prev);
+    if (prev != d) cudaSetDevice(d);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+class ServeEngine;
+
+// Cached launch plan of one batch shape: device descriptor arrays at fixed
+// addresses plus the captured graph.
+struct BatchPlan {
+  std::vector<int64_t> shape_key;
+  DevBuf planes, partial, subsets, jobs, items, split_ids, counter;
+  int64_t n_items = 0, total_ctas = 0, max_split_pairs = 0;
+  int n_split = 0;
+  int mode = 0, split_policy = 0, grid = 0;
+  std::vector<int64_t> plane_offsets;   // bytes into planes
+  std::vector<int64_t> partial_offsets; // bytes into partial, -1 if not split
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  int64_t tiles = 0;
+};
+
+struct TuneEntry {
+  int mode = -1;
+  int split_policy = 0;
+  double ms = 0;
+};
+
+}  // namespace ibs
+
+struct ibs_ctx {
+  int device = 0;
+  int flags = 0;
+  size_t ws_limit = 0;
+  std::string tune_path;
+  int num_sms = 0;
+  int cc_major = 0, cc_minor = 0;
+  int default_mode = 1;
+
+  std::mutex mu;                  // guards memory accounting
+  size_t owned_bytes = 0;
+
+  ibs::DevBuf planes, partial;
+  int* status_host = nullptr;     // mapped pinned status word
+  int* status_dev = nullptr;
+
+  int64_t last_info[3] = {0, 0, 0};
+
+  // IBS_TIMING: events around each kernel of ibs_compute, summed by ibs_kernel_times.
+  struct TimingRec {
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    int n = 0;
+  };
+  std::vector<TimingRec> timing_used, timing_free;
+
+  std::map<std::vector<int64_t>, std::unique_ptr<ibs::BatchPlan>> plans;
+  std::map<std::string, ibs::TuneEntry> tune;
+
+  std::shared_ptr<ibs::ServeEngine> serve;  // guarded by mu
+};
+
+namespace ibs {
+
+ibs_status ensure_buf(ibs_ctx* ctx, DevBuf& b, size_t need);
+void free_buf(ibs_ctx* ctx, DevBuf& b);
+bool reserve_bytes(ibs_ctx* ctx, size_t bytes);
+void release_bytes(ibs_ctx* ctx, size_t bytes);
+int pick_mode(const ibs_ctx* ctx);
+
+// Serving engine (ibs_serve.cu).
+ibs_status serve_panel_load(ibs_ctx* ctx, const uint8_t* panel, int64_t n_panel, int64_t m);
+ibs_status serve_query(ibs_ctx* ctx, const uint8_t* q, int64_t nq, int k, int32_t* oc, int32_t* oi, double* od,
+                       uint64_t* id);
+ibs_status serve_query_sync(ibs_ctx* ctx, const uint8_t* q, int64_t nq, int k, int32_t* oc, int32_t* oi,
+                            double* od);
+ibs_status serve_wait(ibs_ctx* ctx, uint64_t id, int64_t timeout_ms);
+ibs_status serve_poll(ibs_ctx* ctx, uint64_t id);
+ibs_status serve_stats(ibs_ctx* ctx, ibs_serve_stats* out);
+void serve_stop(ibs_ctx* ctx);
+std::shared_ptr<ServeEngine> engine_of(ibs_ctx* ctx);
+
+}  // namespace ibs

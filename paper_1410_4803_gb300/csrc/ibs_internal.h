@@ -1,0 +1,107 @@
+// Host-side declarations shared by the libibs translation units (not part of
+// the public C ABI, which is include/ibs.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ibs {
+
+// Geometry of a bit-plane buffer (see ibs_device.cuh for the memory order).
+struct PlaneGeom {
+  int64_t n = 0;         // samples
+  int64_t m = 0;         // markers
+  int64_t n_blocks = 0;  // ceil(n / 64)
+  int64_t n_chunks = 0;  // ceil(ceil(m / 32) / 12)
+  size_t bytes() const { return (size_t)n_blocks * (size_t)n_chunks * 12u * 64u * 4u * 4u; }
+  static PlaneGeom make(int64_t n, int64_t m) {
+    PlaneGeom g;
+    g.n = n;
+    g.m = m;
+    g.n_blocks = (n + 63) / 64;
+    const int64_t words = (m + 31) / 32;
+    g.n_chunks = (words + 11) / 12;
+    return g;
+  }
+};
+
+// Source of a gather-transpose: rows var_begin .. var_begin+m-1 of a packed
+// matrix with row_bytes bytes per row; sample r of the output is sample
+// sel[r] of the source (sel == nullptr: sample r).
+struct BedSource {
+  const uint8_t* packed = nullptr;
+  int64_t row_bytes = 0;
+  int64_t var_begin = 0;
+  const int64_t* sel = nullptr;
+  int64_t n_src = 0;     // samples in the source (bound for sel entries)
+};
+
+// One subset of a batched launch, as the device sees it.
+struct SubsetDev {
+  const uint32_t* planes;  // this subset's bit planes
+  int64_t n;
+  int64_t n_blocks;
+  int64_t n_chunks;
+  int32_t* out_counts;
+  double* out_dist;
+  int32_t* partial;        // split-K accumulation, triangle [P][4], or nullptr
+  int64_t pad;
+};
+
+// A (subset, tile, K-range) work item of the persistent batched kernel.
+struct WorkItem {
+  int32_t subset;
+  int32_t I, J;
+  int32_t c0, c1;
+  int32_t split;  // 1 when the tile is split over K (accumulate into partial)
+};
+
+// Per-subset plane-build job for the batched gather-transpose.
+struct PlaneJob {
+  BedSource src;
+  int64_t m;             // markers in the window
+  int64_t n;             // samples
+  uint32_t* planes;
+  int64_t n_blocks;
+  int64_t n_chunks;
+  int64_t cta_begin;     // first CTA index of this job in the flattened grid
+  int64_t groups;        // ceil(n_blocks / 2)
+};
+
+// Serving: one query-block x panel-block work item of a step.
+struct CrossItem {
+  const uint32_t* qplanes;  // query block planes base (block already applied)
+  int32_t* out_counts;      // row 0 of this query block in the request's [q][n_panel][4] buffer
+  int32_t q_rows;           // valid query rows in the block (<= 64)
+  int32_t pb;               // panel block
+};
+
+// Kernel launchers (ibs_planes.cu / ibs_pairs.cu / ibs_misc.cu).
+cudaError_t launch_planes(const BedSource& src, int64_t n, int64_t m, const PlaneGeom& g, uint32_t* planes,
+                          int* status, cudaStream_t st);
+cudaError_t launch_planes_batch(const PlaneJob* jobs_dev, int n_jobs, int64_t total_ctas, int* status,
+                                cudaStream_t st);
+
+int tri_splits_for(int64_t tiles, int64_t n_chunks, int num_sms);
+cudaError_t launch_tri(int mode, const uint32_t* planes, const PlaneGeom& g, int splits, int32_t* out_counts,
+                       double* out_dist, int32_t* partial, bool square, int* status, int num_sms,
+                       cudaStream_t st);
+cudaError_t launch_finalize(const int32_t* partial, int64_t n, int32_t* out_counts, double* out_dist,
+                            bool square, cudaStream_t st);
+cudaError_t launch_batch(int mode, const SubsetDev* subsets, const WorkItem* items, int64_t n_items,
+                         int* counter, int* status, int grid, cudaStream_t st);
+cudaError_t launch_finalize_batch(const SubsetDev* subsets, const int32_t* subset_ids, int n_split_subsets,
+                                  int64_t max_pairs, cudaStream_t st);
+cudaError_t launch_cross(int mode, const uint32_t* panel_planes, int64_t n_panel, int64_t panel_blocks,
+                         int64_t n_chunks, const CrossItem* items, int64_t n_items, int* status,
+                         cudaStream_t st);
+cudaError_t launch_topk(const int32_t* counts, int64_t q, int64_t n_panel, int k, int32_t* out_idx,
+                        double* out_dist, cudaStream_t st);
+int pair_kernel_ctas_per_sm(int mode);
+size_t pair_kernel_smem_bytes();
+
+// Integer-pipe microbenchmark (ibs_probe.cu).
+cudaError_t probe_int_pipes(int device, double out[5]);
+
+}  // namespace ibs

@@ -1,0 +1,564 @@
+// Serving engine: a resident reference panel and continuous batching of
+// query requests.
+//
+// The panel's bit planes stay on the device.  A host thread owns a CUDA stream
+// and runs steps; one step processes one panel chunk (a range of 64-sample
+// panel blocks) for EVERY admitted request, so each panel byte is streamed
+// from HBM once per step however many requests are in flight, and the items
+// of a step are ordered panel-block-major so the CTAs sharing a panel block
+// run together and hit it in L2.  A request admitted while others are running
+// joins at the next step, starts at the current panel chunk and finishes after
+// one full cycle over the chunks; then its top-k kernel runs and its outputs
+// are copied back.  Admission is FIFO, bounded by a row-slot limit and by free
+// device memory (or the context's workspace limit).  At most two steps are in
+// flight, so admission and completion are checked between steps while the
+// GPU stays busy.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <thread>
+#include <unordered_map>
+
+#include "ibs_ctx.h"
+#include "ibs_device.cuh"
+
+namespace ibs {
+
+namespace {
+
+constexpr int kMaxQuery = 4096;     // rows per request
+constexpr int kMaxK = 64;           // top-k limit of the kernel
+constexpr int64_t kMaxRows = 4096;  // query rows admitted at once (slot limit)
+constexpr int kCycleChunks = 8;     // panel chunks per full cycle
+constexpr size_t kMemMargin = (size_t)1 << 30;
+
+enum class RState { Pending, Active, Finishing, Done };
+
+struct Request {
+  uint64_t id = 0;
+  int64_t q = 0;
+  int k = 0;
+  int32_t* user_counts = nullptr;
+  int32_t* user_idx = nullptr;
+  double* user_dist = nullptr;
+  bool counts_on_dev = false, topk_on_dev = false;
+  std::vector<uint8_t> host_packed;
+  DevBuf packed, planes, counts, tidx, tdist;
+  size_t reserved = 0;
+  PlaneGeom g;
+  int64_t chunks_done = 0;
+  cudaEvent_t done_ev = nullptr;
+  ibs_status status = IBS_OK;
+  RState state = RState::Pending;
+};
+
+enum class PtrKind { Device, PinnedHost, Pageable };
+
+PtrKind ptr_kind(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return PtrKind::Pageable;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return PtrKind::Device;
+  if (a.type == cudaMemoryTypeHost) return PtrKind::PinnedHost;
+  return PtrKind::Pageable;
+}
+
+}  // namespace
+
+class ServeEngine {
+ public:
+  ibs_ctx* ctx;
+  PlaneGeom pg;
+  DevBuf panel_planes;
+  cudaStream_t stream = nullptr;
+  std::thread worker;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  bool stop = false;
+  std::deque<std::shared_ptr<Request>> pending;
+  std::vector<std::shared_ptr<Request>> active, finishing;
+  std::unordered_map<uint64_t, std::shared_ptr<Request>> all;
+  std::atomic<uint64_t> next_id{1};
+  ibs_serve_stats stats{};
+  int64_t cursor = 0;  // current panel chunk
+  int64_t blocks_per_chunk = 0;
+  int64_t n_cycle = 0;
+  // double-buffered item arrays
+  DevBuf items_dev[2];
+  CrossItem* items_host[2] = {nullptr, nullptr};
+  size_t items_cap = 0;
+  cudaEvent_t step_ev[2] = {nullptr, nullptr};
+  int64_t step_no = 0;
+
+  explicit ServeEngine(ibs_ctx* c) : ctx(c) {}
+
+  size_t mem_need(int64_t q, int k, bool counts_dev, bool topk_dev) const {
+    const PlaneGeom g = PlaneGeom::make(q, pg.m);
+    size_t b = (size_t)pg.m * (size_t)((q + 3) / 4) + g.bytes();
+    if (!counts_dev) b += (size_t)q * pg.n * 16;
+    if (!topk_dev) b += (size_t)q * k * 12;
+    return b + 4096;
+  }
+
+  void release(Request& r) {
+    for (DevBuf* b : {&r.packed, &r.planes, &r.counts, &r.tidx, &r.tdist}) {
+      if (b->p) cudaFree(b->p);
+      b->p = nullptr;
+      b->cap = 0;
+    }
+    if (r.reserved) release_bytes(ctx, r.reserved);
+    r.reserved = 0;
+    if (r.done_ev) cudaEventDestroy(r.done_ev);
+    r.done_ev = nullptr;
+  }
+
+  ibs_status alloc(DevBuf& b, size_t bytes) {
+    if (bytes == 0) return IBS_OK;
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      b.p = nullptr;
+      return IBS_ENOMEM;
+    }
+    b.cap = bytes;
+    return IBS_OK;
+  }
+
+  // Try to admit r (engine thread).  Returns false if it must wait.
+  bool admit(const std::shared_ptr<Request>& r, int64_t active_rows) {
+    if (active_rows + r->q > kMaxRows && active_rows > 0) return false;
+    const size_t need = mem_need(r->q, r->k, r->counts_on_dev, r->topk_on_dev);
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    if (need + kMemMargin > free_b) return false;
+    if (!reserve_bytes(ctx, need)) return false;
+    r->reserved = need;
+    r->g = PlaneGeom::make(r->q, pg.m);
+    const size_t pk = (size_t)pg.m * (size_t)((r->q + 3) / 4);
+    if (alloc(r->packed, pk) || alloc(r->planes, r->g.bytes()) ||
+        (!r->counts_on_dev && alloc(r->counts, (size_t)r->q * pg.n * 16)) ||
+        (!r->topk_on_dev && r->k > 0 && (alloc(r->tidx, (size_t)r->q * r->k * 4) || alloc(r->tdist, (size_t)r->q * r->k * 8)))) {
+      release(*r);
+      return false;
+    }
+    cudaMemcpyAsync(r->packed.p, r->host_packed.data(), pk, cudaMemcpyHostToDevice, stream);
+    BedSource src;
+    src.packed = static_cast<const uint8_t*>(r->packed.p);
+    src.row_bytes = (r->q + 3) / 4;
+    src.n_src = r->q;
+    launch_planes(src, r->q, pg.m, r->g, static_cast<uint32_t*>(r->planes.p), ctx->status_dev, stream);
+    cudaEventCreateWithFlags(&r->done_ev, cudaEventDisableTiming);
+    r->chunks_done = 0;
+    r->state = RState::Active;
+    return true;
+  }
+
+  int32_t* counts_ptr(Request& r) { return r.counts_on_dev ? r.user_counts : static_cast<int32_t*>(r.counts.p); }
+
+  void finish(Request& r) {
+    int32_t* cnt = counts_ptr(r);
+    int32_t* oi = r.topk_on_dev ? r.user_idx : static_cast<int32_t*>(r.tidx.p);
+    double* od = r.topk_on_dev ? r.user_dist : static_cast<double*>(r.tdist.p);
+    if (r.k > 0) launch_topk(cnt, r.q, pg.n, r.k, oi, od, stream);
+    if (!r.counts_on_dev && r.user_counts)
+      cudaMemcpyAsync(r.user_counts, r.counts.p, (size_t)r.q * pg.n * 16, cudaMemcpyDeviceToHost, stream);
+    if (!r.topk_on_dev && r.k > 0) {
+      cudaMemcpyAsync(r.user_idx, r.tidx.p, (size_t)r.q * r.k * 4, cudaMemcpyDeviceToHost, stream);
+      cudaMemcpyAsync(r.user_dist, r.tdist.p, (size_t)r.q * r.k * 8, cudaMemcpyDeviceToHost, stream);
+    }
+    cudaEventRecord(r.done_ev, stream);
+    r.state = RState::Finishing;
+  }
+
+  void ensure_items(size_t n) {
+    if (n <= items_cap) return;
+    for (int s = 0; s < 2; ++s) {
+      if (step_ev[s]) cudaEventSynchronize(step_ev[s]);
+      if (items_dev[s].p) cudaFree(items_dev[s].p);
+      if (items_host[s]) cudaFreeHost(items_host[s]);
+      cudaMalloc(&items_dev[s].p, n * sizeof(CrossItem));
+      cudaHostAlloc(reinterpret_cast<void**>(&items_host[s]), n * sizeof(CrossItem), cudaHostAllocDefault);
+    }
+    items_cap = n;
+  }
+
+  void run_step() {
+    const int slot = (int)(step_no & 1);
+    if (step_ev[slot]) cudaEventSynchronize(step_ev[slot]);  // slot's previous step is done
+    const int64_t pb0 = cursor * blocks_per_chunk;
+    const int64_t pb1 = std::min<int64_t>(pg.n_blocks, pb0 + blocks_per_chunk);
+    size_t qblocks = 0;
+    for (auto& r : active) qblocks += (size_t)r->g.n_blocks;
+    const size_t n_items = qblocks * (size_t)std::max<int64_t>(0, pb1 - pb0);
+    ensure_items(std::max<size_t>(n_items, 1));
+    CrossItem* h = items_host[slot];
+    size_t t = 0;
+    for (int64_t pb = pb0; pb < pb1; ++pb)
+      for (auto& r : active)
+        for (int64_t qb = 0; qb < r->g.n_blocks; ++qb) {
+          CrossItem& it = h[t++];
+          it.qplanes = static_cast<const uint32_t*>(r->planes.p) + (size_t)qb * r->g.n_chunks * kChunkWords;
+          it.out_counts = counts_ptr(*r) + (size_t)qb * kSB * pg.n * 4;
+          it.q_rows = (int32_t)std::min<int64_t>(kSB, r->q - qb * kSB);
+          it.pb = (int32_t)pb;
+        }
+    if (t > 0) {
+      cudaMemcpyAsync(items_dev[slot].p, h, t * sizeof(CrossItem), cudaMemcpyHostToDevice, stream);
+      launch_cross(pick_mode(ctx), static_cast<const uint32_t*>(panel_planes.p), pg.n, pg.n_blocks, pg.n_chunks,
+                   static_cast<const CrossItem*>(items_dev[slot].p), (int64_t)t, ctx->status_dev, stream);
+    }
+    cursor = (cursor + 1) % n_cycle;
+    std::vector<std::shared_ptr<Request>> still;
+    for (auto& r : active) {
+      if (++r->chunks_done >= n_cycle) {
+        finish(*r);
+        finishing.push_back(r);
+      } else {
+        still.push_back(r);
+      }
+    }
+    active.swap(still);
+    if (!step_ev[slot]) cudaEventCreateWithFlags(&step_ev[slot], cudaEventDisableTiming);
+    cudaEventRecord(step_ev[slot], stream);
+    ++step_no;
+    std::lock_guard<std::mutex> lk(mu);
+    stats.steps++;
+  }
+
+  void check_finishing() {
+    std::vector<std::shared_ptr<Request>> still;
+    bool any = false;
+    for (auto& r : finishing) {
+      if (cudaEventQuery(r->done_ev) == cudaSuccess) {
+        const int st = __atomic_load_n(ctx->status_host, __ATOMIC_SEQ_CST);
+        std::lock_guard<std::mutex> lk(mu);
+        r->status = st == kDevTimeout ? IBS_ETIMEOUT : IBS_OK;
+        release(*r);
+        r->state = RState::Done;
+        stats.requests_done++;
+        any = true;
+      } else {
+        still.push_back(r);
+      }
+    }
+    finishing.swap(still);
+    if (any) cv_done.notify_all();
+  }
+
+  void loop() {
+    cudaSetDevice(ctx->device);
+    for (;;) {
+      check_finishing();
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        if (stop) break;
+        int64_t rows = 0;
+        for (auto& r : active) rows += r->q;
+        while (!pending.empty()) {
+          auto r = pending.front();
+          lk.unlock();
+          const bool ok = admit(r, rows);
+          lk.lock();
+          if (!ok) break;
+          pending.pop_front();
+          active.push_back(r);
+          rows += r->q;
+          stats.peak_rows = std::max<uint64_t>(stats.peak_rows, (uint64_t)rows);
+        }
+        if (active.empty()) {
+          if (finishing.empty())
+            cv_work.wait(lk, [&] { return stop || !pending.empty(); });
+          else
+            cv_work.wait_for(lk, std::chrono::microseconds(200));
+          continue;
+        }
+      }
+      run_step();
+    }
+  }
+
+  void start() { worker = std::thread([this] { loop(); }); }
+
+  void shutdown() {
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      stop = true;
+    }
+    cv_work.notify_all();
+    if (worker.joinable()) worker.join();
+    cudaStreamSynchronize(stream);
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto& kv : all) {
+      Request& r = *kv.second;
+      if (r.state != RState::Done) {
+        r.status = IBS_ECANCELLED;
+        r.state = RState::Done;
+      }
+      release(r);
+    }
+    pending.clear();
+    active.clear();
+    finishing.clear();
+    cv_done.notify_all();
+    for (int s = 0; s < 2; ++s) {
+      if (items_dev[s].p) cudaFree(items_dev[s].p);
+      if (items_host[s]) cudaFreeHost(items_host[s]);
+      if (step_ev[s]) cudaEventDestroy(step_ev[s]);
+      items_dev[s].p = nullptr;
+      items_host[s] = nullptr;
+      step_ev[s] = nullptr;
+    }
+    if (panel_planes.p) free_buf(ctx, panel_planes);
+    if (stream) cudaStreamDestroy(stream);
+    stream = nullptr;
+  }
+};
+
+std::shared_ptr<ServeEngine> engine_of(ibs_ctx* ctx) {
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  return ctx->serve;
+}
+
+void serve_stop(ibs_ctx* ctx) {
+  std::shared_ptr<ServeEngine> e;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    e.swap(ctx->serve);
+  }
+  // Waiters hold their own reference, so the engine outlives them.
+  if (e) e->shutdown();
+}
+
+ibs_status serve_panel_load(ibs_ctx* ctx, const uint8_t* panel, int64_t n_panel, int64_t m) {
+  if (!panel) return fail(IBS_EINVAL, "panel_packed is NULL");
+  if (n_panel < 1 || n_panel > 2147483647LL || m < 1 || m > 2147483647LL)
+    return fail(IBS_EINVAL, "panel size out of range");
+  DeviceGuard g(ctx->device);
+  serve_stop(ctx);
+  auto eng = std::make_shared<ServeEngine>(ctx);
+  eng->pg = PlaneGeom::make(n_panel, m);
+  IBS_CUDA_TRY(cudaStreamCreateWithFlags(&eng->stream, cudaStreamNonBlocking));
+  if (ibs_status s = ensure_buf(ctx, eng->panel_planes, eng->pg.bytes())) {
+    cudaStreamDestroy(eng->stream);
+    return s;
+  }
+  const size_t bytes = (size_t)m * (size_t)((n_panel + 3) / 4);
+  const uint8_t* src_dev = panel;
+  void* tmp = nullptr;
+  if (ptr_kind(panel) != PtrKind::Device) {
+    cudaError_t e = cudaMalloc(&tmp, bytes);
+    if (e != cudaSuccess) {
+      free_buf(ctx, eng->panel_planes);
+      cudaStreamDestroy(eng->stream);
+      cudaGetLastError();
+      return fail(IBS_ENOMEM, "panel staging cudaMalloc(%zu) failed", bytes);
+    }
+    IBS_CUDA_TRY(cudaMemcpyAsync(tmp, panel, bytes, cudaMemcpyHostToDevice, eng->stream));
+    src_dev = static_cast<const uint8_t*>(tmp);
+  }
+  BedSource src;
+  src.packed = src_dev;
+  src.row_bytes = (n_panel + 3) / 4;
+  src.n_src = n_panel;
+  IBS_CUDA_TRY(launch_planes(src, n_panel, m, eng->pg, static_cast<uint32_t*>(eng->panel_planes.p), ctx->status_dev,
+                             eng->stream));
+  IBS_CUDA_TRY(cudaStreamSynchronize(eng->stream));
+  if (tmp) cudaFree(tmp);
+  eng->n_cycle = std::min<int64_t>(kCycleChunks, eng->pg.n_blocks);
+  eng->blocks_per_chunk = (eng->pg.n_blocks + eng->n_cycle - 1) / eng->n_cycle;
+  eng->n_cycle = (eng->pg.n_blocks + eng->blocks_per_chunk - 1) / eng->blocks_per_chunk;
+  eng->start();
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ctx->serve = std::move(eng);
+  return IBS_OK;
+}
+
+namespace {
+
+ibs_status validate_query(const std::shared_ptr<ServeEngine>& eng, const uint8_t* q, int64_t nq, int k, int32_t* oc,
+                          int32_t* oi, double* od, bool& counts_dev, bool& topk_dev) {
+  if (!eng) return fail(IBS_ESTATE, "no panel loaded (call ibs_panel_load first)");
+  if (!q) return fail(IBS_EINVAL, "query_packed is NULL");
+  if (nq < 1 || nq > kMaxQuery) return fail(IBS_EINVAL, "n_query %lld out of range [1, %d]", (long long)nq, kMaxQuery);
+  if (k < 0 || k > kMaxK) return fail(IBS_EINVAL, "k=%d out of range [0, %d]", k, kMaxK);
+  if (k > 0 && (!oi || !od)) return fail(IBS_EINVAL, "k > 0 needs out_topk_idx and out_topk_dist");
+  if (oc && reinterpret_cast<uintptr_t>(oc) % 16) return fail(IBS_EINVAL, "out_counts must be 16-byte aligned");
+  counts_dev = oc ? ptr_kind(oc) == PtrKind::Device : false;
+  if (oc && !counts_dev && ptr_kind(oc) != PtrKind::PinnedHost)
+    return fail(IBS_EINVAL, "out_counts must be device memory or pinned host memory");
+  topk_dev = false;
+  if (k > 0) {
+    const PtrKind a = ptr_kind(oi), b = ptr_kind(od);
+    if (a != b) return fail(IBS_EINVAL, "out_topk_idx and out_topk_dist must be the same kind of memory");
+    if (a == PtrKind::Pageable) return fail(IBS_EINVAL, "top-k outputs must be device memory or pinned host memory");
+    topk_dev = a == PtrKind::Device;
+  }
+  return IBS_OK;
+}
+
+std::vector<uint8_t> copy_query(const uint8_t* q, size_t bytes) {
+  std::vector<uint8_t> v(bytes);
+  if (ptr_kind(q) == PtrKind::Device) cudaMemcpy(v.data(), q, bytes, cudaMemcpyDeviceToHost);
+  else std::memcpy(v.data(), q, bytes);
+  return v;
+}
+
+}  // namespace
+
+ibs_status serve_query(ibs_ctx* ctx, const uint8_t* q, int64_t nq, int k, int32_t* oc, int32_t* oi, double* od,
+                       uint64_t* id) {
+  if (!id) return fail(IBS_EINVAL, "req_id is NULL");
+  DeviceGuard g(ctx->device);
+  bool counts_dev = false, topk_dev = false;
+  auto eng = engine_of(ctx);
+  if (ibs_status s = validate_query(eng, q, nq, k, oc, oi, od, counts_dev, topk_dev)) return s;
+  ServeEngine& e = *eng;
+  const size_t need = e.mem_need(nq, k, counts_dev, topk_dev);
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  const size_t cap = ctx->ws_limit ? ctx->ws_limit : total_b;
+  if (need + (ctx->ws_limit ? 0 : kMemMargin) > cap) {
+    std::lock_guard<std::mutex> lk(e.mu);
+    e.stats.rejected++;
+    return fail(IBS_EBUSY, "request needs %zu bytes, more than the serving budget %zu", need, cap);
+  }
+  auto r = std::make_shared<Request>();
+  r->q = nq;
+  r->k = k;
+  r->user_counts = oc;
+  r->user_idx = oi;
+  r->user_dist = od;
+  r->counts_on_dev = counts_dev;
+  r->topk_on_dev = topk_dev;
+  r->host_packed = copy_query(q, (size_t)e.pg.m * (size_t)((nq + 3) / 4));
+  r->id = e.next_id.fetch_add(1);
+  {
+    std::lock_guard<std::mutex> lk(e.mu);
+    if (e.stop) return fail(IBS_ECANCELLED, "engine is shutting down");
+    e.all[r->id] = r;
+    e.pending.push_back(r);
+  }
+  e.cv_work.notify_all();
+  *id = r->id;
+  return IBS_OK;
+}
+
+ibs_status serve_wait(ibs_ctx* ctx, uint64_t id, int64_t timeout_ms) {
+  auto eng = engine_of(ctx);
+  if (!eng) return fail(IBS_ESTATE, "no panel loaded");
+  ServeEngine& e = *eng;
+  std::unique_lock<std::mutex> lk(e.mu);
+  auto it = e.all.find(id);
+  if (it == e.all.end()) return fail(IBS_EINVAL, "unknown request id %llu", (unsigned long long)id);
+  auto r = it->second;
+  auto done = [&] { return r->state == RState::Done; };
+  if (timeout_ms < 0) {
+    e.cv_done.wait(lk, done);
+  } else if (!e.cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), done)) {
+    return fail(IBS_ETIMEOUT, "request %llu not done after %lld ms", (unsigned long long)id, (long long)timeout_ms);
+  }
+  e.all.erase(id);
+  if (r->status != IBS_OK) return fail(r->status, "request %llu failed with status %d", (unsigned long long)id, r->status);
+  return IBS_OK;
+}
+
+ibs_status serve_poll(ibs_ctx* ctx, uint64_t id) {
+  auto eng = engine_of(ctx);
+  if (!eng) return fail(IBS_ESTATE, "no panel loaded");
+  ServeEngine& e = *eng;
+  std::lock_guard<std::mutex> lk(e.mu);
+  auto it = e.all.find(id);
+  if (it == e.all.end()) return fail(IBS_EINVAL, "unknown request id");
+  return it->second->state == RState::Done ? IBS_OK : IBS_EBUSY;
+}
+
+ibs_status serve_stats(ibs_ctx* ctx, ibs_serve_stats* out) {
+  auto eng = engine_of(ctx);
+  if (!eng) return fail(IBS_ESTATE, "no panel loaded");
+  std::lock_guard<std::mutex> lk(eng->mu);
+  *out = eng->stats;
+  return IBS_OK;
+}
+
+// One request, one launch sequence, synchronous: the unbatched baseline.
+ibs_status serve_query_sync(ibs_ctx* ctx, const uint8_t* q, int64_t nq, int k, int32_t* oc, int32_t* oi, double* od) {
+  DeviceGuard g(ctx->device);
+  bool counts_dev = false, topk_dev = false;
+  auto eng = engine_of(ctx);
+  if (ibs_status s = validate_query(eng, q, nq, k, oc, oi, od, counts_dev, topk_dev)) return s;
+  ServeEngine& e = *eng;
+  const PlaneGeom pg = e.pg;
+  const PlaneGeom qg = PlaneGeom::make(nq, pg.m);
+  const size_t pk = (size_t)pg.m * (size_t)((nq + 3) / 4);
+  Request r;
+  r.q = nq;
+  r.k = k;
+  ibs_status st = IBS_OK;
+  cudaStream_t s;
+  IBS_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  const size_t need = e.mem_need(nq, k, counts_dev, topk_dev);
+  if (!reserve_bytes(ctx, need)) {
+    cudaStreamDestroy(s);
+    return fail(IBS_ENOMEM, "workspace limit exceeded");
+  }
+  r.reserved = need;
+  if (e.alloc(r.packed, pk) || e.alloc(r.planes, qg.bytes()) ||
+      (!counts_dev && e.alloc(r.counts, (size_t)nq * pg.n * 16)) ||
+      (!topk_dev && k > 0 && (e.alloc(r.tidx, (size_t)nq * k * 4) || e.alloc(r.tdist, (size_t)nq * k * 8)))) {
+    e.release(r);
+    cudaStreamDestroy(s);
+    return fail(IBS_ENOMEM, "device allocation failed");
+  }
+  int32_t* cnt = counts_dev ? oc : static_cast<int32_t*>(r.counts.p);
+  std::vector<CrossItem> items;
+  for (int64_t pb = 0; pb < pg.n_blocks; ++pb)
+    for (int64_t qb = 0; qb < qg.n_blocks; ++qb) {
+      CrossItem it;
+      it.qplanes = static_cast<const uint32_t*>(r.planes.p) + (size_t)qb * qg.n_chunks * kChunkWords;
+      it.out_counts = cnt + (size_t)qb * kSB * pg.n * 4;
+      it.q_rows = (int32_t)std::min<int64_t>(kSB, nq - qb * kSB);
+      it.pb = (int32_t)pb;
+      items.push_back(it);
+    }
+  DevBuf items_dev;
+  cudaError_t ce = cudaMalloc(&items_dev.p, items.size() * sizeof(CrossItem));
+  if (ce == cudaSuccess) {
+    if (ptr_kind(q) == PtrKind::Device) ce = cudaMemcpyAsync(r.packed.p, q, pk, cudaMemcpyDeviceToDevice, s);
+    else ce = cudaMemcpyAsync(r.packed.p, q, pk, cudaMemcpyHostToDevice, s);
+  }
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(items_dev.p, items.data(), items.size() * sizeof(CrossItem), cudaMemcpyHostToDevice, s);
+  BedSource src;
+  src.packed = static_cast<const uint8_t*>(r.packed.p);
+  src.row_bytes = (nq + 3) / 4;
+  src.n_src = nq;
+  if (ce == cudaSuccess) ce = launch_planes(src, nq, pg.m, qg, static_cast<uint32_t*>(r.planes.p), ctx->status_dev, s);
+  if (ce == cudaSuccess)
+    ce = launch_cross(pick_mode(ctx), static_cast<const uint32_t*>(e.panel_planes.p), pg.n, pg.n_blocks, pg.n_chunks,
+                      static_cast<const CrossItem*>(items_dev.p), (int64_t)items.size(), ctx->status_dev, s);
+  if (ce == cudaSuccess && k > 0)
+    ce = launch_topk(cnt, nq, pg.n, k, topk_dev ? oi : static_cast<int32_t*>(r.tidx.p),
+                     topk_dev ? od : static_cast<double*>(r.tdist.p), s);
+  if (ce == cudaSuccess && oc && !counts_dev)
+    ce = cudaMemcpyAsync(oc, r.counts.p, (size_t)nq * pg.n * 16, cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess && k > 0 && !topk_dev) {
+    ce = cudaMemcpyAsync(oi, r.tidx.p, (size_t)nq * k * 4, cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(od, r.tdist.p, (size_t)nq * k * 8, cudaMemcpyDeviceToHost, s);
+  }
+  cudaError_t se = cudaStreamSynchronize(s);
+  if (ce == cudaSuccess) ce = se;
+  if (items_dev.p) cudaFree(items_dev.p);
+  e.release(r);
+  cudaStreamDestroy(s);
+  if (ce != cudaSuccess) st = fail(IBS_ECUDA, "query_sync failed: %s", cudaGetErrorString(ce));
+  else if (__atomic_load_n(ctx->status_host, __ATOMIC_SEQ_CST) == kDevTimeout)
+    st = fail(IBS_ETIMEOUT, "a bounded device wait timed out");
+  return st;
+}
+
+}  // namespace ibs
