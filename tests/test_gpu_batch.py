@@ -1,0 +1,137 @@
+"""Batched path (ibs_compute_batch): many subsets of a pool over uneven
+variant windows in one persistent launch under a CUDA graph.  Each subset's
+result must equal the plain path on that subset alone and the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import assert_dist_close, pack_codes
+
+pytestmark = pytest.mark.gpu
+
+
+def _subset_packed(pool_codes, idx, vb, vl):
+    return pack_codes(pool_codes[idx][:, vb:vb + vl])
+
+
+@pytest.fixture(scope="module")
+def pool():
+    from paper_1410_4803_gb300 import synth
+    w = synth.batch_pool(pool_n=1500, pool_m=30000, seed=11)
+    codes = oracle.unpack(w.packed, w.n, w.m)
+    return w, codes
+
+
+def _make_subsets(rng, pool_n, pool_m):
+    spec = [(1, 1), (2, 31), (63, 33), (64, 385), (65, 1000), (130, 4097), (700, 20000), (257, 383),
+            (5, 29999), (400, 12345), (129, 64), (900, 7000)]
+    subs = []
+    for n, vl in spec:
+        idx = rng.choice(pool_n, size=n, replace=False).astype(np.int64)
+        if rng.random() < 0.5:
+            idx = np.sort(idx)
+        vb = int(rng.integers(0, pool_m - vl + 1))
+        subs.append((idx, vb, vl))
+    return subs
+
+
+def _run_batch(ctx, w, subs, dev_packed):
+    import torch
+    from paper_1410_4803_gb300 import ibs
+    args, outs = [], []
+    for idx, vb, vl in subs:
+        n = idx.size
+        P = n * (n + 1) // 2
+        c = torch.full((P, 4), -7, dtype=torch.int32, device="cuda")
+        d = torch.empty(P, dtype=torch.float64, device="cuda")
+        it = torch.from_numpy(idx).cuda()
+        args.append((it, vb, vl, c, d))
+        outs.append((c, d, it))
+    ibs.ibs_compute_batch(ctx, dev_packed, w.n, w.m, args)
+    ibs.ibs_synchronize(ctx)
+    return [(c.cpu().numpy(), d.cpu().numpy()) for c, d, _ in outs]
+
+
+def test_batch_matches_plain_and_oracle(pool, tmp_path):
+    import torch
+    from paper_1410_4803_gb300 import ibs
+    w, codes = pool
+    rng = np.random.default_rng(5)
+    subs = _make_subsets(rng, w.n, w.m)
+    dev_packed = torch.from_numpy(w.packed).cuda()
+    ctx = ibs.ibs_init(0, autotune_cache_path=str(tmp_path / "tune.jsonl"))
+    plain = ibs.ibs_init(0)
+    try:
+        first = _run_batch(ctx, w, subs, dev_packed)
+        second = _run_batch(ctx, w, subs, dev_packed)  # graph replay with new output buffers
+        for (idx, vb, vl), (c1, d1), (c2, d2) in zip(subs, first, second):
+            n = idx.size
+            assert (c1 == c2).all()
+            sp = _subset_packed(codes, idx, vb, vl)
+            pc, pd = ibs.compute(plain, torch.from_numpy(sp).cuda(), n, vl)
+            ibs.ibs_synchronize(plain)
+            assert (c1 == pc.cpu().numpy()).all(), f"batch != plain for n={n} window={vb}+{vl}"
+            G = oracle.unpack_subset(w.packed, w.n, w.m, idx, vb, vl)
+            oc, od, _ = oracle.ibs_triangle_from_codes(G)
+            assert (c1 == oc).all(), f"batch != oracle for n={n} window={vb}+{vl}"
+            assert_dist_close(d1, od)
+        info = ibs.ibs_batch_plan_info(ctx)
+        assert info["items"] > 0 and info["grid"] > 0
+        assert (tmp_path / "tune.jsonl").exists()
+    finally:
+        ibs.ibs_shutdown(plain)
+        ibs.ibs_shutdown(ctx)
+
+
+@pytest.mark.parametrize("flags_name", ["IBS_KERNEL_PLAIN", "IBS_KERNEL_CSA"])
+def test_batch_forced_modes(pool, flags_name):
+    import torch
+    from paper_1410_4803_gb300 import ibs
+    w, codes = pool
+    rng = np.random.default_rng(6)
+    subs = _make_subsets(rng, w.n, w.m)[:6]
+    ctx = ibs.ibs_init(0, flags=getattr(ibs, flags_name))
+    try:
+        res = _run_batch(ctx, w, subs, torch.from_numpy(w.packed).cuda())
+        for (idx, vb, vl), (c, d) in zip(subs, res):
+            G = oracle.unpack_subset(w.packed, w.n, w.m, idx, vb, vl)
+            oc, od, _ = oracle.ibs_triangle_from_codes(G)
+            assert (c == oc).all()
+    finally:
+        ibs.ibs_shutdown(ctx)
+
+
+def test_batch_out_of_range_index_is_reported(pool):
+    """A corrupted sample index is not read: the kernel treats that sample as
+    all-missing and ibs_synchronize reports IBS_EINVAL."""
+    import torch
+    from paper_1410_4803_gb300 import ibs
+    w, _ = pool
+    ctx = ibs.ibs_init(0)
+    try:
+        idx = torch.tensor([0, 5, w.n + 100], dtype=torch.int64, device="cuda")
+        c = torch.empty((6, 4), dtype=torch.int32, device="cuda")
+        ibs.ibs_compute_batch(ctx, torch.from_numpy(w.packed).cuda(), w.n, w.m, [(idx, 0, 500, c, None)])
+        with pytest.raises(ibs.IbsError) as ei:
+            ibs.ibs_synchronize(ctx)
+        assert ei.value.status == ibs.IBS_EINVAL
+        got = c.cpu().numpy()
+        # pairs with the bad sample have N = 0
+        assert got[oracle.tri_index(0, 2, 3), 3] == 0 and got[oracle.tri_index(2, 2, 3), 3] == 0
+    finally:
+        ibs.ibs_shutdown(ctx)
+
+
+def test_batch_validation_errors(pool):
+    import torch
+    from paper_1410_4803_gb300 import ibs
+    w, _ = pool
+    ctx = ibs.ibs_init(0)
+    try:
+        idx = torch.arange(10, dtype=torch.int64, device="cuda")
+        c = torch.empty((55, 4), dtype=torch.int32, device="cuda")
+        with pytest.raises(ibs.IbsError) as ei:
+            ibs.ibs_compute_batch(ctx, torch.from_numpy(w.packed).cuda(), w.n, w.m, [(idx, w.m - 10, 20, c, None)])
+        assert ei.value.status == ibs.IBS_EINVAL
+    finally:
+        ibs.ibs_shutdown(ctx)

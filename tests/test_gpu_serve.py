@@ -1,0 +1,186 @@
+"""Serving engine: resident panel, continuous batching, admission, top-k.
+Each request's result must be the same alone (ibs_query_sync) and in the mix,
+and equal to the oracle."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def panel():
+    from paper_1410_4803_gb300 import synth
+    w = synth.serving_panel(n_base_per_pop=560, n_pop=5, m=20000, n_offspring=30, n_dup=10, seed=21)
+    G = oracle.unpack(w.packed, w.n, w.m)
+    return w, G
+
+
+def _pinned(shape, dtype):
+    import torch
+    return torch.empty(shape, dtype=dtype).pin_memory()
+
+
+def test_serving_mix_equals_alone_and_oracle(panel):
+    import torch
+    from paper_1410_4803_gb300 import ibs, synth
+    w, Gp = panel
+    ctx = ibs.ibs_init(0)
+    try:
+        ibs.ibs_panel_load(ctx, torch.from_numpy(w.packed).cuda(), w.n, w.m)
+        sizes = [1, 64, 65, 3, 150, 17, 128, 2, 90, 33, 7, 129]
+        k = 16
+        reqs = []
+        for r, q in enumerate(sizes):
+            qp, qs = synth.serving_queries(w, q, request_id=r, related_frac=0.3, seed=21)
+            reqs.append((q, qp, qs))
+        results = [None] * len(reqs)
+        ids = [None] * len(reqs)
+        errors = []
+
+        def submit(slot_list):
+            try:
+                for i in slot_list:
+                    q, qp, _ = reqs[i]
+                    oc = _pinned((q, w.n, 4), torch.int32)
+                    oi = _pinned((q, k), torch.int32)
+                    od = _pinned((q, k), torch.float64)
+                    ids[i] = ibs.ibs_query(ctx, qp, q, k, oc, oi, od)
+                    results[i] = (oc, oi, od)
+                    time.sleep(0.002 * (i % 3))
+            except Exception as e:  # pragma: no cover
+                errors.append(e)
+
+        threads = [threading.Thread(target=submit, args=(list(range(j, len(reqs), 3)),)) for j in range(3)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        assert not errors, errors
+        for i in range(len(reqs)):
+            ibs.ibs_wait(ctx, ids[i], timeout_ms=120000)
+        stats = ibs.ibs_serve_stats_get(ctx)
+        assert stats["requests_done"] == len(reqs)
+        assert stats["peak_rows"] > max(sizes), "requests never shared a step"
+        for i, (q, qp, _) in enumerate(reqs):
+            oc, oi, od = (x.numpy() for x in results[i])
+            # alone, through the unbatched path
+            ac = _pinned((q, w.n, 4), torch.int32)
+            ai = _pinned((q, k), torch.int32)
+            ad = _pinned((q, k), torch.float64)
+            ibs.ibs_query_sync(ctx, qp, q, k, ac, ai, ad)
+            assert (oc == ac.numpy()).all(), f"request {i}: counts differ alone vs mixed"
+            assert (oi == ai.numpy()).all()
+            np.testing.assert_array_equal(od, ad.numpy())
+            # oracle
+            Gq = oracle.unpack(qp, q, w.m)
+            wc, wd = oracle.ibs_block(Gq, Gp)
+            assert (oc == wc).all(), f"request {i}: counts differ from the oracle"
+            for r in range(q):
+                ti, td = oracle.topk(wd[r], k)
+                assert (oi[r] == ti).all(), f"request {i} row {r}: top-k indices differ"
+                fin = ~np.isnan(td)
+                assert (np.isnan(od[r]) == ~fin).all()
+                assert np.allclose(od[r][fin], td[fin], rtol=1e-12, atol=0)
+    finally:
+        ibs.ibs_shutdown(ctx)
+
+
+def test_serving_device_outputs_and_relatives(panel):
+    import torch
+    from paper_1410_4803_gb300 import ibs, synth
+    w, Gp = panel
+    ctx = ibs.ibs_init(0)
+    try:
+        ibs.ibs_panel_load(ctx, w.packed, w.n, w.m)  # host panel
+        q, k = 40, 5
+        qp, qs = synth.serving_queries(w, q, request_id=99, related_frac=1.0, seed=21)
+        oc = torch.empty((q, w.n, 4), dtype=torch.int32, device="cuda")
+        oi = torch.empty((q, k), dtype=torch.int32, device="cuda")
+        od = torch.empty((q, k), dtype=torch.float64, device="cuda")
+        rid = ibs.ibs_query(ctx, torch.from_numpy(qp).cuda(), q, k, oc, oi, od)
+        ibs.ibs_wait(ctx, rid, timeout_ms=60000)
+        oi = oi.cpu().numpy()
+        gid = {int(g): i for i, g in enumerate(w.samples.gid)}
+        oc = oc.cpu().numpy()
+        for r in range(q):
+            src = gid[int(qs.src_gid[r])]
+            if qs.kind[r] == synth.DUPLICATE:
+                # the source is the nearest panel sample (or second, behind a panel duplicate of it)
+                assert src in oi[r, :2].tolist()
+            if qs.kind[r] == synth.OFFSPRING:
+                assert oc[r, src, 0] == 0  # a parent and child share an allele at every marker
+    finally:
+        ibs.ibs_shutdown(ctx)
+
+
+def test_serving_k_larger_than_panel_and_admission():
+    import torch
+    from paper_1410_4803_gb300 import ibs
+    from helpers import pack_codes, random_codes
+    rng = np.random.default_rng(1)
+    n_panel, m = 10, 700
+    pcodes = random_codes(rng, n_panel, m)
+    pcodes[3] = 1  # all-missing panel sample: NaN distance, ranked last
+    pp = pack_codes(pcodes)
+    ctx = ibs.ibs_init(0, workspace_bytes=1 << 20)
+    try:
+        ibs.ibs_panel_load(ctx, pp, n_panel, m)
+        qc = random_codes(rng, 3, m)
+        qp = pack_codes(qc)
+        k = 16
+        oi = _pinned((3, k), torch.int32)
+        od = _pinned((3, k), torch.float64)
+        rid = ibs.ibs_query(ctx, qp, 3, k, None, oi, od)
+        ibs.ibs_wait(ctx, rid, timeout_ms=60000)
+        _, wd = oracle.ibs_block(qc, pcodes)
+        for r in range(3):
+            ti, td = oracle.topk(wd[r], k)
+            assert (oi.numpy()[r] == ti).all()
+            assert (oi.numpy()[r, n_panel:] == -1).all() and np.isnan(od.numpy()[r, n_panel - 1:]).all()
+        # a request that can never fit the 1 MiB budget (about 2.9 MB of planes and staging) is refused at once
+        big = 4096
+        with pytest.raises(ibs.IbsError) as ei:
+            ibs.ibs_query(ctx, np.zeros((m, big // 4), np.uint8), big, k, _pinned((big, n_panel, 4), torch.int32),
+                          _pinned((big, k), torch.int32), _pinned((big, k), torch.float64))
+        assert ei.value.status in (ibs.IBS_EBUSY, ibs.IBS_EINVAL)
+        # pageable output buffers are refused
+        with pytest.raises(ibs.IbsError):
+            ibs.ibs_query(ctx, qp, 3, k, None, np.zeros((3, k), np.int32), np.zeros((3, k)))
+    finally:
+        ibs.ibs_shutdown(ctx)
+
+
+def test_shutdown_cancels_pending(panel):
+    import torch
+    from paper_1410_4803_gb300 import ibs, synth
+    w, _ = panel
+    ctx = ibs.ibs_init(0)
+    ibs.ibs_panel_load(ctx, w.packed, w.n, w.m)
+    q = 512
+    qp, _ = synth.serving_queries(w, q, request_id=7, seed=21)
+    statuses = []
+    rids = []
+    for _ in range(6):
+        rids.append(ibs.ibs_query(ctx, qp, q, 4, None, _pinned((q, 4), torch.int32), _pinned((q, 4), torch.float64)))
+
+    def waiter(rid):
+        try:
+            ibs.ibs_wait(ctx, rid, timeout_ms=120000)
+            statuses.append(ibs.IBS_OK)
+        except ibs.IbsError as e:
+            statuses.append(e.status)
+
+    ts = [threading.Thread(target=waiter, args=(r,)) for r in rids]
+    for t in ts:
+        t.start()
+    time.sleep(0.5)
+    ibs.ibs_shutdown(ctx)
+    for t in ts:
+        t.join(timeout=60)
+    assert len(statuses) == len(rids)
+    assert all(s in (ibs.IBS_OK, ibs.IBS_ECANCELLED) for s in statuses)
