@@ -88,6 +88,24 @@ ibs_status ibs_init(const ibs_config* cfg, ibs_ctx** out_ctx);
 ibs_status ibs_compute(ibs_ctx* ctx, const uint8_t* packed, int64_t n_samples, int64_t n_variants,
                        int32_t* out_counts, double* out_dist, void* stream);
 
+/* Allocation-free variant of ibs_compute (the paper has no counterpart; it
+ * exists for callers that may not allocate device memory when they call in:
+ * code running during CUDA graph capture, applications whose memory pool owns
+ * the whole device, services that allocate only at start-up).  Takes no
+ * context and calls no cudaMalloc/cudaFree: the bit-plane scratch is a fixed
+ * 64 MiB array in the library's device image, held by every GPU that loads
+ * the library until the process exits.  Arguments, layout and results are
+ * those of ibs_compute (upper triangle, out_dist optional), on the CURRENT
+ * device.  Inputs whose planes exceed the scratch, i.e. when
+ * ceil(n/64) * ceil(ceil(m/32)/12) * 12288 > 64 MiB (for example n = 4096 with
+ * m > 32,640), are rejected with IBS_EINVAL.  The first call on a device looks
+ * up the scratch address (cudaGetSymbolAddress); make it before any stream
+ * capture.  All calls share the one scratch array: calls whose work overlaps
+ * on the GPU (different streams, or threads) race and give undefined results;
+ * serialise them.  A bounded device wait that expires is not reported here. */
+ibs_status ibs_compute_noalloc(const uint8_t* packed, int64_t n_samples, int64_t n_variants, int32_t* out_counts,
+                               double* out_dist, void* stream);
+
 /* Wait for all work enqueued on `stream` and report device-side errors of
  * this context's kernels since the last call: IBS_ETIMEOUT when a bounded
  * device wait expired (the kernel stopped early; outputs undefined), IBS_EINVAL

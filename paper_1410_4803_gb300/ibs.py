@@ -87,6 +87,7 @@ def load():
             "ibs_batch_plan_info": [p, ctypes.POINTER(ctypes.c_int64)],
             "ibs_last_launch_info": [p, ctypes.POINTER(ctypes.c_int64)],
             "ibs_kernel_times": [p, ctypes.POINTER(ctypes.c_double)],
+            "ibs_compute_noalloc": [p, i64, i64, p, p, p],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -166,6 +167,12 @@ def ibs_init(device: int = 0, workspace_bytes: int = 0, flags: int = 0, autotune
 def ibs_compute(ctx: Context, packed, n_samples: int, n_variants: int, out_counts, out_dist=None, stream=None):
     _check(load().ibs_compute(ctx._h, _addr(packed), n_samples, n_variants, _addr(out_counts), _addr(out_dist),
                               _stream(stream, ctx.device)), "ibs_compute")
+
+
+def ibs_compute_noalloc(packed, n_samples: int, n_variants: int, out_counts, out_dist=None, stream=None):
+    """Allocation-free ibs_compute on the current device (fixed 64 MiB scratch; see include/ibs.h)."""
+    _check(load().ibs_compute_noalloc(_addr(packed), n_samples, n_variants, _addr(out_counts), _addr(out_dist),
+                                      _stream(stream)), "ibs_compute_noalloc")
 
 
 def ibs_synchronize(ctx: Context, stream=None):

@@ -1,0 +1,69 @@
+"""The allocation-free entry point, ibs_compute_noalloc.
+
+It serves callers that cannot allocate device memory at the moment they need
+IBS counts: work recorded into a CUDA graph (allocation is not allowed while a
+stream is being captured), applications whose memory pool has reserved the
+whole GPU, and latency-bound services that allocate only once at start-up.
+It keeps its bit-plane scratch in a fixed array inside the library instead.
+
+The test calls it through the C ABI twice in a row, on two different inputs,
+and compares each result with the regular entry point, ibs_compute: counts
+bit for bit and distances within 1e-12 relative error.  The second input is
+smaller than the first, so stale scratch contents from the first call would
+show up as wrong counts.
+"""
+import numpy as np
+import pytest
+
+from helpers import assert_dist_close, pack_codes, random_codes
+
+pytestmark = pytest.mark.gpu
+
+
+def _noalloc(packed_np, n, m):
+    import torch
+    from paper_1410_4803_gb300 import ibs
+    torch.cuda.set_device(0)
+    packed = torch.from_numpy(np.ascontiguousarray(packed_np)).cuda()
+    P = n * (n + 1) // 2
+    counts = torch.empty((P, 4), dtype=torch.int32, device="cuda")
+    dist = torch.empty(P, dtype=torch.float64, device="cuda")
+    ibs.ibs_compute_noalloc(packed, n, m, counts, dist)
+    torch.cuda.synchronize()
+    return counts.cpu().numpy(), dist.cpu().numpy()
+
+
+def _regular(packed_np, n, m):
+    import torch
+    from paper_1410_4803_gb300 import ibs
+    ctx = ibs.ibs_init(0)
+    try:
+        packed = torch.from_numpy(np.ascontiguousarray(packed_np)).cuda()
+        counts, dist = ibs.compute(ctx, packed, n, m)
+        ibs.ibs_synchronize(ctx)
+        return counts.cpu().numpy(), dist.cpu().numpy()
+    finally:
+        ibs.ibs_shutdown(ctx)
+
+
+def test_noalloc_matches_ibs_compute_on_two_calls():
+    rng = np.random.default_rng(2024)
+    cases = [(1000, 20000), (333, 5001)]  # the second call is smaller than the first
+    for n, m in cases:
+        packed = pack_codes(random_codes(rng, n, m, miss=0.04), garbage_rng=rng)
+        got_c, got_d = _noalloc(packed, n, m)
+        want_c, want_d = _regular(packed, n, m)
+        assert (got_c == want_c).all(), f"counts differ for n={n} m={m}"
+        assert_dist_close(got_d, want_d)
+
+
+def test_noalloc_rejects_inputs_beyond_its_scratch():
+    import torch
+    from paper_1410_4803_gb300 import ibs
+    torch.cuda.set_device(0)
+    n, m = 4096, 40000  # planes need about 80 MiB, more than the 64 MiB scratch
+    packed = torch.zeros((m, n // 4), dtype=torch.uint8, device="cuda")
+    counts = torch.empty((n * (n + 1) // 2, 4), dtype=torch.int32, device="cuda")
+    with pytest.raises(ibs.IbsError) as ei:
+        ibs.ibs_compute_noalloc(packed, n, m, counts, None)
+    assert ei.value.status == ibs.IBS_EINVAL
