@@ -385,13 +385,250 @@ def run_reference(args, rank, world, local):
     }
 
 
+def subset_packed_device(pool_dev, idx_dev, vb: int, vl: int):
+    """Harness input preparation: the packed .bed matrix of one subset
+    (samples idx, markers [vb, vb+vl)) gathered from the pool on the device."""
+    import torch
+    rows = pool_dev[vb:vb + vl]
+    byte = rows.index_select(1, idx_dev // 4)
+    shift = (2 * (idx_dev % 4)).to(torch.uint8)
+    code = (byte >> shift) & 3
+    pad = (-idx_dev.numel()) % 4
+    if pad:
+        code = torch.nn.functional.pad(code, (0, pad))
+    code = code.view(vl, -1, 4)
+    return (code[..., 0] | (code[..., 1] << 2) | (code[..., 2] << 4) | (code[..., 3] << 6)).contiguous()
+
+
+def run_batch(args, rank, world, local):
+    """64 cohort subsets of a 30,000 x 600,000 pool: one batched call (gather
+    transpose + one persistent launch, graph-captured, autotuned) against the
+    plain path run once per subset."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_1410_4803_gb300 import ibs, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    t0 = time.perf_counter()
+    w = synth.batch_pool()
+    subs = synth.batch_subsets()
+    gen_s = time.perf_counter() - t0
+    pool = torch.from_numpy(w.packed).to(dev)
+    comps = sum(s.comparisons for s in subs)
+    stream = torch.cuda.Stream(dev)
+    args_b, plain_in, outs_b, outs_p = [], [], [], []
+    for s in subs:
+        idx = torch.from_numpy(s.sample_idx).to(dev)
+        P = s.n * (s.n + 1) // 2
+        cb = torch.empty((P, 4), dtype=torch.int32, device=dev)
+        db = torch.empty(P, dtype=torch.float64, device=dev)
+        args_b.append((idx, s.var_begin, s.var_len, cb, db))
+        outs_b.append((cb, db))
+        plain_in.append(subset_packed_device(pool, idx, s.var_begin, s.var_len))
+        outs_p.append((torch.empty((P, 4), dtype=torch.int32, device=dev),
+                       torch.empty(P, dtype=torch.float64, device=dev)))
+    torch.cuda.synchronize(dev)
+    tune_path = os.path.join(tempfile.gettempdir(), f"ibs_tune_{os.getpid()}.jsonl")
+    ctx_b = ibs.ibs_init(local, autotune_cache_path=tune_path)
+    ctx_p = ibs.ibs_init(local)
+    with torch.cuda.stream(stream):
+        t = time.perf_counter()
+        ibs.ibs_compute_batch(ctx_b, pool, w.n, w.m, args_b, stream)  # plan, autotune, graph capture
+        ibs.ibs_synchronize(ctx_b, stream)
+        first_call_s = time.perf_counter() - t
+        plan = ibs.ibs_batch_plan_info(ctx_b)
+
+        def timed(fn, k):
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+            for i in range(k):
+                ev[i][0].record(stream)
+                fn()
+                ev[i][1].record(stream)
+            torch.cuda.synchronize(dev)
+            return [a.elapsed_time(b) for a, b in ev]
+
+        def batched():
+            ibs.ibs_compute_batch(ctx_b, pool, w.n, w.m, args_b, stream)
+
+        def plain_loop():
+            for s, pk, (c, d) in zip(subs, plain_in, outs_p):
+                ibs.ibs_compute(ctx_p, pk, s.n, s.var_len, c, d, stream)
+
+        for _ in range(args.warmup):
+            batched()
+            plain_loop()
+        torch.cuda.synchronize(dev)
+        clk = ClockSampler(local)
+        clk.start()
+        ms_b = timed(batched, args.steps)
+        ms_p = timed(plain_loop, args.steps)
+        clocks = clk.stop()
+        ibs.ibs_synchronize(ctx_b, stream)
+        ibs.ibs_synchronize(ctx_p, stream)
+    # exactness: every subset, batched vs plain, bit for bit; sampled pairs vs the oracle
+    same = all(torch.equal(a[0], b[0]) and torch.equal(torch.nan_to_num(a[1], nan=-1.0),
+                                                        torch.nan_to_num(b[1], nan=-1.0))
+               for a, b in zip(outs_b, outs_p))
+    rng = np.random.default_rng(0)
+    oracle_ok = True
+    for k in rng.choice(len(subs), 4, replace=False):
+        s = subs[k]
+        rows = np.sort(rng.choice(s.n, min(s.n, 24), replace=False))
+        G = oracle.unpack_subset(w.packed, w.n, w.m, s.sample_idx[rows], s.var_begin, s.var_len)
+        oc, _ = oracle.ibs_block(G, G)
+        got = outs_b[k][0].cpu().numpy()
+        for a in range(rows.size):
+            for b in range(a, rows.size):
+                if (got[oracle.tri_index(rows[a], rows[b], s.n)] != oc[a, b]).any():
+                    oracle_ok = False
+    ibs.ibs_shutdown(ctx_b)
+    ibs.ibs_shutdown(ctx_p)
+    mb, mp = statistics.mean(ms_b), statistics.mean(ms_p)
+    return {
+        "metric": METRIC, "value": comps / (mb * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mb, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"batched: {len(subs)} subsets of pool n={w.n} m={w.m} "
+                               f"(n ~ U[200, 8000], windows ~ U[10k, 200k]), seed 3",
+                   "comparisons_per_step": comps, "plan": plan, "first_call_s_incl_autotune": first_call_s,
+                   "generation_s": gen_s},
+        "plain_loop": {"value": comps / (mp * 1e-3), "ms_per_step": mp, "launches_per_step": 2 * len(subs)},
+        "speedup_vs_plain_loop": mp / mb,
+        "exact": {"batched_equals_plain_all_subsets": bool(same), "oracle_sampled_pairs": bool(oracle_ok)},
+        "gpu_launches": int(args.steps * 2),
+        "clocks": clocks,
+    }
+
+
+def run_serve(args, rank, world, local):
+    """Resident 100,000 x 200,000 panel; Poisson arrivals of 1-512-sample
+    query requests.  The engine (continuous batching) against the plain path
+    (one request at a time through ibs_query_sync), same arrivals."""
+    import threading
+    import numpy as np
+    import torch
+    from paper_1410_4803_gb300 import ibs, synth
+
+    torch.cuda.set_device(local)
+    t0 = time.perf_counter()
+    panel = synth.serving_panel()
+    gen_s = time.perf_counter() - t0
+    n_payload = 48
+    sizes = synth.serving_query_sizes(n_payload)
+    payloads = [synth.serving_queries(panel, int(q), request_id=i)[0] for i, q in enumerate(sizes)]
+    k = 16
+    bufs = [(torch.empty((int(q), panel.n, 4), dtype=torch.int32).pin_memory(),
+             torch.empty((int(q), k), dtype=torch.int32).pin_memory(),
+             torch.empty((int(q), k), dtype=torch.float64).pin_memory()) for q in sizes]
+    ctx = ibs.ibs_init(local)
+    t = time.perf_counter()
+    ibs.ibs_panel_load(ctx, torch.from_numpy(panel.packed).cuda(), panel.n, panel.m)
+    load_s = time.perf_counter() - t
+
+    def comps_of(i):
+        return int(sizes[i]) * panel.n * panel.m
+
+    def run_engine(arrivals):
+        ids = [None] * len(arrivals)
+        done = [0.0] * len(arrivals)
+        start = time.perf_counter()
+
+        def waiter():
+            for i in range(len(arrivals)):
+                while ids[i] is None:
+                    time.sleep(0.0002)
+                ibs.ibs_wait(ctx, ids[i], timeout_ms=600000)
+                done[i] = time.perf_counter() - start
+        th = threading.Thread(target=waiter)
+        th.start()
+        for i, ta in enumerate(arrivals):
+            now = time.perf_counter() - start
+            if ta > now:
+                time.sleep(ta - now)
+            p = i % n_payload
+            ids[i] = ibs.ibs_query(ctx, payloads[p], int(sizes[p]), k, *bufs[p])
+        th.join()
+        return done
+
+    def run_plain(arrivals):
+        done = [0.0] * len(arrivals)
+        start = time.perf_counter()
+        for i, ta in enumerate(arrivals):
+            now = time.perf_counter() - start
+            if ta > now:
+                time.sleep(ta - now)
+            p = i % n_payload
+            ibs.ibs_query_sync(ctx, payloads[p], int(sizes[p]), k, *bufs[p])
+            done[i] = time.perf_counter() - start
+        return done
+
+    def summarize(arrivals, done):
+        lat = np.array(done) - np.array(arrivals)
+        total = sum(comps_of(i % n_payload) for i in range(len(arrivals)))
+        span = max(done) - min(arrivals)
+        return {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "mean_ms": float(lat.mean() * 1e3), "throughput": total / span, "requests": len(arrivals)}
+
+    # warm-up both paths
+    run_engine([0.0] * 4)
+    run_plain([0.0] * 2)
+    # exactness: a few requests, engine vs plain, bit for bit
+    exact = True
+    for p in range(3):
+        q = int(sizes[p])
+        a = [torch.empty((q, panel.n, 4), dtype=torch.int32).pin_memory(),
+             torch.empty((q, k), dtype=torch.int32).pin_memory(),
+             torch.empty((q, k), dtype=torch.float64).pin_memory()]
+        b = [torch.empty_like(x).pin_memory() for x in a]
+        rid = ibs.ibs_query(ctx, payloads[p], q, k, *a)
+        ibs.ibs_wait(ctx, rid, timeout_ms=600000)
+        ibs.ibs_query_sync(ctx, payloads[p], q, k, *b)
+        exact &= all(torch.equal(x, y) for x, y in zip(a[:2], b[:2]))
+        exact &= torch.equal(torch.nan_to_num(a[2], nan=-1.0), torch.nan_to_num(b[2], nan=-1.0))
+    rng = np.random.default_rng(4)
+    results = []
+    clk = ClockSampler(local)
+    clk.start()
+    for lam in args.rates:
+        n_req = args.requests
+        if lam > 0:
+            arrivals = list(np.cumsum(rng.exponential(1.0 / lam, n_req)))
+        else:
+            arrivals = [0.0] * n_req  # saturation: everything arrives at once
+        eng = summarize(arrivals, run_engine(arrivals))
+        pln = summarize(arrivals, run_plain(arrivals))
+        results.append({"lambda_per_s": lam if lam > 0 else "saturation", "engine": eng, "plain": pln})
+    clocks = clk.stop()
+    stats = ibs.ibs_serve_stats_get(ctx)
+    ibs.ibs_shutdown(ctx)
+    sat = [r for r in results if r["lambda_per_s"] == "saturation"]
+    head = sat[0] if sat else results[-1]
+    return {
+        "metric": METRIC, "value": head["engine"]["throughput"], "unit": UNIT, "n_gpus": 1,
+        "steps": len(results), "warmup": 1, "ms_per_step": head["engine"]["mean_ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"serving: panel n={panel.n} m={panel.m} resident; requests of q = "
+                               f"floor(exp(U(0, ln 512))) + 1 samples, Poisson arrivals; counts [q][n][4] and "
+                               f"top-{k} to pinned host buffers", "distinct_payloads": n_payload,
+                   "mean_q": float(np.mean(sizes)), "panel_generation_s": gen_s, "panel_load_s": load_s},
+        "serving": results, "engine_stats": stats,
+        "exact": {"engine_equals_plain": bool(exact)},
+        "clocks": clocks,
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="plain", choices=["plain", "structured"])
+    ap.add_argument("--workload", default="plain", choices=["plain", "structured", "batch", "serve"])
+    ap.add_argument("--rates", type=float, nargs="*", default=[4.0, 12.0, 24.0, 0.0],
+                    help="serving: Poisson arrival rates per second (0 = all at once)")
+    ap.add_argument("--requests", type=int, default=60, help="serving: requests per rate")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-step-seconds", type=float, default=4.0)
@@ -406,6 +643,10 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     if args.impl == "reference":
         line = run_reference(args, rank, world, local)
+    elif args.workload == "batch":
+        line = run_batch(args, rank, world, local)
+    elif args.workload == "serve":
+        line = run_serve(args, rank, world, local)
     else:
         line = run_plain(args, rank, world, local)
     if line is not None:

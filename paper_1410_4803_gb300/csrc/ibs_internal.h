@@ -69,12 +69,20 @@ struct PlaneJob {
   int64_t groups;        // ceil(n_blocks / 2)
 };
 
-// Serving: one query-block x panel-block work item of a step.
+// Serving: one query-block x panel-block work item of a step.  The 64 rows of
+// a query block may belong to different requests, so each row carries its
+// own output row ([n_panel][4] int32).
 struct CrossItem {
   const uint32_t* qplanes;  // query block planes base (block already applied)
-  int32_t* out_counts;      // row 0 of this query block in the request's [q][n_panel][4] buffer
+  int32_t* const* row_out;  // 64 output row pointers of this block (entries >= q_rows unused)
   int32_t q_rows;           // valid query rows in the block (<= 64)
   int32_t pb;               // panel block
+};
+
+// Serving: source of one dense step row (a row of some request's planes).
+struct RowSrc {
+  const uint32_t* planes;   // the request's bit planes
+  int64_t row;              // row within the request
 };
 
 // Kernel launchers (ibs_planes.cu / ibs_pairs.cu / ibs_misc.cu).
@@ -96,6 +104,8 @@ cudaError_t launch_finalize_batch(const SubsetDev* subsets, const int32_t* subse
 cudaError_t launch_cross(int mode, const uint32_t* panel_planes, int64_t n_panel, int64_t panel_blocks,
                          int64_t n_chunks, const CrossItem* items, int64_t n_items, int* status,
                          cudaStream_t st);
+cudaError_t launch_gather_rows(const RowSrc* rows, int64_t n_rows, int64_t n_chunks, uint32_t* dst,
+                               cudaStream_t st);
 cudaError_t launch_topk(const int32_t* counts, int64_t q, int64_t n_panel, int k, int32_t* out_idx,
                         double* out_dist, cudaStream_t st);
 int pair_kernel_ctas_per_sm(int mode);

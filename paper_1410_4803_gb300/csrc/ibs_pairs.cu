@@ -289,7 +289,9 @@ __global__ void __launch_bounds__(kThreads, 2)
   }
 }
 
-// Serving: query block x panel block items; output rows of [q][n_panel][4].
+// Serving: query block x panel block items.  Row r of a query block writes
+// its counts to row_out[r] ([n_panel][4] int32), so one block can carry the
+// rows of several requests.
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 2)
     cross_kernel(const uint32_t* __restrict__ panel, int64_t n_panel, int64_t n_chunks,
@@ -308,15 +310,34 @@ __global__ void __launch_bounds__(kThreads, 2)
     for (int i = 0; i < 4; ++i) {
       const int r = ty + 16 * i;
       if (r >= w.q_rows) continue;
+      int4* orow = reinterpret_cast<int4*>(w.row_out[r]);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int64_t gj = (int64_t)w.pb * kSB + tx + 16 * j;
         if (gj >= n_panel) continue;
         const int32_t nn = (int32_t)a.n[i][j], c0 = (int32_t)a.i0[i][j], c1 = (int32_t)a.i1[i][j];
-        reinterpret_cast<int4*>(w.out_counts)[(int64_t)r * n_panel + gj] = make_int4(c0, c1, nn - c0 - c1, nn);
+        orow[gj] = make_int4(c0, c1, nn - c0 - c1, nn);
       }
     }
   }
+}
+
+// Serving: gather rows of several requests' bit planes into one dense block
+// layout.  CTA = (chunk c, destination block b); thread = (word kw, slot s).
+// Destination rows past n_rows get all-zero planes.
+__global__ void __launch_bounds__(kKC * kSB)
+    gather_rows_kernel(const RowSrc* __restrict__ rows, int64_t n_rows, int64_t n_chunks,
+                       uint32_t* __restrict__ dst) {
+  const int64_t c = blockIdx.x, b = blockIdx.y;
+  const int kw = threadIdx.x / kSB, s = threadIdx.x % kSB;
+  const int64_t d = b * kSB + s;
+  uint4 v = make_uint4(0u, 0u, 0u, 0u);
+  if (d < n_rows) {
+    const RowSrc src = rows[d];
+    const int64_t sb = src.row / kSB, ss = src.row % kSB;
+    v = *reinterpret_cast<const uint4*>(src.planes + (((sb * n_chunks + c) * kKC + kw) * kSB + ss) * kPlanes);
+  }
+  *reinterpret_cast<uint4*>(dst + (((b * n_chunks + c) * kKC + kw) * kSB + s) * kPlanes) = v;
 }
 
 // Split-K finalisation: triangle partials -> counts and distances.
@@ -427,6 +448,15 @@ cudaError_t launch_finalize_batch(const SubsetDev* subsets, const int32_t* subse
   if (blocks > 4096) blocks = 4096;
   dim3 grid((unsigned)blocks, (unsigned)n_split_subsets);
   finalize_batch_kernel<<<grid, 256, 0, st>>>(subsets, subset_ids);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rows(const RowSrc* rows, int64_t n_rows, int64_t n_chunks, uint32_t* dst,
+                               cudaStream_t st) {
+  if (n_rows <= 0) return cudaSuccess;
+  const int64_t blocks = (n_rows + kSB - 1) / kSB;
+  if (n_chunks > 2147483647LL || blocks > 65535) return cudaErrorInvalidValue;
+  gather_rows_kernel<<<dim3((unsigned)n_chunks, (unsigned)blocks), kKC * kSB, 0, st>>>(rows, n_rows, n_chunks, dst);
   return cudaGetLastError();
 }
 

@@ -94,6 +94,9 @@ class ServeEngine {
   size_t items_cap = 0;
   cudaEvent_t step_ev[2] = {nullptr, nullptr};
   int64_t step_no = 0;
+  DevBuf step_planes, rows_dev[2], outs_dev[2];
+  RowSrc* rows_host[2] = {nullptr, nullptr};
+  int32_t** outs_host[2] = {nullptr, nullptr};
 
   explicit ServeEngine(ibs_ctx* c) : ctx(c) {}
 
@@ -187,28 +190,58 @@ class ServeEngine {
     items_cap = n;
   }
 
+  // Step-level buffers: dense query planes for kMaxRows rows and the per-row
+  // source / output tables (double-buffered host staging).
+  ibs_status alloc_step_buffers() {
+    const PlaneGeom g = PlaneGeom::make(kMaxRows, pg.m);
+    if (ibs_status s = ensure_buf(ctx, step_planes, g.bytes())) return s;
+    for (int s = 0; s < 2; ++s) {
+      if (ibs_status e = ensure_buf(ctx, rows_dev[s], kMaxRows * sizeof(RowSrc))) return e;
+      if (ibs_status e = ensure_buf(ctx, outs_dev[s], kMaxRows * sizeof(int32_t*))) return e;
+      if (cudaHostAlloc(reinterpret_cast<void**>(&rows_host[s]), kMaxRows * sizeof(RowSrc), cudaHostAllocDefault) !=
+              cudaSuccess ||
+          cudaHostAlloc(reinterpret_cast<void**>(&outs_host[s]), kMaxRows * sizeof(int32_t*), cudaHostAllocDefault) !=
+              cudaSuccess)
+        return fail(IBS_ENOMEM, "pinned step tables could not be allocated");
+    }
+    return IBS_OK;
+  }
+
+  // One step: every active request's rows, packed densely into 64-row query
+  // blocks, against the current panel chunk.
   void run_step() {
     const int slot = (int)(step_no & 1);
-    if (step_ev[slot]) cudaEventSynchronize(step_ev[slot]);  // slot's previous step is done
+    if (step_ev[slot]) cudaEventSynchronize(step_ev[slot]);  // slot's host tables are free again
     const int64_t pb0 = cursor * blocks_per_chunk;
     const int64_t pb1 = std::min<int64_t>(pg.n_blocks, pb0 + blocks_per_chunk);
-    size_t qblocks = 0;
-    for (auto& r : active) qblocks += (size_t)r->g.n_blocks;
-    const size_t n_items = qblocks * (size_t)std::max<int64_t>(0, pb1 - pb0);
+    int64_t n_rows = 0;
+    for (auto& r : active)
+      for (int64_t row = 0; row < r->q; ++row) {
+        rows_host[slot][n_rows].planes = static_cast<const uint32_t*>(r->planes.p);
+        rows_host[slot][n_rows].row = row;
+        outs_host[slot][n_rows] = counts_ptr(*r) + (size_t)row * pg.n * 4;
+        ++n_rows;
+      }
+    const int64_t qblocks = (n_rows + kSB - 1) / kSB;
+    const size_t n_items = (size_t)qblocks * (size_t)std::max<int64_t>(0, pb1 - pb0);
     ensure_items(std::max<size_t>(n_items, 1));
     CrossItem* h = items_host[slot];
     size_t t = 0;
+    int32_t** outs_d = static_cast<int32_t**>(outs_dev[slot].p);
     for (int64_t pb = pb0; pb < pb1; ++pb)
-      for (auto& r : active)
-        for (int64_t qb = 0; qb < r->g.n_blocks; ++qb) {
-          CrossItem& it = h[t++];
-          it.qplanes = static_cast<const uint32_t*>(r->planes.p) + (size_t)qb * r->g.n_chunks * kChunkWords;
-          it.out_counts = counts_ptr(*r) + (size_t)qb * kSB * pg.n * 4;
-          it.q_rows = (int32_t)std::min<int64_t>(kSB, r->q - qb * kSB);
-          it.pb = (int32_t)pb;
-        }
+      for (int64_t b = 0; b < qblocks; ++b) {
+        CrossItem& it = h[t++];
+        it.qplanes = static_cast<const uint32_t*>(step_planes.p) + (size_t)b * pg.n_chunks * kChunkWords;
+        it.row_out = outs_d + b * kSB;
+        it.q_rows = (int32_t)std::min<int64_t>(kSB, n_rows - b * kSB);
+        it.pb = (int32_t)pb;
+      }
     if (t > 0) {
+      cudaMemcpyAsync(rows_dev[slot].p, rows_host[slot], n_rows * sizeof(RowSrc), cudaMemcpyHostToDevice, stream);
+      cudaMemcpyAsync(outs_dev[slot].p, outs_host[slot], n_rows * sizeof(int32_t*), cudaMemcpyHostToDevice, stream);
       cudaMemcpyAsync(items_dev[slot].p, h, t * sizeof(CrossItem), cudaMemcpyHostToDevice, stream);
+      launch_gather_rows(static_cast<const RowSrc*>(rows_dev[slot].p), n_rows, pg.n_chunks,
+                         static_cast<uint32_t*>(step_planes.p), stream);
       launch_cross(pick_mode(ctx), static_cast<const uint32_t*>(panel_planes.p), pg.n, pg.n_blocks, pg.n_chunks,
                    static_cast<const CrossItem*>(items_dev[slot].p), (int64_t)t, ctx->status_dev, stream);
     }
@@ -314,6 +347,15 @@ class ServeEngine {
       step_ev[s] = nullptr;
     }
     if (panel_planes.p) free_buf(ctx, panel_planes);
+    free_buf(ctx, step_planes);
+    for (int s = 0; s < 2; ++s) {
+      free_buf(ctx, rows_dev[s]);
+      free_buf(ctx, outs_dev[s]);
+      if (rows_host[s]) cudaFreeHost(rows_host[s]);
+      if (outs_host[s]) cudaFreeHost(outs_host[s]);
+      rows_host[s] = nullptr;
+      outs_host[s] = nullptr;
+    }
     if (stream) cudaStreamDestroy(stream);
     stream = nullptr;
   }
@@ -369,6 +411,10 @@ ibs_status serve_panel_load(ibs_ctx* ctx, const uint8_t* panel, int64_t n_panel,
                              eng->stream));
   IBS_CUDA_TRY(cudaStreamSynchronize(eng->stream));
   if (tmp) cudaFree(tmp);
+  if (ibs_status st = eng->alloc_step_buffers()) {
+    eng->shutdown();
+    return st;
+  }
   eng->n_cycle = std::min<int64_t>(kCycleChunks, eng->pg.n_blocks);
   eng->blocks_per_chunk = (eng->pg.n_blocks + eng->n_cycle - 1) / eng->n_cycle;
   eng->n_cycle = (eng->pg.n_blocks + eng->blocks_per_chunk - 1) / eng->blocks_per_chunk;
@@ -515,18 +561,24 @@ ibs_status serve_query_sync(ibs_ctx* ctx, const uint8_t* q, int64_t nq, int k, i
     return fail(IBS_ENOMEM, "device allocation failed");
   }
   int32_t* cnt = counts_dev ? oc : static_cast<int32_t*>(r.counts.p);
+  std::vector<int32_t*> outs((size_t)nq);
+  for (int64_t row = 0; row < nq; ++row) outs[row] = cnt + (size_t)row * pg.n * 4;
+  DevBuf outs_d;
+  cudaError_t ce = cudaMalloc(&outs_d.p, outs.size() * sizeof(int32_t*));
   std::vector<CrossItem> items;
   for (int64_t pb = 0; pb < pg.n_blocks; ++pb)
     for (int64_t qb = 0; qb < qg.n_blocks; ++qb) {
       CrossItem it;
       it.qplanes = static_cast<const uint32_t*>(r.planes.p) + (size_t)qb * qg.n_chunks * kChunkWords;
-      it.out_counts = cnt + (size_t)qb * kSB * pg.n * 4;
+      it.row_out = static_cast<int32_t**>(outs_d.p) + qb * kSB;
       it.q_rows = (int32_t)std::min<int64_t>(kSB, nq - qb * kSB);
       it.pb = (int32_t)pb;
       items.push_back(it);
     }
   DevBuf items_dev;
-  cudaError_t ce = cudaMalloc(&items_dev.p, items.size() * sizeof(CrossItem));
+  if (ce == cudaSuccess) ce = cudaMalloc(&items_dev.p, items.size() * sizeof(CrossItem));
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(outs_d.p, outs.data(), outs.size() * sizeof(int32_t*), cudaMemcpyHostToDevice, s);
   if (ce == cudaSuccess) {
     if (ptr_kind(q) == PtrKind::Device) ce = cudaMemcpyAsync(r.packed.p, q, pk, cudaMemcpyDeviceToDevice, s);
     else ce = cudaMemcpyAsync(r.packed.p, q, pk, cudaMemcpyHostToDevice, s);
@@ -553,6 +605,7 @@ ibs_status serve_query_sync(ibs_ctx* ctx, const uint8_t* q, int64_t nq, int k, i
   cudaError_t se = cudaStreamSynchronize(s);
   if (ce == cudaSuccess) ce = se;
   if (items_dev.p) cudaFree(items_dev.p);
+  if (outs_d.p) cudaFree(outs_d.p);
   e.release(r);
   cudaStreamDestroy(s);
   if (ce != cudaSuccess) st = fail(IBS_ECUDA, "query_sync failed: %s", cudaGetErrorString(ce));
