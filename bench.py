@@ -294,7 +294,7 @@ def run_plain(args, rank, world, local):
     planes_ms = kt["planes_ms"] / max(1, kt["calls"])
     roof = int_pipe_roofline(probe, clocks.get("sm_mhz"))
     achieved = comps / (pairs_ms * 1e-3)
-    mode = "plain" if os.environ.get("IBS_PAIR_MODE", "1") == "0" else "csa3"
+    mode = {"0": "plain", "1": "csa3", "2": "csa3-1cta"}.get(os.environ.get("IBS_PAIR_MODE", "1"), "csa3")
     # transpose: read the 2-bit input once, write 16 bytes per (padded) sample-word of planes
     words = (m + 31) // 32
     n_blocks, n_chunks = (n + 63) // 64, (words + 11) // 12
@@ -432,7 +432,7 @@ def run_batch(args, rank, world, local):
     torch.cuda.synchronize(dev)
     tune_path = os.path.join(tempfile.gettempdir(), f"ibs_tune_{os.getpid()}.jsonl")
     ctx_b = ibs.ibs_init(local, autotune_cache_path=tune_path)
-    ctx_p = ibs.ibs_init(local)
+    ctx_p = ibs.ibs_init(local, flags=ibs.IBS_TIMING)
     with torch.cuda.stream(stream):
         t = time.perf_counter()
         ibs.ibs_compute_batch(ctx_b, pool, w.n, w.m, args_b, stream)  # plan, autotune, graph capture
@@ -460,6 +460,7 @@ def run_batch(args, rank, world, local):
             batched()
             plain_loop()
         torch.cuda.synchronize(dev)
+        ibs.ibs_kernel_times(ctx_p)  # drop warm-up records
         clk = ClockSampler(local)
         clk.start()
         ms_b = timed(batched, args.steps)
@@ -467,6 +468,7 @@ def run_batch(args, rank, world, local):
         clocks = clk.stop()
         ibs.ibs_synchronize(ctx_b, stream)
         ibs.ibs_synchronize(ctx_p, stream)
+        kt_p = ibs.ibs_kernel_times(ctx_p)
     # exactness: every subset, batched vs plain, bit for bit; sampled pairs vs the oracle
     same = all(torch.equal(a[0], b[0]) and torch.equal(torch.nan_to_num(a[1], nan=-1.0),
                                                         torch.nan_to_num(b[1], nan=-1.0))
@@ -494,7 +496,10 @@ def run_batch(args, rank, world, local):
                                f"(n ~ U[200, 8000], windows ~ U[10k, 200k]), seed 3",
                    "comparisons_per_step": comps, "plan": plan, "first_call_s_incl_autotune": first_call_s,
                    "generation_s": gen_s},
-        "plain_loop": {"value": comps / (mp * 1e-3), "ms_per_step": mp, "launches_per_step": 2 * len(subs)},
+        "plain_loop": {"value": comps / (mp * 1e-3), "ms_per_step": mp, "launches_per_step": 2 * len(subs),
+                       "transpose_ms_per_step": kt_p["planes_ms"] / args.steps,
+                       "pair_kernel_ms_per_step": kt_p["pairs_ms"] / args.steps,
+                       "finalize_ms_per_step": kt_p["finalize_ms"] / args.steps},
         "speedup_vs_plain_loop": mp / mb,
         "exact": {"batched_equals_plain_all_subsets": bool(same), "oracle_sampled_pairs": bool(oracle_ok)},
         "gpu_launches": int(args.steps * 2),

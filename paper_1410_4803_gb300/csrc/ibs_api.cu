@@ -139,7 +139,7 @@ ibs_status ibs_init(const ibs_config* cfg, ibs_ctx** out_ctx) {
   ctx->cc_major = prop.major;
   ctx->cc_minor = prop.minor;
   const char* env = getenv("IBS_PAIR_MODE");
-  if (env && (env[0] == '0' || env[0] == '1')) ctx->default_mode = env[0] - '0';
+  if (env && env[0] >= '0' && env[0] <= '2' && env[1] == 0) ctx->default_mode = env[0] - '0';
   e = cudaHostAlloc(reinterpret_cast<void**>(&ctx->status_host), sizeof(int), cudaHostAllocMapped);
   if (e != cudaSuccess) {
     delete ctx;
@@ -514,7 +514,7 @@ extern "C" ibs_status ibs_compute_batch(ibs_ctx* ctx, const uint8_t* pool, int64
       policy = te->second.split_policy;
     } else if (!getenv("IBS_NO_AUTOTUNE")) {
       double best = 1e30;
-      for (int cm = 0; cm < 2; ++cm) {
+      for (int cm = 0; cm < 3; ++cm) {
         if (forced >= 0 && cm != forced) continue;
         for (int cp = 0; cp < 2; ++cp) {
           BatchPlan trial;

@@ -18,6 +18,8 @@
 //      words cost two POPCs instead of three: popc(a)+popc(b)+popc(c) =
 //      popc(a^b^c) + 2*popc(maj(a,b,c)).  POPC issues at a quarter of the
 //      LOP3 rate on this SM, so trading POPCs for LOP3s raises the ceiling.
+//   2  carry-save as 1, compiled for one CTA per SM so the loop is not held to
+//      128 registers (no spills, fewer warps to hide latency).
 //
 // Every mbarrier wait is bounded (2 s of %globaltimer); on expiry the kernel
 // writes IBS_ETIMEOUT into the status word, waits (bounded) for its own
@@ -238,8 +240,8 @@ __device__ __forceinline__ void store_partial(const Acc& a, int64_t I, int64_t J
 }
 
 // Plain all-pairs: one CTA per (triangular tile, K split).
-template <int MODE>
-__global__ void __launch_bounds__(kThreads, 2)
+template <int MODE, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB)
     tri_kernel(const uint32_t* __restrict__ planes, int64_t n, int64_t n_blocks, int64_t n_chunks, int splits,
                int32_t* __restrict__ out_counts, double* __restrict__ out_dist, int32_t* __restrict__ partial,
                int square, int* status) {
@@ -261,39 +263,47 @@ __global__ void __launch_bounds__(kThreads, 2)
   else store_partial(a, I, J, n, tx, ty, partial);
 }
 
-// Batched: a persistent kernel pulling (subset, tile, K range) items.
-template <int MODE>
-__global__ void __launch_bounds__(kThreads, 2)
+// Batched: a persistent kernel pulling (subset, tile, K range) items.  The
+// item and its subset descriptor are staged in shared memory so that none of
+// their fields stays live in registers across the K loop.
+template <int MODE, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB)
     batch_kernel(const SubsetDev* __restrict__ subsets, const WorkItem* __restrict__ items, int64_t n_items,
                  int* counter, int* status) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ int64_t next_item;
+  __shared__ WorkItem s_item;
+  __shared__ SubsetDev s_sub;
   Pipe p;
   pipe_init(p, smem);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   for (;;) {
-    if (threadIdx.x == 0) next_item = atomicAdd(counter, 1);
+    if (threadIdx.x == 0) {
+      const int64_t it = atomicAdd(counter, 1);
+      next_item = it;
+      if (it < n_items) {
+        s_item = items[it];
+        s_sub = subsets[s_item.subset];
+      }
+    }
     __syncthreads();
-    const int64_t it = next_item;
-    __syncthreads();
-    if (it >= n_items) break;
-    const WorkItem w = items[it];
-    const SubsetDev sd = subsets[w.subset];
-    const uint32_t* rowblk = sd.planes + (size_t)w.I * sd.n_chunks * kChunkWords;
-    const uint32_t* colblk = sd.planes + (size_t)w.J * sd.n_chunks * kChunkWords;
+    if (next_item >= n_items) break;
+    const uint32_t* rowblk = s_sub.planes + (size_t)s_item.I * s_sub.n_chunks * kChunkWords;
+    const uint32_t* colblk = s_sub.planes + (size_t)s_item.J * s_sub.n_chunks * kChunkWords;
     Acc a;
     acc_zero(a);
-    if (!run_tile<MODE>(p, rowblk, colblk, w.c0, w.c1, tx, ty, a, status)) return;
-    if (w.split) store_partial(a, w.I, w.J, sd.n, tx, ty, sd.partial);
-    else store_final(a, w.I, w.J, sd.n, tx, ty, sd.out_counts, sd.out_dist, false);
+    if (!run_tile<MODE>(p, rowblk, colblk, s_item.c0, s_item.c1, tx, ty, a, status)) return;
+    if (s_item.split) store_partial(a, s_item.I, s_item.J, s_sub.n, tx, ty, s_sub.partial);
+    else store_final(a, s_item.I, s_item.J, s_sub.n, tx, ty, s_sub.out_counts, s_sub.out_dist, false);
+    __syncthreads();  // everyone has read s_item / s_sub before thread 0 replaces them
   }
 }
 
 // Serving: query block x panel block items.  Row r of a query block writes
 // its counts to row_out[r] ([n_panel][4] int32), so one block can carry the
 // rows of several requests.
-template <int MODE>
-__global__ void __launch_bounds__(kThreads, 2)
+template <int MODE, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB)
     cross_kernel(const uint32_t* __restrict__ panel, int64_t n_panel, int64_t n_chunks,
                  const CrossItem* __restrict__ items, int64_t n_items, int* status) {
   extern __shared__ __align__(128) uint8_t smem[];
@@ -390,7 +400,10 @@ cudaError_t set_smem(K kernel) {
 }  // namespace
 
 size_t pair_kernel_smem_bytes() { return kSmemBytes; }
-int pair_kernel_ctas_per_sm(int) { return 2; }
+
+// Kernel variants: 0 = plain (2 CTAs/SM), 1 = carry-save (2 CTAs/SM, 128
+// registers), 2 = carry-save with 1 CTA/SM (no register cap below 255).
+int pair_kernel_ctas_per_sm(int mode) { return mode == 2 ? 1 : 2; }
 
 int tri_splits_for(int64_t tiles, int64_t n_chunks, int num_sms) {
   const int64_t target = (int64_t)num_sms * 2 * 2;  // two waves of two CTAs per SM
@@ -401,22 +414,44 @@ int tri_splits_for(int64_t tiles, int64_t n_chunks, int num_sms) {
   return s < 1 ? 1 : (int)s;
 }
 
+namespace {
+template <int MODE, int MINB>
+cudaError_t tri_launch(const uint32_t* planes, const PlaneGeom& g, int splits, int32_t* out_counts, double* out_dist,
+                       int32_t* partial, bool square, int* status, int64_t grid, cudaStream_t st) {
+  cudaError_t e = set_smem(tri_kernel<MODE, MINB>);
+  if (e != cudaSuccess) return e;
+  tri_kernel<MODE, MINB><<<(unsigned)grid, kThreads, kSmemBytes, st>>>(planes, g.n, g.n_blocks, g.n_chunks, splits,
+                                                                       out_counts, out_dist, partial,
+                                                                       square ? 1 : 0, status);
+  return cudaGetLastError();
+}
+template <int MODE, int MINB>
+cudaError_t batch_launch(const SubsetDev* subsets, const WorkItem* items, int64_t n_items, int* counter, int* status,
+                         int grid, cudaStream_t st) {
+  cudaError_t e = set_smem(batch_kernel<MODE, MINB>);
+  if (e != cudaSuccess) return e;
+  batch_kernel<MODE, MINB><<<grid, kThreads, kSmemBytes, st>>>(subsets, items, n_items, counter, status);
+  return cudaGetLastError();
+}
+template <int MODE, int MINB>
+cudaError_t cross_launch(const uint32_t* panel, int64_t n_panel, int64_t n_chunks, const CrossItem* items,
+                         int64_t n_items, int* status, int64_t grid, cudaStream_t st) {
+  cudaError_t e = set_smem(cross_kernel<MODE, MINB>);
+  if (e != cudaSuccess) return e;
+  cross_kernel<MODE, MINB><<<(unsigned)grid, kThreads, kSmemBytes, st>>>(panel, n_panel, n_chunks, items, n_items,
+                                                                         status);
+  return cudaGetLastError();
+}
+}  // namespace
+
 cudaError_t launch_tri(int mode, const uint32_t* planes, const PlaneGeom& g, int splits, int32_t* out_counts,
                        double* out_dist, int32_t* partial, bool square, int* status, int, cudaStream_t st) {
   const int64_t tiles = g.n_blocks * (g.n_blocks + 1) / 2;
   const int64_t grid = tiles * splits;
   if (grid > 2147483647LL) return cudaErrorInvalidValue;
-  cudaError_t e;
-  if (mode == 1) {
-    if ((e = set_smem(tri_kernel<1>)) != cudaSuccess) return e;
-    tri_kernel<1><<<(unsigned)grid, kThreads, kSmemBytes, st>>>(planes, g.n, g.n_blocks, g.n_chunks, splits,
-                                                                 out_counts, out_dist, partial, square, status);
-  } else {
-    if ((e = set_smem(tri_kernel<0>)) != cudaSuccess) return e;
-    tri_kernel<0><<<(unsigned)grid, kThreads, kSmemBytes, st>>>(planes, g.n, g.n_blocks, g.n_chunks, splits,
-                                                                 out_counts, out_dist, partial, square, status);
-  }
-  return cudaGetLastError();
+  if (mode == 2) return tri_launch<1, 1>(planes, g, splits, out_counts, out_dist, partial, square, status, grid, st);
+  if (mode == 1) return tri_launch<1, 2>(planes, g, splits, out_counts, out_dist, partial, square, status, grid, st);
+  return tri_launch<0, 2>(planes, g, splits, out_counts, out_dist, partial, square, status, grid, st);
 }
 
 cudaError_t launch_finalize(const int32_t* partial, int64_t n, int32_t* out_counts, double* out_dist, bool square,
@@ -430,15 +465,9 @@ cudaError_t launch_finalize(const int32_t* partial, int64_t n, int32_t* out_coun
 
 cudaError_t launch_batch(int mode, const SubsetDev* subsets, const WorkItem* items, int64_t n_items, int* counter,
                          int* status, int grid, cudaStream_t st) {
-  cudaError_t e;
-  if (mode == 1) {
-    if ((e = set_smem(batch_kernel<1>)) != cudaSuccess) return e;
-    batch_kernel<1><<<grid, kThreads, kSmemBytes, st>>>(subsets, items, n_items, counter, status);
-  } else {
-    if ((e = set_smem(batch_kernel<0>)) != cudaSuccess) return e;
-    batch_kernel<0><<<grid, kThreads, kSmemBytes, st>>>(subsets, items, n_items, counter, status);
-  }
-  return cudaGetLastError();
+  if (mode == 2) return batch_launch<1, 1>(subsets, items, n_items, counter, status, grid, st);
+  if (mode == 1) return batch_launch<1, 2>(subsets, items, n_items, counter, status, grid, st);
+  return batch_launch<0, 2>(subsets, items, n_items, counter, status, grid, st);
 }
 
 cudaError_t launch_finalize_batch(const SubsetDev* subsets, const int32_t* subset_ids, int n_split_subsets,
@@ -466,19 +495,11 @@ cudaError_t launch_cross(int mode, const uint32_t* panel_planes, int64_t n_panel
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int64_t grid = (int64_t)sms * 2;
+  int64_t grid = (int64_t)sms * pair_kernel_ctas_per_sm(mode);
   if (grid > n_items) grid = n_items;
-  cudaError_t e;
-  if (mode == 1) {
-    if ((e = set_smem(cross_kernel<1>)) != cudaSuccess) return e;
-    cross_kernel<1><<<(unsigned)grid, kThreads, kSmemBytes, st>>>(panel_planes, n_panel, n_chunks, items, n_items,
-                                                                  status);
-  } else {
-    if ((e = set_smem(cross_kernel<0>)) != cudaSuccess) return e;
-    cross_kernel<0><<<(unsigned)grid, kThreads, kSmemBytes, st>>>(panel_planes, n_panel, n_chunks, items, n_items,
-                                                                  status);
-  }
-  return cudaGetLastError();
+  if (mode == 2) return cross_launch<1, 1>(panel_planes, n_panel, n_chunks, items, n_items, status, grid, st);
+  if (mode == 1) return cross_launch<1, 2>(panel_planes, n_panel, n_chunks, items, n_items, status, grid, st);
+  return cross_launch<0, 2>(panel_planes, n_panel, n_chunks, items, n_items, status, grid, st);
 }
 
 }  // namespace ibs

@@ -104,6 +104,59 @@ __global__ void __launch_bounds__(kKC * 32) planes_kernel(JobView jv) {
   planes_body(jv, blockIdx.x, blockIdx.y, sel_s);
 }
 
+// Contiguous samples with 16-byte aligned rows: each lane reads 64 bytes of
+// its .bed row (256 samples) with four 16-byte loads, so a warp moves whole
+// 32-byte sectors with few instructions, and the CTA covers 4 plane blocks of
+// one chunk.
+constexpr int kWideGroup = 256;
+
+__global__ void __launch_bounds__(kKC * 32, 2) planes_wide_kernel(JobView jv) {
+  const int kw = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t c = blockIdx.x, g = blockIdx.y;
+  const int64_t s_base = g * kWideGroup;
+  const int64_t marker = (c * kKC + kw) * 32 + lane;
+  const bool marker_ok = marker < jv.m;
+  const uint8_t* row = jv.src.packed + (jv.src.var_begin + (marker_ok ? marker : 0)) * jv.src.row_bytes;
+  const int64_t byte0 = s_base >> 2;  // first byte of this group in the row
+  uint32_t d[kWideGroup / 16];
+#pragma unroll
+  for (int v = 0; v < kWideGroup / 64; ++v) {
+    uint4 x = make_uint4(0x55555555u, 0x55555555u, 0x55555555u, 0x55555555u);  // "missing"
+    if (marker_ok && byte0 + 16 * v < jv.src.row_bytes) x = __ldg(reinterpret_cast<const uint4*>(row + byte0 + 16 * v));
+    d[4 * v + 0] = x.x;
+    d[4 * v + 1] = x.y;
+    d[4 * v + 2] = x.z;
+    d[4 * v + 3] = x.w;
+  }
+#pragma unroll
+  for (int r = 0; r < kWideGroup / 32; ++r) {
+    uint32_t myH = 0, myL = 0;
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      const int s = 32 * r + t;  // sample within the group
+      uint32_t code = (d[s >> 4] >> (2 * (s & 15))) & 3u;
+      if (s_base + s >= jv.n) code = 1u;
+      const uint32_t h = __ballot_sync(0xffffffffu, code >> 1);
+      const uint32_t l = __ballot_sync(0xffffffffu, code & 1u);
+      if (lane == t) {
+        myH = h;
+        myL = l;
+      }
+    }
+    const uint32_t V = myH | ~myL;
+    const uint32_t P = myH & ~myL;
+    const uint32_t Q = myH & myL;
+    const uint32_t R = ~myH & ~myL;
+    const int64_t s_local = 32 * r + lane;
+    const int64_t b = g * (kWideGroup / kSB) + (s_local >> 6);
+    if (b < jv.n_blocks) {
+      const int64_t off = (((b * jv.n_chunks + c) * kKC + kw) * kSB + (s_local & 63)) * kPlanes;
+      *reinterpret_cast<uint4*>(jv.planes + off) = make_uint4(V, P, Q, R);
+    }
+  }
+}
+
 // Batched: one flattened grid over all jobs; each CTA finds its job by
 // binary search on cta_begin.
 __global__ void __launch_bounds__(kKC * 32) planes_batch_kernel(const PlaneJob* __restrict__ jobs, int n_jobs,
@@ -141,10 +194,14 @@ cudaError_t launch_planes(const BedSource& src, int64_t n, int64_t m, const Plan
   jv.n_blocks = g.n_blocks;
   jv.n_chunks = g.n_chunks;
   jv.status = status;
-  const int64_t groups = (g.n_blocks + 1) / 2;
+  const bool wide = src.sel == nullptr && src.row_bytes % 16 == 0 &&
+                    reinterpret_cast<uintptr_t>(src.packed) % 16 == 0;
+  const int64_t per = wide ? kWideGroup / kSB : 2;
+  const int64_t groups = (g.n_blocks + per - 1) / per;
   if (g.n_chunks > 2147483647LL || groups > 65535) return cudaErrorInvalidValue;
   dim3 grid((unsigned)g.n_chunks, (unsigned)groups);
-  planes_kernel<<<grid, kKC * 32, 0, st>>>(jv);
+  if (wide) planes_wide_kernel<<<grid, kKC * 32, 0, st>>>(jv);
+  else planes_kernel<<<grid, kKC * 32, 0, st>>>(jv);
   return cudaGetLastError();
 }
 

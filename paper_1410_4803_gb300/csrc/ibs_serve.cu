@@ -32,7 +32,8 @@ namespace {
 constexpr int kMaxQuery = 4096;     // rows per request
 constexpr int kMaxK = 64;           // top-k limit of the kernel
 constexpr int64_t kMaxRows = 4096;  // query rows admitted at once (slot limit)
-constexpr int kCycleChunks = 8;     // panel chunks per full cycle
+constexpr int64_t kStepWaves = 4;   // a step aims at this many waves of (query block, panel block) tiles
+constexpr int64_t kMinStepDiv = 32; // ... and covers at least 1/32 of the panel
 constexpr size_t kMemMargin = (size_t)1 << 30;
 
 enum class RState { Pending, Active, Finishing, Done };
@@ -49,7 +50,7 @@ struct Request {
   DevBuf packed, planes, counts, tidx, tdist;
   size_t reserved = 0;
   PlaneGeom g;
-  int64_t chunks_done = 0;
+  int64_t blocks_done = 0;  // panel blocks processed since admission
   cudaEvent_t done_ev = nullptr;
   ibs_status status = IBS_OK;
   RState state = RState::Pending;
@@ -85,9 +86,9 @@ class ServeEngine {
   std::unordered_map<uint64_t, std::shared_ptr<Request>> all;
   std::atomic<uint64_t> next_id{1};
   ibs_serve_stats stats{};
-  int64_t cursor = 0;  // current panel chunk
-  int64_t blocks_per_chunk = 0;
-  int64_t n_cycle = 0;
+  int64_t cursor = 0;  // first panel block of the next step
+  int grid_ctas = 0;   // persistent cross-kernel CTAs (SMs x 2)
+  size_t fixed_bytes = 0;  // panel planes + step buffers
   // double-buffered item arrays
   DevBuf items_dev[2];
   CrossItem* items_host[2] = {nullptr, nullptr};
@@ -156,7 +157,7 @@ class ServeEngine {
     src.n_src = r->q;
     launch_planes(src, r->q, pg.m, r->g, static_cast<uint32_t*>(r->planes.p), ctx->status_dev, stream);
     cudaEventCreateWithFlags(&r->done_ev, cudaEventDisableTiming);
-    r->chunks_done = 0;
+    r->blocks_done = 0;
     r->state = RState::Active;
     return true;
   }
@@ -212,8 +213,6 @@ class ServeEngine {
   void run_step() {
     const int slot = (int)(step_no & 1);
     if (step_ev[slot]) cudaEventSynchronize(step_ev[slot]);  // slot's host tables are free again
-    const int64_t pb0 = cursor * blocks_per_chunk;
-    const int64_t pb1 = std::min<int64_t>(pg.n_blocks, pb0 + blocks_per_chunk);
     int64_t n_rows = 0;
     for (auto& r : active)
       for (int64_t row = 0; row < r->q; ++row) {
@@ -223,12 +222,20 @@ class ServeEngine {
         ++n_rows;
       }
     const int64_t qblocks = (n_rows + kSB - 1) / kSB;
-    const size_t n_items = (size_t)qblocks * (size_t)std::max<int64_t>(0, pb1 - pb0);
+    // Step length: about kStepWaves waves of tiles, at least 1/kMinStepDiv of
+    // the panel, at most the whole panel.  Few rows in flight -> long steps
+    // (one launch covers the panel); many rows -> short steps that new
+    // requests can join quickly.
+    int64_t len = (kStepWaves * grid_ctas + qblocks - 1) / std::max<int64_t>(1, qblocks);
+    len = std::max<int64_t>(len, (pg.n_blocks + kMinStepDiv - 1) / kMinStepDiv);
+    len = std::min<int64_t>(len, pg.n_blocks);
+    const size_t n_items = (size_t)qblocks * (size_t)len;
     ensure_items(std::max<size_t>(n_items, 1));
     CrossItem* h = items_host[slot];
     size_t t = 0;
     int32_t** outs_d = static_cast<int32_t**>(outs_dev[slot].p);
-    for (int64_t pb = pb0; pb < pb1; ++pb)
+    for (int64_t k = 0; k < len; ++k) {
+      const int64_t pb = (cursor + k) % pg.n_blocks;  // wraps around the panel
       for (int64_t b = 0; b < qblocks; ++b) {
         CrossItem& it = h[t++];
         it.qplanes = static_cast<const uint32_t*>(step_planes.p) + (size_t)b * pg.n_chunks * kChunkWords;
@@ -236,6 +243,7 @@ class ServeEngine {
         it.q_rows = (int32_t)std::min<int64_t>(kSB, n_rows - b * kSB);
         it.pb = (int32_t)pb;
       }
+    }
     if (t > 0) {
       cudaMemcpyAsync(rows_dev[slot].p, rows_host[slot], n_rows * sizeof(RowSrc), cudaMemcpyHostToDevice, stream);
       cudaMemcpyAsync(outs_dev[slot].p, outs_host[slot], n_rows * sizeof(int32_t*), cudaMemcpyHostToDevice, stream);
@@ -245,10 +253,14 @@ class ServeEngine {
       launch_cross(pick_mode(ctx), static_cast<const uint32_t*>(panel_planes.p), pg.n, pg.n_blocks, pg.n_chunks,
                    static_cast<const CrossItem*>(items_dev[slot].p), (int64_t)t, ctx->status_dev, stream);
     }
-    cursor = (cursor + 1) % n_cycle;
+    cursor = (cursor + len) % pg.n_blocks;
     std::vector<std::shared_ptr<Request>> still;
     for (auto& r : active) {
-      if (++r->chunks_done >= n_cycle) {
+      // A request joined at some cursor position and is done once it has seen
+      // every panel block (blocks seen twice near the end are rewritten with
+      // the same counts).
+      r->blocks_done += len;
+      if (r->blocks_done >= pg.n_blocks) {
         finish(*r);
         finishing.push_back(r);
       } else {
@@ -415,9 +427,9 @@ ibs_status serve_panel_load(ibs_ctx* ctx, const uint8_t* panel, int64_t n_panel,
     eng->shutdown();
     return st;
   }
-  eng->n_cycle = std::min<int64_t>(kCycleChunks, eng->pg.n_blocks);
-  eng->blocks_per_chunk = (eng->pg.n_blocks + eng->n_cycle - 1) / eng->n_cycle;
-  eng->n_cycle = (eng->pg.n_blocks + eng->blocks_per_chunk - 1) / eng->blocks_per_chunk;
+  eng->grid_ctas = ctx->num_sms * pair_kernel_ctas_per_sm(pick_mode(ctx));
+  eng->fixed_bytes = eng->panel_planes.cap + eng->step_planes.cap +
+                     2 * (eng->rows_dev[0].cap + eng->outs_dev[0].cap);
   eng->start();
   std::lock_guard<std::mutex> lk(ctx->mu);
   ctx->serve = std::move(eng);
@@ -467,11 +479,14 @@ ibs_status serve_query(ibs_ctx* ctx, const uint8_t* q, int64_t nq, int k, int32_
   const size_t need = e.mem_need(nq, k, counts_dev, topk_dev);
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
+  // The engine's own buffers (panel planes, step tables) are always held, so a
+  // request is refused at once when it could not fit even beside them alone.
   const size_t cap = ctx->ws_limit ? ctx->ws_limit : total_b;
-  if (need + (ctx->ws_limit ? 0 : kMemMargin) > cap) {
+  const size_t avail = cap > e.fixed_bytes ? cap - e.fixed_bytes : 0;
+  if (need + (ctx->ws_limit ? 0 : kMemMargin) > avail) {
     std::lock_guard<std::mutex> lk(e.mu);
     e.stats.rejected++;
-    return fail(IBS_EBUSY, "request needs %zu bytes, more than the serving budget %zu", need, cap);
+    return fail(IBS_EBUSY, "request needs %zu bytes, more than the %zu bytes the serving budget leaves", need, avail);
   }
   auto r = std::make_shared<Request>();
   r->q = nq;
