@@ -32,7 +32,7 @@ namespace {
 constexpr int kMaxQuery = 4096;     // rows per request
 constexpr int kMaxK = 64;           // top-k limit of the kernel
 constexpr int64_t kMaxRows = 4096;  // query rows admitted at once (slot limit)
-constexpr int64_t kStepWaves = 4;   // a step aims at this many waves of (query block, panel block) tiles
+constexpr int64_t kStepWaves = 16;  // a step aims at this many waves of (query block, panel block) tiles
 constexpr int64_t kMinStepDiv = 32; // ... and covers at least 1/32 of the panel
 constexpr size_t kMemMargin = (size_t)1 << 30;
 
@@ -223,9 +223,10 @@ class ServeEngine {
       }
     const int64_t qblocks = (n_rows + kSB - 1) / kSB;
     // Step length: about kStepWaves waves of tiles, at least 1/kMinStepDiv of
-    // the panel, at most the whole panel.  Few rows in flight -> long steps
-    // (one launch covers the panel); many rows -> short steps that new
-    // requests can join quickly.
+    // the panel, at most the whole panel.  Few rows in flight -> one step
+    // covers the whole panel (a lone request costs one launch, as on the
+    // unbatched path); many rows -> shorter steps that new requests can join
+    // between.
     int64_t len = (kStepWaves * grid_ctas + qblocks - 1) / std::max<int64_t>(1, qblocks);
     len = std::max<int64_t>(len, (pg.n_blocks + kMinStepDiv - 1) / kMinStepDiv);
     len = std::min<int64_t>(len, pg.n_blocks);
