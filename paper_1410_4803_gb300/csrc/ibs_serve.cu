@@ -2,17 +2,22 @@
 // query requests.
 //
 // The panel's bit planes stay on the device.  A host thread owns a CUDA stream
-// and runs steps; one step processes one panel chunk (a range of 64-sample
-// panel blocks) for EVERY admitted request, so each panel byte is streamed
-// from HBM once per step however many requests are in flight, and the items
-// of a step are ordered panel-block-major so the CTAs sharing a panel block
-// run together and hit it in L2.  A request admitted while others are running
-// joins at the next step, starts at the current panel chunk and finishes after
-// one full cycle over the chunks; then its top-k kernel runs and its outputs
-// are copied back.  Admission is FIFO, bounded by a row-slot limit and by free
-// device memory (or the context's workspace limit).  At most two steps are in
-// flight, so admission and completion are checked between steps while the
-// GPU stays busy.
+// and runs steps.  A step packs the query rows of EVERY admitted request
+// densely into 64-row query blocks (a gather kernel copies each row's planes,
+// and every row keeps its own output pointer) and runs them against a range
+// of 64-sample panel blocks.  Each panel block is therefore read once per step
+// however many requests are in flight, and the items of a step are ordered
+// panel-block-major so the CTAs sharing a panel block run together and hit it
+// in L2.  The step length adapts to the load: with few rows in flight one step
+// covers the whole panel, with many it covers about 16 waves of tiles so that
+// new requests can join between steps.  A request joins at the current panel
+// position and is done once it has seen every panel block; then its top-k
+// kernel runs and its outputs are copied back.  Admission is FIFO, bounded by
+// a row-slot limit and by a memory budget (free device memory at panel load,
+// and the context's workspace limit).  Request buffers come from the
+// stream-ordered memory pool, so freeing them never synchronises the device.
+// At most two steps are in flight, so admission and completion are handled
+// between steps while the GPU stays busy.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -96,6 +101,9 @@ class ServeEngine {
   cudaEvent_t step_ev[2] = {nullptr, nullptr};
   int64_t step_no = 0;
   DevBuf step_planes, rows_dev[2], outs_dev[2];
+  std::mutex budget_mu;
+  size_t pool_budget = 0;  // bytes the requests may hold together
+  size_t pool_bytes = 0;   // bytes they hold now
   RowSrc* rows_host[2] = {nullptr, nullptr};
   int32_t** outs_host[2] = {nullptr, nullptr};
 
@@ -109,21 +117,29 @@ class ServeEngine {
     return b + 4096;
   }
 
-  void release(Request& r) {
+  // Per-request buffers come from the device's stream-ordered memory pool
+  // (cudaMallocAsync / cudaFreeAsync on the stream that uses them): no
+  // device-wide synchronisation when a request's memory is returned, so the
+  // step pipeline never stalls on a free.
+  void release(Request& r, cudaStream_t s) {
     for (DevBuf* b : {&r.packed, &r.planes, &r.counts, &r.tidx, &r.tdist}) {
-      if (b->p) cudaFree(b->p);
+      if (b->p) cudaFreeAsync(b->p, s);
       b->p = nullptr;
       b->cap = 0;
     }
-    if (r.reserved) release_bytes(ctx, r.reserved);
+    if (r.reserved) {
+      release_bytes(ctx, r.reserved);
+      std::lock_guard<std::mutex> lk(budget_mu);
+      pool_bytes -= r.reserved;
+    }
     r.reserved = 0;
     if (r.done_ev) cudaEventDestroy(r.done_ev);
     r.done_ev = nullptr;
   }
 
-  ibs_status alloc(DevBuf& b, size_t bytes) {
+  ibs_status alloc(DevBuf& b, size_t bytes, cudaStream_t s) {
     if (bytes == 0) return IBS_OK;
-    cudaError_t e = cudaMalloc(&b.p, bytes);
+    cudaError_t e = cudaMallocAsync(&b.p, bytes, s);
     if (e != cudaSuccess) {
       cudaGetLastError();
       b.p = nullptr;
@@ -133,21 +149,35 @@ class ServeEngine {
     return IBS_OK;
   }
 
+  // Reserve a request's bytes against the serving budget (free device memory
+  // at panel load minus a margin, and the context's workspace limit).
+  bool reserve_request(Request& r, size_t need) {
+    {
+      std::lock_guard<std::mutex> lk(budget_mu);
+      if (pool_bytes + need > pool_budget) return false;
+      pool_bytes += need;
+    }
+    if (!reserve_bytes(ctx, need)) {
+      std::lock_guard<std::mutex> lk(budget_mu);
+      pool_bytes -= need;
+      return false;
+    }
+    r.reserved = need;
+    return true;
+  }
+
   // Try to admit r (engine thread).  Returns false if it must wait.
   bool admit(const std::shared_ptr<Request>& r, int64_t active_rows) {
     if (active_rows + r->q > kMaxRows && active_rows > 0) return false;
     const size_t need = mem_need(r->q, r->k, r->counts_on_dev, r->topk_on_dev);
-    size_t free_b = 0, total_b = 0;
-    cudaMemGetInfo(&free_b, &total_b);
-    if (need + kMemMargin > free_b) return false;
-    if (!reserve_bytes(ctx, need)) return false;
-    r->reserved = need;
+    if (!reserve_request(*r, need)) return false;
     r->g = PlaneGeom::make(r->q, pg.m);
     const size_t pk = (size_t)pg.m * (size_t)((r->q + 3) / 4);
-    if (alloc(r->packed, pk) || alloc(r->planes, r->g.bytes()) ||
-        (!r->counts_on_dev && alloc(r->counts, (size_t)r->q * pg.n * 16)) ||
-        (!r->topk_on_dev && r->k > 0 && (alloc(r->tidx, (size_t)r->q * r->k * 4) || alloc(r->tdist, (size_t)r->q * r->k * 8)))) {
-      release(*r);
+    if (alloc(r->packed, pk, stream) || alloc(r->planes, r->g.bytes(), stream) ||
+        (!r->counts_on_dev && alloc(r->counts, (size_t)r->q * pg.n * 16, stream)) ||
+        (!r->topk_on_dev && r->k > 0 &&
+         (alloc(r->tidx, (size_t)r->q * r->k * 4, stream) || alloc(r->tdist, (size_t)r->q * r->k * 8, stream)))) {
+      release(*r, stream);
       return false;
     }
     cudaMemcpyAsync(r->packed.p, r->host_packed.data(), pk, cudaMemcpyHostToDevice, stream);
@@ -284,7 +314,7 @@ class ServeEngine {
         const int st = __atomic_load_n(ctx->status_host, __ATOMIC_SEQ_CST);
         std::lock_guard<std::mutex> lk(mu);
         r->status = st == kDevTimeout ? IBS_ETIMEOUT : IBS_OK;
-        release(*r);
+        release(*r, stream);
         r->state = RState::Done;
         stats.requests_done++;
         any = true;
@@ -345,7 +375,7 @@ class ServeEngine {
         r.status = IBS_ECANCELLED;
         r.state = RState::Done;
       }
-      release(r);
+      release(r, stream);
     }
     pending.clear();
     active.clear();
@@ -429,6 +459,18 @@ ibs_status serve_panel_load(ibs_ctx* ctx, const uint8_t* panel, int64_t n_panel,
     return st;
   }
   eng->grid_ctas = ctx->num_sms * pair_kernel_ctas_per_sm(pick_mode(ctx));
+  // Requests draw on the device's default stream-ordered pool; keep freed
+  // blocks cached in it so steady-state serving does not go back to the driver.
+  cudaMemPool_t mp;
+  if (cudaDeviceGetDefaultMemPool(&mp, ctx->device) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  {
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    eng->pool_budget = free_b > kMemMargin ? free_b - kMemMargin : 0;
+  }
   eng->fixed_bytes = eng->panel_planes.cap + eng->step_planes.cap +
                      2 * (eng->rows_dev[0].cap + eng->outs_dev[0].cap);
   eng->start();
@@ -478,13 +520,11 @@ ibs_status serve_query(ibs_ctx* ctx, const uint8_t* q, int64_t nq, int k, int32_
   if (ibs_status s = validate_query(eng, q, nq, k, oc, oi, od, counts_dev, topk_dev)) return s;
   ServeEngine& e = *eng;
   const size_t need = e.mem_need(nq, k, counts_dev, topk_dev);
-  size_t free_b = 0, total_b = 0;
-  cudaMemGetInfo(&free_b, &total_b);
   // The engine's own buffers (panel planes, step tables) are always held, so a
   // request is refused at once when it could not fit even beside them alone.
-  const size_t cap = ctx->ws_limit ? ctx->ws_limit : total_b;
-  const size_t avail = cap > e.fixed_bytes ? cap - e.fixed_bytes : 0;
-  if (need + (ctx->ws_limit ? 0 : kMemMargin) > avail) {
+  size_t avail = e.pool_budget;
+  if (ctx->ws_limit) avail = std::min(avail, ctx->ws_limit > e.fixed_bytes ? ctx->ws_limit - e.fixed_bytes : 0);
+  if (need > avail) {
     std::lock_guard<std::mutex> lk(e.mu);
     e.stats.rejected++;
     return fail(IBS_EBUSY, "request needs %zu bytes, more than the %zu bytes the serving budget leaves", need, avail);
@@ -564,15 +604,15 @@ ibs_status serve_query_sync(ibs_ctx* ctx, const uint8_t* q, int64_t nq, int k, i
   cudaStream_t s;
   IBS_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
   const size_t need = e.mem_need(nq, k, counts_dev, topk_dev);
-  if (!reserve_bytes(ctx, need)) {
+  if (!e.reserve_request(r, need)) {
     cudaStreamDestroy(s);
-    return fail(IBS_ENOMEM, "workspace limit exceeded");
+    return fail(IBS_ENOMEM, "the serving memory budget is exhausted");
   }
-  r.reserved = need;
-  if (e.alloc(r.packed, pk) || e.alloc(r.planes, qg.bytes()) ||
-      (!counts_dev && e.alloc(r.counts, (size_t)nq * pg.n * 16)) ||
-      (!topk_dev && k > 0 && (e.alloc(r.tidx, (size_t)nq * k * 4) || e.alloc(r.tdist, (size_t)nq * k * 8)))) {
-    e.release(r);
+  if (e.alloc(r.packed, pk, s) || e.alloc(r.planes, qg.bytes(), s) ||
+      (!counts_dev && e.alloc(r.counts, (size_t)nq * pg.n * 16, s)) ||
+      (!topk_dev && k > 0 && (e.alloc(r.tidx, (size_t)nq * k * 4, s) || e.alloc(r.tdist, (size_t)nq * k * 8, s)))) {
+    e.release(r, s);
+    cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
     return fail(IBS_ENOMEM, "device allocation failed");
   }
@@ -580,7 +620,7 @@ ibs_status serve_query_sync(ibs_ctx* ctx, const uint8_t* q, int64_t nq, int k, i
   std::vector<int32_t*> outs((size_t)nq);
   for (int64_t row = 0; row < nq; ++row) outs[row] = cnt + (size_t)row * pg.n * 4;
   DevBuf outs_d;
-  cudaError_t ce = cudaMalloc(&outs_d.p, outs.size() * sizeof(int32_t*));
+  cudaError_t ce = cudaMallocAsync(&outs_d.p, outs.size() * sizeof(int32_t*), s);
   std::vector<CrossItem> items;
   for (int64_t pb = 0; pb < pg.n_blocks; ++pb)
     for (int64_t qb = 0; qb < qg.n_blocks; ++qb) {
@@ -592,7 +632,7 @@ ibs_status serve_query_sync(ibs_ctx* ctx, const uint8_t* q, int64_t nq, int k, i
       items.push_back(it);
     }
   DevBuf items_dev;
-  if (ce == cudaSuccess) ce = cudaMalloc(&items_dev.p, items.size() * sizeof(CrossItem));
+  if (ce == cudaSuccess) ce = cudaMallocAsync(&items_dev.p, items.size() * sizeof(CrossItem), s);
   if (ce == cudaSuccess)
     ce = cudaMemcpyAsync(outs_d.p, outs.data(), outs.size() * sizeof(int32_t*), cudaMemcpyHostToDevice, s);
   if (ce == cudaSuccess) {
@@ -618,11 +658,11 @@ ibs_status serve_query_sync(ibs_ctx* ctx, const uint8_t* q, int64_t nq, int k, i
     ce = cudaMemcpyAsync(oi, r.tidx.p, (size_t)nq * k * 4, cudaMemcpyDeviceToHost, s);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(od, r.tdist.p, (size_t)nq * k * 8, cudaMemcpyDeviceToHost, s);
   }
+  if (items_dev.p) cudaFreeAsync(items_dev.p, s);
+  if (outs_d.p) cudaFreeAsync(outs_d.p, s);
+  e.release(r, s);
   cudaError_t se = cudaStreamSynchronize(s);
   if (ce == cudaSuccess) ce = se;
-  if (items_dev.p) cudaFree(items_dev.p);
-  if (outs_d.p) cudaFree(outs_d.p);
-  e.release(r);
   cudaStreamDestroy(s);
   if (ce != cudaSuccess) st = fail(IBS_ECUDA, "query_sync failed: %s", cudaGetErrorString(ce));
   else if (__atomic_load_n(ctx->status_host, __ATOMIC_SEQ_CST) == kDevTimeout)
