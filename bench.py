@@ -125,6 +125,13 @@ def int_pipe_roofline(probe: dict, sm_mhz: float | None) -> dict:
             "peak": comps_clk_sm * probe["sms"] * mhz * 1e6}
 
 
+def measured_peak(key: str, fallback: float) -> float:
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))[key])
+    except Exception:
+        return fallback
+
+
 def hbm_peak_gbs() -> float:
     """Measured copy bandwidth of the GB300s; 6.8 TB/s fallback when absent."""
     try:
@@ -230,7 +237,8 @@ def run_plain(args, rank, world, local):
     counts = torch.empty((P, 4), dtype=torch.int32, device=dev)
     dist_t = torch.empty(P, dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
-    ctx = ibs.ibs_init(local, flags=ibs.IBS_TIMING)
+    use_tc = os.environ.get("IBS_USE_TC", "0") == "1"
+    ctx = ibs.ibs_init(local, flags=ibs.IBS_TIMING | (ibs.IBS_KERNEL_TC if use_tc else 0))
     probe = ibs.ibs_probe_int_pipes(ctx)
 
     with torch.cuda.stream(stream):
@@ -294,11 +302,19 @@ def run_plain(args, rank, world, local):
     planes_ms = kt["planes_ms"] / max(1, kt["calls"])
     roof = int_pipe_roofline(probe, clocks.get("sm_mhz"))
     achieved = comps / (pairs_ms * 1e-3)
+    if use_tc:
+        # FP8 tensor peak: the measured bf16 burst rate x the nominal FP8/bf16 ratio (2);
+        # 4 MACs = 8 flops per comparison.
+        fp8_tflops = 2.0 * measured_peak("bf16_tflops", 1900.0)
     mode = {"0": "plain", "1": "csa3", "2": "csa3-1cta"}.get(os.environ.get("IBS_PAIR_MODE", "1"), "csa3")
+    if use_tc:
+        mode = "tc-fp8"
     # transpose: read the 2-bit input once, write 16 bytes per (padded) sample-word of planes
     words = (m + 31) // 32
     n_blocks, n_chunks = (n + 63) // 64, (words + 11) // 12
     transpose_bytes = m * ((n + 3) // 4) + n_blocks * n_chunks * 12 * 64 * 16
+    if use_tc:  # FP8 planes: 4 bytes per padded genotype
+        transpose_bytes = m * ((n + 3) // 4) + ((n + 127) // 128) * 128 * ((m + 31) // 32) * 32 * 4
     ibs.ibs_shutdown(ctx)
 
     if rank != 0:
@@ -322,14 +338,21 @@ def run_plain(args, rank, world, local):
                    "comparisons_per_step": comps,
                    "l2": "flushed between steps (256 MiB write, outside the step events)",
                    "parallelism": f"replicas x{world}", "kernel_mode": mode},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": roof["peak"], "unit": UNIT,
-                     "frac": achieved / roof["peak"],
-                     "traffic": profiled_traffic(f"pair_kernel_{args.workload}.md"),
-                     "kernel": "tri_kernel (pair counts)", "kernel_ms": pairs_ms,
-                     "peak_basis": f"{roof['comps_per_clk_sm']:.1f} comparisons/clk/SM x {probe['sms']} SMs x "
-                                   f"{roof['sm_mhz']:.0f} MHz (median SM clock in the timed region); pipe rates "
-                                   f"measured live: POPC {probe['popc_per_clk_sm']:.2f}, LOP3 "
-                                   f"{probe['lop3_per_clk_sm']:.2f}, IADD3 {probe['iadd3_per_clk_sm']:.2f} /clk/SM"},
+        "roofline": ({"bound": "alu", "achieved": achieved, "peak": roof["peak"], "unit": UNIT,
+                      "frac": achieved / roof["peak"],
+                      "traffic": profiled_traffic(f"pair_kernel_{args.workload}.md"),
+                      "kernel": "tri_kernel (pair counts)", "kernel_ms": pairs_ms,
+                      "peak_basis": f"{roof['comps_per_clk_sm']:.1f} comparisons/clk/SM x {probe['sms']} SMs x "
+                                    f"{roof['sm_mhz']:.0f} MHz (median SM clock in the timed region); pipe rates "
+                                    f"measured live: POPC {probe['popc_per_clk_sm']:.2f}, LOP3 "
+                                    f"{probe['lop3_per_clk_sm']:.2f}, IADD3 {probe['iadd3_per_clk_sm']:.2f} /clk/SM"}
+                     if not use_tc else
+                     {"bound": "tensor", "achieved": 8.0 * achieved / 1e12, "peak": fp8_tflops, "unit": "TFLOP/s",
+                      "frac": 8.0 * achieved / 1e12 / fp8_tflops,
+                      "traffic": profiled_traffic(f"tc_kernel_{args.workload}.md"),
+                      "kernel": "tc_tri_kernel (tcgen05 FP8 indicator GEMMs)", "kernel_ms": pairs_ms,
+                      "peak_basis": "measured bf16 burst TFLOP/s (MEASURED_PEAKS.json) x 2, the nominal FP8/bf16 ratio; "
+                                    "algorithmic flops = 8 per comparison (4 MACs: VV^T, UU^T, QR^T, RQ^T)"}),
         "transpose": {"kernel_ms": planes_ms, "bytes": transpose_bytes,
                       "achieved_gbs": transpose_bytes / (planes_ms * 1e-3) / 1e9,
                       "peak_gbs": hbm_peak_gbs(), "frac": transpose_bytes / (planes_ms * 1e-3) / 1e9 / hbm_peak_gbs()},

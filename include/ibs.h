@@ -63,6 +63,7 @@ typedef enum {
 #define IBS_KERNEL_PLAIN 0x10 /* pair loop variant: one POPC per count and 32-marker word */
 #define IBS_KERNEL_CSA 0x20   /* pair loop variant: carry-save reduction of 3 words before POPC */
 #define IBS_TIMING 0x40       /* record CUDA events around each kernel of ibs_compute (ibs_kernel_times) */
+#define IBS_KERNEL_TC 0x80    /* ibs_compute: tensor-core pair counts (tcgen05 FP8 indicator GEMMs, exact) */
 
 typedef struct {
   int device;                      /* CUDA device ordinal */

@@ -99,6 +99,10 @@ ibs_status check_ctx(ibs_ctx* ctx) {
   return IBS_OK;
 }
 
+constexpr int kFlagTc = 0x80;  // tensor-core (tcgen05 FP8 indicator GEMM) pair counts
+
+bool use_tc(const ibs_ctx* ctx) { return (ctx->flags & kFlagTc) != 0; }
+
 int mode_for(const ibs_ctx* ctx) {
   if (ctx->flags & kFlagPlain) return 0;
   if (ctx->flags & kFlagCsa) return 1;
@@ -183,10 +187,12 @@ ibs_status ibs_compute(ibs_ctx* ctx, const uint8_t* packed, int64_t n, int64_t m
   if (ctx->flags & IBS_NO_DIST) out_dist = nullptr;
   const bool square = (ctx->flags & IBS_OUT_SQUARE) != 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const bool tc = use_tc(ctx);
   const PlaneGeom geo = PlaneGeom::make(n, m);
-  if (ibs_status s = ensure_buf(ctx, ctx->planes, geo.bytes())) return s;
-  const int64_t tiles = geo.n_blocks * (geo.n_blocks + 1) / 2;
-  const int splits = tri_splits_for(tiles, geo.n_chunks, ctx->num_sms);
+  if (ibs_status s = ensure_buf(ctx, ctx->planes, tc ? tc_planes_bytes(n, m) : geo.bytes())) return s;
+  const int64_t tiles = tc ? tc_tiles(n) : geo.n_blocks * (geo.n_blocks + 1) / 2;
+  const int splits = tc ? tc_splits_for(tiles, tc_chunks(m), ctx->num_sms)
+                        : tri_splits_for(tiles, geo.n_chunks, ctx->num_sms);
   const int64_t P = n * (n + 1) / 2;
   if (splits > 1) {
     if (ibs_status s = ensure_buf(ctx, ctx->partial, (size_t)P * 16)) return s;
@@ -208,10 +214,18 @@ ibs_status ibs_compute(ibs_ctx* ctx, const uint8_t* packed, int64_t n, int64_t m
     rec.n = splits > 1 ? 4 : 3;
     IBS_CUDA_TRY(cudaEventRecord(rec.ev[0], st));
   }
-  IBS_CUDA_TRY(launch_planes(src, n, m, geo, static_cast<uint32_t*>(ctx->planes.p), ctx->status_dev, st));
-  if (timing) IBS_CUDA_TRY(cudaEventRecord(rec.ev[1], st));
-  IBS_CUDA_TRY(launch_tri(mode_for(ctx), static_cast<const uint32_t*>(ctx->planes.p), geo, splits, out_counts,
-                          out_dist, static_cast<int32_t*>(ctx->partial.p), square, ctx->status_dev, ctx->num_sms, st));
+  if (tc) {
+    IBS_CUDA_TRY(launch_tc_planes(packed, n, m, static_cast<uint8_t*>(ctx->planes.p), st));
+    if (timing) IBS_CUDA_TRY(cudaEventRecord(rec.ev[1], st));
+    IBS_CUDA_TRY(launch_tc_pairs(static_cast<const uint8_t*>(ctx->planes.p), n, m, splits, out_counts, out_dist,
+                                 static_cast<int32_t*>(ctx->partial.p), square, ctx->status_dev, st));
+  } else {
+    IBS_CUDA_TRY(launch_planes(src, n, m, geo, static_cast<uint32_t*>(ctx->planes.p), ctx->status_dev, st));
+    if (timing) IBS_CUDA_TRY(cudaEventRecord(rec.ev[1], st));
+    IBS_CUDA_TRY(launch_tri(mode_for(ctx), static_cast<const uint32_t*>(ctx->planes.p), geo, splits, out_counts,
+                            out_dist, static_cast<int32_t*>(ctx->partial.p), square, ctx->status_dev, ctx->num_sms,
+                            st));
+  }
   if (timing) IBS_CUDA_TRY(cudaEventRecord(rec.ev[2], st));
   if (splits > 1)
     IBS_CUDA_TRY(launch_finalize(static_cast<const int32_t*>(ctx->partial.p), n, out_counts, out_dist, square, st));

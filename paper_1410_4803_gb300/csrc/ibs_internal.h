@@ -109,6 +109,15 @@ cudaError_t launch_gather_rows(const RowSrc* rows, int64_t n_rows, int64_t n_chu
 cudaError_t launch_topk(const int32_t* counts, int64_t q, int64_t n_panel, int k, int32_t* out_idx,
                         double* out_dist, cudaStream_t st);
 int pair_kernel_ctas_per_sm(int mode);
+
+// Tensor-core form (ibs_tc.cu): FP8 indicator planes and tcgen05 pair tiles.
+size_t tc_planes_bytes(int64_t n, int64_t m);
+int tc_splits_for(int64_t tiles, int64_t n_chunks, int num_sms);
+int64_t tc_tiles(int64_t n);
+int64_t tc_chunks(int64_t m);
+cudaError_t launch_tc_planes(const uint8_t* packed, int64_t n, int64_t m, uint8_t* planes, cudaStream_t st);
+cudaError_t launch_tc_pairs(const uint8_t* planes, int64_t n, int64_t m, int splits, int32_t* out_counts,
+                            double* out_dist, int32_t* partial, bool square, int* status, cudaStream_t st);
 size_t pair_kernel_smem_bytes();
 
 // Integer-pipe microbenchmark (ibs_probe.cu).

@@ -1,0 +1,318 @@
+// Tensor-core form of the pair counts (tcgen05, FP8 indicator GEMMs).
+//
+// The per-marker rule of the paper ("Improvements in PLINK 1.9 / Bitwise
+// parallelism") is bilinear in one-hot indicators of the genotype codes, so the
+// counts of all pairs are matrix products over the marker axis.  With, per
+// sample and marker,
+//   V = 1 if the call is present          U = +1 homozygous, -1 heterozygous
+//   Q = 1 if homozygous A2                R = 1 if homozygous A1
+// (all 0 for a missing call):
+//   N     = V V^T                  (both present)
+//   UU^T  = IBS2 + IBS0 - IBS1     (hom-hom and het-het pairs +1, hom-het -1)
+//   IBS0  = Q R^T + R Q^T          (opposite homozygotes)
+// so IBS1 = (N - UU^T) / 2 and IBS2 = N - IBS0 - IBS1.  The values -1, 0, +1
+// are exact in FP8 (E4M3), every product is exact, and every partial sum is an
+// integer of magnitude at most the marker count, far below 2^24, so FP32
+// accumulation is exact.  Four 128 x 128 x 32 MMAs per 32 markers.
+//
+// Layout: one (128-sample block, 32-marker chunk) is 4 planes x 4 KiB, each
+// plane a 128 x 32 byte tile in the tensor core's canonical K-major layout
+// without swizzle: 8-row x 16-byte core matrices, the two core matrices of a
+// row group 128 bytes apart (leading byte offset) and row groups 256 bytes
+// apart (stride byte offset).  A CTA computes one 128 x 128 tile of pairs:
+// thread 0 streams chunks of the row and column blocks through a 4-stage
+// shared-memory ring with TMA bulk copies, thread 32 issues the MMAs into three
+// FP32 accumulators in tensor memory (columns 0, 128, 256) and frees each
+// stage with tcgen05.commit, and after the last chunk all four warps read the
+// accumulators back (tcgen05.ld), decode the counts and store them.
+//
+// Every wait is bounded (2 s of %globaltimer); on expiry the status word is
+// set, and the CTA still waits (bounded) for its MMAs and frees its tensor
+// memory before returning.
+#include "ibs_device.cuh"
+#include "ibs_internal.h"
+
+namespace ibs {
+
+namespace {
+
+constexpr int kTB = 128;                          // samples per block (tile edge)
+constexpr int kTK = 32;                           // markers per chunk (one MMA K step)
+constexpr int kTPlanes = 4;                       // V, U, Q, R
+constexpr int kTileBytes = kTB * kTK;             // one plane of one chunk: 4 KiB
+constexpr int kTChunkBytes = kTPlanes * kTileBytes;  // 16 KiB per (block, chunk)
+constexpr int kTStages = 4;
+constexpr int kTThreads = 128;
+constexpr size_t kTSmem = (size_t)kTStages * 2 * kTChunkBytes + 1024;
+constexpr uint32_t kTmemCols = 512;               // 3 x 128 used
+constexpr uint8_t kFp8One = 0x38, kFp8MinusOne = 0xB8;
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)(128 >> 4) << 16;   // leading byte offset: next core matrix along K
+  d |= (uint64_t)(256 >> 4) << 32;   // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;            // descriptor version
+  return d;                          // no swizzle
+}
+
+// E4M3 x E4M3 -> F32, K-major A and B, N = 128, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(128 >> 3) << 17) |
+                            ((uint32_t)(128 >> 4) << 24);
+
+__device__ __forceinline__ void umma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+
+// Byte offset of (sample row r, marker k) inside one 128 x 32 canonical tile.
+__device__ __forceinline__ int tile_off(int r, int k) {
+  return (r >> 3) * 256 + (k >> 4) * 128 + (r & 7) * 16 + (k & 15);
+}
+
+// ---------------------------------------------------------------------------
+// Transpose: packed .bed rows -> FP8 planes.  CTA = (chunk c, block b), one
+// thread per sample; each thread reads its 2-bit code at the chunk's 32
+// markers and writes 2 x 16 bytes per plane.
+__global__ void __launch_bounds__(kTB) tc_planes_kernel(const uint8_t* __restrict__ packed, int64_t row_bytes,
+                                                        int64_t n, int64_t m, uint8_t* __restrict__ planes,
+                                                        int64_t n_chunks) {
+  const int64_t c = blockIdx.x, b = blockIdx.y;
+  const int r = threadIdx.x;
+  const int64_t s = b * kTB + r;
+  uint32_t w[kTPlanes][8];  // 32 bytes per plane, little-endian words
+#pragma unroll
+  for (int p = 0; p < kTPlanes; ++p)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) w[p][q] = 0;
+  if (s < n) {
+    const uint8_t* col = packed + (s >> 2);
+    const int sh = 2 * (int)(s & 3);
+#pragma unroll
+    for (int k = 0; k < kTK; ++k) {
+      const int64_t marker = c * kTK + k;
+      const uint32_t code = marker < m ? (__ldg(col + marker * row_bytes) >> sh) & 3u : 1u;  // past the end: missing
+      const uint32_t shift = 8 * (k & 3);
+      const int q = k >> 2;
+      if (code != 1u) w[0][q] |= (uint32_t)kFp8One << shift;                               // V
+      if (code != 1u) w[1][q] |= (uint32_t)(code == 2u ? kFp8MinusOne : kFp8One) << shift;  // U
+      if (code == 3u) w[2][q] |= (uint32_t)kFp8One << shift;                               // Q
+      if (code == 0u) w[3][q] |= (uint32_t)kFp8One << shift;                               // R
+    }
+  }
+  uint8_t* base = planes + (size_t)(b * n_chunks + c) * kTChunkBytes;
+#pragma unroll
+  for (int p = 0; p < kTPlanes; ++p)
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      uint4 v = make_uint4(w[p][4 * half + 0], w[p][4 * half + 1], w[p][4 * half + 2], w[p][4 * half + 3]);
+      *reinterpret_cast<uint4*>(base + p * kTileBytes + tile_off(r, 16 * half)) = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pair tile kernel.
+__global__ void __launch_bounds__(kTThreads, 1)
+    tc_tri_kernel(const uint8_t* __restrict__ planes, int64_t n, int64_t n_blocks, int64_t n_chunks, int splits,
+                  int32_t* __restrict__ out_counts, double* __restrict__ out_dist, int32_t* __restrict__ partial,
+                  int square, int* status) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  // 1024-byte aligned ring (the dynamic base is only guaranteed 16-byte aligned)
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* ring = smem;                                            // kTStages x [A 16 KiB | B 16 KiB]
+  __shared__ __align__(8) uint64_t full[kTStages], empty[kTStages], done;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+
+  const int warp = threadIdx.x >> 5;
+  const int64_t t = blockIdx.x / splits;
+  const int split = (int)(blockIdx.x % splits);
+  int64_t I, J;
+  tri_tile(t, n_blocks, I, J);
+  const int64_t c0 = n_chunks * split / splits, c1 = n_chunks * (split + 1) / splits;
+  const int64_t nk = c1 - c0;
+  const uint8_t* rowblk = planes + (size_t)I * n_chunks * kTChunkBytes;
+  const uint8_t* colblk = planes + (size_t)J * n_chunks * kTChunkBytes;
+  const bool same = I == J;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kTStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&done, 1);
+    mbar_fence_init();
+    abort_flag = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  if (threadIdx.x == 0) {
+    // Producer: TMA bulk copies of each chunk into the ring.
+    for (int64_t k = 0; k < nk; ++k) {
+      const int s = (int)(k % kTStages);
+      if (k >= kTStages && !mbar_wait_bounded(&empty[s], (uint32_t)((k / kTStages - 1) & 1))) {
+        atomicExch(status, kDevTimeout);
+        atomicExch(&abort_flag, 1);
+        break;
+      }
+      if (*(volatile int*)&abort_flag) break;
+      uint8_t* dst = ring + (size_t)s * 2 * kTChunkBytes;
+      mbar_arrive_expect_tx(&full[s], same ? kTChunkBytes : 2 * kTChunkBytes);
+      bulk_g2s(dst, rowblk + (size_t)(c0 + k) * kTChunkBytes, kTChunkBytes, &full[s]);
+      if (!same) bulk_g2s(dst + kTChunkBytes, colblk + (size_t)(c0 + k) * kTChunkBytes, kTChunkBytes, &full[s]);
+    }
+  } else if (threadIdx.x == 32) {
+    // MMA issuer.
+    int64_t k = 0;
+    for (; k < nk; ++k) {
+      const int s = (int)(k % kTStages);
+      if (!mbar_wait_bounded(&full[s], (uint32_t)((k / kTStages) & 1))) {
+        atomicExch(status, kDevTimeout);
+        atomicExch(&abort_flag, 1);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = smem_addr(ring + (size_t)s * 2 * kTChunkBytes);
+      const uint32_t b0 = same ? a0 : a0 + kTChunkBytes;
+      const uint32_t acc = k > 0 ? 1u : 0u;
+      umma(tmem + 0, umma_desc(a0 + 0 * kTileBytes), umma_desc(b0 + 0 * kTileBytes), acc);    // V V^T
+      umma(tmem + 128, umma_desc(a0 + 1 * kTileBytes), umma_desc(b0 + 1 * kTileBytes), acc);  // U U^T
+      umma(tmem + 256, umma_desc(a0 + 2 * kTileBytes), umma_desc(b0 + 3 * kTileBytes), acc);  // Q R^T
+      umma(tmem + 256, umma_desc(a0 + 3 * kTileBytes), umma_desc(b0 + 2 * kTileBytes), 1u);   // + R Q^T
+      umma_commit(&empty[s]);  // the stage is free once these MMAs have read it
+    }
+    umma_commit(&done);  // arrives when every MMA issued above has completed
+  }
+  // Everyone waits for the accumulators.
+  const bool ok = mbar_wait_bounded(&done, 0);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncthreads();
+  const bool good = ok && abort_flag == 0;
+  if (!ok && threadIdx.x == 0) atomicExch(status, kDevTimeout);
+
+  if (good) {
+    // Warp w owns TMEM lanes 32w..32w+31 = tile rows.
+    const int row = warp * 32 + (threadIdx.x & 31);
+    const int64_t gi = I * kTB + row;
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (int cg = 0; cg < kTB / 32; ++cg) {
+      uint32_t vn[32], vu[32], v0[32];
+      tmem_ld32(lane_base + 0 + cg * 32, vn);
+      tmem_ld32(lane_base + 128 + cg * 32, vu);
+      tmem_ld32(lane_base + 256 + cg * 32, v0);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (gi >= n) continue;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int64_t gj = J * kTB + cg * 32 + j;
+        if (gj >= n || gj < gi) continue;
+        const int32_t nn = __float2int_rn(__uint_as_float(vn[j]));
+        const int32_t uu = __float2int_rn(__uint_as_float(vu[j]));
+        const int32_t i0 = __float2int_rn(__uint_as_float(v0[j]));
+        const int32_t i1 = (nn - uu) / 2;
+        if (splits > 1) {
+          int32_t* o = partial + tri_index(gi, gj, n) * 4;
+          atomicAdd(o + 0, i0);
+          atomicAdd(o + 1, i1);
+          atomicAdd(o + 3, nn);
+          continue;
+        }
+        const int4 v = make_int4(i0, i1, nn - i0 - i1, nn);
+        double d = 0.0;
+        if (out_dist) d = nn == 0 ? __longlong_as_double(0x7ff8000000000000LL)
+                                  : (double)(i1 + 2 * i0) / (2.0 * (double)nn);
+        if (!square) {
+          const int64_t p = tri_index(gi, gj, n);
+          reinterpret_cast<int4*>(out_counts)[p] = v;
+          if (out_dist) out_dist[p] = d;
+        } else {
+          reinterpret_cast<int4*>(out_counts)[gi * n + gj] = v;
+          if (out_dist) out_dist[gi * n + gj] = d;
+          if (gi != gj) {
+            reinterpret_cast<int4*>(out_counts)[gj * n + gi] = v;
+            if (out_dist) out_dist[gj * n + gi] = d;
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+}  // namespace
+
+size_t tc_planes_bytes(int64_t n, int64_t m) {
+  const int64_t nb = (n + kTB - 1) / kTB, nc = (m + kTK - 1) / kTK;
+  return (size_t)nb * (size_t)nc * kTChunkBytes;
+}
+
+int tc_splits_for(int64_t tiles, int64_t n_chunks, int num_sms) {
+  const int64_t target = (int64_t)num_sms * 2;  // two waves of one CTA per SM
+  if (tiles >= target) return 1;
+  int64_t s = (target + tiles - 1) / tiles;
+  if (s > n_chunks) s = n_chunks;
+  if (s > 64) s = 64;
+  return s < 1 ? 1 : (int)s;
+}
+
+cudaError_t launch_tc_planes(const uint8_t* packed, int64_t n, int64_t m, uint8_t* planes, cudaStream_t st) {
+  const int64_t nb = (n + kTB - 1) / kTB, nc = (m + kTK - 1) / kTK;
+  if (nc > 2147483647LL || nb > 65535) return cudaErrorInvalidValue;
+  tc_planes_kernel<<<dim3((unsigned)nc, (unsigned)nb), kTB, 0, st>>>(packed, (n + 3) / 4, n, m, planes, nc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_pairs(const uint8_t* planes, int64_t n, int64_t m, int splits, int32_t* out_counts,
+                            double* out_dist, int32_t* partial, bool square, int* status, cudaStream_t st) {
+  const int64_t nb = (n + kTB - 1) / kTB, nc = (m + kTK - 1) / kTK;
+  const int64_t tiles = nb * (nb + 1) / 2;
+  const int64_t grid = tiles * splits;
+  if (grid > 2147483647LL) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(tc_tri_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTSmem);
+  if (e != cudaSuccess) return e;
+  tc_tri_kernel<<<(unsigned)grid, kTThreads, kTSmem, st>>>(planes, n, nb, nc, splits, out_counts, out_dist, partial,
+                                                          square ? 1 : 0, status);
+  return cudaGetLastError();
+}
+
+int64_t tc_tiles(int64_t n) {
+  const int64_t nb = (n + kTB - 1) / kTB;
+  return nb * (nb + 1) / 2;
+}
+
+int64_t tc_chunks(int64_t m) { return (m + kTK - 1) / kTK; }
+
+}  // namespace ibs

@@ -26,6 +26,7 @@ IBS_NO_DIST = 0x2
 IBS_KERNEL_PLAIN = 0x10
 IBS_KERNEL_CSA = 0x20
 IBS_TIMING = 0x40
+IBS_KERNEL_TC = 0x80
 
 
 class IbsError(RuntimeError):

@@ -11,6 +11,16 @@ from helpers import assert_dist_close
 pytestmark = pytest.mark.gpu
 
 
+_CONFIG3 = []
+
+
+def _config3():
+    from paper_1410_4803_gb300 import synth
+    if not _CONFIG3:
+        _CONFIG3.append(synth.structured_config3())
+    return _CONFIG3[0]
+
+
 def _whole_output_invariants(counts, n, nonmiss):
     """IBS0+IBS1+IBS2 = N, all counts >= 0, diagonal = (0, 0, N_i, N_i)."""
     import torch
@@ -24,12 +34,13 @@ def _whole_output_invariants(counts, n, nonmiss):
     assert bool((diag[:, 2] == nm).all() and (diag[:, 3] == nm).all())
 
 
-def test_plain_n4096_m100000_sampled_rows():
+@pytest.mark.parametrize("kernel", ["popc", "tc"])
+def test_plain_n4096_m100000_sampled_rows(kernel):
     import torch
     from paper_1410_4803_gb300 import ibs, synth
     w = synth.plain_config2()
     n, m = w.n, w.m
-    ctx = ibs.ibs_init(0)
+    ctx = ibs.ibs_init(0, flags=ibs.IBS_KERNEL_TC if kernel == "tc" else 0)
     try:
         counts, dist = ibs.compute(ctx, torch.from_numpy(w.packed).cuda(), n, m)
         ibs.ibs_synchronize(ctx)
@@ -49,14 +60,17 @@ def test_plain_n4096_m100000_sampled_rows():
         ibs.ibs_shutdown(ctx)
 
 
-def test_structured_n20000_m500000_sampled_pairs():
+@pytest.mark.parametrize("kernel", ["popc", "tc"])
+def test_structured_n20000_m500000_sampled_pairs(kernel):
     """Five subpopulations, injected parent-offspring pairs and duplicates: the
-    oracle checks a block of sampled pairs plus every relative pair."""
+    oracle checks a block of sampled pairs plus every relative pair.  With
+    m = 500,000 the counts reach 2^19, so the tensor-core form's FP32
+    accumulation is checked far above 2^14."""
     import torch
     from paper_1410_4803_gb300 import ibs, synth
-    w = synth.structured_config3()
+    w = _config3()
     n, m = w.n, w.m
-    ctx = ibs.ibs_init(0)
+    ctx = ibs.ibs_init(0, flags=ibs.IBS_KERNEL_TC if kernel == "tc" else 0)
     try:
         counts, dist = ibs.compute(ctx, torch.from_numpy(w.packed).cuda(), n, m)
         ibs.ibs_synchronize(ctx)

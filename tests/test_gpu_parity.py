@@ -13,10 +13,10 @@ N_EDGE = [1, 2, 3, 4, 5, 31, 32, 33, 63, 64, 65, 127, 128, 129, 255, 256, 257]
 M_EDGE = [1, 15, 16, 17, 31, 32, 33, 63, 64, 65, 383, 384, 385, 959, 960, 961, 1023, 1024, 1025]
 
 
-@pytest.fixture(scope="module", params=["plain", "csa"])
+@pytest.fixture(scope="module", params=["plain", "csa", "tc"])
 def ctx(request):
     from paper_1410_4803_gb300 import ibs
-    flags = ibs.IBS_KERNEL_PLAIN if request.param == "plain" else ibs.IBS_KERNEL_CSA
+    flags = {"plain": ibs.IBS_KERNEL_PLAIN, "csa": ibs.IBS_KERNEL_CSA, "tc": ibs.IBS_KERNEL_TC}[request.param]
     c = ibs.ibs_init(0, flags=flags)
     yield c
     ibs.ibs_shutdown(c)
@@ -57,7 +57,8 @@ def test_degenerate_inputs(ctx):
     check(ctx, random_codes(rng, 66, 400, miss=0.0))
 
 
-def test_square_output():
+@pytest.mark.parametrize("tc", [False, True])
+def test_square_output(tc):
     from paper_1410_4803_gb300 import ibs
     rng = np.random.default_rng(3)
     n, m = 130, 1500
@@ -65,7 +66,7 @@ def test_square_output():
     packed = pack_codes(codes)
     G = oracle.unpack(packed, n, m)
     want_c, want_d = oracle.ibs_block(G, G)
-    c = ibs.ibs_init(0, flags=ibs.IBS_OUT_SQUARE)
+    c = ibs.ibs_init(0, flags=ibs.IBS_OUT_SQUARE | (ibs.IBS_KERNEL_TC if tc else 0))
     try:
         got_c, got_d = gpu_compute(c, packed, n, m, square=True)
     finally:
@@ -111,13 +112,13 @@ def test_modes_agree_on_structured_cohort():
     from paper_1410_4803_gb300 import ibs, synth
     w = synth.structured_config3(n_base_per_pop=100, m=20000, n_offspring=20, n_dup=10)
     outs = []
-    for flags in (ibs.IBS_KERNEL_PLAIN, ibs.IBS_KERNEL_CSA):
+    for flags in (ibs.IBS_KERNEL_PLAIN, ibs.IBS_KERNEL_CSA, ibs.IBS_KERNEL_TC):
         c = ibs.ibs_init(0, flags=flags)
         try:
             outs.append(gpu_compute(c, w.packed, w.n, w.m))
         finally:
             ibs.ibs_shutdown(c)
-    assert (outs[0][0] == outs[1][0]).all()
+    assert (outs[0][0] == outs[1][0]).all() and (outs[0][0] == outs[2][0]).all()
     want_c, want_d = oracle.ibs_triangle(w.packed, w.n, w.m)
     assert (outs[0][0] == want_c).all()
     s = w.samples
