@@ -29,6 +29,8 @@
 // Every wait is bounded (2 s of %globaltimer); on expiry the status word is
 // set, and the CTA still waits (bounded) for its MMAs and frees its tensor
 // memory before returning.
+#include <cstdlib>
+
 #include "ibs_device.cuh"
 #include "ibs_internal.h"
 
@@ -41,9 +43,8 @@ constexpr int kTK = 32;                           // markers per chunk (one MMA 
 constexpr int kTPlanes = 4;                       // V, U, Q, R
 constexpr int kTileBytes = kTB * kTK;             // one plane of one chunk: 4 KiB
 constexpr int kTChunkBytes = kTPlanes * kTileBytes;  // 16 KiB per (block, chunk)
-constexpr int kTStages = 4;
 constexpr int kTThreads = 128;
-constexpr size_t kTSmem = (size_t)kTStages * 2 * kTChunkBytes + 1024;
+constexpr size_t tc_smem(int stages) { return (size_t)stages * 2 * kTChunkBytes + 1024; }
 constexpr uint32_t kTmemCols = 512;               // 3 x 128 used
 constexpr uint8_t kFp8One = 0x38, kFp8MinusOne = 0xB8;
 
@@ -130,7 +131,8 @@ __global__ void __launch_bounds__(kTB) tc_planes_kernel(const uint8_t* __restric
 }
 
 // ---------------------------------------------------------------------------
-// Pair tile kernel.
+// Pair tile kernel (kTStages-deep ring).
+template <int kTStages>
 __global__ void __launch_bounds__(kTThreads, 1)
     tc_tri_kernel(const uint8_t* __restrict__ planes, int64_t n, int64_t n_blocks, int64_t n_chunks, int splits,
                   int32_t* __restrict__ out_counts, double* __restrict__ out_dist, int32_t* __restrict__ partial,
@@ -301,10 +303,22 @@ cudaError_t launch_tc_pairs(const uint8_t* planes, int64_t n, int64_t m, int spl
   const int64_t tiles = nb * (nb + 1) / 2;
   const int64_t grid = tiles * splits;
   if (grid > 2147483647LL) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(tc_tri_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTSmem);
-  if (e != cudaSuccess) return e;
-  tc_tri_kernel<<<(unsigned)grid, kTThreads, kTSmem, st>>>(planes, n, nb, nc, splits, out_counts, out_dist, partial,
-                                                          square ? 1 : 0, status);
+  static const int stages = [] {
+    const char* e = getenv("IBS_TC_STAGES");
+    return (e && e[0] == '6') ? 6 : 4;
+  }();
+  cudaError_t e;
+  if (stages == 6) {
+    e = cudaFuncSetAttribute(tc_tri_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(6));
+    if (e != cudaSuccess) return e;
+    tc_tri_kernel<6><<<(unsigned)grid, kTThreads, tc_smem(6), st>>>(planes, n, nb, nc, splits, out_counts, out_dist,
+                                                                   partial, square ? 1 : 0, status);
+  } else {
+    e = cudaFuncSetAttribute(tc_tri_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(4));
+    if (e != cudaSuccess) return e;
+    tc_tri_kernel<4><<<(unsigned)grid, kTThreads, tc_smem(4), st>>>(planes, n, nb, nc, splits, out_counts, out_dist,
+                                                                   partial, square ? 1 : 0, status);
+  }
   return cudaGetLastError();
 }
 
