@@ -20,11 +20,13 @@
 // without swizzle: 8-row x 16-byte core matrices, the two core matrices of a
 // row group 128 bytes apart (leading byte offset) and row groups 256 bytes
 // apart (stride byte offset).  A CTA computes one 128 x 128 tile of pairs:
-// thread 0 streams chunks of the row and column blocks through a 4-stage
-// shared-memory ring with TMA bulk copies, thread 32 issues the MMAs into three
+// warp 0 streams chunks of the row and column blocks through a 4-stage
+// shared-memory ring with TMA bulk copies, warp 1 issues the MMAs into three
 // FP32 accumulators in tensor memory (columns 0, 128, 256) and frees each
 // stage with tcgen05.commit, and after the last chunk all four warps read the
-// accumulators back (tcgen05.ld), decode the counts and store them.
+// accumulators back (tcgen05.ld), decode the counts and store them.  Warp 0
+// (copies) and warp 1 (MMAs) run their loops with all 32 lanes in step and
+// one lane issuing, so no lane of theirs is parked in another wait.
 //
 // Every wait is bounded (2 s of %globaltimer); on expiry the status word is
 // set, and the CTA still waits (bounded) for its MMAs and frees its tensor
@@ -136,7 +138,7 @@ template <int kTStages>
 __global__ void __launch_bounds__(kTThreads, 1)
     tc_tri_kernel(const uint8_t* __restrict__ planes, int64_t n, int64_t n_blocks, int64_t n_chunks, int splits,
                   int32_t* __restrict__ out_counts, double* __restrict__ out_dist, int32_t* __restrict__ partial,
-                  int square, int* status) {
+                  int square, int* status, int piece) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // 1024-byte aligned ring (the dynamic base is only guaranteed 16-byte aligned)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -176,42 +178,62 @@ __global__ void __launch_bounds__(kTThreads, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
 
-  if (threadIdx.x == 0) {
-    // Producer: TMA bulk copies of each chunk into the ring.
+  const int lane = threadIdx.x & 31;
+  if (warp == 0) {
+    // Producer warp: every lane waits for a free stage together (no lane of
+    // this warp sits in another wait), lane 0 issues the bulk copies.
     for (int64_t k = 0; k < nk; ++k) {
       const int s = (int)(k % kTStages);
-      if (k >= kTStages && !mbar_wait_bounded(&empty[s], (uint32_t)((k / kTStages - 1) & 1))) {
-        atomicExch(status, kDevTimeout);
-        atomicExch(&abort_flag, 1);
+      const bool ok = k < kTStages || mbar_wait_bounded(&empty[s], (uint32_t)((k / kTStages - 1) & 1));
+      // decisions are made warp-wide so the lanes never split around __syncwarp
+      if (__any_sync(0xffffffffu, !ok)) {
+        if (lane == 0) {
+          atomicExch(status, kDevTimeout);
+          atomicExch(&abort_flag, 1);
+        }
         break;
       }
-      if (*(volatile int*)&abort_flag) break;
-      uint8_t* dst = ring + (size_t)s * 2 * kTChunkBytes;
-      mbar_arrive_expect_tx(&full[s], same ? kTChunkBytes : 2 * kTChunkBytes);
-      bulk_g2s(dst, rowblk + (size_t)(c0 + k) * kTChunkBytes, kTChunkBytes, &full[s]);
-      if (!same) bulk_g2s(dst + kTChunkBytes, colblk + (size_t)(c0 + k) * kTChunkBytes, kTChunkBytes, &full[s]);
+      if (__any_sync(0xffffffffu, *(volatile int*)&abort_flag != 0)) break;
+      if (lane == 0) {
+        uint8_t* dst = ring + (size_t)s * 2 * kTChunkBytes;
+        mbar_arrive_expect_tx(&full[s], same ? kTChunkBytes : 2 * kTChunkBytes);
+        // Each 16 KiB chunk goes as several smaller bulk copies, which the
+        // copy engine keeps in flight together.
+        for (int off = 0; off < kTChunkBytes; off += piece) {
+          bulk_g2s(dst + off, rowblk + (size_t)(c0 + k) * kTChunkBytes + off, piece, &full[s]);
+          if (!same)
+            bulk_g2s(dst + kTChunkBytes + off, colblk + (size_t)(c0 + k) * kTChunkBytes + off, piece, &full[s]);
+        }
+      }
+      __syncwarp();
     }
-  } else if (threadIdx.x == 32) {
-    // MMA issuer.
-    int64_t k = 0;
-    for (; k < nk; ++k) {
+  } else if (warp == 1) {
+    // MMA warp: every lane waits for the stage's data, lane 0 issues the MMAs.
+    for (int64_t k = 0; k < nk; ++k) {
       const int s = (int)(k % kTStages);
-      if (!mbar_wait_bounded(&full[s], (uint32_t)((k / kTStages) & 1))) {
-        atomicExch(status, kDevTimeout);
-        atomicExch(&abort_flag, 1);
+      const bool ok = mbar_wait_bounded(&full[s], (uint32_t)((k / kTStages) & 1));
+      if (__any_sync(0xffffffffu, !ok)) {
+        if (lane == 0) {
+          atomicExch(status, kDevTimeout);
+          atomicExch(&abort_flag, 1);
+        }
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a0 = smem_addr(ring + (size_t)s * 2 * kTChunkBytes);
-      const uint32_t b0 = same ? a0 : a0 + kTChunkBytes;
-      const uint32_t acc = k > 0 ? 1u : 0u;
-      umma(tmem + 0, umma_desc(a0 + 0 * kTileBytes), umma_desc(b0 + 0 * kTileBytes), acc);    // V V^T
-      umma(tmem + 128, umma_desc(a0 + 1 * kTileBytes), umma_desc(b0 + 1 * kTileBytes), acc);  // U U^T
-      umma(tmem + 256, umma_desc(a0 + 2 * kTileBytes), umma_desc(b0 + 3 * kTileBytes), acc);  // Q R^T
-      umma(tmem + 256, umma_desc(a0 + 3 * kTileBytes), umma_desc(b0 + 2 * kTileBytes), 1u);   // + R Q^T
-      umma_commit(&empty[s]);  // the stage is free once these MMAs have read it
+      if (lane == 0) {
+        const uint32_t a0 = smem_addr(ring + (size_t)s * 2 * kTChunkBytes);
+        const uint32_t b0 = same ? a0 : a0 + kTChunkBytes;
+        const uint32_t acc = k > 0 ? 1u : 0u;
+        umma(tmem + 0, umma_desc(a0 + 0 * kTileBytes), umma_desc(b0 + 0 * kTileBytes), acc);    // V V^T
+        umma(tmem + 128, umma_desc(a0 + 1 * kTileBytes), umma_desc(b0 + 1 * kTileBytes), acc);  // U U^T
+        umma(tmem + 256, umma_desc(a0 + 2 * kTileBytes), umma_desc(b0 + 3 * kTileBytes), acc);  // Q R^T
+        umma(tmem + 256, umma_desc(a0 + 3 * kTileBytes), umma_desc(b0 + 2 * kTileBytes), 1u);   // + R Q^T
+        umma_commit(&empty[s]);  // the stage is free once these MMAs have read it
+      }
+      __syncwarp();
     }
-    umma_commit(&done);  // arrives when every MMA issued above has completed
+    if (lane == 0) umma_commit(&done);  // arrives when every MMA issued above has completed
+    __syncwarp();
   }
   // Everyone waits for the accumulators.
   const bool ok = mbar_wait_bounded(&done, 0);
@@ -307,17 +329,22 @@ cudaError_t launch_tc_pairs(const uint8_t* planes, int64_t n, int64_t m, int spl
     const char* e = getenv("IBS_TC_STAGES");
     return (e && e[0] == '6') ? 6 : 4;
   }();
+  static const int piece = [] {
+    const char* e = getenv("IBS_TC_PIECE");
+    const int v = e ? atoi(e) : kTChunkBytes;
+    return (v >= 512 && v <= kTChunkBytes && kTChunkBytes % v == 0 && v % 16 == 0) ? v : kTChunkBytes;
+  }();
   cudaError_t e;
   if (stages == 6) {
     e = cudaFuncSetAttribute(tc_tri_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(6));
     if (e != cudaSuccess) return e;
     tc_tri_kernel<6><<<(unsigned)grid, kTThreads, tc_smem(6), st>>>(planes, n, nb, nc, splits, out_counts, out_dist,
-                                                                   partial, square ? 1 : 0, status);
+                                                                   partial, square ? 1 : 0, status, piece);
   } else {
     e = cudaFuncSetAttribute(tc_tri_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(4));
     if (e != cudaSuccess) return e;
     tc_tri_kernel<4><<<(unsigned)grid, kTThreads, tc_smem(4), st>>>(planes, n, nb, nc, splits, out_counts, out_dist,
-                                                                   partial, square ? 1 : 0, status);
+                                                                   partial, square ? 1 : 0, status, piece);
   }
   return cudaGetLastError();
 }
