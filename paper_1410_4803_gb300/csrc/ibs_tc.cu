@@ -93,43 +93,75 @@ __device__ __forceinline__ int tile_off(int r, int k) {
 }
 
 // ---------------------------------------------------------------------------
-// Transpose: packed .bed rows -> FP8 planes.  CTA = (chunk c, block b), one
-// thread per sample; each thread reads its 2-bit code at the chunk's 32
-// markers and writes 2 x 16 bytes per plane.
-__global__ void __launch_bounds__(kTB) tc_planes_kernel(const uint8_t* __restrict__ packed, int64_t row_bytes,
+// Transpose: packed .bed rows -> FP8 planes.  CTA = (chunk c of 32 markers,
+// block b of 128 samples), 8 warps of 16 samples.  Lane t of a warp holds one
+// 32-bit word of .bed row t (its 16 samples' 2-bit codes); a 32 x 32 bit
+// transpose by warp shuffles leaves lane 2k with the low code bits and lane
+// 2k+1 with the high code bits of sample k at the 32 markers.  After one
+// exchange each lane of the pair has both words; lane 2k writes markers 0..15
+// and lane 2k+1 markers 16..31 of the sample's four FP8 plane rows.  Bits
+// become bytes with a multiply: (x * 0x204081) & 0x01010101 spreads 4 bits
+// to 4 bytes, and a second multiply turns each 1 into the FP8 value.
+__device__ __forceinline__ uint32_t tc_transpose32(uint32_t x, int lane) {
+  constexpr uint32_t kMask[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    const int j = 16 >> r;
+    const uint32_t m = kMask[r];
+    const uint32_t y = __shfl_xor_sync(0xffffffffu, x, j);
+    x = (lane & j) == 0 ? ((x & m) | ((y & m) << j)) : ((x & ~m) | ((y & ~m) >> j));
+  }
+  return x;
+}
+
+__device__ __forceinline__ uint32_t spread4(uint32_t x) { return (x * 0x00204081u) & 0x01010101u; }
+
+__global__ void __launch_bounds__(256) tc_planes_kernel(const uint8_t* __restrict__ packed, int64_t row_bytes,
                                                         int64_t n, int64_t m, uint8_t* __restrict__ planes,
                                                         int64_t n_chunks) {
   const int64_t c = blockIdx.x, b = blockIdx.y;
-  const int r = threadIdx.x;
-  const int64_t s = b * kTB + r;
-  uint32_t w[kTPlanes][8];  // 32 bytes per plane, little-endian words
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t marker = c * kTK + lane;
+  const int64_t s0 = b * kTB + warp * 16;  // first sample of this warp
+  const int64_t byte0 = s0 >> 2;           // 4 bytes = 16 samples
+  uint32_t x = 0x55555555u;                // "missing" for every slot
+  if (marker < m && s0 < n) {
+    const uint8_t* row = packed + marker * row_bytes;
+    if (row_bytes % 4 == 0 && (reinterpret_cast<uintptr_t>(packed) & 3) == 0 && byte0 + 4 <= row_bytes) {
+      x = __ldg(reinterpret_cast<const uint32_t*>(row + byte0));
+    } else {
+      x = 0;
 #pragma unroll
-  for (int p = 0; p < kTPlanes; ++p)
-#pragma unroll
-    for (int q = 0; q < 8; ++q) w[p][q] = 0;
-  if (s < n) {
-    const uint8_t* col = packed + (s >> 2);
-    const int sh = 2 * (int)(s & 3);
-#pragma unroll
-    for (int k = 0; k < kTK; ++k) {
-      const int64_t marker = c * kTK + k;
-      const uint32_t code = marker < m ? (__ldg(col + marker * row_bytes) >> sh) & 3u : 1u;  // past the end: missing
-      const uint32_t shift = 8 * (k & 3);
-      const int q = k >> 2;
-      if (code != 1u) w[0][q] |= (uint32_t)kFp8One << shift;                               // V
-      if (code != 1u) w[1][q] |= (uint32_t)(code == 2u ? kFp8MinusOne : kFp8One) << shift;  // U
-      if (code == 3u) w[2][q] |= (uint32_t)kFp8One << shift;                               // Q
-      if (code == 0u) w[3][q] |= (uint32_t)kFp8One << shift;                               // R
+      for (int q = 0; q < 4; ++q) x |= (uint32_t)(byte0 + q < row_bytes ? __ldg(row + byte0 + q) : 0x55u) << (8 * q);
     }
   }
-  uint8_t* base = planes + (size_t)(b * n_chunks + c) * kTChunkBytes;
+  x = tc_transpose32(x, lane);
+  const uint32_t partner = __shfl_xor_sync(0xffffffffu, x, 1);
+  const bool odd = (lane & 1) != 0;
+  const uint32_t H = odd ? x : partner, L = odd ? partner : x;
+  const int r = warp * 16 + (lane >> 1);  // row inside the 128-sample block
+  const bool valid = b * kTB + r < n;
+  // this lane's 16 markers: bits 0..15 (even lane) or 16..31 (odd lane)
+  const int sh = odd ? 16 : 0;
+  const uint32_t h = (H >> sh) & 0xFFFFu, l = (L >> sh) & 0xFFFFu;
+  const uint32_t vb = valid ? (h | ~l) & 0xFFFFu : 0u;  // present
+  const uint32_t pb = vb & h & ~l;                       // het
+  const uint32_t qb = vb & h & l;                        // hom A2
+  const uint32_t rb = vb & ~h & ~l;                      // hom A1
+  uint32_t wv[4], wu[4], wq[4], wr[4];
 #pragma unroll
-  for (int p = 0; p < kTPlanes; ++p)
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      uint4 v = make_uint4(w[p][4 * half + 0], w[p][4 * half + 1], w[p][4 * half + 2], w[p][4 * half + 3]);
-      *reinterpret_cast<uint4*>(base + p * kTileBytes + tile_off(r, 16 * half)) = v;
-    }
+  for (int g = 0; g < 4; ++g) {
+    const uint32_t sv = spread4((vb >> (4 * g)) & 0xFu), sp = spread4((pb >> (4 * g)) & 0xFu);
+    wv[g] = sv * kFp8One;
+    wu[g] = sv * kFp8One | sp * 0x80u;  // heterozygous: sign bit -> -1
+    wq[g] = spread4((qb >> (4 * g)) & 0xFu) * kFp8One;
+    wr[g] = spread4((rb >> (4 * g)) & 0xFu) * kFp8One;
+  }
+  uint8_t* base = planes + (size_t)(b * n_chunks + c) * kTChunkBytes + tile_off(r, odd ? 16 : 0);
+  *reinterpret_cast<uint4*>(base + 0 * kTileBytes) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+  *reinterpret_cast<uint4*>(base + 1 * kTileBytes) = make_uint4(wu[0], wu[1], wu[2], wu[3]);
+  *reinterpret_cast<uint4*>(base + 2 * kTileBytes) = make_uint4(wq[0], wq[1], wq[2], wq[3]);
+  *reinterpret_cast<uint4*>(base + 3 * kTileBytes) = make_uint4(wr[0], wr[1], wr[2], wr[3]);
 }
 
 // ---------------------------------------------------------------------------
@@ -303,19 +335,28 @@ size_t tc_planes_bytes(int64_t n, int64_t m) {
   return (size_t)nb * (size_t)nc * kTChunkBytes;
 }
 
+// Split count over the marker axis.  All tiles of one launch cost the same,
+// so the launch takes ceil(tiles * s / SMs) waves of 1/s of a tile each; pick
+// the s in 1..8 (at most one chunk per split) with the fewest tile-equivalents,
+// charging splits 3% for the partial-count atomics and the finalisation pass.
 int tc_splits_for(int64_t tiles, int64_t n_chunks, int num_sms) {
-  const int64_t target = (int64_t)num_sms * 2;  // two waves of one CTA per SM
-  if (tiles >= target) return 1;
-  int64_t s = (target + tiles - 1) / tiles;
-  if (s > n_chunks) s = n_chunks;
-  if (s > 64) s = 64;
-  return s < 1 ? 1 : (int)s;
+  int best = 1;
+  double best_cost = 1e300;
+  for (int s = 1; s <= 8 && s <= n_chunks; ++s) {
+    const double waves = (double)((tiles * s + num_sms - 1) / num_sms);
+    const double cost = waves / s * (s > 1 ? 1.03 : 1.0);
+    if (cost < best_cost - 1e-9) {
+      best_cost = cost;
+      best = s;
+    }
+  }
+  return best;
 }
 
 cudaError_t launch_tc_planes(const uint8_t* packed, int64_t n, int64_t m, uint8_t* planes, cudaStream_t st) {
   const int64_t nb = (n + kTB - 1) / kTB, nc = (m + kTK - 1) / kTK;
   if (nc > 2147483647LL || nb > 65535) return cudaErrorInvalidValue;
-  tc_planes_kernel<<<dim3((unsigned)nc, (unsigned)nb), kTB, 0, st>>>(packed, (n + 3) / 4, n, m, planes, nc);
+  tc_planes_kernel<<<dim3((unsigned)nc, (unsigned)nb), 256, 0, st>>>(packed, (n + 3) / 4, n, m, planes, nc);
   return cudaGetLastError();
 }
 
