@@ -237,8 +237,9 @@ def run_plain(args, rank, world, local):
     counts = torch.empty((P, 4), dtype=torch.int32, device=dev)
     dist_t = torch.empty(P, dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
-    use_tc = os.environ.get("IBS_USE_TC", "0") == "1"
-    ctx = ibs.ibs_init(local, flags=ibs.IBS_TIMING | (ibs.IBS_KERNEL_TC if use_tc else 0))
+    # default: the tensor-core form; IBS_DEFAULT_KERNEL=popc times the bit-plane POPC kernel instead
+    use_tc = os.environ.get("IBS_DEFAULT_KERNEL", "tc") != "popc"
+    ctx = ibs.ibs_init(local, flags=ibs.IBS_TIMING | (ibs.IBS_KERNEL_TC if use_tc else ibs.IBS_KERNEL_CSA))
     probe = ibs.ibs_probe_int_pipes(ctx)
 
     with torch.cuda.stream(stream):

@@ -101,7 +101,13 @@ ibs_status check_ctx(ibs_ctx* ctx) {
 
 constexpr int kFlagTc = 0x80;  // tensor-core (tcgen05 FP8 indicator GEMM) pair counts
 
-bool use_tc(const ibs_ctx* ctx) { return (ctx->flags & kFlagTc) != 0; }
+// The tensor-core form is the default for ibs_compute; IBS_KERNEL_PLAIN or
+// IBS_KERNEL_CSA select the bit-plane POPC kernels instead.
+bool use_tc(const ibs_ctx* ctx) {
+  if (ctx->flags & kFlagTc) return true;
+  if (ctx->flags & (kFlagPlain | kFlagCsa)) return false;
+  return ctx->default_tc;
+}
 
 int mode_for(const ibs_ctx* ctx) {
   if (ctx->flags & kFlagPlain) return 0;
@@ -142,6 +148,8 @@ ibs_status ibs_init(const ibs_config* cfg, ibs_ctx** out_ctx) {
   ctx->num_sms = prop.multiProcessorCount;
   ctx->cc_major = prop.major;
   ctx->cc_minor = prop.minor;
+  const char* tcenv = getenv("IBS_DEFAULT_KERNEL");
+  ctx->default_tc = !(tcenv && strcmp(tcenv, "popc") == 0);
   const char* env = getenv("IBS_PAIR_MODE");
   if (env && env[0] >= '0' && env[0] <= '2' && env[1] == 0) ctx->default_mode = env[0] - '0';
   e = cudaHostAlloc(reinterpret_cast<void**>(&ctx->status_host), sizeof(int), cudaHostAllocMapped);
@@ -215,10 +223,26 @@ ibs_status ibs_compute(ibs_ctx* ctx, const uint8_t* packed, int64_t n, int64_t m
     IBS_CUDA_TRY(cudaEventRecord(rec.ev[0], st));
   }
   if (tc) {
+    const int64_t T = (n + 127) / 128;
+    if (ctx->tile_list_T != T) {
+      static const int group = [] {
+        const char* e = getenv("IBS_TC_GROUP");
+        const int v = e ? atoi(e) : 16;
+        return v >= 1 && v <= 1024 ? v : 16;
+      }();
+      std::vector<int2> order;
+      tc_tile_order(T, group, order);
+      if (ibs_status s = ensure_buf(ctx, ctx->tile_list, order.size() * sizeof(int2))) return s;
+      // pageable source: the copy is staged before return
+      IBS_CUDA_TRY(cudaMemcpyAsync(ctx->tile_list.p, order.data(), order.size() * sizeof(int2),
+                                   cudaMemcpyHostToDevice, st));
+      ctx->tile_list_T = T;
+    }
     IBS_CUDA_TRY(launch_tc_planes(packed, n, m, static_cast<uint8_t*>(ctx->planes.p), st));
     if (timing) IBS_CUDA_TRY(cudaEventRecord(rec.ev[1], st));
     IBS_CUDA_TRY(launch_tc_pairs(static_cast<const uint8_t*>(ctx->planes.p), n, m, splits, out_counts, out_dist,
-                                 static_cast<int32_t*>(ctx->partial.p), square, ctx->status_dev, st));
+                                 static_cast<int32_t*>(ctx->partial.p), square, ctx->status_dev,
+                                 static_cast<const int2*>(ctx->tile_list.p), st));
   } else {
     IBS_CUDA_TRY(launch_planes(src, n, m, geo, static_cast<uint32_t*>(ctx->planes.p), ctx->status_dev, st));
     if (timing) IBS_CUDA_TRY(cudaEventRecord(rec.ev[1], st));
@@ -630,6 +654,7 @@ extern "C" ibs_status ibs_shutdown(ibs_ctx* ctx) {
     ctx->plans.clear();
     free_buf(ctx, ctx->planes);
     free_buf(ctx, ctx->partial);
+    free_buf(ctx, ctx->tile_list);
     for (auto* v : {&ctx->timing_used, &ctx->timing_free})
       for (auto& r : *v)
         for (auto& e : r.ev)

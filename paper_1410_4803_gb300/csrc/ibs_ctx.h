@@ -77,11 +77,14 @@ struct ibs_ctx {
   int num_sms = 0;
   int cc_major = 0, cc_minor = 0;
   int default_mode = 1;
+  bool default_tc = true;         // ibs_compute uses the tensor-core form unless told otherwise
 
   std::mutex mu;                  // guards memory accounting
   size_t owned_bytes = 0;
 
   ibs::DevBuf planes, partial;
+  ibs::DevBuf tile_list;          // tensor-core grouped tile order, for tile_list_T tiles per side
+  int64_t tile_list_T = -1;
   int* status_host = nullptr;     // mapped pinned status word
   int* status_dev = nullptr;
 

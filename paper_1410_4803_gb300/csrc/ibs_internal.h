@@ -4,6 +4,8 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
+
 #include <cuda_runtime.h>
 
 namespace ibs {
@@ -117,7 +119,9 @@ int64_t tc_tiles(int64_t n);
 int64_t tc_chunks(int64_t m);
 cudaError_t launch_tc_planes(const uint8_t* packed, int64_t n, int64_t m, uint8_t* planes, cudaStream_t st);
 cudaError_t launch_tc_pairs(const uint8_t* planes, int64_t n, int64_t m, int splits, int32_t* out_counts,
-                            double* out_dist, int32_t* partial, bool square, int* status, cudaStream_t st);
+                            double* out_dist, int32_t* partial, bool square, int* status, const int2* tile_list,
+                            cudaStream_t st);
+void tc_tile_order(int64_t T, int G, std::vector<int2>& out);
 size_t pair_kernel_smem_bytes();
 
 // Integer-pipe microbenchmark (ibs_probe.cu).

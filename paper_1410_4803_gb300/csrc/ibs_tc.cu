@@ -32,6 +32,7 @@
 // set, and the CTA still waits (bounded) for its MMAs and frees its tensor
 // memory before returning.
 #include <cstdlib>
+#include <vector>
 
 #include "ibs_device.cuh"
 #include "ibs_internal.h"
@@ -170,7 +171,7 @@ template <int kTStages>
 __global__ void __launch_bounds__(kTThreads, 1)
     tc_tri_kernel(const uint8_t* __restrict__ planes, int64_t n, int64_t n_blocks, int64_t n_chunks, int splits,
                   int32_t* __restrict__ out_counts, double* __restrict__ out_dist, int32_t* __restrict__ partial,
-                  int square, int* status, int piece) {
+                  int square, int* status, int piece, const int2* __restrict__ tile_list) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // 1024-byte aligned ring (the dynamic base is only guaranteed 16-byte aligned)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -183,7 +184,13 @@ __global__ void __launch_bounds__(kTThreads, 1)
   const int64_t t = blockIdx.x / splits;
   const int split = (int)(blockIdx.x % splits);
   int64_t I, J;
-  tri_tile(t, n_blocks, I, J);
+  if (tile_list != nullptr) {
+    const int2 ij = tile_list[t];
+    I = ij.x;
+    J = ij.y;
+  } else {
+    tri_tile(t, n_blocks, I, J);
+  }
   const int64_t c0 = n_chunks * split / splits, c1 = n_chunks * (split + 1) / splits;
   const int64_t nk = c1 - c0;
   const uint8_t* rowblk = planes + (size_t)I * n_chunks * kTChunkBytes;
@@ -337,12 +344,12 @@ size_t tc_planes_bytes(int64_t n, int64_t m) {
 
 // Split count over the marker axis.  All tiles of one launch cost the same,
 // so the launch takes ceil(tiles * s / SMs) waves of 1/s of a tile each; pick
-// the s in 1..8 (at most one chunk per split) with the fewest tile-equivalents,
+// the s in 1..64 (at least one chunk per split) with the fewest tile-equivalents,
 // charging splits 3% for the partial-count atomics and the finalisation pass.
 int tc_splits_for(int64_t tiles, int64_t n_chunks, int num_sms) {
   int best = 1;
   double best_cost = 1e300;
-  for (int s = 1; s <= 8 && s <= n_chunks; ++s) {
+  for (int s = 1; s <= 64 && s <= n_chunks; ++s) {
     const double waves = (double)((tiles * s + num_sms - 1) / num_sms);
     const double cost = waves / s * (s > 1 ? 1.03 : 1.0);
     if (cost < best_cost - 1e-9) {
@@ -361,7 +368,8 @@ cudaError_t launch_tc_planes(const uint8_t* packed, int64_t n, int64_t m, uint8_
 }
 
 cudaError_t launch_tc_pairs(const uint8_t* planes, int64_t n, int64_t m, int splits, int32_t* out_counts,
-                            double* out_dist, int32_t* partial, bool square, int* status, cudaStream_t st) {
+                            double* out_dist, int32_t* partial, bool square, int* status, const int2* tile_list,
+                            cudaStream_t st) {
   const int64_t nb = (n + kTB - 1) / kTB, nc = (m + kTK - 1) / kTK;
   const int64_t tiles = nb * (nb + 1) / 2;
   const int64_t grid = tiles * splits;
@@ -380,14 +388,29 @@ cudaError_t launch_tc_pairs(const uint8_t* planes, int64_t n, int64_t m, int spl
     e = cudaFuncSetAttribute(tc_tri_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(6));
     if (e != cudaSuccess) return e;
     tc_tri_kernel<6><<<(unsigned)grid, kTThreads, tc_smem(6), st>>>(planes, n, nb, nc, splits, out_counts, out_dist,
-                                                                   partial, square ? 1 : 0, status, piece);
+                                                                   partial, square ? 1 : 0, status, piece, tile_list);
   } else {
     e = cudaFuncSetAttribute(tc_tri_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(4));
     if (e != cudaSuccess) return e;
     tc_tri_kernel<4><<<(unsigned)grid, kTThreads, tc_smem(4), st>>>(planes, n, nb, nc, splits, out_counts, out_dist,
-                                                                   partial, square ? 1 : 0, status, piece);
+                                                                   partial, square ? 1 : 0, status, piece, tile_list);
   }
   return cudaGetLastError();
+}
+
+// Grouped tile order: the upper triangle of T x T tiles in bands of G tile
+// rows; inside a band, column by column.  The CTAs running at the same time
+// then cover about G rows x (SMs / G) columns, so each block of planes they
+// stream is shared by many of them through L2 instead of being fetched from
+// HBM once per tile.
+void tc_tile_order(int64_t T, int G, std::vector<int2>& out) {
+  out.clear();
+  out.reserve((size_t)(T * (T + 1) / 2));
+  for (int64_t g0 = 0; g0 < T; g0 += G) {
+    const int64_t g1 = g0 + G < T ? g0 + G : T;
+    for (int64_t J = g0; J < T; ++J)
+      for (int64_t I = g0; I < g1 && I <= J; ++I) out.push_back(make_int2((int)I, (int)J));
+  }
 }
 
 int64_t tc_tiles(int64_t n) {

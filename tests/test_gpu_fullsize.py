@@ -40,7 +40,7 @@ def test_plain_n4096_m100000_sampled_rows(kernel):
     from paper_1410_4803_gb300 import ibs, synth
     w = synth.plain_config2()
     n, m = w.n, w.m
-    ctx = ibs.ibs_init(0, flags=ibs.IBS_KERNEL_TC if kernel == "tc" else 0)
+    ctx = ibs.ibs_init(0, flags=ibs.IBS_KERNEL_TC if kernel == "tc" else ibs.IBS_KERNEL_CSA)
     try:
         counts, dist = ibs.compute(ctx, torch.from_numpy(w.packed).cuda(), n, m)
         ibs.ibs_synchronize(ctx)
@@ -70,7 +70,7 @@ def test_structured_n20000_m500000_sampled_pairs(kernel):
     from paper_1410_4803_gb300 import ibs, synth
     w = _config3()
     n, m = w.n, w.m
-    ctx = ibs.ibs_init(0, flags=ibs.IBS_KERNEL_TC if kernel == "tc" else 0)
+    ctx = ibs.ibs_init(0, flags=ibs.IBS_KERNEL_TC if kernel == "tc" else ibs.IBS_KERNEL_CSA)
     try:
         counts, dist = ibs.compute(ctx, torch.from_numpy(w.packed).cuda(), n, m)
         ibs.ibs_synchronize(ctx)

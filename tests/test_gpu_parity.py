@@ -66,7 +66,7 @@ def test_square_output(tc):
     packed = pack_codes(codes)
     G = oracle.unpack(packed, n, m)
     want_c, want_d = oracle.ibs_block(G, G)
-    c = ibs.ibs_init(0, flags=ibs.IBS_OUT_SQUARE | (ibs.IBS_KERNEL_TC if tc else 0))
+    c = ibs.ibs_init(0, flags=ibs.IBS_OUT_SQUARE | (ibs.IBS_KERNEL_TC if tc else ibs.IBS_KERNEL_CSA))
     try:
         got_c, got_d = gpu_compute(c, packed, n, m, square=True)
     finally:
