@@ -140,23 +140,24 @@ def hbm_peak_gbs() -> float:
         return 6800.0
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(files=("ibs_pairs.cu", "ibs_device.cuh")) -> str:
     h = hashlib.sha256()
-    for f in ("ibs_pairs.cu", "ibs_device.cuh"):
+    for f in files:
         h.update(open(os.path.join(ROOT, "paper_1410_4803_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(name: str):
+def profiled_traffic(name: str, files=("ibs_pairs.cu", "ibs_device.cuh")):
     """DRAM bytes per launch of the pair kernel from the committed ncu summary,
-    or None when the summary is missing or the kernel source changed since."""
+    or None when the summary is missing or the kernel source (`files`) changed
+    since."""
     path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
     text = open(path).read()
     m_hash = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", text)
     m_bytes = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    if not m_hash or not m_bytes or m_hash.group(1) != kernel_source_hash():
+    if not m_hash or not m_bytes or m_hash.group(1) != kernel_source_hash(files):
         return None
     return float(m_bytes.group(1))
 
@@ -241,6 +242,7 @@ def run_plain(args, rank, world, local):
     use_tc = os.environ.get("IBS_DEFAULT_KERNEL", "tc") != "popc"
     ctx = ibs.ibs_init(local, flags=ibs.IBS_TIMING | (ibs.IBS_KERNEL_TC if use_tc else ibs.IBS_KERNEL_CSA))
     probe = ibs.ibs_probe_int_pipes(ctx)
+    kinfo = ibs.ibs_kernel_info(ctx)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -303,19 +305,23 @@ def run_plain(args, rank, world, local):
     planes_ms = kt["planes_ms"] / max(1, kt["calls"])
     roof = int_pipe_roofline(probe, clocks.get("sm_mhz"))
     achieved = comps / (pairs_ms * 1e-3)
+    fp4 = use_tc and kinfo["tc_format"] == "e2m1"
     if use_tc:
-        # FP8 tensor peak: the measured bf16 burst rate x the nominal FP8/bf16 ratio (2);
-        # 4 MACs = 8 flops per comparison.
-        fp8_tflops = 2.0 * measured_peak("bf16_tflops", 1900.0)
+        # tensor peak of the operand type: the measured bf16 burst rate x the nominal
+        # dense ratio (FP8 4.5 / bf16 2.25 = 2; FP4 13.5 / 2.25 = 6); 4 MACs = 8 flops
+        # per comparison.
+        tc_ratio = 6.0 if fp4 else 2.0
+        tc_tflops = tc_ratio * measured_peak("bf16_tflops", 1900.0)
     mode = {"0": "plain", "1": "csa3", "2": "csa3-1cta"}.get(os.environ.get("IBS_PAIR_MODE", "1"), "csa3")
     if use_tc:
-        mode = "tc-fp8"
+        mode = "tc-fp4" if fp4 else "tc-fp8"
     # transpose: read the 2-bit input once, write 16 bytes per (padded) sample-word of planes
     words = (m + 31) // 32
     n_blocks, n_chunks = (n + 63) // 64, (words + 11) // 12
     transpose_bytes = m * ((n + 3) // 4) + n_blocks * n_chunks * 12 * 64 * 16
-    if use_tc:  # FP8 planes: 4 bytes per padded genotype
-        transpose_bytes = m * ((n + 3) // 4) + ((n + 127) // 128) * 128 * ((m + 31) // 32) * 32 * 4
+    if use_tc:  # operand planes: 4 planes of 1 byte (FP8) or half a byte (FP4) per padded genotype
+        k = 64 if fp4 else 32
+        transpose_bytes = m * ((n + 3) // 4) + ((n + 127) // 128) * 128 * ((m + k - 1) // k) * k * 4 // (2 if fp4 else 1)
     ibs.ibs_shutdown(ctx)
 
     if rank != 0:
@@ -348,12 +354,15 @@ def run_plain(args, rank, world, local):
                                     f"measured live: POPC {probe['popc_per_clk_sm']:.2f}, LOP3 "
                                     f"{probe['lop3_per_clk_sm']:.2f}, IADD3 {probe['iadd3_per_clk_sm']:.2f} /clk/SM"}
                      if not use_tc else
-                     {"bound": "tensor", "achieved": 8.0 * achieved / 1e12, "peak": fp8_tflops, "unit": "TFLOP/s",
-                      "frac": 8.0 * achieved / 1e12 / fp8_tflops,
-                      "traffic": profiled_traffic(f"tc_kernel_{args.workload}.md"),
-                      "kernel": "tc_tri_kernel (tcgen05 FP8 indicator GEMMs)", "kernel_ms": pairs_ms,
-                      "peak_basis": "measured bf16 burst TFLOP/s (MEASURED_PEAKS.json) x 2, the nominal FP8/bf16 ratio; "
-                                    "algorithmic flops = 8 per comparison (4 MACs: VV^T, UU^T, QR^T, RQ^T)"}),
+                     {"bound": "tensor", "achieved": 8.0 * achieved / 1e12, "peak": tc_tflops, "unit": "TFLOP/s",
+                      "frac": 8.0 * achieved / 1e12 / tc_tflops,
+                      "traffic": profiled_traffic(f"tc_kernel_{'fp4' if fp4 else 'fp8'}_{args.workload}.md",
+                                                  ("ibs_tc.cu", "ibs_device.cuh")),
+                      "kernel": f"tc_tri_kernel (tcgen05 {'E2M1 kind::mxf4' if fp4 else 'E4M3 kind::f8f6f4'} "
+                                f"indicator GEMMs)", "kernel_ms": pairs_ms,
+                      "peak_basis": f"measured bf16 burst TFLOP/s (MEASURED_PEAKS.json) x {tc_ratio:.0f}, the nominal "
+                                    f"{'FP4' if fp4 else 'FP8'}/bf16 dense ratio; algorithmic flops = 8 per comparison "
+                                    "(4 MACs: VV^T, UU^T, QR^T, RQ^T)"}),
         "transpose": {"kernel_ms": planes_ms, "bytes": transpose_bytes,
                       "achieved_gbs": transpose_bytes / (planes_ms * 1e-3) / 1e9,
                       "peak_gbs": hbm_peak_gbs(), "frac": transpose_bytes / (planes_ms * 1e-3) / 1e9 / hbm_peak_gbs()},
@@ -491,16 +500,23 @@ def run_batch(args, rank, world, local):
             batched()
             plain_loop()
         torch.cuda.synchronize(dev)
+        batched()
+        launches_b = ibs.ibs_last_launch_info(ctx_b)["launches"]
+        launches_p = 0
+        for s, pk, (c, d) in zip(subs, plain_in, outs_p):
+            ibs.ibs_compute(ctx_p, pk, s.n, s.var_len, c, d, stream)
+            launches_p += ibs.ibs_last_launch_info(ctx_p)["launches"]
+        torch.cuda.synchronize(dev)
         ibs.ibs_kernel_times(ctx_p)  # drop warm-up records
         clk = ClockSampler(local)
         clk.start()
         ms_b = timed(batched, args.steps)
         ms_p = timed(plain_loop, args.steps)
+        kt_p = ibs.ibs_kernel_times(ctx_p)  # the plain loop's kernels only
         ms_pe = timed(plain_loop_from_pool, 1)
         clocks = clk.stop()
         ibs.ibs_synchronize(ctx_b, stream)
         ibs.ibs_synchronize(ctx_p, stream)
-        kt_p = ibs.ibs_kernel_times(ctx_p)
     # exactness: every subset, batched vs plain, bit for bit; sampled pairs vs the oracle
     same = all(torch.equal(a[0], b[0]) and torch.equal(torch.nan_to_num(a[1], nan=-1.0),
                                                         torch.nan_to_num(b[1], nan=-1.0))
@@ -528,7 +544,7 @@ def run_batch(args, rank, world, local):
                                f"(n ~ U[200, 8000], windows ~ U[10k, 200k]), seed 3",
                    "comparisons_per_step": comps, "plan": plan, "first_call_s_incl_autotune": first_call_s,
                    "generation_s": gen_s},
-        "plain_loop": {"value": comps / (mp * 1e-3), "ms_per_step": mp, "launches_per_step": 2 * len(subs),
+        "plain_loop": {"value": comps / (mp * 1e-3), "ms_per_step": mp, "launches_per_step": launches_p,
                        "transpose_ms_per_step": kt_p["planes_ms"] / args.steps,
                        "pair_kernel_ms_per_step": kt_p["pairs_ms"] / args.steps,
                        "finalize_ms_per_step": kt_p["finalize_ms"] / args.steps},
@@ -537,7 +553,7 @@ def run_batch(args, rank, world, local):
         "speedup_vs_plain_loop": mp / mb,
         "speedup_vs_plain_loop_from_pool": ms_pe[0] / mb,
         "exact": {"batched_equals_plain_all_subsets": bool(same), "oracle_sampled_pairs": bool(oracle_ok)},
-        "gpu_launches": int(args.steps * 2),
+        "gpu_launches": int(args.steps * launches_b),
         "clocks": clocks,
     }
 

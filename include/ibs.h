@@ -63,7 +63,11 @@ typedef enum {
 #define IBS_KERNEL_PLAIN 0x10 /* pair loop variant: one POPC per count and 32-marker word */
 #define IBS_KERNEL_CSA 0x20   /* pair loop variant: carry-save reduction of 3 words before POPC */
 #define IBS_TIMING 0x40       /* record CUDA events around each kernel of ibs_compute (ibs_kernel_times) */
-#define IBS_KERNEL_TC 0x80    /* ibs_compute: tensor-core pair counts (tcgen05 FP8 indicator GEMMs, exact) */
+#define IBS_KERNEL_TC 0x80    /* ibs_compute: tensor-core pair counts (tcgen05 indicator GEMMs, exact) */
+#define IBS_TC_FP8 0x100      /* tensor-core form with E4M3 operands (kind::f8f6f4, 32 markers per MMA) */
+#define IBS_TC_FP4 0x200      /* tensor-core form with E2M1 operands (kind::mxf4, unit scales, 64 markers per MMA);
+                                 neither flag: the library default, E2M1 (environment IBS_TC_FORMAT=fp8|fp4
+                                 overrides) */
 
 typedef struct {
   int device;                      /* CUDA device ordinal */
@@ -129,10 +133,14 @@ typedef struct {
 /* Batched all-pairs IBS of many subsets of one pool (paper "Multicore and
  * cluster parallelism": independent pieces of sample x sample matrices).  All
  * subsets' bit planes are built by one gather-transpose launch and all their
- * pair tiles run in ONE persistent launch that takes (subset, tile) work items
- * from a device work list, longest first.  The launch sequence is captured
- * into a CUDA graph per batch shape and replayed; tile splitting is chosen by
- * the autotuner.  pool_packed is DEVICE [pool_m][ceil(pool_n/4)].  Results are
+ * pair tiles run in ONE persistent launch over a (subset, tile, K range) work
+ * list sorted longest first.  The pair kernel follows ibs_compute's choice:
+ * the tensor-core form by default (one more launch expands every subset's bit
+ * planes to FP8 indicator planes, 4 bytes per genotype, held for the call),
+ * the POPC kernels under IBS_KERNEL_PLAIN / IBS_KERNEL_CSA.  The launch
+ * sequence is captured into a CUDA graph per batch shape and replayed; tile
+ * splitting (and, for POPC, the kernel variant) is chosen by the autotuner.
+ * pool_packed is DEVICE [pool_m][ceil(pool_n/4)].  Results are
  * bit-identical to ibs_compute on each subset alone. */
 ibs_status ibs_compute_batch(ibs_ctx* ctx, const uint8_t* pool_packed, int64_t pool_n, int64_t pool_m,
                              const ibs_subset* subsets, int n_subsets, void* stream);
@@ -198,7 +206,9 @@ const char* ibs_last_error(void);
 ibs_status ibs_probe_int_pipes(ibs_ctx* ctx, double out[5]);
 
 /* The largest cached batched-launch plan: out[0] = kernel mode (0 plain,
- * 1 carry-save), out[1] = split policy, out[2] = work items, out[3] = grid. */
+ * 1 carry-save 2 CTAs/SM, 2 carry-save 1 CTA/SM, 3 tensor core E4M3, 4 tensor
+ * core E2M1), out[1] =
+ * split policy, out[2] = work items, out[3] = grid. */
 ibs_status ibs_batch_plan_info(ibs_ctx* ctx, int64_t out[4]);
 
 /* With IBS_TIMING: wait for the recorded events and return the summed device
@@ -206,6 +216,11 @@ ibs_status ibs_batch_plan_info(ibs_ctx* ctx, int64_t out[4]);
  * out[0] = bit-plane transpose, out[1] = pair-count kernel, out[2] = split-K
  * finalisation, out[3] = number of calls.  Resets the sums. */
 ibs_status ibs_kernel_times(ibs_ctx* ctx, double out[4]);
+
+/* The kernels this context's ibs_compute uses: out[0] = pair kernel family
+ * (0 POPC plain, 1 POPC carry-save, 2 tensor core), out[1] = tensor-core
+ * operand format (0 E4M3, 1 E2M1), out[2] = SMs of the device, out[3] = device. */
+ibs_status ibs_kernel_info(ibs_ctx* ctx, int64_t out[4]);
 
 /* Counters of the last ibs_compute / ibs_compute_batch on this context:
  * out[0] = kernel launches enqueued, out[1] = pair tiles, out[2] = K splits. */

@@ -99,7 +99,9 @@ ibs_status check_ctx(ibs_ctx* ctx) {
   return IBS_OK;
 }
 
-constexpr int kFlagTc = 0x80;  // tensor-core (tcgen05 FP8 indicator GEMM) pair counts
+constexpr int kFlagTc = 0x80;     // tensor-core (tcgen05 indicator GEMM) pair counts
+constexpr int kFlagTcFp8 = 0x100;  // tensor-core operands in E4M3
+constexpr int kFlagTcFp4 = 0x200;  // tensor-core operands in E2M1 (block-scaled MMA, unit scales)
 
 // The tensor-core form is the default for ibs_compute; IBS_KERNEL_PLAIN or
 // IBS_KERNEL_CSA select the bit-plane POPC kernels instead.
@@ -107,6 +109,12 @@ bool use_tc(const ibs_ctx* ctx) {
   if (ctx->flags & kFlagTc) return true;
   if (ctx->flags & (kFlagPlain | kFlagCsa)) return false;
   return ctx->default_tc;
+}
+
+int tc_format_for(const ibs_ctx* ctx) {
+  if (ctx->flags & kFlagTcFp4) return kTcFp4;
+  if (ctx->flags & kFlagTcFp8) return kTcFp8;
+  return tc_default_format();
 }
 
 int mode_for(const ibs_ctx* ctx) {
@@ -134,6 +142,7 @@ ibs_status ibs_init(const ibs_config* cfg, ibs_ctx** out_ctx) {
     return fail(IBS_ECUDA, "no CUDA device available (%s)", cudaGetErrorString(e));
   }
   if (c.device < 0 || c.device >= ndev) return fail(IBS_EINVAL, "device %d out of range [0, %d)", c.device, ndev);
+  if ((c.flags & kFlagTcFp8) && (c.flags & kFlagTcFp4)) return fail(IBS_EINVAL, "IBS_TC_FP8 and IBS_TC_FP4 both set");
   DeviceGuard g(c.device);
   cudaDeviceProp prop;
   IBS_CUDA_TRY(cudaGetDeviceProperties(&prop, c.device));
@@ -196,10 +205,11 @@ ibs_status ibs_compute(ibs_ctx* ctx, const uint8_t* packed, int64_t n, int64_t m
   const bool square = (ctx->flags & IBS_OUT_SQUARE) != 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const bool tc = use_tc(ctx);
+  const int fmt = tc_format_for(ctx);
   const PlaneGeom geo = PlaneGeom::make(n, m);
-  if (ibs_status s = ensure_buf(ctx, ctx->planes, tc ? tc_planes_bytes(n, m) : geo.bytes())) return s;
+  if (ibs_status s = ensure_buf(ctx, ctx->planes, tc ? tc_planes_bytes(n, m, fmt) : geo.bytes())) return s;
   const int64_t tiles = tc ? tc_tiles(n) : geo.n_blocks * (geo.n_blocks + 1) / 2;
-  const int splits = tc ? tc_splits_for(tiles, tc_chunks(m), ctx->num_sms)
+  const int splits = tc ? tc_splits_for(tiles, tc_chunks(m, fmt), ctx->num_sms)
                         : tri_splits_for(tiles, geo.n_chunks, ctx->num_sms);
   const int64_t P = n * (n + 1) / 2;
   if (splits > 1) {
@@ -238,9 +248,9 @@ ibs_status ibs_compute(ibs_ctx* ctx, const uint8_t* packed, int64_t n, int64_t m
                                    cudaMemcpyHostToDevice, st));
       ctx->tile_list_T = T;
     }
-    IBS_CUDA_TRY(launch_tc_planes(packed, n, m, static_cast<uint8_t*>(ctx->planes.p), st));
+    IBS_CUDA_TRY(launch_tc_planes(packed, n, m, static_cast<uint8_t*>(ctx->planes.p), fmt, st));
     if (timing) IBS_CUDA_TRY(cudaEventRecord(rec.ev[1], st));
-    IBS_CUDA_TRY(launch_tc_pairs(static_cast<const uint8_t*>(ctx->planes.p), n, m, splits, out_counts, out_dist,
+    IBS_CUDA_TRY(launch_tc_pairs(static_cast<const uint8_t*>(ctx->planes.p), n, m, fmt, splits, out_counts, out_dist,
                                  static_cast<int32_t*>(ctx->partial.p), square, ctx->status_dev,
                                  static_cast<const int2*>(ctx->tile_list.p), st));
   } else {
@@ -327,44 +337,89 @@ struct SubsetShape {
   PlaneGeom g;
 };
 
+// Batched modes: 0 = plain POPC, 1 = carry-save POPC (2 CTAs/SM), 2 = carry-save
+// (1 CTA/SM), 3 + fmt = tensor core (indicator GEMMs, 128-sample tiles) with
+// operand format fmt (kTcFp8 / kTcFp4).
+constexpr int kBatchModeTc = 3;
+bool is_tc_mode(int mode) { return mode >= kBatchModeTc; }
+int tc_fmt_of(int mode) { return mode - kBatchModeTc; }
+constexpr int kTcBatchGroup = 16;  // tile rows per band of the grouped order
+
+// Tile grid of one subset in the units of the pair kernel of `mode`: blocks
+// per side and K chunks.
+struct ItemGeom {
+  int64_t T, nc;
+};
+ItemGeom item_geom(const SubsetShape& s, int mode) {
+  if (is_tc_mode(mode)) return {(s.n + 127) / 128, tc_chunks(s.m, tc_fmt_of(mode))};
+  return {s.g.n_blocks, s.g.n_chunks};
+}
+
 // Build the work list for a batch: every (subset, tile) item, K-split for
 // subsets whose tiles would be too large relative to one CTA's fair share
 // (split_policy 1), sorted by descending cost (longest processing time first).
-void build_items(const std::vector<SubsetShape>& shapes, int split_policy, int grid, std::vector<WorkItem>& items,
-                 std::vector<int>& subset_split, int64_t& tiles_total) {
+void build_items(const std::vector<SubsetShape>& shapes, int mode, int split_policy, int grid,
+                 std::vector<WorkItem>& items, std::vector<int>& subset_split, int64_t& tiles_total) {
   items.clear();
   subset_split.assign(shapes.size(), 1);
   double total = 0;
   tiles_total = 0;
   for (const auto& s : shapes) {
-    const int64_t T = s.g.n_blocks;
-    total += (double)(T * (T + 1) / 2) * (double)s.g.n_chunks;
-    tiles_total += T * (T + 1) / 2;
+    const ItemGeom ig = item_geom(s, mode);
+    total += (double)(ig.T * (ig.T + 1) / 2) * (double)ig.nc;
+    tiles_total += ig.T * (ig.T + 1) / 2;
   }
   const double share = total / std::max(1, grid);
   for (size_t k = 0; k < shapes.size(); ++k) {
-    const auto& s = shapes[k];
+    const ItemGeom ig = item_geom(shapes[k], mode);
     if (split_policy == 1) {
-      const double item = (double)s.g.n_chunks;
+      const double item = (double)ig.nc;
       // aim for items no larger than a quarter of a CTA's fair share
       int pieces = (int)std::ceil(item / std::max(1.0, share / 4.0));
-      pieces = std::max(1, std::min<int>(pieces, (int)std::min<int64_t>(s.g.n_chunks, 64)));
+      pieces = std::max(1, std::min<int>(pieces, (int)std::min<int64_t>(ig.nc, 64)));
       subset_split[k] = pieces;
     }
   }
+  if (is_tc_mode(mode)) {
+    // Claimed in list order by whichever CTA is free: subsets by decreasing
+    // tile cost, each subset's tiles in the grouped order, so the CTAs
+    // running at one time share row and column blocks through L2.
+    std::vector<size_t> order(shapes.size());
+    for (size_t k = 0; k < order.size(); ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+      return item_geom(shapes[a], mode).nc > item_geom(shapes[b], mode).nc;
+    });
+    std::vector<int2> tiles;
+    for (size_t k : order) {
+      const ItemGeom ig = item_geom(shapes[k], mode);
+      const int pieces = subset_split[k];
+      tc_tile_order(ig.T, kTcBatchGroup, tiles);
+      for (const int2& t : tiles)
+        for (int p = 0; p < pieces; ++p) {
+          WorkItem w;
+          w.subset = (int32_t)k;
+          w.I = t.x;
+          w.J = t.y;
+          w.c0 = (int32_t)(ig.nc * p / pieces);
+          w.c1 = (int32_t)(ig.nc * (p + 1) / pieces);
+          w.split = pieces > 1 ? 1 : 0;
+          items.push_back(w);
+        }
+    }
+    return;
+  }
   for (size_t k = 0; k < shapes.size(); ++k) {
-    const auto& s = shapes[k];
-    const int64_t T = s.g.n_blocks;
+    const ItemGeom ig = item_geom(shapes[k], mode);
     const int pieces = subset_split[k];
-    for (int64_t I = 0; I < T; ++I)
-      for (int64_t J = I; J < T; ++J)
+    for (int64_t I = 0; I < ig.T; ++I)
+      for (int64_t J = I; J < ig.T; ++J)
         for (int p = 0; p < pieces; ++p) {
           WorkItem w;
           w.subset = (int32_t)k;
           w.I = (int32_t)I;
           w.J = (int32_t)J;
-          w.c0 = (int32_t)(s.g.n_chunks * p / pieces);
-          w.c1 = (int32_t)(s.g.n_chunks * (p + 1) / pieces);
+          w.c0 = (int32_t)(ig.nc * p / pieces);
+          w.c1 = (int32_t)(ig.nc * (p + 1) / pieces);
           w.split = pieces > 1 ? 1 : 0;
           items.push_back(w);
         }
@@ -394,10 +449,11 @@ ibs_status plan_build(ibs_ctx* ctx, BatchPlan& plan, const std::vector<SubsetSha
                       int split_policy) {
   plan.mode = mode;
   plan.split_policy = split_policy;
-  plan.grid = ctx->num_sms * pair_kernel_ctas_per_sm(mode);
+  const bool tc = is_tc_mode(mode);
+  plan.grid = ctx->num_sms * (tc ? 1 : pair_kernel_ctas_per_sm(mode));
   std::vector<WorkItem> items;
   std::vector<int> split;
-  build_items(shapes, split_policy, plan.grid, items, split, plan.tiles);
+  build_items(shapes, mode, split_policy, plan.grid, items, split, plan.tiles);
   plan.n_items = (int64_t)items.size();
   if (plan.grid > plan.n_items) plan.grid = (int)std::max<int64_t>(1, plan.n_items);
   // planes and partial offsets
@@ -420,6 +476,20 @@ ibs_status plan_build(ibs_ctx* ctx, BatchPlan& plan, const std::vector<SubsetSha
   plan.n_split = (int)split_ids.size();
   plan.total_ctas = 0;
   for (const auto& s : shapes) plan.total_ctas += s.g.n_chunks * ((s.g.n_blocks + 1) / 2);
+  if (tc) {
+    size_t tb = 0;
+    plan.tc_offsets.resize(shapes.size());
+    plan.tc_ctas = 0;
+    for (size_t k = 0; k < shapes.size(); ++k) {
+      plan.tc_offsets[k] = (int64_t)tb;
+      tb += (tc_planes_bytes(shapes[k].n, shapes[k].m, tc_fmt_of(mode)) + 1023) / 1024 * 1024;
+      const ItemGeom ig = item_geom(shapes[k], mode);
+      plan.tc_ctas += ig.T * ig.nc;
+    }
+    if (plan.tc_ctas > 2147483647LL) return fail(IBS_EINVAL, "batch too large for one expansion launch");
+    if (ibs_status s = ensure_buf(ctx, plan.tc_planes, tb)) return s;
+    if (ibs_status s = ensure_buf(ctx, plan.tc_jobs, sizeof(TcExpandJob) * shapes.size())) return s;
+  }
   if (ibs_status s = ensure_buf(ctx, plan.planes, pb)) return s;
   if (ibs_status s = ensure_buf(ctx, plan.partial, qb)) return s;
   if (ibs_status s = ensure_buf(ctx, plan.subsets, sizeof(SubsetDev) * shapes.size())) return s;
@@ -468,6 +538,27 @@ ibs_status plan_upload(ibs_ctx* ctx, BatchPlan& plan, const uint8_t* pool, int64
     jobs[i].cta_begin = cta;
     cta += shapes[i].g.n_chunks * jobs[i].groups;
   }
+  if (is_tc_mode(plan.mode)) {
+    // the pair kernel reads operand planes, in 128-sample blocks and MMA-K chunks
+    std::vector<TcExpandJob> tj(k);
+    int64_t tcta = 0;
+    for (size_t i = 0; i < k; ++i) {
+      const ItemGeom ig = item_geom(shapes[i], plan.mode);
+      uint8_t* tcp = static_cast<uint8_t*>(plan.tc_planes.p) + plan.tc_offsets[i];
+      sd[i].planes = reinterpret_cast<const uint32_t*>(tcp);
+      sd[i].n_blocks = ig.T;
+      sd[i].n_chunks = ig.nc;
+      tj[i].bits = jobs[i].planes;
+      tj[i].bit_chunks = shapes[i].g.n_chunks;
+      tj[i].tc = tcp;
+      tj[i].n = shapes[i].n;
+      tj[i].nb = ig.T;
+      tj[i].nc = ig.nc;
+      tj[i].cta_begin = tcta;
+      tcta += ig.T * ig.nc;
+    }
+    IBS_CUDA_TRY(cudaMemcpyAsync(plan.tc_jobs.p, tj.data(), sizeof(TcExpandJob) * k, cudaMemcpyHostToDevice, st));
+  }
   // Pageable sources: the copy is staged before return, so the vectors may go.
   IBS_CUDA_TRY(cudaMemcpyAsync(plan.subsets.p, sd.data(), sizeof(SubsetDev) * k, cudaMemcpyHostToDevice, st));
   IBS_CUDA_TRY(cudaMemcpyAsync(plan.jobs.p, jobs.data(), sizeof(PlaneJob) * k, cudaMemcpyHostToDevice, st));
@@ -480,9 +571,17 @@ ibs_status plan_enqueue(ibs_ctx* ctx, BatchPlan& plan, int n_subsets, cudaStream
   if (plan.n_split > 0) IBS_CUDA_TRY(cudaMemsetAsync(plan.partial.p, 0, plan.partial.cap, st));
   IBS_CUDA_TRY(launch_planes_batch(static_cast<const PlaneJob*>(plan.jobs.p), n_subsets, plan.total_ctas,
                                    ctx->status_dev, st));
-  IBS_CUDA_TRY(launch_batch(plan.mode, static_cast<const SubsetDev*>(plan.subsets.p),
-                            static_cast<const WorkItem*>(plan.items.p), plan.n_items,
-                            static_cast<int*>(plan.counter.p), ctx->status_dev, plan.grid, st));
+  if (is_tc_mode(plan.mode)) {
+    const int fmt = tc_fmt_of(plan.mode);
+    IBS_CUDA_TRY(launch_tc_expand(static_cast<const TcExpandJob*>(plan.tc_jobs.p), n_subsets, plan.tc_ctas, fmt, st));
+    IBS_CUDA_TRY(launch_tc_batch(static_cast<const SubsetDev*>(plan.subsets.p),
+                                 static_cast<const WorkItem*>(plan.items.p), plan.n_items, plan.grid, fmt,
+                                 static_cast<int*>(plan.counter.p), ctx->status_dev, st));
+  } else {
+    IBS_CUDA_TRY(launch_batch(plan.mode, static_cast<const SubsetDev*>(plan.subsets.p),
+                              static_cast<const WorkItem*>(plan.items.p), plan.n_items,
+                              static_cast<int*>(plan.counter.p), ctx->status_dev, plan.grid, st));
+  }
   if (plan.n_split > 0)
     IBS_CUDA_TRY(launch_finalize_batch(static_cast<const SubsetDev*>(plan.subsets.p),
                                        static_cast<const int32_t*>(plan.split_ids.p), plan.n_split,
@@ -496,7 +595,7 @@ void plan_free(ibs_ctx* ctx, BatchPlan& plan) {
   plan.exec = nullptr;
   plan.graph = nullptr;
   for (DevBuf* b : {&plan.planes, &plan.partial, &plan.subsets, &plan.jobs, &plan.items, &plan.split_ids,
-                    &plan.counter})
+                    &plan.counter, &plan.tc_planes, &plan.tc_jobs})
     free_buf(ctx, *b);
 }
 
@@ -538,22 +637,30 @@ extern "C" ibs_status ibs_compute_batch(ibs_ctx* ctx, const uint8_t* pool, int64
     key.push_back(s.var_len);
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int forced = (ctx->flags & kFlagPlain) ? 0 : ((ctx->flags & kFlagCsa) ? 1 : -1);
+  // Kernel family: the tensor-core form unless a POPC kernel is asked for (by
+  // flag, or by the context's default); within POPC, a flag fixes the mode.
+  const bool tc = use_tc(ctx);
+  const int forced = tc                          ? kBatchModeTc + tc_format_for(ctx)
+                     : (ctx->flags & kFlagPlain) ? 0
+                     : (ctx->flags & kFlagCsa)   ? 1
+                                                 : -1;
   key.push_back(forced);
+  key.push_back(tc ? 1 : 0);
 
   auto it = ctx->plans.find(key);
   if (it == ctx->plans.end()) {
     // Choose mode and split policy: cached tuning result, or measure the candidates now.
-    const std::string tk = tune_key(ctx, shapes);
-    int mode = forced >= 0 ? forced : ctx->default_mode, policy = 0;
+    const std::string tk = tune_key(ctx, shapes) + (tc ? "_tc" : "");
+    int mode = forced >= 0 ? forced : (tc ? kBatchModeTc : ctx->default_mode), policy = 0;
     auto te = ctx->tune.find(tk);
     if (te != ctx->tune.end()) {
       if (forced < 0) mode = te->second.mode;
       policy = te->second.split_policy;
     } else if (!getenv("IBS_NO_AUTOTUNE")) {
       double best = 1e30;
-      for (int cm = 0; cm < 3; ++cm) {
+      for (int cm = 0; cm <= kBatchModeTc + kTcFp4; ++cm) {
         if (forced >= 0 && cm != forced) continue;
+        if (is_tc_mode(cm) != tc) continue;
         for (int cp = 0; cp < 2; ++cp) {
           BatchPlan trial;
           if (ibs_status s = plan_build(ctx, trial, shapes, cm, cp)) {
@@ -621,9 +728,20 @@ extern "C" ibs_status ibs_compute_batch(ibs_ctx* ctx, const uint8_t* pool, int64
   BatchPlan& plan = *it->second;
   if (ibs_status s = plan_upload(ctx, plan, pool, pool_n, subs, shapes, st)) return s;
   IBS_CUDA_TRY(cudaGraphLaunch(plan.exec, st));
-  ctx->last_info[0] = 3 + (plan.n_split > 0 ? 1 : 0);
+  ctx->last_info[0] = (is_tc_mode(plan.mode) ? 4 : 3) + (plan.n_split > 0 ? 1 : 0);
   ctx->last_info[1] = plan.tiles;
   ctx->last_info[2] = plan.split_policy;
+  return IBS_OK;
+}
+
+extern "C" ibs_status ibs_kernel_info(ibs_ctx* ctx, int64_t out[4]) {
+  clear_error();
+  if (ibs_status s = check_ctx(ctx)) return s;
+  if (!out) return fail(IBS_EINVAL, "out is NULL");
+  out[0] = use_tc(ctx) ? 2 : mode_for(ctx) == 0 ? 0 : 1;
+  out[1] = tc_format_for(ctx);
+  out[2] = ctx->num_sms;
+  out[3] = ctx->device;
   return IBS_OK;
 }
 

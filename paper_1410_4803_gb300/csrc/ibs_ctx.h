@@ -51,10 +51,12 @@ class ServeEngine;
 struct BatchPlan {
   std::vector<int64_t> shape_key;
   DevBuf planes, partial, subsets, jobs, items, split_ids, counter;
-  int64_t n_items = 0, total_ctas = 0, max_split_pairs = 0;
+  DevBuf tc_planes, tc_jobs;            // mode 3: FP8 planes and their expansion jobs
+  int64_t n_items = 0, total_ctas = 0, max_split_pairs = 0, tc_ctas = 0;
   int n_split = 0;
   int mode = 0, split_policy = 0, grid = 0;
   std::vector<int64_t> plane_offsets;   // bytes into planes
+  std::vector<int64_t> tc_offsets;      // bytes into tc_planes (mode 3)
   std::vector<int64_t> partial_offsets; // bytes into partial, -1 if not split
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;

@@ -112,16 +112,36 @@ cudaError_t launch_topk(const int32_t* counts, int64_t q, int64_t n_panel, int k
                         double* out_dist, cudaStream_t st);
 int pair_kernel_ctas_per_sm(int mode);
 
-// Tensor-core form (ibs_tc.cu): FP8 indicator planes and tcgen05 pair tiles.
-size_t tc_planes_bytes(int64_t n, int64_t m);
+// Expansion of one subset's bit planes into its FP8 planes.
+struct TcExpandJob {
+  const uint32_t* bits;   // bit planes (64-sample blocks, 12-word chunks)
+  int64_t bit_chunks;     // 12-word chunks of the bit planes
+  uint8_t* tc;            // FP8 planes
+  int64_t n, nb, nc;
+  int64_t cta_begin;      // first CTA of this job in the flattened grid
+};
+
+// Tensor-core form (ibs_tc.cu): indicator planes and tcgen05 pair tiles, in
+// one of two operand formats.
+constexpr int kTcFp8 = 0;  // E4M3, kind::f8f6f4, 32 markers per chunk
+constexpr int kTcFp4 = 1;  // E2M1, kind::mxf4 with unit scale factors, 64 markers per chunk
+int tc_default_format();   // IBS_TC_FORMAT=fp4|fp8, else the built-in default
+size_t tc_planes_bytes(int64_t n, int64_t m, int fmt);
 int tc_splits_for(int64_t tiles, int64_t n_chunks, int num_sms);
 int64_t tc_tiles(int64_t n);
-int64_t tc_chunks(int64_t m);
-cudaError_t launch_tc_planes(const uint8_t* packed, int64_t n, int64_t m, uint8_t* planes, cudaStream_t st);
-cudaError_t launch_tc_pairs(const uint8_t* planes, int64_t n, int64_t m, int splits, int32_t* out_counts,
+int64_t tc_chunks(int64_t m, int fmt);
+cudaError_t launch_tc_planes(const uint8_t* packed, int64_t n, int64_t m, uint8_t* planes, int fmt,
+                             cudaStream_t st);
+cudaError_t launch_tc_pairs(const uint8_t* planes, int64_t n, int64_t m, int fmt, int splits, int32_t* out_counts,
                             double* out_dist, int32_t* partial, bool square, int* status, const int2* tile_list,
                             cudaStream_t st);
 void tc_tile_order(int64_t T, int G, std::vector<int2>& out);
+cudaError_t launch_tc_expand(const TcExpandJob* jobs_dev, int n_jobs, int64_t total_ctas, int fmt, cudaStream_t st);
+// Batched tensor-core pairs: SubsetDev.planes holds operand planes, n_blocks and
+// n_chunks count 128-sample blocks and chunks, and WorkItem tiles and K ranges
+// are in those units.
+cudaError_t launch_tc_batch(const SubsetDev* subs, const WorkItem* items, int64_t n_items, int grid, int fmt,
+                            int* counter, int* status, cudaStream_t st);
 size_t pair_kernel_smem_bytes();
 
 // Integer-pipe microbenchmark (ibs_probe.cu).

@@ -1,4 +1,4 @@
-// Tensor-core form of the pair counts (tcgen05, FP8 indicator GEMMs).
+// Tensor-core form of the pair counts (tcgen05 indicator GEMMs).
 //
 // The per-marker rule of the paper ("Improvements in PLINK 1.9 / Bitwise
 // parallelism") is bilinear in one-hot indicators of the genotype codes, so the
@@ -11,27 +11,35 @@
 //   UU^T  = IBS2 + IBS0 - IBS1     (hom-hom and het-het pairs +1, hom-het -1)
 //   IBS0  = Q R^T + R Q^T          (opposite homozygotes)
 // so IBS1 = (N - UU^T) / 2 and IBS2 = N - IBS0 - IBS1.  The values -1, 0, +1
-// are exact in FP8 (E4M3), every product is exact, and every partial sum is an
-// integer of magnitude at most the marker count, far below 2^24, so FP32
-// accumulation is exact.  Four 128 x 128 x 32 MMAs per 32 markers.
+// are exact in every float format used here, every product is exact, and every
+// partial sum is an integer of magnitude at most the marker count, far below
+// 2^24, so FP32 accumulation is exact.  Four 128 x 128 MMAs per marker chunk.
 //
-// Layout: one (128-sample block, 32-marker chunk) is 4 planes x 4 KiB, each
-// plane a 128 x 32 byte tile in the tensor core's canonical K-major layout
-// without swizzle: 8-row x 16-byte core matrices, the two core matrices of a
-// row group 128 bytes apart (leading byte offset) and row groups 256 bytes
-// apart (stride byte offset).  A CTA computes one 128 x 128 tile of pairs:
-// warp 0 streams chunks of the row and column blocks through a 4-stage
-// shared-memory ring with TMA bulk copies, warp 1 issues the MMAs into three
-// FP32 accumulators in tensor memory (columns 0, 128, 256) and frees each
-// stage with tcgen05.commit, and after the last chunk all four warps read the
-// accumulators back (tcgen05.ld), decode the counts and store them.  Warp 0
-// (copies) and warp 1 (MMAs) run their loops with all 32 lanes in step and
-// one lane issuing, so no lane of theirs is parked in another wait.
+// Two operand formats share everything but the MMA kind and the packing:
+//   FP8  E4M3, kind::f8f6f4, one byte per indicator, 32 markers per chunk;
+//   FP4  E2M1, kind::mxf4 with block scale factors all 1.0 (UE8M0 127, held in
+//        tensor memory), two indicators per byte, 64 markers per chunk.
+// Either way one (128-sample block, chunk) is 4 planes x 4 KiB, each plane a
+// 128-row x 32-byte tile in the tensor core's canonical K-major layout without
+// swizzle: 8-row x 16-byte core matrices, the two core matrices of a row group
+// 128 bytes apart (leading byte offset) and row groups 256 bytes apart (stride
+// byte offset).  FP4 thus moves half the bytes per marker.
+//
+// A CTA computes one 128 x 128 tile of pairs: warp 0 streams chunks of the row
+// and column blocks through a 4-stage shared-memory ring with TMA bulk copies,
+// warp 1 issues the MMAs into three FP32 accumulators in tensor memory
+// (columns 0, 128, 256) and frees each stage with tcgen05.commit, and after
+// the last chunk all four warps read the accumulators back (tcgen05.ld),
+// decode the counts and store them.  Warp 0 (copies) and warp 1 (MMAs) run
+// their loops with all 32 lanes in step and one lane issuing, so no lane of
+// theirs is parked in another wait.
 //
 // Every wait is bounded (2 s of %globaltimer); on expiry the status word is
 // set, and the CTA still waits (bounded) for its MMAs and frees its tensor
 // memory before returning.
+#include <algorithm>
 #include <cstdlib>
+#include <cstring>
 #include <vector>
 
 #include "ibs_device.cuh"
@@ -42,14 +50,19 @@ namespace ibs {
 namespace {
 
 constexpr int kTB = 128;                          // samples per block (tile edge)
-constexpr int kTK = 32;                           // markers per chunk (one MMA K step)
 constexpr int kTPlanes = 4;                       // V, U, Q, R
-constexpr int kTileBytes = kTB * kTK;             // one plane of one chunk: 4 KiB
+constexpr int kTileBytes = kTB * 32;              // one plane of one chunk: 128 rows x 32 bytes
 constexpr int kTChunkBytes = kTPlanes * kTileBytes;  // 16 KiB per (block, chunk)
 constexpr int kTThreads = 128;
-constexpr size_t tc_smem(int stages) { return (size_t)stages * 2 * kTChunkBytes + 1024; }
-constexpr uint32_t kTmemCols = 512;               // 3 x 128 used
-constexpr uint8_t kFp8One = 0x38, kFp8MinusOne = 0xB8;
+constexpr int kTStages = 4;
+constexpr size_t kTcSmem = (size_t)kTStages * 2 * kTChunkBytes + 1024;
+constexpr uint32_t kTmemCols = 512;               // accumulators at 0/128/256, FP4 scale factors at 384..511
+constexpr uint32_t kSfCol = 384;                  // scale factors of A at 384, of B at 448
+constexpr uint8_t kFp8One = 0x38;                 // E4M3 1.0 (sign bit 0x80 makes -1.0)
+
+// markers per chunk: one MMA K step
+template <int F>
+constexpr int kMarkers = F == kTcFp4 ? 64 : 32;
 
 __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
   uint64_t d = 0;
@@ -60,16 +73,59 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
   return d;                          // no swizzle
 }
 
-// E4M3 x E4M3 -> F32, K-major A and B, N = 128, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(128 >> 3) << 17) |
-                            ((uint32_t)(128 >> 4) << 24);
+// E4M3 x E4M3 -> F32, K-major A and B, N = 128, M = 128: D format F32 (bit
+// 4), A and B formats E4M3 (0), N >> 3 at bit 17, M >> 4 at bit 24.
+constexpr uint32_t kIdescFp8 = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(128 >> 3) << 17) |
+                               ((uint32_t)(128 >> 4) << 24);
+// Block-scaled E2M1 x E2M1 -> F32 (kind::mxf4), K-major, N = 128, M = 128:
+// scale-factor ids 0 (bits 4 and 29), A and B formats E2M1 (1 at bits 7 and
+// 10), N >> 3 at bit 17, scale format UE8M0 (bit 23), M >> 4 at bit 24, K = 64.
+constexpr uint32_t kIdescFp4 = (1u << 7) | (1u << 10) | ((uint32_t)(128 >> 3) << 17) | (1u << 23) |
+                               ((uint32_t)(128 >> 4) << 24);
 
-__device__ __forceinline__ void umma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
-      : "memory");
+template <int F>
+__device__ __forceinline__ void umma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc, uint32_t sf) {
+  if constexpr (F == kTcFp4) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%5], [%6], p;\n\t}" ::"r"(
+            tmem),
+        "l"(a), "l"(b), "r"(kIdescFp4), "r"(acc), "r"(sf), "r"(sf + 64u)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(kIdescFp8), "r"(acc)
+        : "memory");
+  }
+}
+
+// The four MMAs of one chunk: V V^T, U U^T, Q R^T + R Q^T.
+template <int F>
+__device__ __forceinline__ void chunk_mmas(uint32_t tmem, uint32_t a0, uint32_t b0, uint32_t acc) {
+  const uint32_t sf = tmem + kSfCol;
+  umma<F>(tmem + 0, umma_desc(a0 + 0 * kTileBytes), umma_desc(b0 + 0 * kTileBytes), acc, sf);    // V V^T
+  umma<F>(tmem + 128, umma_desc(a0 + 1 * kTileBytes), umma_desc(b0 + 1 * kTileBytes), acc, sf);  // U U^T
+  umma<F>(tmem + 256, umma_desc(a0 + 2 * kTileBytes), umma_desc(b0 + 3 * kTileBytes), acc, sf);  // Q R^T
+  umma<F>(tmem + 256, umma_desc(a0 + 3 * kTileBytes), umma_desc(b0 + 2 * kTileBytes), 1u, sf);   // + R Q^T
+}
+
+// FP4: every scale factor the MMAs can read is 1.0.  The calling warp fills
+// its 32 TMEM lanes (quarter = warp % 4) at columns 384..511 with UE8M0 127
+// bytes, so the factors read are 1.0 whichever byte and column of that range
+// the hardware picks for a row.
+__device__ __forceinline__ void tmem_fill_unit_scales(uint32_t tmem, int quarter) {
+  const uint32_t base = tmem + ((uint32_t)(quarter * 32) << 16) + kSfCol;
+  const uint32_t one = 0x7F7F7F7Fu;
+#pragma unroll
+  for (int c = 0; c < 128; c += 32)
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,"
+        "%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(base + c),
+        "r"(one)
+        : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
@@ -88,21 +144,63 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
       : "r"(taddr));
 }
 
-// Byte offset of (sample row r, marker k) inside one 128 x 32 canonical tile.
+// Byte offset of (sample row r, byte column k) inside one 128 x 32-byte
+// canonical tile (FP8: k is the marker; FP4: marker pair k holds markers 2k, 2k+1).
 __device__ __forceinline__ int tile_off(int r, int k) {
   return (r >> 3) * 256 + (k >> 4) * 128 + (r & 7) * 16 + (k & 15);
 }
 
 // ---------------------------------------------------------------------------
-// Transpose: packed .bed rows -> FP8 planes.  CTA = (chunk c of 32 markers,
-// block b of 128 samples), 8 warps of 16 samples.  Lane t of a warp holds one
-// 32-bit word of .bed row t (its 16 samples' 2-bit codes); a 32 x 32 bit
-// transpose by warp shuffles leaves lane 2k with the low code bits and lane
-// 2k+1 with the high code bits of sample k at the 32 markers.  After one
-// exchange each lane of the pair has both words; lane 2k writes markers 0..15
-// and lane 2k+1 markers 16..31 of the sample's four FP8 plane rows.  Bits
-// become bytes with a multiply: (x * 0x204081) & 0x01010101 spreads 4 bits
-// to 4 bytes, and a second multiply turns each 1 into the FP8 value.
+// Indicator bits -> operand bytes.  FP8: 4 bits become 4 bytes with a
+// multiply, (x * 0x204081) & 0x01010101, and a second multiply makes each 1
+// the E4M3 value.  FP4: 8 bits become 8 nibbles (bit t to bit 4t) by three
+// shift-or-mask steps; E2M1 1.0 is 0b0010 and -1.0 is 0b1010.
+__device__ __forceinline__ uint32_t spread4(uint32_t x) { return (x * 0x00204081u) & 0x01010101u; }
+
+__device__ __forceinline__ uint32_t nib8(uint32_t x) {
+  x &= 0xFFu;
+  x = (x | (x << 12)) & 0x000F000Fu;
+  x = (x | (x << 6)) & 0x03030303u;
+  x = (x | (x << 3)) & 0x11111111u;
+  return x;
+}
+
+// Store one row's 16 bytes of each plane at `base` (the row's place in the
+// chunk's V plane).  FP8: vb..rb hold 16 markers (bits 0..15); FP4: 32.
+template <int F>
+__device__ __forceinline__ void store_plane_row(uint8_t* base, uint32_t vb, uint32_t pb, uint32_t qb, uint32_t rb) {
+  uint32_t wv[4], wu[4], wq[4], wr[4];
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    if constexpr (F == kTcFp4) {
+      const uint32_t sv = nib8(vb >> (8 * g)), sp = nib8(pb >> (8 * g));
+      wv[g] = sv << 1;
+      wu[g] = (sv << 1) | (sp << 3);  // heterozygous: sign bit -> -1
+      wq[g] = nib8(qb >> (8 * g)) << 1;
+      wr[g] = nib8(rb >> (8 * g)) << 1;
+    } else {
+      const uint32_t sv = spread4((vb >> (4 * g)) & 0xFu), sp = spread4((pb >> (4 * g)) & 0xFu);
+      wv[g] = sv * kFp8One;
+      wu[g] = sv * kFp8One | sp * 0x80u;  // heterozygous: sign bit -> -1
+      wq[g] = spread4((qb >> (4 * g)) & 0xFu) * kFp8One;
+      wr[g] = spread4((rb >> (4 * g)) & 0xFu) * kFp8One;
+    }
+  }
+  *reinterpret_cast<uint4*>(base + 0 * kTileBytes) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+  *reinterpret_cast<uint4*>(base + 1 * kTileBytes) = make_uint4(wu[0], wu[1], wu[2], wu[3]);
+  *reinterpret_cast<uint4*>(base + 2 * kTileBytes) = make_uint4(wq[0], wq[1], wq[2], wq[3]);
+  *reinterpret_cast<uint4*>(base + 3 * kTileBytes) = make_uint4(wr[0], wr[1], wr[2], wr[3]);
+}
+
+// Transpose: packed .bed rows -> operand planes.  CTA = (chunk c, block b of
+// 128 samples), 8 warps of 16 samples.  Lane t of a warp holds one 32-bit word
+// of .bed row t of each 32-marker group of the chunk (its 16 samples' 2-bit
+// codes); a 32 x 32 bit transpose by warp shuffles leaves lane 2k with the low
+// code bits and lane 2k+1 with the high code bits of sample k at those 32
+// markers.  One exchange with the neighbour lane then gives each lane both
+// bits of its part of the row: FP8, lane 2k markers 0..15 and lane 2k+1
+// markers 16..31; FP4 (two groups), lane 2k markers 0..31 and lane 2k+1
+// markers 32..63.  Each lane writes 16 bytes of each of the sample's planes.
 __device__ __forceinline__ uint32_t tc_transpose32(uint32_t x, int lane) {
   constexpr uint32_t kMask[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
 #pragma unroll
@@ -115,63 +213,66 @@ __device__ __forceinline__ uint32_t tc_transpose32(uint32_t x, int lane) {
   return x;
 }
 
-__device__ __forceinline__ uint32_t spread4(uint32_t x) { return (x * 0x00204081u) & 0x01010101u; }
-
+template <int F>
 __global__ void __launch_bounds__(256) tc_planes_kernel(const uint8_t* __restrict__ packed, int64_t row_bytes,
                                                         int64_t n, int64_t m, uint8_t* __restrict__ planes,
                                                         int64_t n_chunks) {
+  constexpr int kGroups = kMarkers<F> / 32;
   const int64_t c = blockIdx.x, b = blockIdx.y;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t marker = c * kTK + lane;
   const int64_t s0 = b * kTB + warp * 16;  // first sample of this warp
   const int64_t byte0 = s0 >> 2;           // 4 bytes = 16 samples
-  uint32_t x = 0x55555555u;                // "missing" for every slot
-  if (marker < m && s0 < n) {
-    const uint8_t* row = packed + marker * row_bytes;
-    if (row_bytes % 4 == 0 && (reinterpret_cast<uintptr_t>(packed) & 3) == 0 && byte0 + 4 <= row_bytes) {
-      x = __ldg(reinterpret_cast<const uint32_t*>(row + byte0));
-    } else {
-      x = 0;
+  const bool fast = row_bytes % 4 == 0 && (reinterpret_cast<uintptr_t>(packed) & 3) == 0 && byte0 + 4 <= row_bytes;
+  uint32_t x[kGroups];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) x |= (uint32_t)(byte0 + q < row_bytes ? __ldg(row + byte0 + q) : 0x55u) << (8 * q);
+  for (int g = 0; g < kGroups; ++g) {
+    const int64_t marker = c * kMarkers<F> + 32 * g + lane;
+    uint32_t v = 0x55555555u;  // "missing" for every slot
+    if (marker < m && s0 < n) {
+      const uint8_t* row = packed + marker * row_bytes;
+      if (fast) {
+        v = __ldg(reinterpret_cast<const uint32_t*>(row + byte0));
+      } else {
+        v = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v |= (uint32_t)(byte0 + q < row_bytes ? __ldg(row + byte0 + q) : 0x55u) << (8 * q);
+      }
     }
+    x[g] = tc_transpose32(v, lane);
   }
-  x = tc_transpose32(x, lane);
-  const uint32_t partner = __shfl_xor_sync(0xffffffffu, x, 1);
   const bool odd = (lane & 1) != 0;
-  const uint32_t H = odd ? x : partner, L = odd ? partner : x;
+  uint32_t h, l, mask;
+  if constexpr (F == kTcFp4) {
+    // even lanes hold L of both groups, odd lanes H: swap L1 against H0
+    const uint32_t partner = __shfl_xor_sync(0xffffffffu, odd ? x[0] : x[kGroups - 1], 1);
+    h = odd ? x[kGroups - 1] : partner;
+    l = odd ? partner : x[0];
+    mask = 0xFFFFFFFFu;
+  } else {
+    const uint32_t partner = __shfl_xor_sync(0xffffffffu, x[0], 1);
+    const uint32_t H = odd ? x[0] : partner, L = odd ? partner : x[0];
+    const int sh = odd ? 16 : 0;
+    h = (H >> sh) & 0xFFFFu;
+    l = (L >> sh) & 0xFFFFu;
+    mask = 0xFFFFu;
+  }
   const int r = warp * 16 + (lane >> 1);  // row inside the 128-sample block
   const bool valid = b * kTB + r < n;
-  // this lane's 16 markers: bits 0..15 (even lane) or 16..31 (odd lane)
-  const int sh = odd ? 16 : 0;
-  const uint32_t h = (H >> sh) & 0xFFFFu, l = (L >> sh) & 0xFFFFu;
-  const uint32_t vb = valid ? (h | ~l) & 0xFFFFu : 0u;  // present
-  const uint32_t pb = vb & h & ~l;                       // het
-  const uint32_t qb = vb & h & l;                        // hom A2
-  const uint32_t rb = vb & ~h & ~l;                      // hom A1
-  uint32_t wv[4], wu[4], wq[4], wr[4];
-#pragma unroll
-  for (int g = 0; g < 4; ++g) {
-    const uint32_t sv = spread4((vb >> (4 * g)) & 0xFu), sp = spread4((pb >> (4 * g)) & 0xFu);
-    wv[g] = sv * kFp8One;
-    wu[g] = sv * kFp8One | sp * 0x80u;  // heterozygous: sign bit -> -1
-    wq[g] = spread4((qb >> (4 * g)) & 0xFu) * kFp8One;
-    wr[g] = spread4((rb >> (4 * g)) & 0xFu) * kFp8One;
-  }
-  uint8_t* base = planes + (size_t)(b * n_chunks + c) * kTChunkBytes + tile_off(r, odd ? 16 : 0);
-  *reinterpret_cast<uint4*>(base + 0 * kTileBytes) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
-  *reinterpret_cast<uint4*>(base + 1 * kTileBytes) = make_uint4(wu[0], wu[1], wu[2], wu[3]);
-  *reinterpret_cast<uint4*>(base + 2 * kTileBytes) = make_uint4(wq[0], wq[1], wq[2], wq[3]);
-  *reinterpret_cast<uint4*>(base + 3 * kTileBytes) = make_uint4(wr[0], wr[1], wr[2], wr[3]);
+  const uint32_t vb = valid ? (h | ~l) & mask : 0u;  // present
+  const uint32_t pb = vb & h & ~l;                    // het
+  const uint32_t qb = vb & h & l;                     // hom A2
+  const uint32_t rb = vb & ~h & ~l;                   // hom A1
+  store_plane_row<F>(planes + (size_t)(b * n_chunks + c) * kTChunkBytes + tile_off(r, odd ? 16 : 0), vb, pb, qb,
+                     rb);
 }
 
 // ---------------------------------------------------------------------------
-// Pair tile kernel (kTStages-deep ring).
-template <int kTStages>
+// Pair tile kernel.
+template <int F>
 __global__ void __launch_bounds__(kTThreads, 1)
     tc_tri_kernel(const uint8_t* __restrict__ planes, int64_t n, int64_t n_blocks, int64_t n_chunks, int splits,
                   int32_t* __restrict__ out_counts, double* __restrict__ out_dist, int32_t* __restrict__ partial,
-                  int square, int* status, int piece, const int2* __restrict__ tile_list) {
+                  int square, int* status, const int2* __restrict__ tile_list) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // 1024-byte aligned ring (the dynamic base is only guaranteed 16-byte aligned)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -216,6 +317,12 @@ __global__ void __launch_bounds__(kTThreads, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
+  if constexpr (F == kTcFp4) {
+    tmem_fill_unit_scales(tmem, warp);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
 
   const int lane = threadIdx.x & 31;
   if (warp == 0) {
@@ -236,13 +343,8 @@ __global__ void __launch_bounds__(kTThreads, 1)
       if (lane == 0) {
         uint8_t* dst = ring + (size_t)s * 2 * kTChunkBytes;
         mbar_arrive_expect_tx(&full[s], same ? kTChunkBytes : 2 * kTChunkBytes);
-        // Each 16 KiB chunk goes as several smaller bulk copies, which the
-        // copy engine keeps in flight together.
-        for (int off = 0; off < kTChunkBytes; off += piece) {
-          bulk_g2s(dst + off, rowblk + (size_t)(c0 + k) * kTChunkBytes + off, piece, &full[s]);
-          if (!same)
-            bulk_g2s(dst + kTChunkBytes + off, colblk + (size_t)(c0 + k) * kTChunkBytes + off, piece, &full[s]);
-        }
+        bulk_g2s(dst, rowblk + (size_t)(c0 + k) * kTChunkBytes, kTChunkBytes, &full[s]);
+        if (!same) bulk_g2s(dst + kTChunkBytes, colblk + (size_t)(c0 + k) * kTChunkBytes, kTChunkBytes, &full[s]);
       }
       __syncwarp();
     }
@@ -262,11 +364,7 @@ __global__ void __launch_bounds__(kTThreads, 1)
       if (lane == 0) {
         const uint32_t a0 = smem_addr(ring + (size_t)s * 2 * kTChunkBytes);
         const uint32_t b0 = same ? a0 : a0 + kTChunkBytes;
-        const uint32_t acc = k > 0 ? 1u : 0u;
-        umma(tmem + 0, umma_desc(a0 + 0 * kTileBytes), umma_desc(b0 + 0 * kTileBytes), acc);    // V V^T
-        umma(tmem + 128, umma_desc(a0 + 1 * kTileBytes), umma_desc(b0 + 1 * kTileBytes), acc);  // U U^T
-        umma(tmem + 256, umma_desc(a0 + 2 * kTileBytes), umma_desc(b0 + 3 * kTileBytes), acc);  // Q R^T
-        umma(tmem + 256, umma_desc(a0 + 3 * kTileBytes), umma_desc(b0 + 2 * kTileBytes), 1u);   // + R Q^T
+        chunk_mmas<F>(tmem, a0, b0, k > 0 ? 1u : 0u);
         umma_commit(&empty[s]);  // the stage is free once these MMAs have read it
       }
       __syncwarp();
@@ -335,23 +433,314 @@ __global__ void __launch_bounds__(kTThreads, 1)
   }
 }
 
-}  // namespace
-
-size_t tc_planes_bytes(int64_t n, int64_t m) {
-  const int64_t nb = (n + kTB - 1) / kTB, nc = (m + kTK - 1) / kTK;
-  return (size_t)nb * (size_t)nc * kTChunkBytes;
+// ---------------------------------------------------------------------------
+// Batched form.  The operand planes of every subset are expanded from the
+// subset's bit planes (V, P, Q, R words, 64-sample blocks, 12-word chunks);
+// one CTA writes one (128-sample block, chunk) tile, a thread 16 bytes of
+// each plane of one sample: FP8, 16 markers of the chunk's bit-plane word;
+// FP4, one of the chunk's two words.
+template <int F>
+__global__ void __launch_bounds__(256) tc_expand_kernel(const TcExpandJob* __restrict__ jobs, int n_jobs) {
+  const int64_t cta = blockIdx.x;
+  int lo = 0, hi = n_jobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].cta_begin <= cta) lo = mid;
+    else hi = mid - 1;
+  }
+  const TcExpandJob& j = jobs[lo];
+  const int64_t local = cta - j.cta_begin;
+  const int64_t b = local / j.nc, c = local % j.nc;  // operand block, operand chunk
+  const int r = threadIdx.x >> 1, half = threadIdx.x & 1;
+  const int64_t s = b * kTB + r;
+  const int64_t word = F == kTcFp4 ? 2 * c + half : c;  // bit-plane word (32 markers)
+  uint4 w = make_uint4(0u, 0u, 0u, 0u);                 // V, P, Q, R words of this sample
+  if (s < j.n && word < j.bit_chunks * kKC) {
+    const int64_t blk = s / kSB, slot = s % kSB, chunk = word / kKC, kw = word % kKC;
+    w = *reinterpret_cast<const uint4*>(j.bits + (((blk * j.bit_chunks + chunk) * kKC + kw) * kSB + slot) * kPlanes);
+  }
+  if constexpr (F != kTcFp4) {
+    const int sh = half ? 16 : 0;
+    w = make_uint4((w.x >> sh) & 0xFFFFu, (w.y >> sh) & 0xFFFFu, (w.z >> sh) & 0xFFFFu, (w.w >> sh) & 0xFFFFu);
+  }
+  store_plane_row<F>(j.tc + (size_t)(b * j.nc + c) * kTChunkBytes + tile_off(r, half ? 16 : 0), w.x, w.y, w.z, w.w);
 }
 
-// Split count over the marker axis.  All tiles of one launch cost the same,
-// so the launch takes ceil(tiles * s / SMs) waves of 1/s of a tile each; pick
-// the s in 1..64 (at least one chunk per split) with the fewest tile-equivalents,
-// charging splits 3% for the partial-count atomics and the finalisation pass.
+// Persistent batched pair kernel: 8 warps.  Warp 0 claims work items from a
+// global counter (the list is ordered for L2 reuse: a subset's tiles in the
+// grouped order, subsets by decreasing cost) and streams each item's chunks
+// through the ring; warp 1 issues the MMAs; warps 4..7 read the accumulators
+// back (warp w reads TMEM lanes 32*(w-4)..) and store the counts; warps 2
+// and 3 only hold the block's shape.  Claimed item indices reach the MMA and
+// epilogue warps through a small shared-memory queue (qfull / qempty, -1
+// ends the stream).  Two barriers hand the accumulators over per item: tfull
+// (the item's MMAs are done) and tempty (the epilogue has read them), so the
+// producer keeps prefetching the next item's chunks while the epilogue runs.
+constexpr int kBatchQueue = 8;
+
+template <int F>
+__global__ void __launch_bounds__(256, 1)
+    tc_batch_kernel(const SubsetDev* __restrict__ subs, const WorkItem* __restrict__ items, int64_t n_items,
+                    int* counter, int* status) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* ring = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t full[kTStages], empty[kTStages], tfull, tempty, drain;
+  __shared__ __align__(8) uint64_t qfull[kBatchQueue], qempty[kBatchQueue];
+  __shared__ int64_t q_item[kBatchQueue];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kTStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int s = 0; s < kBatchQueue; ++s) {
+      mbar_init(&qfull[s], 1);
+      mbar_init(&qempty[s], 5);  // the MMA warp and the four epilogue warps
+    }
+    mbar_init(&tfull, 1);
+    mbar_init(&tempty, 4);  // one arrival per epilogue warp
+    mbar_init(&drain, 1);
+    mbar_fence_init();
+    abort_flag = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  if constexpr (F == kTcFp4) {
+    if (warp >= 4) tmem_fill_unit_scales(tmem, warp - 4);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+
+  auto fail = [&](bool cond) {
+    // warp-uniform: record a timeout once and tell the other roles to stop
+    if (lane == 0 && cond) {
+      atomicExch(status, kDevTimeout);
+      atomicExch(&abort_flag, 1);
+    }
+  };
+  auto aborted = [&]() { return __any_sync(0xffffffffu, *(volatile int*)&abort_flag != 0); };
+  // Wait for queue slot e and read the item index there (-1: no more items).
+  auto queue_get = [&](uint32_t e, int64_t& it) {
+    const int qs = (int)(e % kBatchQueue);
+    const bool ok = mbar_wait_bounded(&qfull[qs], (e / kBatchQueue) & 1u);
+    if (__any_sync(0xffffffffu, !ok)) return false;
+    it = *(volatile int64_t*)&q_item[qs];
+    __syncwarp();
+    if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&qempty[qs])) : "memory");
+    return true;
+  };
+
+  if (warp == 0) {
+    uint32_t g = 0;  // chunks streamed so far (ring position)
+    for (uint32_t e = 0;; ++e) {
+      int64_t it = 0;
+      if (lane == 0) it = atomicAdd(counter, 1);
+      it = __shfl_sync(0xffffffffu, it, 0);
+      const bool last = it >= n_items;
+      const int qs = (int)(e % kBatchQueue);
+      const bool qok = e < (uint32_t)kBatchQueue || mbar_wait_bounded(&qempty[qs], ((e / kBatchQueue) - 1) & 1u);
+      if (__any_sync(0xffffffffu, !qok)) {
+        fail(true);
+        break;
+      }
+      if (aborted()) break;
+      if (lane == 0) {
+        q_item[qs] = last ? -1 : it;
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&qfull[qs])) : "memory");
+      }
+      __syncwarp();
+      if (last) break;
+      const WorkItem w = items[it];
+      const SubsetDev sd = subs[w.subset];
+      const uint8_t* pl = reinterpret_cast<const uint8_t*>(sd.planes);
+      const uint8_t* rowblk = pl + (size_t)w.I * sd.n_chunks * kTChunkBytes;
+      const uint8_t* colblk = pl + (size_t)w.J * sd.n_chunks * kTChunkBytes;
+      const bool same = w.I == w.J;
+      bool stop = false;
+      for (int64_t k = w.c0; k < w.c1; ++k, ++g) {
+        const int s = (int)(g % kTStages);
+        const bool ok = g < (uint32_t)kTStages || mbar_wait_bounded(&empty[s], ((g / kTStages) - 1) & 1u);
+        if (__any_sync(0xffffffffu, !ok)) {
+          fail(true);
+          stop = true;
+          break;
+        }
+        if (aborted()) {
+          stop = true;
+          break;
+        }
+        if (lane == 0) {
+          uint8_t* dst = ring + (size_t)s * 2 * kTChunkBytes;
+          mbar_arrive_expect_tx(&full[s], same ? kTChunkBytes : 2 * kTChunkBytes);
+          bulk_g2s(dst, rowblk + (size_t)k * kTChunkBytes, kTChunkBytes, &full[s]);
+          if (!same) bulk_g2s(dst + kTChunkBytes, colblk + (size_t)k * kTChunkBytes, kTChunkBytes, &full[s]);
+        }
+        __syncwarp();
+      }
+      if (stop) break;
+    }
+  } else if (warp == 1) {
+    uint32_t g = 0;
+    for (uint32_t e = 0;; ++e) {
+      int64_t it;
+      if (!queue_get(e, it)) {
+        fail(true);
+        break;
+      }
+      if (it < 0) break;
+      const WorkItem w = items[it];
+      const bool same = w.I == w.J;
+      // the epilogue must have read the previous item's accumulators
+      const bool free_ok = e == 0 || mbar_wait_bounded(&tempty, (e - 1) & 1u);
+      bool stop = __any_sync(0xffffffffu, !free_ok);
+      if (!stop) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (int64_t k = w.c0; k < w.c1; ++k, ++g) {
+          const int s = (int)(g % kTStages);
+          const bool ok = mbar_wait_bounded(&full[s], (g / kTStages) & 1u);
+          if (__any_sync(0xffffffffu, !ok)) {
+            stop = true;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          if (lane == 0) {
+            const uint32_t a0 = smem_addr(ring + (size_t)s * 2 * kTChunkBytes);
+            const uint32_t b0 = same ? a0 : a0 + kTChunkBytes;
+            chunk_mmas<F>(tmem, a0, b0, k > w.c0 ? 1u : 0u);
+            umma_commit(&empty[s]);
+          }
+          __syncwarp();
+        }
+      }
+      if (stop || aborted()) {
+        fail(stop);
+        break;
+      }
+      if (lane == 0) umma_commit(&tfull);
+      __syncwarp();
+    }
+    // arrives once every MMA issued above has completed
+    if (lane == 0) umma_commit(&drain);
+    __syncwarp();
+    const bool drained = mbar_wait_bounded(&drain, 0);
+    if (lane == 0 && !drained) atomicExch(status, kDevTimeout);
+  } else if (warp >= 4) {
+    const int quarter = warp - 4;  // TMEM lanes 32*quarter .. 32*quarter+31
+    const int row = quarter * 32 + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+    for (uint32_t e = 0;; ++e) {
+      int64_t it;
+      if (!queue_get(e, it)) {
+        fail(true);
+        break;
+      }
+      if (it < 0) break;
+      const bool ok = mbar_wait_bounded(&tfull, e & 1u);
+      if (__any_sync(0xffffffffu, !ok) || aborted()) {
+        fail(true);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const WorkItem w = items[it];
+      const SubsetDev sd = subs[w.subset];
+      const int64_t gi = (int64_t)w.I * kTB + row;
+#pragma unroll 1
+      for (int cg = 0; cg < kTB / 32; ++cg) {
+        uint32_t vn[32], vu[32], v0[32];
+        tmem_ld32(lane_base + 0 + cg * 32, vn);
+        tmem_ld32(lane_base + 128 + cg * 32, vu);
+        tmem_ld32(lane_base + 256 + cg * 32, v0);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (cg == kTB / 32 - 1) {
+          // every accumulator of this item is in registers: hand TMEM back
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&tempty)) : "memory");
+        }
+        if (gi >= sd.n) continue;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int64_t gj = (int64_t)w.J * kTB + cg * 32 + j;
+          if (gj >= sd.n || gj < gi) continue;
+          const int32_t nn = __float2int_rn(__uint_as_float(vn[j]));
+          const int32_t uu = __float2int_rn(__uint_as_float(vu[j]));
+          const int32_t i0 = __float2int_rn(__uint_as_float(v0[j]));
+          const int32_t i1 = (nn - uu) / 2;
+          const int64_t p = tri_index(gi, gj, sd.n);
+          if (w.split) {
+            int32_t* o = sd.partial + p * 4;
+            atomicAdd(o + 0, i0);
+            atomicAdd(o + 1, i1);
+            atomicAdd(o + 3, nn);
+            continue;
+          }
+          reinterpret_cast<int4*>(sd.out_counts)[p] = make_int4(i0, i1, nn - i0 - i1, nn);
+          if (sd.out_dist)
+            sd.out_dist[p] = nn == 0 ? __longlong_as_double(0x7ff8000000000000LL)
+                                     : (double)(i1 + 2 * i0) / (2.0 * (double)nn);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+}  // namespace
+
+int tc_default_format() {
+  static const int f = [] {
+    const char* e = getenv("IBS_TC_FORMAT");
+    if (e && strcmp(e, "fp4") == 0) return kTcFp4;
+    if (e && strcmp(e, "fp8") == 0) return kTcFp8;
+    return kTcFp4;  // half the operand bytes per marker and the faster MMA kind
+  }();
+  return f;
+}
+
+int64_t tc_chunks(int64_t m, int fmt) {
+  const int64_t k = fmt == kTcFp4 ? kMarkers<kTcFp4> : kMarkers<kTcFp8>;
+  return (m + k - 1) / k;
+}
+
+size_t tc_planes_bytes(int64_t n, int64_t m, int fmt) {
+  const int64_t nb = (n + kTB - 1) / kTB;
+  return (size_t)nb * (size_t)tc_chunks(m, fmt) * kTChunkBytes;
+}
+
+// Split count over the marker axis.  All tiles of one launch cost the same:
+// with s splits the launch runs ceil(tiles * s / SMs) waves, each of n_chunks/s
+// chunks of MMAs plus, when s > 1, an epilogue of 3 x 128 x 128 partial-count
+// atomics, charged as kSplitEpilogueChunks chunks of MMA time.  Pick the s in
+// 1..64 (at least one chunk per split) of least total time.  IBS_TC_SPLITS
+// overrides the choice (clamped to 1..min(64, n_chunks)).
+constexpr double kSplitEpilogueChunks = 160.0;
+
 int tc_splits_for(int64_t tiles, int64_t n_chunks, int num_sms) {
+  static const int forced = [] {
+    const char* e = getenv("IBS_TC_SPLITS");
+    return e ? atoi(e) : 0;
+  }();
+  if (forced > 0) return (int)std::min<int64_t>(std::min(forced, 64), std::max<int64_t>(1, n_chunks));
   int best = 1;
   double best_cost = 1e300;
   for (int s = 1; s <= 64 && s <= n_chunks; ++s) {
     const double waves = (double)((tiles * s + num_sms - 1) / num_sms);
-    const double cost = waves / s * (s > 1 ? 1.03 : 1.0);
+    const double cost = waves * ((double)n_chunks / s + (s > 1 ? kSplitEpilogueChunks : 0.0));
     if (cost < best_cost - 1e-9) {
       best_cost = cost;
       best = s;
@@ -360,41 +749,30 @@ int tc_splits_for(int64_t tiles, int64_t n_chunks, int num_sms) {
   return best;
 }
 
-cudaError_t launch_tc_planes(const uint8_t* packed, int64_t n, int64_t m, uint8_t* planes, cudaStream_t st) {
-  const int64_t nb = (n + kTB - 1) / kTB, nc = (m + kTK - 1) / kTK;
+cudaError_t launch_tc_planes(const uint8_t* packed, int64_t n, int64_t m, uint8_t* planes, int fmt,
+                             cudaStream_t st) {
+  const int64_t nb = (n + kTB - 1) / kTB, nc = tc_chunks(m, fmt);
   if (nc > 2147483647LL || nb > 65535) return cudaErrorInvalidValue;
-  tc_planes_kernel<<<dim3((unsigned)nc, (unsigned)nb), 256, 0, st>>>(packed, (n + 3) / 4, n, m, planes, nc);
+  const dim3 grid((unsigned)nc, (unsigned)nb);
+  if (fmt == kTcFp4)
+    tc_planes_kernel<kTcFp4><<<grid, 256, 0, st>>>(packed, (n + 3) / 4, n, m, planes, nc);
+  else
+    tc_planes_kernel<kTcFp8><<<grid, 256, 0, st>>>(packed, (n + 3) / 4, n, m, planes, nc);
   return cudaGetLastError();
 }
 
-cudaError_t launch_tc_pairs(const uint8_t* planes, int64_t n, int64_t m, int splits, int32_t* out_counts,
+cudaError_t launch_tc_pairs(const uint8_t* planes, int64_t n, int64_t m, int fmt, int splits, int32_t* out_counts,
                             double* out_dist, int32_t* partial, bool square, int* status, const int2* tile_list,
                             cudaStream_t st) {
-  const int64_t nb = (n + kTB - 1) / kTB, nc = (m + kTK - 1) / kTK;
+  const int64_t nb = (n + kTB - 1) / kTB, nc = tc_chunks(m, fmt);
   const int64_t tiles = nb * (nb + 1) / 2;
   const int64_t grid = tiles * splits;
   if (grid > 2147483647LL) return cudaErrorInvalidValue;
-  static const int stages = [] {
-    const char* e = getenv("IBS_TC_STAGES");
-    return (e && e[0] == '6') ? 6 : 4;
-  }();
-  static const int piece = [] {
-    const char* e = getenv("IBS_TC_PIECE");
-    const int v = e ? atoi(e) : kTChunkBytes;
-    return (v >= 512 && v <= kTChunkBytes && kTChunkBytes % v == 0 && v % 16 == 0) ? v : kTChunkBytes;
-  }();
-  cudaError_t e;
-  if (stages == 6) {
-    e = cudaFuncSetAttribute(tc_tri_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(6));
-    if (e != cudaSuccess) return e;
-    tc_tri_kernel<6><<<(unsigned)grid, kTThreads, tc_smem(6), st>>>(planes, n, nb, nc, splits, out_counts, out_dist,
-                                                                   partial, square ? 1 : 0, status, piece, tile_list);
-  } else {
-    e = cudaFuncSetAttribute(tc_tri_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(4));
-    if (e != cudaSuccess) return e;
-    tc_tri_kernel<4><<<(unsigned)grid, kTThreads, tc_smem(4), st>>>(planes, n, nb, nc, splits, out_counts, out_dist,
-                                                                   partial, square ? 1 : 0, status, piece, tile_list);
-  }
+  auto kern = fmt == kTcFp4 ? tc_tri_kernel<kTcFp4> : tc_tri_kernel<kTcFp8>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)grid, kTThreads, kTcSmem, st>>>(planes, n, nb, nc, splits, out_counts, out_dist, partial,
+                                                   square ? 1 : 0, status, tile_list);
   return cudaGetLastError();
 }
 
@@ -418,6 +796,25 @@ int64_t tc_tiles(int64_t n) {
   return nb * (nb + 1) / 2;
 }
 
-int64_t tc_chunks(int64_t m) { return (m + kTK - 1) / kTK; }
+cudaError_t launch_tc_expand(const TcExpandJob* jobs_dev, int n_jobs, int64_t total_ctas, int fmt, cudaStream_t st) {
+  if (total_ctas <= 0) return cudaSuccess;
+  if (total_ctas > 2147483647LL) return cudaErrorInvalidValue;
+  if (fmt == kTcFp4)
+    tc_expand_kernel<kTcFp4><<<(unsigned)total_ctas, 256, 0, st>>>(jobs_dev, n_jobs);
+  else
+    tc_expand_kernel<kTcFp8><<<(unsigned)total_ctas, 256, 0, st>>>(jobs_dev, n_jobs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_batch(const SubsetDev* subs, const WorkItem* items, int64_t n_items, int grid, int fmt,
+                            int* counter, int* status, cudaStream_t st) {
+  if (n_items <= 0) return cudaSuccess;
+  if (n_items > 2147483647LL - grid) return cudaErrorInvalidValue;  // the claim counter is an int
+  auto kern = fmt == kTcFp4 ? tc_batch_kernel<kTcFp4> : tc_batch_kernel<kTcFp8>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, 256, kTcSmem, st>>>(subs, items, n_items, counter, status);
+  return cudaGetLastError();
+}
 
 }  // namespace ibs

@@ -27,6 +27,8 @@ IBS_KERNEL_PLAIN = 0x10
 IBS_KERNEL_CSA = 0x20
 IBS_TIMING = 0x40
 IBS_KERNEL_TC = 0x80
+IBS_TC_FP8 = 0x100
+IBS_TC_FP4 = 0x200
 
 
 class IbsError(RuntimeError):
@@ -86,6 +88,7 @@ def load():
             "ibs_shutdown": [p],
             "ibs_probe_int_pipes": [p, ctypes.POINTER(ctypes.c_double)],
             "ibs_batch_plan_info": [p, ctypes.POINTER(ctypes.c_int64)],
+            "ibs_kernel_info": [p, ctypes.POINTER(ctypes.c_int64)],
             "ibs_last_launch_info": [p, ctypes.POINTER(ctypes.c_int64)],
             "ibs_kernel_times": [p, ctypes.POINTER(ctypes.c_double)],
             "ibs_compute_noalloc": [p, i64, i64, p, p, p],
@@ -247,6 +250,13 @@ def ibs_kernel_times(ctx: Context) -> dict:
     out = (ctypes.c_double * 4)()
     _check(load().ibs_kernel_times(ctx._h, out), "ibs_kernel_times")
     return {"planes_ms": out[0], "pairs_ms": out[1], "finalize_ms": out[2], "calls": int(out[3])}
+
+
+def ibs_kernel_info(ctx: Context) -> dict:
+    out = (ctypes.c_int64 * 4)()
+    _check(load().ibs_kernel_info(ctx._h, out), "ibs_kernel_info")
+    return {"family": ("popc-plain", "popc-csa", "tensor-core")[out[0]], "tc_format": ("e4m3", "e2m1")[out[1]],
+            "sms": out[2], "device": out[3]}
 
 
 def ibs_batch_plan_info(ctx: Context) -> dict:

@@ -77,26 +77,58 @@ def test_batch_matches_plain_and_oracle(pool, tmp_path):
             assert_dist_close(d1, od)
         info = ibs.ibs_batch_plan_info(ctx)
         assert info["items"] > 0 and info["grid"] > 0
+        assert info["mode"] in (3, 4)  # tensor-core form by default, as ibs_compute
         assert (tmp_path / "tune.jsonl").exists()
     finally:
         ibs.ibs_shutdown(plain)
         ibs.ibs_shutdown(ctx)
 
 
-@pytest.mark.parametrize("flags_name", ["IBS_KERNEL_PLAIN", "IBS_KERNEL_CSA"])
+def _flags(ibs, names):
+    f = 0
+    for nm in names.split("|"):
+        f |= getattr(ibs, nm)
+    return f
+
+
+@pytest.mark.parametrize("flags_name", ["IBS_KERNEL_PLAIN", "IBS_KERNEL_CSA", "IBS_KERNEL_TC|IBS_TC_FP8",
+                                        "IBS_KERNEL_TC|IBS_TC_FP4"])
 def test_batch_forced_modes(pool, flags_name):
     import torch
     from paper_1410_4803_gb300 import ibs
     w, codes = pool
     rng = np.random.default_rng(6)
     subs = _make_subsets(rng, w.n, w.m)[:6]
-    ctx = ibs.ibs_init(0, flags=getattr(ibs, flags_name))
+    ctx = ibs.ibs_init(0, flags=_flags(ibs, flags_name))
     try:
         res = _run_batch(ctx, w, subs, torch.from_numpy(w.packed).cuda())
         for (idx, vb, vl), (c, d) in zip(subs, res):
             G = oracle.unpack_subset(w.packed, w.n, w.m, idx, vb, vl)
             oc, od, _ = oracle.ibs_triangle_from_codes(G)
             assert (c == oc).all()
+    finally:
+        ibs.ibs_shutdown(ctx)
+
+
+@pytest.mark.parametrize("flags_name", ["IBS_KERNEL_CSA", "IBS_KERNEL_TC|IBS_TC_FP8", "IBS_KERNEL_TC|IBS_TC_FP4"])
+def test_batch_split_items(pool, flags_name):
+    """One subset of few tiles and many chunks: the autotuner splits the
+    marker axis into items that add into a partial triangle, and a finalize
+    launch writes the counts."""
+    import torch
+    from paper_1410_4803_gb300 import ibs
+    w, _ = pool
+    rng = np.random.default_rng(8)
+    subs = [(np.sort(rng.choice(w.n, size=150, replace=False)).astype(np.int64), 17, 29000)]
+    ctx = ibs.ibs_init(0, flags=_flags(ibs, flags_name))
+    try:
+        (c, d), = _run_batch(ctx, w, subs, torch.from_numpy(w.packed).cuda())
+        assert ibs.ibs_batch_plan_info(ctx)["split_policy"] == 1
+        idx, vb, vl = subs[0]
+        G = oracle.unpack_subset(w.packed, w.n, w.m, idx, vb, vl)
+        oc, od, _ = oracle.ibs_triangle_from_codes(G)
+        assert (c == oc).all()
+        assert_dist_close(d, od)
     finally:
         ibs.ibs_shutdown(ctx)
 

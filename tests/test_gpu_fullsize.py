@@ -34,13 +34,21 @@ def _whole_output_invariants(counts, n, nonmiss):
     assert bool((diag[:, 2] == nm).all() and (diag[:, 3] == nm).all())
 
 
-@pytest.mark.parametrize("kernel", ["popc", "tc"])
+_FLAGS = {"popc": "IBS_KERNEL_CSA", "tc8": ("IBS_KERNEL_TC", "IBS_TC_FP8"), "tc4": ("IBS_KERNEL_TC", "IBS_TC_FP4")}
+
+
+def _flags(ibs, kernel):
+    f = _FLAGS[kernel]
+    return getattr(ibs, f) if isinstance(f, str) else getattr(ibs, f[0]) | getattr(ibs, f[1])
+
+
+@pytest.mark.parametrize("kernel", ["popc", "tc8", "tc4"])
 def test_plain_n4096_m100000_sampled_rows(kernel):
     import torch
     from paper_1410_4803_gb300 import ibs, synth
     w = synth.plain_config2()
     n, m = w.n, w.m
-    ctx = ibs.ibs_init(0, flags=ibs.IBS_KERNEL_TC if kernel == "tc" else ibs.IBS_KERNEL_CSA)
+    ctx = ibs.ibs_init(0, flags=_flags(ibs, kernel))
     try:
         counts, dist = ibs.compute(ctx, torch.from_numpy(w.packed).cuda(), n, m)
         ibs.ibs_synchronize(ctx)
@@ -60,17 +68,17 @@ def test_plain_n4096_m100000_sampled_rows(kernel):
         ibs.ibs_shutdown(ctx)
 
 
-@pytest.mark.parametrize("kernel", ["popc", "tc"])
+@pytest.mark.parametrize("kernel", ["popc", "tc8", "tc4"])
 def test_structured_n20000_m500000_sampled_pairs(kernel):
     """Five subpopulations, injected parent-offspring pairs and duplicates: the
     oracle checks a block of sampled pairs plus every relative pair.  With
-    m = 500,000 the counts reach 2^19, so the tensor-core form's FP32
+    m = 500,000 the counts reach 2^19, so the tensor-core forms' FP32
     accumulation is checked far above 2^14."""
     import torch
     from paper_1410_4803_gb300 import ibs, synth
     w = _config3()
     n, m = w.n, w.m
-    ctx = ibs.ibs_init(0, flags=ibs.IBS_KERNEL_TC if kernel == "tc" else ibs.IBS_KERNEL_CSA)
+    ctx = ibs.ibs_init(0, flags=_flags(ibs, kernel))
     try:
         counts, dist = ibs.compute(ctx, torch.from_numpy(w.packed).cuda(), n, m)
         ibs.ibs_synchronize(ctx)

@@ -13,10 +13,21 @@ N_EDGE = [1, 2, 3, 4, 5, 31, 32, 33, 63, 64, 65, 127, 128, 129, 255, 256, 257]
 M_EDGE = [1, 15, 16, 17, 31, 32, 33, 63, 64, 65, 383, 384, 385, 959, 960, 961, 1023, 1024, 1025]
 
 
-@pytest.fixture(scope="module", params=["plain", "csa", "tc"])
+KERNELS = ["plain", "csa", "tc8", "tc4"]
+
+
+def kernel_flags(name):
+    """Context flags selecting one pair kernel: the two POPC variants and the
+    tensor-core form with E4M3 or E2M1 operands."""
+    from paper_1410_4803_gb300 import ibs
+    return {"plain": ibs.IBS_KERNEL_PLAIN, "csa": ibs.IBS_KERNEL_CSA,
+            "tc8": ibs.IBS_KERNEL_TC | ibs.IBS_TC_FP8, "tc4": ibs.IBS_KERNEL_TC | ibs.IBS_TC_FP4}[name]
+
+
+@pytest.fixture(scope="module", params=KERNELS)
 def ctx(request):
     from paper_1410_4803_gb300 import ibs
-    flags = {"plain": ibs.IBS_KERNEL_PLAIN, "csa": ibs.IBS_KERNEL_CSA, "tc": ibs.IBS_KERNEL_TC}[request.param]
+    flags = kernel_flags(request.param)
     c = ibs.ibs_init(0, flags=flags)
     yield c
     ibs.ibs_shutdown(c)
@@ -57,8 +68,8 @@ def test_degenerate_inputs(ctx):
     check(ctx, random_codes(rng, 66, 400, miss=0.0))
 
 
-@pytest.mark.parametrize("tc", [False, True])
-def test_square_output(tc):
+@pytest.mark.parametrize("kernel", ["csa", "tc8", "tc4"])
+def test_square_output(kernel):
     from paper_1410_4803_gb300 import ibs
     rng = np.random.default_rng(3)
     n, m = 130, 1500
@@ -66,7 +77,7 @@ def test_square_output(tc):
     packed = pack_codes(codes)
     G = oracle.unpack(packed, n, m)
     want_c, want_d = oracle.ibs_block(G, G)
-    c = ibs.ibs_init(0, flags=ibs.IBS_OUT_SQUARE | (ibs.IBS_KERNEL_TC if tc else ibs.IBS_KERNEL_CSA))
+    c = ibs.ibs_init(0, flags=ibs.IBS_OUT_SQUARE | kernel_flags(kernel))
     try:
         got_c, got_d = gpu_compute(c, packed, n, m, square=True)
     finally:
@@ -106,19 +117,20 @@ def test_repeat_calls_identical(ctx):
 
 
 def test_modes_agree_on_structured_cohort():
-    """Structured cohort (five subpopulations, relatives): both kernel
-    variants, sampled against the oracle, and the relatives' IBS0 = 0."""
+    """Structured cohort (five subpopulations, relatives): every kernel
+    variant gives the same counts, equal to the oracle, and the relatives'
+    IBS0 = 0."""
     import torch
     from paper_1410_4803_gb300 import ibs, synth
     w = synth.structured_config3(n_base_per_pop=100, m=20000, n_offspring=20, n_dup=10)
     outs = []
-    for flags in (ibs.IBS_KERNEL_PLAIN, ibs.IBS_KERNEL_CSA, ibs.IBS_KERNEL_TC):
-        c = ibs.ibs_init(0, flags=flags)
+    for name in KERNELS:
+        c = ibs.ibs_init(0, flags=kernel_flags(name))
         try:
             outs.append(gpu_compute(c, w.packed, w.n, w.m))
         finally:
             ibs.ibs_shutdown(c)
-    assert (outs[0][0] == outs[1][0]).all() and (outs[0][0] == outs[2][0]).all()
+    assert all((outs[0][0] == o[0]).all() for o in outs[1:])
     want_c, want_d = oracle.ibs_triangle(w.packed, w.n, w.m)
     assert (outs[0][0] == want_c).all()
     s = w.samples
