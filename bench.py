@@ -297,6 +297,24 @@ def run_plain(args, rank, world, local):
         ibs.ibs_kernel_times(ctx)
         e2e_ms = [a.elapsed_time(b) for a, b in e2e_ev]
 
+        # The integer-pipe kernel (bit planes, carry-save LOP3/POPC) on the same
+        # input, timed the same way: its fraction of the integer-pipe roofline.
+        popc = None
+        if use_tc:
+            ctx_i = ibs.ibs_init(local, flags=ibs.IBS_TIMING | ibs.IBS_KERNEL_CSA)
+            k_i = max(1, min(args.steps, 10))
+            for _ in range(2):
+                ibs.ibs_compute(ctx_i, packed, n, m, counts, dist_t, stream)
+            ibs.ibs_synchronize(ctx_i, stream)
+            ibs.ibs_kernel_times(ctx_i)
+            for _ in range(k_i):
+                flush.zero_()
+                ibs.ibs_compute(ctx_i, packed, n, m, counts, dist_t, stream)
+            ibs.ibs_synchronize(ctx_i, stream)
+            kt_i = ibs.ibs_kernel_times(ctx_i)
+            ibs.ibs_shutdown(ctx_i)
+            popc = kt_i["pairs_ms"] / max(1, kt_i["calls"])
+
     # spot check of the last result against the oracle on a few rows (rank 0)
     total_ms = reduce_max(sum(step_ms), world)
     e2e_total = reduce_max(sum(e2e_ms), world)
@@ -363,6 +381,11 @@ def run_plain(args, rank, world, local):
                       "peak_basis": f"measured bf16 burst TFLOP/s (MEASURED_PEAKS.json) x {tc_ratio:.0f}, the nominal "
                                     f"{'FP4' if fp4 else 'FP8'}/bf16 dense ratio; algorithmic flops = 8 per comparison "
                                     "(4 MACs: VV^T, UU^T, QR^T, RQ^T)"}),
+        "integer_kernel": None if popc is None else {
+            "kernel": "tri_kernel, carry-save LOP3/POPC over bit planes (IBS_KERNEL_CSA)",
+            "kernel_ms": popc, "value": comps / (popc * 1e-3), "unit": UNIT,
+            "roofline_peak": roof["peak"], "frac": comps / (popc * 1e-3) / roof["peak"],
+            "peak_basis": "integer-pipe roofline as for the POPC bench line (measured pipe rates x SMs x clock)"},
         "transpose": {"kernel_ms": planes_ms, "bytes": transpose_bytes,
                       "achieved_gbs": transpose_bytes / (planes_ms * 1e-3) / 1e9,
                       "peak_gbs": hbm_peak_gbs(), "frac": transpose_bytes / (planes_ms * 1e-3) / 1e9 / hbm_peak_gbs()},

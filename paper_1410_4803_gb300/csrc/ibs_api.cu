@@ -125,6 +125,12 @@ int mode_for(const ibs_ctx* ctx) {
 
 }  // namespace
 
+namespace ibs {
+bool ctx_use_tc(const ibs_ctx* ctx) { return use_tc(ctx); }
+int ctx_tc_format(const ibs_ctx* ctx) { return tc_format_for(ctx); }
+int ctx_popc_mode(const ibs_ctx* ctx) { return mode_for(ctx); }
+}  // namespace ibs
+
 extern "C" {
 
 const char* ibs_last_error(void) { return ibs::last_error_cstr(); }
@@ -206,11 +212,46 @@ ibs_status ibs_compute(ibs_ctx* ctx, const uint8_t* packed, int64_t n, int64_t m
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const bool tc = use_tc(ctx);
   const int fmt = tc_format_for(ctx);
+  // Tensor-core form, triangle output: the persistent kernel over a work list
+  // (tail wave split over K).  Square output, or IBS_TC_TILE_KERNEL set: one
+  // CTA per tile (or tile piece).
+  static const bool tile_kernel = getenv("IBS_TC_TILE_KERNEL") != nullptr;
+  const bool persistent = tc && !square && !tile_kernel;
+  static const int group = [] {
+    const char* e = getenv("IBS_TC_GROUP");
+    const int v = e ? atoi(e) : 16;
+    return v >= 1 && v <= 1024 ? v : 16;
+  }();
   const PlaneGeom geo = PlaneGeom::make(n, m);
   if (ibs_status s = ensure_buf(ctx, ctx->planes, tc ? tc_planes_bytes(n, m, fmt) : geo.bytes())) return s;
   const int64_t tiles = tc ? tc_tiles(n) : geo.n_blocks * (geo.n_blocks + 1) / 2;
-  const int splits = tc ? tc_splits_for(tiles, tc_chunks(m, fmt), ctx->num_sms)
-                        : tri_splits_for(tiles, geo.n_chunks, ctx->num_sms);
+  int splits = 1;
+  if (persistent) {
+    const std::vector<int64_t> key = {n, m, fmt, ctx->num_sms, group};
+    if (ctx->single_key != key) {
+      std::vector<WorkItem> items;
+      std::vector<int2> split_tiles;
+      tc_single_items(n, m, fmt, ctx->num_sms, group, items, split_tiles);
+      if (ibs_status s = ensure_buf(ctx, ctx->single_items, items.size() * sizeof(WorkItem))) return s;
+      if (ibs_status s = ensure_buf(ctx, ctx->single_split, std::max<size_t>(1, split_tiles.size()) * sizeof(int2)))
+        return s;
+      if (ibs_status s = ensure_buf(ctx, ctx->single_counter, 256)) return s;
+      // pageable sources: the copies are staged before return
+      IBS_CUDA_TRY(cudaMemcpyAsync(ctx->single_items.p, items.data(), items.size() * sizeof(WorkItem),
+                                   cudaMemcpyHostToDevice, st));
+      if (!split_tiles.empty())
+        IBS_CUDA_TRY(cudaMemcpyAsync(ctx->single_split.p, split_tiles.data(), split_tiles.size() * sizeof(int2),
+                                     cudaMemcpyHostToDevice, st));
+      ctx->single_n_items = (int64_t)items.size();
+      ctx->single_n_split = (int64_t)split_tiles.size();
+      ctx->single_key = key;
+    }
+    splits = ctx->single_n_split > 0 ? 2 : 1;  // > 1: partial counts and a finalisation pass
+  } else if (tc) {
+    splits = tc_splits_for(tiles, tc_chunks(m, fmt), ctx->num_sms);
+  } else {
+    splits = tri_splits_for(tiles, geo.n_chunks, ctx->num_sms);
+  }
   const int64_t P = n * (n + 1) / 2;
   if (splits > 1) {
     if (ibs_status s = ensure_buf(ctx, ctx->partial, (size_t)P * 16)) return s;
@@ -232,14 +273,24 @@ ibs_status ibs_compute(ibs_ctx* ctx, const uint8_t* packed, int64_t n, int64_t m
     rec.n = splits > 1 ? 4 : 3;
     IBS_CUDA_TRY(cudaEventRecord(rec.ev[0], st));
   }
-  if (tc) {
+  if (persistent) {
+    IBS_CUDA_TRY(launch_tc_planes(packed, n, m, static_cast<uint8_t*>(ctx->planes.p), fmt, st));
+    if (timing) IBS_CUDA_TRY(cudaEventRecord(rec.ev[1], st));
+    SubsetDev sd;
+    sd.planes = static_cast<const uint32_t*>(ctx->planes.p);
+    sd.n = n;
+    sd.n_blocks = (n + 127) / 128;
+    sd.n_chunks = tc_chunks(m, fmt);
+    sd.out_counts = out_counts;
+    sd.out_dist = out_dist;
+    sd.partial = splits > 1 ? static_cast<int32_t*>(ctx->partial.p) : nullptr;
+    sd.pad = 0;
+    const int grid = (int)std::min<int64_t>(ctx->num_sms, ctx->single_n_items);
+    IBS_CUDA_TRY(launch_tc_single(sd, static_cast<const WorkItem*>(ctx->single_items.p), ctx->single_n_items, grid,
+                                  fmt, static_cast<int*>(ctx->single_counter.p), ctx->status_dev, st));
+  } else if (tc) {
     const int64_t T = (n + 127) / 128;
     if (ctx->tile_list_T != T) {
-      static const int group = [] {
-        const char* e = getenv("IBS_TC_GROUP");
-        const int v = e ? atoi(e) : 16;
-        return v >= 1 && v <= 1024 ? v : 16;
-      }();
       std::vector<int2> order;
       tc_tile_order(T, group, order);
       if (ibs_status s = ensure_buf(ctx, ctx->tile_list, order.size() * sizeof(int2))) return s;
@@ -261,8 +312,14 @@ ibs_status ibs_compute(ibs_ctx* ctx, const uint8_t* packed, int64_t n, int64_t m
                             st));
   }
   if (timing) IBS_CUDA_TRY(cudaEventRecord(rec.ev[2], st));
-  if (splits > 1)
-    IBS_CUDA_TRY(launch_finalize(static_cast<const int32_t*>(ctx->partial.p), n, out_counts, out_dist, square, st));
+  if (splits > 1) {
+    if (persistent)
+      IBS_CUDA_TRY(launch_tc_finalize_tiles(static_cast<const int2*>(ctx->single_split.p), ctx->single_n_split,
+                                            static_cast<const int32_t*>(ctx->partial.p), n, out_counts, out_dist,
+                                            st));
+    else
+      IBS_CUDA_TRY(launch_finalize(static_cast<const int32_t*>(ctx->partial.p), n, out_counts, out_dist, square, st));
+  }
   if (timing) {
     if (splits > 1) IBS_CUDA_TRY(cudaEventRecord(rec.ev[3], st));
     ctx->timing_used.push_back(rec);
@@ -477,18 +534,19 @@ ibs_status plan_build(ibs_ctx* ctx, BatchPlan& plan, const std::vector<SubsetSha
   plan.total_ctas = 0;
   for (const auto& s : shapes) plan.total_ctas += s.g.n_chunks * ((s.g.n_blocks + 1) / 2);
   if (tc) {
+    // the tensor-core form gathers straight into operand planes: no bit planes
     size_t tb = 0;
     plan.tc_offsets.resize(shapes.size());
     plan.tc_ctas = 0;
     for (size_t k = 0; k < shapes.size(); ++k) {
       plan.tc_offsets[k] = (int64_t)tb;
       tb += (tc_planes_bytes(shapes[k].n, shapes[k].m, tc_fmt_of(mode)) + 1023) / 1024 * 1024;
-      const ItemGeom ig = item_geom(shapes[k], mode);
-      plan.tc_ctas += ig.T * ig.nc;
+      plan.tc_ctas += tc_gather_ctas(shapes[k].n, item_geom(shapes[k], mode).nc);
     }
-    if (plan.tc_ctas > 2147483647LL) return fail(IBS_EINVAL, "batch too large for one expansion launch");
+    if (plan.tc_ctas > 2147483647LL) return fail(IBS_EINVAL, "batch too large for one gather launch");
     if (ibs_status s = ensure_buf(ctx, plan.tc_planes, tb)) return s;
-    if (ibs_status s = ensure_buf(ctx, plan.tc_jobs, sizeof(TcExpandJob) * shapes.size())) return s;
+    if (ibs_status s = ensure_buf(ctx, plan.tc_jobs, sizeof(TcGatherJob) * shapes.size())) return s;
+    pb = 0;
   }
   if (ibs_status s = ensure_buf(ctx, plan.planes, pb)) return s;
   if (ibs_status s = ensure_buf(ctx, plan.partial, qb)) return s;
@@ -540,7 +598,7 @@ ibs_status plan_upload(ibs_ctx* ctx, BatchPlan& plan, const uint8_t* pool, int64
   }
   if (is_tc_mode(plan.mode)) {
     // the pair kernel reads operand planes, in 128-sample blocks and MMA-K chunks
-    std::vector<TcExpandJob> tj(k);
+    std::vector<TcGatherJob> tj(k);
     int64_t tcta = 0;
     for (size_t i = 0; i < k; ++i) {
       const ItemGeom ig = item_geom(shapes[i], plan.mode);
@@ -548,16 +606,16 @@ ibs_status plan_upload(ibs_ctx* ctx, BatchPlan& plan, const uint8_t* pool, int64
       sd[i].planes = reinterpret_cast<const uint32_t*>(tcp);
       sd[i].n_blocks = ig.T;
       sd[i].n_chunks = ig.nc;
-      tj[i].bits = jobs[i].planes;
-      tj[i].bit_chunks = shapes[i].g.n_chunks;
-      tj[i].tc = tcp;
+      tj[i].src = jobs[i].src;
+      tj[i].m = shapes[i].m;
       tj[i].n = shapes[i].n;
+      tj[i].tc = tcp;
       tj[i].nb = ig.T;
       tj[i].nc = ig.nc;
       tj[i].cta_begin = tcta;
-      tcta += ig.T * ig.nc;
+      tcta += tc_gather_ctas(shapes[i].n, ig.nc);
     }
-    IBS_CUDA_TRY(cudaMemcpyAsync(plan.tc_jobs.p, tj.data(), sizeof(TcExpandJob) * k, cudaMemcpyHostToDevice, st));
+    IBS_CUDA_TRY(cudaMemcpyAsync(plan.tc_jobs.p, tj.data(), sizeof(TcGatherJob) * k, cudaMemcpyHostToDevice, st));
   }
   // Pageable sources: the copy is staged before return, so the vectors may go.
   IBS_CUDA_TRY(cudaMemcpyAsync(plan.subsets.p, sd.data(), sizeof(SubsetDev) * k, cudaMemcpyHostToDevice, st));
@@ -569,15 +627,16 @@ ibs_status plan_upload(ibs_ctx* ctx, BatchPlan& plan, const uint8_t* pool, int64
 ibs_status plan_enqueue(ibs_ctx* ctx, BatchPlan& plan, int n_subsets, cudaStream_t st) {
   IBS_CUDA_TRY(cudaMemsetAsync(plan.counter.p, 0, sizeof(int), st));
   if (plan.n_split > 0) IBS_CUDA_TRY(cudaMemsetAsync(plan.partial.p, 0, plan.partial.cap, st));
-  IBS_CUDA_TRY(launch_planes_batch(static_cast<const PlaneJob*>(plan.jobs.p), n_subsets, plan.total_ctas,
-                                   ctx->status_dev, st));
   if (is_tc_mode(plan.mode)) {
     const int fmt = tc_fmt_of(plan.mode);
-    IBS_CUDA_TRY(launch_tc_expand(static_cast<const TcExpandJob*>(plan.tc_jobs.p), n_subsets, plan.tc_ctas, fmt, st));
+    IBS_CUDA_TRY(launch_tc_gather(static_cast<const TcGatherJob*>(plan.tc_jobs.p), n_subsets, plan.tc_ctas, fmt,
+                                  ctx->status_dev, st));
     IBS_CUDA_TRY(launch_tc_batch(static_cast<const SubsetDev*>(plan.subsets.p),
                                  static_cast<const WorkItem*>(plan.items.p), plan.n_items, plan.grid, fmt,
                                  static_cast<int*>(plan.counter.p), ctx->status_dev, st));
   } else {
+    IBS_CUDA_TRY(launch_planes_batch(static_cast<const PlaneJob*>(plan.jobs.p), n_subsets, plan.total_ctas,
+                                     ctx->status_dev, st));
     IBS_CUDA_TRY(launch_batch(plan.mode, static_cast<const SubsetDev*>(plan.subsets.p),
                               static_cast<const WorkItem*>(plan.items.p), plan.n_items,
                               static_cast<int*>(plan.counter.p), ctx->status_dev, plan.grid, st));
@@ -728,7 +787,7 @@ extern "C" ibs_status ibs_compute_batch(ibs_ctx* ctx, const uint8_t* pool, int64
   BatchPlan& plan = *it->second;
   if (ibs_status s = plan_upload(ctx, plan, pool, pool_n, subs, shapes, st)) return s;
   IBS_CUDA_TRY(cudaGraphLaunch(plan.exec, st));
-  ctx->last_info[0] = (is_tc_mode(plan.mode) ? 4 : 3) + (plan.n_split > 0 ? 1 : 0);
+  ctx->last_info[0] = 3 + (plan.n_split > 0 ? 1 : 0);
   ctx->last_info[1] = plan.tiles;
   ctx->last_info[2] = plan.split_policy;
   return IBS_OK;
@@ -773,6 +832,7 @@ extern "C" ibs_status ibs_shutdown(ibs_ctx* ctx) {
     free_buf(ctx, ctx->planes);
     free_buf(ctx, ctx->partial);
     free_buf(ctx, ctx->tile_list);
+    for (DevBuf* b : {&ctx->single_items, &ctx->single_split, &ctx->single_counter}) free_buf(ctx, *b);
     for (auto* v : {&ctx->timing_used, &ctx->timing_free})
       for (auto& r : *v)
         for (auto& e : r.ev)

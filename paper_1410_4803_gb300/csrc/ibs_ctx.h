@@ -87,6 +87,10 @@ struct ibs_ctx {
   ibs::DevBuf planes, partial;
   ibs::DevBuf tile_list;          // tensor-core grouped tile order, for tile_list_T tiles per side
   int64_t tile_list_T = -1;
+  // persistent tensor-core work list of the last (n, m, format, SMs, group)
+  std::vector<int64_t> single_key;
+  ibs::DevBuf single_items, single_split, single_counter;
+  int64_t single_n_items = 0, single_n_split = 0;
   int* status_host = nullptr;     // mapped pinned status word
   int* status_dev = nullptr;
 
@@ -112,6 +116,12 @@ void free_buf(ibs_ctx* ctx, DevBuf& b);
 bool reserve_bytes(ibs_ctx* ctx, size_t bytes);
 void release_bytes(ibs_ctx* ctx, size_t bytes);
 int pick_mode(const ibs_ctx* ctx);
+// The pair kernels a context uses (flags, else the library defaults): the
+// tensor-core form or a POPC kernel, the tensor-core operand format, the
+// POPC variant.
+bool ctx_use_tc(const ibs_ctx* ctx);
+int ctx_tc_format(const ibs_ctx* ctx);
+int ctx_popc_mode(const ibs_ctx* ctx);
 
 // Serving engine (ibs_serve.cu).
 ibs_status serve_panel_load(ibs_ctx* ctx, const uint8_t* panel, int64_t n_panel, int64_t m);

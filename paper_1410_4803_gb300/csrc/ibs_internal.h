@@ -112,12 +112,13 @@ cudaError_t launch_topk(const int32_t* counts, int64_t q, int64_t n_panel, int k
                         double* out_dist, cudaStream_t st);
 int pair_kernel_ctas_per_sm(int mode);
 
-// Expansion of one subset's bit planes into its FP8 planes.
-struct TcExpandJob {
-  const uint32_t* bits;   // bit planes (64-sample blocks, 12-word chunks)
-  int64_t bit_chunks;     // 12-word chunks of the bit planes
-  uint8_t* tc;            // FP8 planes
-  int64_t n, nb, nc;
+// Gather-transpose of one subset straight into tensor-core operand planes:
+// samples sel[0..n) of the source pool over markers var_begin .. var_begin+m-1.
+struct TcGatherJob {
+  BedSource src;          // pool rows, sample index list, pool size
+  int64_t m, n;           // markers in the window, samples
+  uint8_t* tc;            // operand planes of the subset
+  int64_t nb, nc;         // 128-sample blocks, chunks
   int64_t cta_begin;      // first CTA of this job in the flattened grid
 };
 
@@ -136,12 +137,29 @@ cudaError_t launch_tc_pairs(const uint8_t* planes, int64_t n, int64_t m, int fmt
                             double* out_dist, int32_t* partial, bool square, int* status, const int2* tile_list,
                             cudaStream_t st);
 void tc_tile_order(int64_t T, int G, std::vector<int2>& out);
-cudaError_t launch_tc_expand(const TcExpandJob* jobs_dev, int n_jobs, int64_t total_ctas, int fmt, cudaStream_t st);
+int64_t tc_gather_ctas(int64_t n, int64_t nc);  // CTAs of one job of the gather launch
+cudaError_t launch_tc_gather(const TcGatherJob* jobs_dev, int n_jobs, int64_t total_ctas, int fmt, int* status,
+                             cudaStream_t st);
 // Batched tensor-core pairs: SubsetDev.planes holds operand planes, n_blocks and
 // n_chunks count 128-sample blocks and chunks, and WorkItem tiles and K ranges
 // are in those units.
 cudaError_t launch_tc_batch(const SubsetDev* subs, const WorkItem* items, int64_t n_items, int grid, int fmt,
                             int* counter, int* status, cudaStream_t st);
+// One matrix through the persistent kernel (ibs_compute): work list, launch,
+// and the finalisation of the split tiles.
+void tc_single_items(int64_t n, int64_t m, int fmt, int num_sms, int group, std::vector<WorkItem>& items,
+                     std::vector<int2>& split_tiles);
+cudaError_t launch_tc_single(const SubsetDev& sd, const WorkItem* items, int64_t n_items, int grid, int fmt,
+                             int* counter, int* status, cudaStream_t st);
+cudaError_t launch_tc_finalize_tiles(const int2* tiles, int64_t n_tiles, const int32_t* partial, int64_t n,
+                                     int32_t* out_counts, double* out_dist, cudaStream_t st);
+// Serving, tensor-core form: CrossItem.qplanes points at a 128-row query block
+// of operand planes, row_out has 128 entries, pb is a 128-sample panel block.
+cudaError_t launch_tc_cross(const uint8_t* panel, int64_t n_panel, int64_t n_chunks, const CrossItem* items,
+                            int64_t n_items, int grid, int fmt, int* counter, int* status, cudaStream_t st);
+cudaError_t launch_tc_gather_rows(const RowSrc* rows, int64_t n_rows, int64_t n_chunks, uint8_t* dst,
+                                  cudaStream_t st);
+int tc_block_samples();  // 128
 size_t pair_kernel_smem_bytes();
 
 // Integer-pipe microbenchmark (ibs_probe.cu).

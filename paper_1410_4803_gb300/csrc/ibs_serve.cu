@@ -1,11 +1,13 @@
 // Serving engine: a resident reference panel and continuous batching of
 // query requests.
 //
-// The panel's bit planes stay on the device.  A host thread owns a CUDA stream
-// and runs steps.  A step packs the query rows of EVERY admitted request
-// densely into 64-row query blocks (a gather kernel copies each row's planes,
+// The panel's planes stay on the device: operand planes of the tensor-core
+// form (128-sample blocks), or bit planes of the POPC kernels (64-sample
+// blocks), whichever the context's pair kernel is.  A host thread owns a CUDA
+// stream and runs steps.  A step packs the query rows of EVERY admitted
+// request densely into query blocks (a gather kernel copies each row's planes,
 // and every row keeps its own output pointer) and runs them against a range
-// of 64-sample panel blocks.  Each panel block is therefore read once per step
+// of panel blocks.  Each panel block is therefore read once per step
 // however many requests are in flight, and the items of a step are ordered
 // panel-block-major so the CTAs sharing a panel block run together and hit it
 // in L2.  The step length adapts to the load: with few rows in flight one step
@@ -38,8 +40,11 @@ constexpr int kMaxQuery = 4096;     // rows per request
 constexpr int kMaxK = 64;           // top-k limit of the kernel
 constexpr int64_t kMaxRows = 4096;  // query rows admitted at once (slot limit)
 constexpr int64_t kStepWaves = 16;  // a step aims at this many waves of (query block, panel block) tiles
+constexpr int64_t kStepWavesTc = 4; // ... of the tensor-core form's 4x larger tiles
 constexpr int64_t kMinStepDiv = 32; // ... and covers at least 1/32 of the panel
 constexpr size_t kMemMargin = (size_t)1 << 30;
+constexpr int64_t kTcBlock = 128;          // samples per tensor-core block
+constexpr size_t kTcChunkBytes = 16384;    // one (block, chunk) of operand planes
 
 enum class RState { Pending, Active, Finishing, Done };
 
@@ -54,7 +59,6 @@ struct Request {
   std::vector<uint8_t> host_packed;
   DevBuf packed, planes, counts, tidx, tdist;
   size_t reserved = 0;
-  PlaneGeom g;
   int64_t blocks_done = 0;  // panel blocks processed since admission
   cudaEvent_t done_ev = nullptr;
   ibs_status status = IBS_OK;
@@ -76,11 +80,21 @@ PtrKind ptr_kind(const void* p) {
 
 }  // namespace
 
+// Planes geometry in the units of the engine's pair kernel.
+struct Geo {
+  int64_t blocks, chunks;  // sample blocks, marker chunks
+  size_t bytes;            // plane bytes
+};
+
 class ServeEngine {
  public:
   ibs_ctx* ctx;
-  PlaneGeom pg;
-  DevBuf panel_planes;
+  PlaneGeom pg;          // panel sizes (pg.n, pg.m) and, for POPC, the bit-plane geometry
+  bool tc = false;       // tensor-core pair kernel (else POPC)
+  int fmt = 0;           // tensor-core operand format
+  int64_t blk = kSB;     // samples per block: 128 (tensor core) or 64 (POPC)
+  Geo pgeo{};            // the panel's geometry
+  DevBuf panel_planes, counter;
   cudaStream_t stream = nullptr;
   std::thread worker;
   std::mutex mu;
@@ -109,9 +123,35 @@ class ServeEngine {
 
   explicit ServeEngine(ibs_ctx* c) : ctx(c) {}
 
+  Geo geo(int64_t n) const {
+    if (tc) return {(n + kTcBlock - 1) / kTcBlock, tc_chunks(pg.m, fmt), tc_planes_bytes(n, pg.m, fmt)};
+    const PlaneGeom g = PlaneGeom::make(n, pg.m);
+    return {g.n_blocks, g.n_chunks, g.bytes()};
+  }
+  size_t chunk_block_bytes() const { return tc ? (size_t)kTcChunkBytes : (size_t)kChunkBytes; }
+
+  // Planes of n samples from a packed device matrix, on stream s.
+  cudaError_t build_planes(const uint8_t* packed, int64_t n, void* planes, cudaStream_t s) const {
+    if (tc) return launch_tc_planes(packed, n, pg.m, static_cast<uint8_t*>(planes), fmt, s);
+    BedSource src;
+    src.packed = packed;
+    src.row_bytes = (n + 3) / 4;
+    src.n_src = n;
+    return launch_planes(src, n, pg.m, PlaneGeom::make(n, pg.m), static_cast<uint32_t*>(planes), ctx->status_dev,
+                         s);
+  }
+
+  cudaError_t cross(const CrossItem* items, int64_t n_items, cudaStream_t s) const {
+    if (tc)
+      return launch_tc_cross(static_cast<const uint8_t*>(panel_planes.p), pg.n, pgeo.chunks, items, n_items,
+                             (int)std::min<int64_t>(ctx->num_sms, std::max<int64_t>(1, n_items)), fmt,
+                             static_cast<int*>(counter.p), ctx->status_dev, s);
+    return launch_cross(pick_mode(ctx), static_cast<const uint32_t*>(panel_planes.p), pg.n, pg.n_blocks,
+                        pg.n_chunks, items, n_items, ctx->status_dev, s);
+  }
+
   size_t mem_need(int64_t q, int k, bool counts_dev, bool topk_dev) const {
-    const PlaneGeom g = PlaneGeom::make(q, pg.m);
-    size_t b = (size_t)pg.m * (size_t)((q + 3) / 4) + g.bytes();
+    size_t b = (size_t)pg.m * (size_t)((q + 3) / 4) + geo(q).bytes;
     if (!counts_dev) b += (size_t)q * pg.n * 16;
     if (!topk_dev) b += (size_t)q * k * 12;
     return b + 4096;
@@ -171,9 +211,8 @@ class ServeEngine {
     if (active_rows + r->q > kMaxRows && active_rows > 0) return false;
     const size_t need = mem_need(r->q, r->k, r->counts_on_dev, r->topk_on_dev);
     if (!reserve_request(*r, need)) return false;
-    r->g = PlaneGeom::make(r->q, pg.m);
     const size_t pk = (size_t)pg.m * (size_t)((r->q + 3) / 4);
-    if (alloc(r->packed, pk, stream) || alloc(r->planes, r->g.bytes(), stream) ||
+    if (alloc(r->packed, pk, stream) || alloc(r->planes, geo(r->q).bytes, stream) ||
         (!r->counts_on_dev && alloc(r->counts, (size_t)r->q * pg.n * 16, stream)) ||
         (!r->topk_on_dev && r->k > 0 &&
          (alloc(r->tidx, (size_t)r->q * r->k * 4, stream) || alloc(r->tdist, (size_t)r->q * r->k * 8, stream)))) {
@@ -181,11 +220,7 @@ class ServeEngine {
       return false;
     }
     cudaMemcpyAsync(r->packed.p, r->host_packed.data(), pk, cudaMemcpyHostToDevice, stream);
-    BedSource src;
-    src.packed = static_cast<const uint8_t*>(r->packed.p);
-    src.row_bytes = (r->q + 3) / 4;
-    src.n_src = r->q;
-    launch_planes(src, r->q, pg.m, r->g, static_cast<uint32_t*>(r->planes.p), ctx->status_dev, stream);
+    build_planes(static_cast<const uint8_t*>(r->packed.p), r->q, r->planes.p, stream);
     cudaEventCreateWithFlags(&r->done_ev, cudaEventDisableTiming);
     r->blocks_done = 0;
     r->state = RState::Active;
@@ -224,8 +259,8 @@ class ServeEngine {
   // Step-level buffers: dense query planes for kMaxRows rows and the per-row
   // source / output tables (double-buffered host staging).
   ibs_status alloc_step_buffers() {
-    const PlaneGeom g = PlaneGeom::make(kMaxRows, pg.m);
-    if (ibs_status s = ensure_buf(ctx, step_planes, g.bytes())) return s;
+    if (ibs_status s = ensure_buf(ctx, step_planes, geo(kMaxRows).bytes)) return s;
+    if (ibs_status s = ensure_buf(ctx, counter, 256)) return s;
     for (int s = 0; s < 2; ++s) {
       if (ibs_status e = ensure_buf(ctx, rows_dev[s], kMaxRows * sizeof(RowSrc))) return e;
       if (ibs_status e = ensure_buf(ctx, outs_dev[s], kMaxRows * sizeof(int32_t*))) return e;
@@ -238,8 +273,8 @@ class ServeEngine {
     return IBS_OK;
   }
 
-  // One step: every active request's rows, packed densely into 64-row query
-  // blocks, against the current panel chunk.
+  // One step: every active request's rows, packed densely into query blocks,
+  // against the current panel chunk.
   void run_step() {
     const int slot = (int)(step_no & 1);
     if (step_ev[slot]) cudaEventSynchronize(step_ev[slot]);  // slot's host tables are free again
@@ -251,27 +286,28 @@ class ServeEngine {
         outs_host[slot][n_rows] = counts_ptr(*r) + (size_t)row * pg.n * 4;
         ++n_rows;
       }
-    const int64_t qblocks = (n_rows + kSB - 1) / kSB;
+    const int64_t qblocks = (n_rows + blk - 1) / blk;
     // Step length: about kStepWaves waves of tiles, at least 1/kMinStepDiv of
     // the panel, at most the whole panel.  Few rows in flight -> one step
     // covers the whole panel (a lone request costs one launch, as on the
     // unbatched path); many rows -> shorter steps that new requests can join
     // between.
-    int64_t len = (kStepWaves * grid_ctas + qblocks - 1) / std::max<int64_t>(1, qblocks);
-    len = std::max<int64_t>(len, (pg.n_blocks + kMinStepDiv - 1) / kMinStepDiv);
-    len = std::min<int64_t>(len, pg.n_blocks);
+    int64_t len = ((tc ? kStepWavesTc : kStepWaves) * grid_ctas + qblocks - 1) / std::max<int64_t>(1, qblocks);
+    len = std::max<int64_t>(len, (pgeo.blocks + kMinStepDiv - 1) / kMinStepDiv);
+    len = std::min<int64_t>(len, pgeo.blocks);
     const size_t n_items = (size_t)qblocks * (size_t)len;
     ensure_items(std::max<size_t>(n_items, 1));
     CrossItem* h = items_host[slot];
     size_t t = 0;
     int32_t** outs_d = static_cast<int32_t**>(outs_dev[slot].p);
+    const size_t qblock_bytes = (size_t)pgeo.chunks * chunk_block_bytes();
     for (int64_t k = 0; k < len; ++k) {
-      const int64_t pb = (cursor + k) % pg.n_blocks;  // wraps around the panel
+      const int64_t pb = (cursor + k) % pgeo.blocks;  // wraps around the panel
       for (int64_t b = 0; b < qblocks; ++b) {
         CrossItem& it = h[t++];
-        it.qplanes = static_cast<const uint32_t*>(step_planes.p) + (size_t)b * pg.n_chunks * kChunkWords;
-        it.row_out = outs_d + b * kSB;
-        it.q_rows = (int32_t)std::min<int64_t>(kSB, n_rows - b * kSB);
+        it.qplanes = reinterpret_cast<const uint32_t*>(static_cast<const uint8_t*>(step_planes.p) + b * qblock_bytes);
+        it.row_out = outs_d + b * blk;
+        it.q_rows = (int32_t)std::min<int64_t>(blk, n_rows - b * blk);
         it.pb = (int32_t)pb;
       }
     }
@@ -279,19 +315,22 @@ class ServeEngine {
       cudaMemcpyAsync(rows_dev[slot].p, rows_host[slot], n_rows * sizeof(RowSrc), cudaMemcpyHostToDevice, stream);
       cudaMemcpyAsync(outs_dev[slot].p, outs_host[slot], n_rows * sizeof(int32_t*), cudaMemcpyHostToDevice, stream);
       cudaMemcpyAsync(items_dev[slot].p, h, t * sizeof(CrossItem), cudaMemcpyHostToDevice, stream);
-      launch_gather_rows(static_cast<const RowSrc*>(rows_dev[slot].p), n_rows, pg.n_chunks,
-                         static_cast<uint32_t*>(step_planes.p), stream);
-      launch_cross(pick_mode(ctx), static_cast<const uint32_t*>(panel_planes.p), pg.n, pg.n_blocks, pg.n_chunks,
-                   static_cast<const CrossItem*>(items_dev[slot].p), (int64_t)t, ctx->status_dev, stream);
+      if (tc)
+        launch_tc_gather_rows(static_cast<const RowSrc*>(rows_dev[slot].p), n_rows, pgeo.chunks,
+                              static_cast<uint8_t*>(step_planes.p), stream);
+      else
+        launch_gather_rows(static_cast<const RowSrc*>(rows_dev[slot].p), n_rows, pg.n_chunks,
+                           static_cast<uint32_t*>(step_planes.p), stream);
+      cross(static_cast<const CrossItem*>(items_dev[slot].p), (int64_t)t, stream);
     }
-    cursor = (cursor + len) % pg.n_blocks;
+    cursor = (cursor + len) % pgeo.blocks;
     std::vector<std::shared_ptr<Request>> still;
     for (auto& r : active) {
       // A request joined at some cursor position and is done once it has seen
       // every panel block (blocks seen twice near the end are rewritten with
       // the same counts).
       r->blocks_done += len;
-      if (r->blocks_done >= pg.n_blocks) {
+      if (r->blocks_done >= pgeo.blocks) {
         finish(*r);
         finishing.push_back(r);
       } else {
@@ -391,6 +430,7 @@ class ServeEngine {
     }
     if (panel_planes.p) free_buf(ctx, panel_planes);
     free_buf(ctx, step_planes);
+    free_buf(ctx, counter);
     for (int s = 0; s < 2; ++s) {
       free_buf(ctx, rows_dev[s]);
       free_buf(ctx, outs_dev[s]);
@@ -427,8 +467,12 @@ ibs_status serve_panel_load(ibs_ctx* ctx, const uint8_t* panel, int64_t n_panel,
   serve_stop(ctx);
   auto eng = std::make_shared<ServeEngine>(ctx);
   eng->pg = PlaneGeom::make(n_panel, m);
+  eng->tc = ctx_use_tc(ctx);
+  eng->fmt = ctx_tc_format(ctx);
+  eng->blk = eng->tc ? kTcBlock : kSB;
+  eng->pgeo = eng->geo(n_panel);
   IBS_CUDA_TRY(cudaStreamCreateWithFlags(&eng->stream, cudaStreamNonBlocking));
-  if (ibs_status s = ensure_buf(ctx, eng->panel_planes, eng->pg.bytes())) {
+  if (ibs_status s = ensure_buf(ctx, eng->panel_planes, eng->pgeo.bytes)) {
     cudaStreamDestroy(eng->stream);
     return s;
   }
@@ -446,19 +490,14 @@ ibs_status serve_panel_load(ibs_ctx* ctx, const uint8_t* panel, int64_t n_panel,
     IBS_CUDA_TRY(cudaMemcpyAsync(tmp, panel, bytes, cudaMemcpyHostToDevice, eng->stream));
     src_dev = static_cast<const uint8_t*>(tmp);
   }
-  BedSource src;
-  src.packed = src_dev;
-  src.row_bytes = (n_panel + 3) / 4;
-  src.n_src = n_panel;
-  IBS_CUDA_TRY(launch_planes(src, n_panel, m, eng->pg, static_cast<uint32_t*>(eng->panel_planes.p), ctx->status_dev,
-                             eng->stream));
+  IBS_CUDA_TRY(eng->build_planes(src_dev, n_panel, eng->panel_planes.p, eng->stream));
   IBS_CUDA_TRY(cudaStreamSynchronize(eng->stream));
   if (tmp) cudaFree(tmp);
   if (ibs_status st = eng->alloc_step_buffers()) {
     eng->shutdown();
     return st;
   }
-  eng->grid_ctas = ctx->num_sms * pair_kernel_ctas_per_sm(pick_mode(ctx));
+  eng->grid_ctas = eng->tc ? ctx->num_sms : ctx->num_sms * pair_kernel_ctas_per_sm(pick_mode(ctx));
   // Requests draw on the device's default stream-ordered pool; keep freed
   // blocks cached in it so steady-state serving does not go back to the driver.
   cudaMemPool_t mp;
@@ -471,7 +510,7 @@ ibs_status serve_panel_load(ibs_ctx* ctx, const uint8_t* panel, int64_t n_panel,
     cudaMemGetInfo(&free_b, &total_b);
     eng->pool_budget = free_b > kMemMargin ? free_b - kMemMargin : 0;
   }
-  eng->fixed_bytes = eng->panel_planes.cap + eng->step_planes.cap +
+  eng->fixed_bytes = eng->panel_planes.cap + eng->step_planes.cap + eng->counter.cap +
                      2 * (eng->rows_dev[0].cap + eng->outs_dev[0].cap);
   eng->start();
   std::lock_guard<std::mutex> lk(ctx->mu);
@@ -595,7 +634,7 @@ ibs_status serve_query_sync(ibs_ctx* ctx, const uint8_t* q, int64_t nq, int k, i
   if (ibs_status s = validate_query(eng, q, nq, k, oc, oi, od, counts_dev, topk_dev)) return s;
   ServeEngine& e = *eng;
   const PlaneGeom pg = e.pg;
-  const PlaneGeom qg = PlaneGeom::make(nq, pg.m);
+  const Geo qg = e.geo(nq);
   const size_t pk = (size_t)pg.m * (size_t)((nq + 3) / 4);
   Request r;
   r.q = nq;
@@ -608,9 +647,11 @@ ibs_status serve_query_sync(ibs_ctx* ctx, const uint8_t* q, int64_t nq, int k, i
     cudaStreamDestroy(s);
     return fail(IBS_ENOMEM, "the serving memory budget is exhausted");
   }
-  if (e.alloc(r.packed, pk, s) || e.alloc(r.planes, qg.bytes(), s) ||
+  DevBuf counter;
+  if (e.alloc(r.packed, pk, s) || e.alloc(r.planes, qg.bytes, s) || e.alloc(counter, 256, s) ||
       (!counts_dev && e.alloc(r.counts, (size_t)nq * pg.n * 16, s)) ||
       (!topk_dev && k > 0 && (e.alloc(r.tidx, (size_t)nq * k * 4, s) || e.alloc(r.tdist, (size_t)nq * k * 8, s)))) {
+    if (counter.p) cudaFreeAsync(counter.p, s);
     e.release(r, s);
     cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
@@ -622,12 +663,13 @@ ibs_status serve_query_sync(ibs_ctx* ctx, const uint8_t* q, int64_t nq, int k, i
   DevBuf outs_d;
   cudaError_t ce = cudaMallocAsync(&outs_d.p, outs.size() * sizeof(int32_t*), s);
   std::vector<CrossItem> items;
-  for (int64_t pb = 0; pb < pg.n_blocks; ++pb)
-    for (int64_t qb = 0; qb < qg.n_blocks; ++qb) {
+  const size_t qblock_bytes = (size_t)qg.chunks * e.chunk_block_bytes();
+  for (int64_t pb = 0; pb < e.pgeo.blocks; ++pb)
+    for (int64_t qb = 0; qb < qg.blocks; ++qb) {
       CrossItem it;
-      it.qplanes = static_cast<const uint32_t*>(r.planes.p) + (size_t)qb * qg.n_chunks * kChunkWords;
-      it.row_out = static_cast<int32_t**>(outs_d.p) + qb * kSB;
-      it.q_rows = (int32_t)std::min<int64_t>(kSB, nq - qb * kSB);
+      it.qplanes = reinterpret_cast<const uint32_t*>(static_cast<const uint8_t*>(r.planes.p) + qb * qblock_bytes);
+      it.row_out = static_cast<int32_t**>(outs_d.p) + qb * e.blk;
+      it.q_rows = (int32_t)std::min<int64_t>(e.blk, nq - qb * e.blk);
       it.pb = (int32_t)pb;
       items.push_back(it);
     }
@@ -641,14 +683,16 @@ ibs_status serve_query_sync(ibs_ctx* ctx, const uint8_t* q, int64_t nq, int k, i
   }
   if (ce == cudaSuccess)
     ce = cudaMemcpyAsync(items_dev.p, items.data(), items.size() * sizeof(CrossItem), cudaMemcpyHostToDevice, s);
-  BedSource src;
-  src.packed = static_cast<const uint8_t*>(r.packed.p);
-  src.row_bytes = (nq + 3) / 4;
-  src.n_src = nq;
-  if (ce == cudaSuccess) ce = launch_planes(src, nq, pg.m, qg, static_cast<uint32_t*>(r.planes.p), ctx->status_dev, s);
-  if (ce == cudaSuccess)
-    ce = launch_cross(pick_mode(ctx), static_cast<const uint32_t*>(e.panel_planes.p), pg.n, pg.n_blocks, pg.n_chunks,
-                      static_cast<const CrossItem*>(items_dev.p), (int64_t)items.size(), ctx->status_dev, s);
+  if (ce == cudaSuccess) ce = e.build_planes(static_cast<const uint8_t*>(r.packed.p), nq, r.planes.p, s);
+  if (ce == cudaSuccess) {
+    if (e.tc)
+      ce = launch_tc_cross(static_cast<const uint8_t*>(e.panel_planes.p), pg.n, e.pgeo.chunks,
+                           static_cast<const CrossItem*>(items_dev.p), (int64_t)items.size(),
+                           (int)std::min<int64_t>(ctx->num_sms, (int64_t)items.size()), e.fmt,
+                           static_cast<int*>(counter.p), ctx->status_dev, s);
+    else
+      ce = e.cross(static_cast<const CrossItem*>(items_dev.p), (int64_t)items.size(), s);
+  }
   if (ce == cudaSuccess && k > 0)
     ce = launch_topk(cnt, nq, pg.n, k, topk_dev ? oi : static_cast<int32_t*>(r.tidx.p),
                      topk_dev ? od : static_cast<double*>(r.tdist.p), s);
@@ -660,6 +704,7 @@ ibs_status serve_query_sync(ibs_ctx* ctx, const uint8_t* q, int64_t nq, int k, i
   }
   if (items_dev.p) cudaFreeAsync(items_dev.p, s);
   if (outs_d.p) cudaFreeAsync(outs_d.p, s);
+  if (counter.p) cudaFreeAsync(counter.p, s);
   e.release(r, s);
   cudaError_t se = cudaStreamSynchronize(s);
   if (ce == cudaSuccess) ce = se;

@@ -54,7 +54,7 @@ constexpr int kTPlanes = 4;                       // V, U, Q, R
 constexpr int kTileBytes = kTB * 32;              // one plane of one chunk: 128 rows x 32 bytes
 constexpr int kTChunkBytes = kTPlanes * kTileBytes;  // 16 KiB per (block, chunk)
 constexpr int kTThreads = 128;
-constexpr int kTStages = 4;
+constexpr int kTStages = 4;                       // ring depth (6 and 7 stages measured no faster)
 constexpr size_t kTcSmem = (size_t)kTStages * 2 * kTChunkBytes + 1024;
 constexpr uint32_t kTmemCols = 512;               // accumulators at 0/128/256, FP4 scale factors at 384..511
 constexpr uint32_t kSfCol = 384;                  // scale factors of A at 384, of B at 448
@@ -434,13 +434,21 @@ __global__ void __launch_bounds__(kTThreads, 1)
 }
 
 // ---------------------------------------------------------------------------
-// Batched form.  The operand planes of every subset are expanded from the
-// subset's bit planes (V, P, Q, R words, 64-sample blocks, 12-word chunks);
-// one CTA writes one (128-sample block, chunk) tile, a thread 16 bytes of
-// each plane of one sample: FP8, 16 markers of the chunk's bit-plane word;
-// FP4, one of the chunk's two words.
+// Batched form: gather-transpose from the pool.  CTA = (subset, 128-sample
+// block, group of kGatherChunks chunks), thread r = sample r of the block.
+// The job lookup and the sample's pool index are read once per CTA; then, per
+// chunk, the thread reads its sample's code at each marker (one byte per
+// marker row, all loads of a chunk independent; the lanes of a warp read
+// neighbouring samples of the same row, so a sorted index list gives
+// near-contiguous reads), builds the present / het / hom A2 / hom A1 masks
+// over the chunk's markers and writes its rows of the four planes.  An index
+// outside the pool is not read: the sample is treated as all-missing and the
+// status word reports it.
+constexpr int kGatherChunks = 8;
+
 template <int F>
-__global__ void __launch_bounds__(256) tc_expand_kernel(const TcExpandJob* __restrict__ jobs, int n_jobs) {
+__global__ void __launch_bounds__(kTB) tc_gather_kernel(const TcGatherJob* __restrict__ jobs, int n_jobs, int* status) {
+  constexpr int K = kMarkers<F>;
   const int64_t cta = blockIdx.x;
   int lo = 0, hi = n_jobs - 1;
   while (lo < hi) {
@@ -448,45 +456,200 @@ __global__ void __launch_bounds__(256) tc_expand_kernel(const TcExpandJob* __res
     if (jobs[mid].cta_begin <= cta) lo = mid;
     else hi = mid - 1;
   }
-  const TcExpandJob& j = jobs[lo];
+  const TcGatherJob j = jobs[lo];
+  const int64_t groups = (j.nc + kGatherChunks - 1) / kGatherChunks;
   const int64_t local = cta - j.cta_begin;
-  const int64_t b = local / j.nc, c = local % j.nc;  // operand block, operand chunk
-  const int r = threadIdx.x >> 1, half = threadIdx.x & 1;
+  const int64_t b = local / groups, cg = local % groups;
+  const int r = threadIdx.x;
   const int64_t s = b * kTB + r;
-  const int64_t word = F == kTcFp4 ? 2 * c + half : c;  // bit-plane word (32 markers)
-  uint4 w = make_uint4(0u, 0u, 0u, 0u);                 // V, P, Q, R words of this sample
-  if (s < j.n && word < j.bit_chunks * kKC) {
-    const int64_t blk = s / kSB, slot = s % kSB, chunk = word / kKC, kw = word % kKC;
-    w = *reinterpret_cast<const uint4*>(j.bits + (((blk * j.bit_chunks + chunk) * kKC + kw) * kSB + slot) * kPlanes);
+  int64_t ps = -1;
+  if (s < j.n) {
+    ps = j.src.sel[s];
+    if (ps < 0 || ps >= j.src.n_src) {
+      atomicExch(status, 1);
+      ps = -1;
+    }
   }
-  if constexpr (F != kTcFp4) {
-    const int sh = half ? 16 : 0;
-    w = make_uint4((w.x >> sh) & 0xFFFFu, (w.y >> sh) & 0xFFFFu, (w.z >> sh) & 0xFFFFu, (w.w >> sh) & 0xFFFFu);
+  const int sh = ps >= 0 ? 2 * (int)(ps & 3) : 0;
+  const int64_t row_bytes = j.src.row_bytes;
+  const uint8_t* col = j.src.packed + j.src.var_begin * row_bytes + (ps >= 0 ? (ps >> 2) : 0);
+  const int64_t c_end = (cg + 1) * kGatherChunks < j.nc ? (cg + 1) * kGatherChunks : j.nc;
+  for (int64_t c = cg * kGatherChunks; c < c_end; ++c) {
+    uint8_t* base = j.tc + (size_t)(b * j.nc + c) * kTChunkBytes;
+    // 32 markers at a time: one 32-bit mask per plane, one K half (16 bytes)
+    // of the FP4 row or the whole FP8 row
+#pragma unroll 1
+    for (int h = 0; h < K / 32; ++h) {
+      const int64_t k0 = c * K + 32 * h;
+      const int kn = (int)(j.m - k0 < 32 ? j.m - k0 : 32);  // markers of this group inside the window
+      uint32_t H = 0, L = ~0u;                             // all missing unless read
+      if (ps >= 0 && kn > 0) {
+        const uint8_t* p = col + k0 * row_bytes;
+        uint32_t byte[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) byte[k] = k < kn ? __ldg(p + (int64_t)k * row_bytes) : 0x55u;
+        H = 0;
+        L = 0;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+          const uint32_t code = (byte[k] >> sh) & 3u;
+          H |= (code >> 1) << k;
+          L |= (code & 1u) << k;
+        }
+      }
+      const uint32_t V = H | ~L, P = H & ~L, Q = H & L, R = ~H & ~L;
+      if constexpr (F == kTcFp4) {
+        store_plane_row<F>(base + tile_off(r, 16 * h), V, P, Q, R);
+      } else {
+        store_plane_row<F>(base + tile_off(r, 0), V & 0xFFFFu, P & 0xFFFFu, Q & 0xFFFFu, R & 0xFFFFu);
+        store_plane_row<F>(base + tile_off(r, 16), V >> 16, P >> 16, Q >> 16, R >> 16);
+      }
+    }
   }
-  store_plane_row<F>(j.tc + (size_t)(b * j.nc + c) * kTChunkBytes + tile_off(r, half ? 16 : 0), w.x, w.y, w.z, w.w);
 }
 
-// Persistent batched pair kernel: 8 warps.  Warp 0 claims work items from a
-// global counter (the list is ordered for L2 reuse: a subset's tiles in the
-// grouped order, subsets by decreasing cost) and streams each item's chunks
-// through the ring; warp 1 issues the MMAs; warps 4..7 read the accumulators
-// back (warp w reads TMEM lanes 32*(w-4)..) and store the counts; warps 2
-// and 3 only hold the block's shape.  Claimed item indices reach the MMA and
-// epilogue warps through a small shared-memory queue (qfull / qempty, -1
-// ends the stream).  Two barriers hand the accumulators over per item: tfull
-// (the item's MMAs are done) and tempty (the epilogue has read them), so the
-// producer keeps prefetching the next item's chunks while the epilogue runs.
-constexpr int kBatchQueue = 8;
+// ---------------------------------------------------------------------------
+// Persistent tensor-core launches (batched subsets, serving steps).  A work
+// policy W maps an item index to the tile it computes (tile(): operand
+// blocks and K range, read by the copy and MMA warps) and to the stores of
+// its counts (epi(): per-row state; store(): 32 accumulator columns).
 
-template <int F>
+// One tile of a persistent launch: the operand blocks it multiplies and its
+// K range in chunks.
+struct TcTile {
+  const uint8_t* a;  // row block, chunk 0
+  const uint8_t* b;  // column block, chunk 0
+  int64_t c0, c1;
+  bool same;         // a == b: one copy per chunk serves both operands
+};
+
+// Decoded counts of one pair from the three accumulators.
+struct PairCounts {
+  int32_t i0, i1, n;
+};
+__device__ __forceinline__ PairCounts decode(uint32_t vn, uint32_t vu, uint32_t v0) {
+  const int32_t nn = __float2int_rn(__uint_as_float(vn));
+  const int32_t uu = __float2int_rn(__uint_as_float(vu));
+  return {__float2int_rn(__uint_as_float(v0)), (nn - uu) / 2, nn};
+}
+
+// (subset, tile, K range) items; upper-triangle outputs (or partial counts
+// when the tile is split over K).
+struct TriEpi {
+  int64_t gi, j0, n;
+  int32_t* counts;
+  double* dist;
+  int32_t* partial;
+  bool split;
+  __device__ void store(int cg, const uint32_t (&vn)[32], const uint32_t (&vu)[32], const uint32_t (&v0)[32]) const {
+    if (gi >= n) return;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int64_t gj = j0 + cg * 32 + j;
+      if (gj >= n || gj < gi) continue;
+      const PairCounts c = decode(vn[j], vu[j], v0[j]);
+      const int64_t p = tri_index(gi, gj, n);
+      if (split) {
+        int32_t* o = partial + p * 4;
+        atomicAdd(o + 0, c.i0);
+        atomicAdd(o + 1, c.i1);
+        atomicAdd(o + 3, c.n);
+        continue;
+      }
+      reinterpret_cast<int4*>(counts)[p] = make_int4(c.i0, c.i1, c.n - c.i0 - c.i1, c.n);
+      if (dist)
+        dist[p] = c.n == 0 ? __longlong_as_double(0x7ff8000000000000LL)
+                           : (double)(c.i1 + 2 * c.i0) / (2.0 * (double)c.n);
+    }
+  }
+};
+__device__ __forceinline__ TcTile tri_tile_of(const WorkItem& w, const SubsetDev& sd) {
+  const uint8_t* pl = reinterpret_cast<const uint8_t*>(sd.planes);
+  return {pl + (size_t)w.I * sd.n_chunks * kTChunkBytes, pl + (size_t)w.J * sd.n_chunks * kTChunkBytes, w.c0, w.c1,
+          w.I == w.J};
+}
+__device__ __forceinline__ TriEpi tri_epi_of(const WorkItem& w, const SubsetDev& sd, int row) {
+  return {(int64_t)w.I * kTB + row, (int64_t)w.J * kTB, sd.n, sd.out_counts, sd.out_dist, sd.partial, w.split != 0};
+}
+
+// Batched subsets: the subset of an item is looked up per item.
+struct BatchWork {
+  const SubsetDev* subs;
+  const WorkItem* items;
+  using Epi = TriEpi;
+  __device__ TcTile tile(int64_t it) const {
+    const WorkItem w = items[it];
+    return tri_tile_of(w, subs[w.subset]);
+  }
+  __device__ Epi epi(int64_t it, int row) const {
+    const WorkItem w = items[it];
+    return tri_epi_of(w, subs[w.subset], row);
+  }
+};
+
+// One matrix (ibs_compute): the subset travels in the kernel parameters.
+struct SingleWork {
+  SubsetDev sd;
+  const WorkItem* items;
+  using Epi = TriEpi;
+  __device__ TcTile tile(int64_t it) const { return tri_tile_of(items[it], sd); }
+  __device__ Epi epi(int64_t it, int row) const { return tri_epi_of(items[it], sd, row); }
+};
+
+// Serving: (128-row query block, 128-sample panel block) items over the
+// whole marker range; row r of the block writes counts [n_panel][4] through
+// its own output pointer.
+struct CrossWork {
+  const CrossItem* items;
+  const uint8_t* panel;
+  int64_t n_panel, n_chunks;
+  __device__ TcTile tile(int64_t it) const {
+    const CrossItem ci = items[it];
+    return {reinterpret_cast<const uint8_t*>(ci.qplanes), panel + (size_t)ci.pb * n_chunks * kTChunkBytes, 0,
+            n_chunks, false};
+  }
+  struct Epi {
+    int32_t* out;
+    int64_t j0, n;
+    __device__ void store(int cg, const uint32_t (&vn)[32], const uint32_t (&vu)[32],
+                          const uint32_t (&v0)[32]) const {
+      if (!out) return;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int64_t gj = j0 + cg * 32 + j;
+        if (gj >= n) continue;
+        const PairCounts c = decode(vn[j], vu[j], v0[j]);
+        reinterpret_cast<int4*>(out)[gj] = make_int4(c.i0, c.i1, c.n - c.i0 - c.i1, c.n);
+      }
+    }
+  };
+  __device__ Epi epi(int64_t it, int row) const {
+    const CrossItem ci = items[it];
+    return {row < ci.q_rows ? ci.row_out[row] : nullptr, (int64_t)ci.pb * kTB, n_panel};
+  }
+};
+
+// The persistent kernel: 8 warps.  Warp 0 claims work items from a global
+// counter (list order, so the CTAs running at one time work on neighbouring
+// tiles and share their operand blocks through L2) and streams each item's
+// chunks through the ring; warp 1 issues the MMAs; warps 4..7 read the
+// accumulators back (warp w reads TMEM lanes 32*(w-4)..) and store the
+// counts; warps 2 and 3 only hold the block's shape.  Claimed item indices
+// reach the MMA and epilogue warps through a small shared-memory queue
+// (qfull / qempty, -1 ends the stream).  Two barriers hand the accumulators
+// over per item: tfull (the item's MMAs are done) and tempty (the epilogue has
+// read them), so the producer keeps prefetching the next item's chunks while
+// the epilogue runs.
+constexpr int kQueue = 8;
+
+template <int F, class W>
 __global__ void __launch_bounds__(256, 1)
-    tc_batch_kernel(const SubsetDev* __restrict__ subs, const WorkItem* __restrict__ items, int64_t n_items,
-                    int* counter, int* status) {
+    tc_persistent_kernel(const W work, int64_t n_items, int* counter, int* status) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* ring = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ __align__(8) uint64_t full[kTStages], empty[kTStages], tfull, tempty, drain;
-  __shared__ __align__(8) uint64_t qfull[kBatchQueue], qempty[kBatchQueue];
-  __shared__ int64_t q_item[kBatchQueue];
+  __shared__ __align__(8) uint64_t qfull[kQueue], qempty[kQueue];
+  __shared__ int64_t q_item[kQueue];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -495,7 +658,7 @@ __global__ void __launch_bounds__(256, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    for (int s = 0; s < kBatchQueue; ++s) {
+    for (int s = 0; s < kQueue; ++s) {
       mbar_init(&qfull[s], 1);
       mbar_init(&qempty[s], 5);  // the MMA warp and the four epilogue warps
     }
@@ -532,8 +695,8 @@ __global__ void __launch_bounds__(256, 1)
   auto aborted = [&]() { return __any_sync(0xffffffffu, *(volatile int*)&abort_flag != 0); };
   // Wait for queue slot e and read the item index there (-1: no more items).
   auto queue_get = [&](uint32_t e, int64_t& it) {
-    const int qs = (int)(e % kBatchQueue);
-    const bool ok = mbar_wait_bounded(&qfull[qs], (e / kBatchQueue) & 1u);
+    const int qs = (int)(e % kQueue);
+    const bool ok = mbar_wait_bounded(&qfull[qs], (e / kQueue) & 1u);
     if (__any_sync(0xffffffffu, !ok)) return false;
     it = *(volatile int64_t*)&q_item[qs];
     __syncwarp();
@@ -548,8 +711,8 @@ __global__ void __launch_bounds__(256, 1)
       if (lane == 0) it = atomicAdd(counter, 1);
       it = __shfl_sync(0xffffffffu, it, 0);
       const bool last = it >= n_items;
-      const int qs = (int)(e % kBatchQueue);
-      const bool qok = e < (uint32_t)kBatchQueue || mbar_wait_bounded(&qempty[qs], ((e / kBatchQueue) - 1) & 1u);
+      const int qs = (int)(e % kQueue);
+      const bool qok = e < (uint32_t)kQueue || mbar_wait_bounded(&qempty[qs], ((e / kQueue) - 1) & 1u);
       if (__any_sync(0xffffffffu, !qok)) {
         fail(true);
         break;
@@ -561,14 +724,9 @@ __global__ void __launch_bounds__(256, 1)
       }
       __syncwarp();
       if (last) break;
-      const WorkItem w = items[it];
-      const SubsetDev sd = subs[w.subset];
-      const uint8_t* pl = reinterpret_cast<const uint8_t*>(sd.planes);
-      const uint8_t* rowblk = pl + (size_t)w.I * sd.n_chunks * kTChunkBytes;
-      const uint8_t* colblk = pl + (size_t)w.J * sd.n_chunks * kTChunkBytes;
-      const bool same = w.I == w.J;
+      const TcTile t = work.tile(it);
       bool stop = false;
-      for (int64_t k = w.c0; k < w.c1; ++k, ++g) {
+      for (int64_t k = t.c0; k < t.c1; ++k, ++g) {
         const int s = (int)(g % kTStages);
         const bool ok = g < (uint32_t)kTStages || mbar_wait_bounded(&empty[s], ((g / kTStages) - 1) & 1u);
         if (__any_sync(0xffffffffu, !ok)) {
@@ -582,9 +740,9 @@ __global__ void __launch_bounds__(256, 1)
         }
         if (lane == 0) {
           uint8_t* dst = ring + (size_t)s * 2 * kTChunkBytes;
-          mbar_arrive_expect_tx(&full[s], same ? kTChunkBytes : 2 * kTChunkBytes);
-          bulk_g2s(dst, rowblk + (size_t)k * kTChunkBytes, kTChunkBytes, &full[s]);
-          if (!same) bulk_g2s(dst + kTChunkBytes, colblk + (size_t)k * kTChunkBytes, kTChunkBytes, &full[s]);
+          mbar_arrive_expect_tx(&full[s], t.same ? kTChunkBytes : 2 * kTChunkBytes);
+          bulk_g2s(dst, t.a + (size_t)k * kTChunkBytes, kTChunkBytes, &full[s]);
+          if (!t.same) bulk_g2s(dst + kTChunkBytes, t.b + (size_t)k * kTChunkBytes, kTChunkBytes, &full[s]);
         }
         __syncwarp();
       }
@@ -599,14 +757,13 @@ __global__ void __launch_bounds__(256, 1)
         break;
       }
       if (it < 0) break;
-      const WorkItem w = items[it];
-      const bool same = w.I == w.J;
+      const TcTile t = work.tile(it);
       // the epilogue must have read the previous item's accumulators
       const bool free_ok = e == 0 || mbar_wait_bounded(&tempty, (e - 1) & 1u);
       bool stop = __any_sync(0xffffffffu, !free_ok);
       if (!stop) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        for (int64_t k = w.c0; k < w.c1; ++k, ++g) {
+        for (int64_t k = t.c0; k < t.c1; ++k, ++g) {
           const int s = (int)(g % kTStages);
           const bool ok = mbar_wait_bounded(&full[s], (g / kTStages) & 1u);
           if (__any_sync(0xffffffffu, !ok)) {
@@ -616,8 +773,8 @@ __global__ void __launch_bounds__(256, 1)
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           if (lane == 0) {
             const uint32_t a0 = smem_addr(ring + (size_t)s * 2 * kTChunkBytes);
-            const uint32_t b0 = same ? a0 : a0 + kTChunkBytes;
-            chunk_mmas<F>(tmem, a0, b0, k > w.c0 ? 1u : 0u);
+            const uint32_t b0 = t.same ? a0 : a0 + kTChunkBytes;
+            chunk_mmas<F>(tmem, a0, b0, k > t.c0 ? 1u : 0u);
             umma_commit(&empty[s]);
           }
           __syncwarp();
@@ -652,9 +809,7 @@ __global__ void __launch_bounds__(256, 1)
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const WorkItem w = items[it];
-      const SubsetDev sd = subs[w.subset];
-      const int64_t gi = (int64_t)w.I * kTB + row;
+      const typename W::Epi ep = work.epi(it, row);
 #pragma unroll 1
       for (int cg = 0; cg < kTB / 32; ++cg) {
         uint32_t vn[32], vu[32], v0[32];
@@ -668,28 +823,7 @@ __global__ void __launch_bounds__(256, 1)
           __syncwarp();
           if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&tempty)) : "memory");
         }
-        if (gi >= sd.n) continue;
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int64_t gj = (int64_t)w.J * kTB + cg * 32 + j;
-          if (gj >= sd.n || gj < gi) continue;
-          const int32_t nn = __float2int_rn(__uint_as_float(vn[j]));
-          const int32_t uu = __float2int_rn(__uint_as_float(vu[j]));
-          const int32_t i0 = __float2int_rn(__uint_as_float(v0[j]));
-          const int32_t i1 = (nn - uu) / 2;
-          const int64_t p = tri_index(gi, gj, sd.n);
-          if (w.split) {
-            int32_t* o = sd.partial + p * 4;
-            atomicAdd(o + 0, i0);
-            atomicAdd(o + 1, i1);
-            atomicAdd(o + 3, nn);
-            continue;
-          }
-          reinterpret_cast<int4*>(sd.out_counts)[p] = make_int4(i0, i1, nn - i0 - i1, nn);
-          if (sd.out_dist)
-            sd.out_dist[p] = nn == 0 ? __longlong_as_double(0x7ff8000000000000LL)
-                                     : (double)(i1 + 2 * i0) / (2.0 * (double)nn);
-        }
+        ep.store(cg, vn, vu, v0);
       }
     }
   }
@@ -697,6 +831,45 @@ __global__ void __launch_bounds__(256, 1)
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+// Serving: copy dense query rows (each a row of some request's operand
+// planes) into 128-row step blocks.  CTA = (step block, chunk); each thread
+// moves 16-byte pieces (row, plane, K half).
+__global__ void __launch_bounds__(256) tc_gather_rows_kernel(const RowSrc* __restrict__ rows, int64_t n_rows,
+                                                             int64_t n_chunks, uint8_t* __restrict__ dst) {
+  const int64_t c = blockIdx.x, qb = blockIdx.y;
+  for (int p = threadIdx.x; p < kTB * 8; p += blockDim.x) {
+    const int r = p % kTB, piece = p / kTB;  // piece = plane * 2 + K half
+    const int64_t d = qb * kTB + r;
+    if (d >= n_rows) continue;
+    const RowSrc src = rows[d];
+    const int64_t sb = src.row / kTB, sr = src.row % kTB;
+    const int off_plane = (piece >> 1) * kTileBytes, half = piece & 1;
+    const uint8_t* from = reinterpret_cast<const uint8_t*>(src.planes) + (size_t)(sb * n_chunks + c) * kTChunkBytes +
+                          off_plane + tile_off((int)sr, half * 16);
+    uint8_t* to = dst + (size_t)(qb * n_chunks + c) * kTChunkBytes + off_plane + tile_off(r, half * 16);
+    *reinterpret_cast<uint4*>(to) = *reinterpret_cast<const uint4*>(from);
+  }
+}
+
+// Split-K finalisation of the listed tiles only: partial [P][4] (IBS0, IBS1,
+// -, N) -> counts and distance of every pair of the tile.
+__global__ void __launch_bounds__(256) tc_finalize_tiles_kernel(const int2* __restrict__ tiles,
+                                                                const int32_t* __restrict__ partial, int64_t n,
+                                                                int32_t* __restrict__ out_counts,
+                                                                double* __restrict__ out_dist) {
+  const int2 t = tiles[blockIdx.x];
+  for (int p = threadIdx.x; p < kTB * kTB; p += blockDim.x) {
+    const int64_t gi = (int64_t)t.x * kTB + p / kTB, gj = (int64_t)t.y * kTB + p % kTB;
+    if (gi >= n || gj >= n || gj < gi) continue;
+    const int64_t q = tri_index(gi, gj, n);
+    const int4 v = reinterpret_cast<const int4*>(partial)[q];
+    reinterpret_cast<int4*>(out_counts)[q] = make_int4(v.x, v.y, v.w - v.x - v.y, v.w);
+    if (out_dist)
+      out_dist[q] = v.w == 0 ? __longlong_as_double(0x7ff8000000000000LL)
+                             : (double)(v.y + 2 * v.x) / (2.0 * (double)v.w);
   }
 }
 
@@ -796,25 +969,108 @@ int64_t tc_tiles(int64_t n) {
   return nb * (nb + 1) / 2;
 }
 
-cudaError_t launch_tc_expand(const TcExpandJob* jobs_dev, int n_jobs, int64_t total_ctas, int fmt, cudaStream_t st) {
+cudaError_t launch_tc_gather(const TcGatherJob* jobs_dev, int n_jobs, int64_t total_ctas, int fmt, int* status,
+                             cudaStream_t st) {
   if (total_ctas <= 0) return cudaSuccess;
   if (total_ctas > 2147483647LL) return cudaErrorInvalidValue;
   if (fmt == kTcFp4)
-    tc_expand_kernel<kTcFp4><<<(unsigned)total_ctas, 256, 0, st>>>(jobs_dev, n_jobs);
+    tc_gather_kernel<kTcFp4><<<(unsigned)total_ctas, kTB, 0, st>>>(jobs_dev, n_jobs, status);
   else
-    tc_expand_kernel<kTcFp8><<<(unsigned)total_ctas, 256, 0, st>>>(jobs_dev, n_jobs);
+    tc_gather_kernel<kTcFp8><<<(unsigned)total_ctas, kTB, 0, st>>>(jobs_dev, n_jobs, status);
+  return cudaGetLastError();
+}
+
+template <class W>
+cudaError_t launch_persistent(const W& work, int64_t n_items, int grid, int fmt, int* counter, int* status,
+                              cudaStream_t st) {
+  if (n_items <= 0) return cudaSuccess;
+  if (grid < 1 || n_items > 2147483647LL - grid) return cudaErrorInvalidValue;  // the claim counter is an int
+  auto kern = fmt == kTcFp4 ? tc_persistent_kernel<kTcFp4, W> : tc_persistent_kernel<kTcFp8, W>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, 256, kTcSmem, st>>>(work, n_items, counter, status);
   return cudaGetLastError();
 }
 
 cudaError_t launch_tc_batch(const SubsetDev* subs, const WorkItem* items, int64_t n_items, int grid, int fmt,
                             int* counter, int* status, cudaStream_t st) {
-  if (n_items <= 0) return cudaSuccess;
-  if (n_items > 2147483647LL - grid) return cudaErrorInvalidValue;  // the claim counter is an int
-  auto kern = fmt == kTcFp4 ? tc_batch_kernel<kTcFp4> : tc_batch_kernel<kTcFp8>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
-  if (e != cudaSuccess) return e;
-  kern<<<grid, 256, kTcSmem, st>>>(subs, items, n_items, counter, status);
+  return launch_persistent(BatchWork{subs, items}, n_items, grid, fmt, counter, status, st);
+}
+
+cudaError_t launch_tc_single(const SubsetDev& sd, const WorkItem* items, int64_t n_items, int grid, int fmt,
+                             int* counter, int* status, cudaStream_t st) {
+  return launch_persistent(SingleWork{sd, items}, n_items, grid, fmt, counter, status, st);
+}
+
+cudaError_t launch_tc_finalize_tiles(const int2* tiles, int64_t n_tiles, const int32_t* partial, int64_t n,
+                                     int32_t* out_counts, double* out_dist, cudaStream_t st) {
+  if (n_tiles <= 0) return cudaSuccess;
+  if (n_tiles > 2147483647LL) return cudaErrorInvalidValue;
+  tc_finalize_tiles_kernel<<<(unsigned)n_tiles, 256, 0, st>>>(tiles, partial, n, out_counts, out_dist);
   return cudaGetLastError();
 }
+
+int64_t tc_gather_ctas(int64_t n, int64_t nc) {
+  return (n + kTB - 1) / kTB * ((nc + kGatherChunks - 1) / kGatherChunks);
+}
+
+// Work list of one n-sample matrix for the persistent kernel: the tiles in
+// the grouped order, whole, except the tiles of a final partial wave, which
+// are split over K into about as many pieces as there are CTAs (their counts
+// are added into the partial triangle and finalised per tile).  Tile counts
+// below one wave split every tile by the split-count rule.
+void tc_single_items(int64_t n, int64_t m, int fmt, int num_sms, int group, std::vector<WorkItem>& items,
+                     std::vector<int2>& split_tiles) {
+  items.clear();
+  split_tiles.clear();
+  const int64_t T = (n + kTB - 1) / kTB, nc = tc_chunks(m, fmt);
+  std::vector<int2> order;
+  tc_tile_order(T, group, order);
+  const int64_t W = (int64_t)order.size();
+  int64_t whole = W, pieces = 1;
+  if (W < num_sms) {
+    whole = 0;
+    pieces = tc_splits_for(W, nc, num_sms);
+  } else {
+    const int64_t R = W % num_sms;
+    if (R > 0 && R * 4 <= num_sms * 3) {  // a tail wave at most 3/4 full
+      whole = W - R;
+      pieces = std::max<int64_t>(2, (num_sms + R / 2) / R);
+    }
+  }
+  pieces = std::max<int64_t>(1, std::min<int64_t>(pieces, std::min<int64_t>(64, nc)));
+  for (int64_t t = 0; t < W; ++t) {
+    const int64_t np = t < whole ? 1 : pieces;
+    if (np > 1) split_tiles.push_back(order[t]);
+    for (int64_t p = 0; p < np; ++p) {
+      WorkItem w;
+      w.subset = 0;
+      w.I = order[t].x;
+      w.J = order[t].y;
+      w.c0 = (int32_t)(nc * p / np);
+      w.c1 = (int32_t)(nc * (p + 1) / np);
+      w.split = np > 1 ? 1 : 0;
+      items.push_back(w);
+    }
+  }
+}
+
+cudaError_t launch_tc_cross(const uint8_t* panel, int64_t n_panel, int64_t n_chunks, const CrossItem* items,
+                            int64_t n_items, int grid, int fmt, int* counter, int* status, cudaStream_t st) {
+  return launch_persistent(CrossWork{items, panel, n_panel, n_chunks}, n_items, grid, fmt, counter, status, st);
+}
+
+cudaError_t launch_tc_gather_rows(const RowSrc* rows, int64_t n_rows, int64_t n_chunks, uint8_t* dst,
+                                  cudaStream_t st) {
+  if (n_rows <= 0) return cudaSuccess;
+  const int64_t qb = (n_rows + kTB - 1) / kTB;
+  if (n_chunks > 2147483647LL || qb > 65535) return cudaErrorInvalidValue;
+  tc_gather_rows_kernel<<<dim3((unsigned)n_chunks, (unsigned)qb), 256, 0, st>>>(rows, n_rows, n_chunks, dst);
+  return cudaGetLastError();
+}
+
+int tc_block_samples() { return kTB; }
 
 }  // namespace ibs

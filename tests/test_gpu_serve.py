@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 @pytest.fixture(scope="module")
 def panel():
     from paper_1410_4803_gb300 import synth
-    # 10,040 panel samples = 157 blocks of 64, more than one step covers for a 2,048-row request
+    # 10,040 panel samples = 157 blocks of 64 (79 of 128), more than one step covers for a 2,048-row request
     w = synth.serving_panel(n_base_per_pop=2000, n_pop=5, m=16000, n_offspring=30, n_dup=10, seed=21)
     G = oracle.unpack(w.packed, w.n, w.m)
     return w, G
@@ -26,16 +26,21 @@ def _pinned(shape, dtype):
     return torch.empty(shape, dtype=dtype).pin_memory()
 
 
-def test_serving_mix_equals_alone_and_oracle(panel):
+@pytest.mark.parametrize("kernel", ["tensor-core", "popc"])
+def test_serving_mix_equals_alone_and_oracle(panel, kernel):
+    """Both pair-kernel families: the tensor-core form (FP4 operand planes,
+    128-sample blocks) and the carry-save POPC kernel (bit planes, 64-sample
+    blocks)."""
     import torch
     from paper_1410_4803_gb300 import ibs, synth
     w, Gp = panel
-    ctx = ibs.ibs_init(0)
+    ctx = ibs.ibs_init(0, flags=ibs.IBS_KERNEL_TC if kernel == "tensor-core" else ibs.IBS_KERNEL_CSA)
     try:
         ibs.ibs_panel_load(ctx, torch.from_numpy(w.packed).cuda(), w.n, w.m)
         # The first request is large enough that its work spans several engine
-        # steps (a step holds about 16 waves of 64 x 64 tiles), so the small
-        # requests submitted right after it join while it is still running.
+        # steps (a step holds about 16 waves of 64 x 64 tiles, or 4 waves of
+        # the tensor-core form's 128 x 128 tiles), so the small requests
+        # submitted right after it join while it is still running.
         sizes = [2048, 1, 64, 65, 3, 150, 17, 128, 2, 90, 33, 7, 129]
         k = 16
         reqs = []
@@ -136,7 +141,14 @@ def test_serving_k_larger_than_panel_and_admission():
     pcodes = random_codes(rng, n_panel, m)
     pcodes[3] = 1  # all-missing panel sample: NaN distance, ranked last
     pp = pack_codes(pcodes)
-    ctx = ibs.ibs_init(0, workspace_bytes=4 << 20)
+    # The engine's fixed buffers (panel planes, step planes for 4,096 rows,
+    # step tables) take ~1.8 MB with bit planes and ~6.2 MB with FP4 operand
+    # planes; the budget leaves room for a small request beside them but not
+    # for a 4,096-row one.
+    probe = ibs.ibs_init(0)
+    tc = ibs.ibs_kernel_info(probe)["family"] == "tensor-core"
+    ibs.ibs_shutdown(probe)
+    ctx = ibs.ibs_init(0, workspace_bytes=(8 << 20) if tc else (4 << 20))
     try:
         ibs.ibs_panel_load(ctx, pp, n_panel, m)
         qc = random_codes(rng, 3, m)
@@ -151,8 +163,8 @@ def test_serving_k_larger_than_panel_and_admission():
             ti, td = oracle.topk(wd[r], k)
             assert (oi.numpy()[r] == ti).all()
             assert (oi.numpy()[r, n_panel:] == -1).all() and np.isnan(od.numpy()[r, n_panel - 1:]).all()
-        # 4 MiB budget: the engine holds ~1.8 MB (panel planes, step buffers); a request needing ~2.9 MB
-        # can never fit beside them and is refused at once
+        # a request needing ~2.9 MB (bit planes) or ~7.2 MB (FP4 planes) can never fit beside the
+        # engine's buffers and is refused at once
         big = 4096
         with pytest.raises(ibs.IbsError) as ei:
             ibs.ibs_query(ctx, np.zeros((m, big // 4), np.uint8), big, k, _pinned((big, n_panel, 4), torch.int32),
