@@ -416,7 +416,8 @@ ItemGeom item_geom(const SubsetShape& s, int mode) {
 // subsets whose tiles would be too large relative to one CTA's fair share
 // (split_policy 1), sorted by descending cost (longest processing time first).
 void build_items(const std::vector<SubsetShape>& shapes, int mode, int split_policy, int grid,
-                 std::vector<WorkItem>& items, std::vector<int>& subset_split, int64_t& tiles_total) {
+                 std::vector<WorkItem>& items, std::vector<int>& subset_split, int64_t& tiles_total,
+                 std::vector<int64_t>* order_out = nullptr, std::vector<int64_t>* item_off_out = nullptr) {
   items.clear();
   subset_split.assign(shapes.size(), 1);
   double total = 0;
@@ -447,9 +448,12 @@ void build_items(const std::vector<SubsetShape>& shapes, int mode, int split_pol
       return item_geom(shapes[a], mode).nc > item_geom(shapes[b], mode).nc;
     });
     std::vector<int2> tiles;
+    if (order_out) order_out->assign(order.begin(), order.end());
+    if (item_off_out) item_off_out->clear();
     for (size_t k : order) {
       const ItemGeom ig = item_geom(shapes[k], mode);
       const int pieces = subset_split[k];
+      if (item_off_out) item_off_out->push_back((int64_t)items.size());
       tc_tile_order(ig.T, kTcBatchGroup, tiles);
       for (const int2& t : tiles)
         for (int p = 0; p < pieces; ++p) {
@@ -463,6 +467,7 @@ void build_items(const std::vector<SubsetShape>& shapes, int mode, int split_pol
           items.push_back(w);
         }
     }
+    if (item_off_out) item_off_out->push_back((int64_t)items.size());
     return;
   }
   for (size_t k = 0; k < shapes.size(); ++k) {
@@ -510,7 +515,8 @@ ibs_status plan_build(ibs_ctx* ctx, BatchPlan& plan, const std::vector<SubsetSha
   plan.grid = ctx->num_sms * (tc ? 1 : pair_kernel_ctas_per_sm(mode));
   std::vector<WorkItem> items;
   std::vector<int> split;
-  build_items(shapes, mode, split_policy, plan.grid, items, split, plan.tiles);
+  std::vector<int64_t> subset_item_off;
+  build_items(shapes, mode, split_policy, plan.grid, items, split, plan.tiles, &plan.order, &subset_item_off);
   plan.n_items = (int64_t)items.size();
   if (plan.grid > plan.n_items) plan.grid = (int)std::max<int64_t>(1, plan.n_items);
   // planes and partial offsets
@@ -544,6 +550,35 @@ ibs_status plan_build(ibs_ctx* ctx, BatchPlan& plan, const std::vector<SubsetSha
       plan.tc_ctas += tc_gather_ctas(shapes[k].n, item_geom(shapes[k], mode).nc);
     }
     if (plan.tc_ctas > 2147483647LL) return fail(IBS_EINVAL, "batch too large for one gather launch");
+    // Stages: about 10% of the comparisons first (its gather is the only one
+    // not overlapped), then three of about 30%.
+    double total = 0;
+    for (const auto& sh : shapes) total += (double)sh.n * (double)sh.n * (double)sh.m;
+    const double bounds[] = {0.10, 0.40, 0.70, 1.01};
+    plan.stage_item_off.assign(1, 0);
+    plan.stage_job_off.assign(1, 0);
+    plan.stage_ctas.clear();
+    double acc = 0;
+    int64_t ctas = 0;
+    int b = 0;
+    for (size_t q = 0; q < plan.order.size(); ++q) {
+      const SubsetShape& sh = shapes[plan.order[q]];
+      acc += (double)sh.n * (double)sh.n * (double)sh.m;
+      ctas += tc_gather_ctas(sh.n, item_geom(sh, mode).nc);
+      const bool last = q + 1 == plan.order.size();
+      if (last || acc >= bounds[b] * total) {
+        plan.stage_item_off.push_back(subset_item_off[q + 1]);
+        plan.stage_job_off.push_back((int64_t)q + 1);
+        plan.stage_ctas.push_back(ctas);
+        ctas = 0;
+        while (b < 3 && acc >= bounds[b] * total) ++b;
+      }
+    }
+    if (plan.stage_ctas.size() > 1) {
+      IBS_CUDA_TRY(cudaStreamCreateWithFlags(&plan.side, cudaStreamNonBlocking));
+      plan.stage_ev.resize(plan.stage_ctas.size(), nullptr);
+      for (auto& e : plan.stage_ev) IBS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
     if (ibs_status s = ensure_buf(ctx, plan.tc_planes, tb)) return s;
     if (ibs_status s = ensure_buf(ctx, plan.tc_jobs, sizeof(TcGatherJob) * shapes.size())) return s;
     pb = 0;
@@ -598,21 +633,28 @@ ibs_status plan_upload(ibs_ctx* ctx, BatchPlan& plan, const uint8_t* pool, int64
   }
   if (is_tc_mode(plan.mode)) {
     // the pair kernel reads operand planes, in 128-sample blocks and MMA-K chunks
+    // gather jobs in processing order; CTA numbering restarts at every stage
     std::vector<TcGatherJob> tj(k);
     int64_t tcta = 0;
-    for (size_t i = 0; i < k; ++i) {
+    size_t stage = 0;
+    for (size_t q = 0; q < k; ++q) {
+      if ((int64_t)q == plan.stage_job_off[stage + 1]) {
+        ++stage;
+        tcta = 0;
+      }
+      const size_t i = (size_t)plan.order[q];
       const ItemGeom ig = item_geom(shapes[i], plan.mode);
       uint8_t* tcp = static_cast<uint8_t*>(plan.tc_planes.p) + plan.tc_offsets[i];
       sd[i].planes = reinterpret_cast<const uint32_t*>(tcp);
       sd[i].n_blocks = ig.T;
       sd[i].n_chunks = ig.nc;
-      tj[i].src = jobs[i].src;
-      tj[i].m = shapes[i].m;
-      tj[i].n = shapes[i].n;
-      tj[i].tc = tcp;
-      tj[i].nb = ig.T;
-      tj[i].nc = ig.nc;
-      tj[i].cta_begin = tcta;
+      tj[q].src = jobs[i].src;
+      tj[q].m = shapes[i].m;
+      tj[q].n = shapes[i].n;
+      tj[q].tc = tcp;
+      tj[q].nb = ig.T;
+      tj[q].nc = ig.nc;
+      tj[q].cta_begin = tcta;
       tcta += tc_gather_ctas(shapes[i].n, ig.nc);
     }
     IBS_CUDA_TRY(cudaMemcpyAsync(plan.tc_jobs.p, tj.data(), sizeof(TcGatherJob) * k, cudaMemcpyHostToDevice, st));
@@ -629,11 +671,30 @@ ibs_status plan_enqueue(ibs_ctx* ctx, BatchPlan& plan, int n_subsets, cudaStream
   if (plan.n_split > 0) IBS_CUDA_TRY(cudaMemsetAsync(plan.partial.p, 0, plan.partial.cap, st));
   if (is_tc_mode(plan.mode)) {
     const int fmt = tc_fmt_of(plan.mode);
-    IBS_CUDA_TRY(launch_tc_gather(static_cast<const TcGatherJob*>(plan.tc_jobs.p), n_subsets, plan.tc_ctas, fmt,
-                                  ctx->status_dev, st));
-    IBS_CUDA_TRY(launch_tc_batch(static_cast<const SubsetDev*>(plan.subsets.p),
-                                 static_cast<const WorkItem*>(plan.items.p), plan.n_items, plan.grid, fmt,
-                                 static_cast<int*>(plan.counter.p), ctx->status_dev, st));
+    const TcGatherJob* jobs = static_cast<const TcGatherJob*>(plan.tc_jobs.p);
+    const WorkItem* items = static_cast<const WorkItem*>(plan.items.p);
+    const int G = (int)plan.stage_ctas.size();
+    auto gather = [&](int g, cudaStream_t s) {
+      return launch_tc_gather(jobs + plan.stage_job_off[g], (int)(plan.stage_job_off[g + 1] - plan.stage_job_off[g]),
+                              plan.stage_ctas[g], fmt, ctx->status_dev, s);
+    };
+    IBS_CUDA_TRY(gather(0, st));
+    if (G > 1) {
+      // fork: the side stream runs the later stages' gathers
+      IBS_CUDA_TRY(cudaEventRecord(plan.stage_ev[0], st));
+      IBS_CUDA_TRY(cudaStreamWaitEvent(plan.side, plan.stage_ev[0], 0));
+    }
+    for (int g = 0; g < G; ++g) {
+      if (g + 1 < G) {
+        IBS_CUDA_TRY(gather(g + 1, plan.side));
+        IBS_CUDA_TRY(cudaEventRecord(plan.stage_ev[g + 1], plan.side));
+      }
+      if (g > 0) IBS_CUDA_TRY(cudaStreamWaitEvent(st, plan.stage_ev[g], 0));  // joins the side stream
+      const int64_t n_items = plan.stage_item_off[g + 1] - plan.stage_item_off[g];
+      IBS_CUDA_TRY(launch_tc_batch(static_cast<const SubsetDev*>(plan.subsets.p), items + plan.stage_item_off[g],
+                                   n_items, (int)std::min<int64_t>(plan.grid, n_items), fmt,
+                                   static_cast<int*>(plan.counter.p), ctx->status_dev, st));
+    }
   } else {
     IBS_CUDA_TRY(launch_planes_batch(static_cast<const PlaneJob*>(plan.jobs.p), n_subsets, plan.total_ctas,
                                      ctx->status_dev, st));
@@ -649,6 +710,12 @@ ibs_status plan_enqueue(ibs_ctx* ctx, BatchPlan& plan, int n_subsets, cudaStream
 }
 
 void plan_free(ibs_ctx* ctx, BatchPlan& plan) {
+  if (plan.side) cudaStreamSynchronize(plan.side);
+  for (auto& e : plan.stage_ev)
+    if (e) cudaEventDestroy(e);
+  plan.stage_ev.clear();
+  if (plan.side) cudaStreamDestroy(plan.side);
+  plan.side = nullptr;
   if (plan.exec) cudaGraphExecDestroy(plan.exec);
   if (plan.graph) cudaGraphDestroy(plan.graph);
   plan.exec = nullptr;
@@ -787,7 +854,7 @@ extern "C" ibs_status ibs_compute_batch(ibs_ctx* ctx, const uint8_t* pool, int64
   BatchPlan& plan = *it->second;
   if (ibs_status s = plan_upload(ctx, plan, pool, pool_n, subs, shapes, st)) return s;
   IBS_CUDA_TRY(cudaGraphLaunch(plan.exec, st));
-  ctx->last_info[0] = 3 + (plan.n_split > 0 ? 1 : 0);
+  ctx->last_info[0] = (is_tc_mode(plan.mode) ? 2 * (int64_t)plan.stage_ctas.size() : 3) + (plan.n_split > 0 ? 1 : 0);
   ctx->last_info[1] = plan.tiles;
   ctx->last_info[2] = plan.split_policy;
   return IBS_OK;

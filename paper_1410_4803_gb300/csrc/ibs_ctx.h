@@ -51,7 +51,14 @@ class ServeEngine;
 struct BatchPlan {
   std::vector<int64_t> shape_key;
   DevBuf planes, partial, subsets, jobs, items, split_ids, counter;
-  DevBuf tc_planes, tc_jobs;            // mode 3: FP8 planes and their expansion jobs
+  DevBuf tc_planes, tc_jobs;            // tensor-core modes: operand planes and their gather jobs
+  // Tensor-core modes: the subsets run in stages (contiguous groups of the
+  // cost-sorted subset order); the gather of stage g+1 runs on `side` while the
+  // pair kernel of stage g runs.
+  std::vector<int64_t> order;           // subset processing order
+  std::vector<int64_t> stage_item_off, stage_job_off, stage_ctas;  // per stage (+1 end entry for offsets)
+  cudaStream_t side = nullptr;
+  std::vector<cudaEvent_t> stage_ev;
   int64_t n_items = 0, total_ctas = 0, max_split_pairs = 0, tc_ctas = 0;
   int n_split = 0;
   int mode = 0, split_policy = 0, grid = 0;

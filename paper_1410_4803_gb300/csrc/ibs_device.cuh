@@ -112,6 +112,23 @@ constexpr int kLutAndOr = 0xEA;   // (a & b) | c
 constexpr int kLutXor3 = 0x96;    // a ^ b ^ c
 constexpr int kLutMaj = 0xE8;     // majority(a, b, c)
 
+// IBS distance (IBS1 + 2 IBS0) / (2N) in FP64, NaN when N = 0.  FP64
+// division is slow on this part, so the quotient is seeded in FP32 and
+// corrected once in FP64 (a Newton-Raphson step in residual form,
+// q1 = q0 + (a - q0 b) r0 with r0 ~ 1/b): the seed is within ~2^-22 of a/b and
+// r0 within 2^-24 of 1/b, so q1 is within ~2^-46 (about 1.1e-14) relative of
+// the exact quotient, well inside the 1e-12 bound.  Every kernel that writes a
+// distance uses this function, so all paths give identical doubles for
+// identical counts.
+__device__ __forceinline__ double ibs_dist(int32_t i0, int32_t i1, int32_t n) {
+  if (n == 0) return __longlong_as_double(0x7ff8000000000000LL);
+  const long long ai = (long long)i1 + 2 * (long long)i0, bi = 2 * (long long)n;
+  const double a = (double)ai, b = (double)bi;
+  const float r0 = __frcp_rn((float)bi);
+  const double q0 = (double)((float)ai * r0);
+  return fma(fma(-q0, b, a), (double)r0, q0);
+}
+
 // Triangle index of pair (i, j), i <= j.
 __host__ __device__ __forceinline__ int64_t tri_index(int64_t i, int64_t j, int64_t n) {
   return i * n - i * (i - 1) / 2 + (j - i);

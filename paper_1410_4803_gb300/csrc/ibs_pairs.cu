@@ -202,8 +202,7 @@ __device__ __forceinline__ void store_final(const Acc& a, int64_t I, int64_t J, 
       const int32_t nn = (int32_t)a.n[i][j], c0 = (int32_t)a.i0[i][j], c1 = (int32_t)a.i1[i][j];
       const int4 v = make_int4(c0, c1, nn - c0 - c1, nn);
       double d = 0.0;
-      if (out_dist) d = nn == 0 ? __longlong_as_double(0x7ff8000000000000LL)
-                                : (double)(c1 + 2 * c0) / (2.0 * (double)nn);
+      if (out_dist) d = ibs_dist(c0, c1, nn);
       if (!square) {
         const int64_t p = tri_index(gi, gj, n);
         reinterpret_cast<int4*>(out_counts)[p] = v;
@@ -365,7 +364,7 @@ __global__ void finalize_kernel(const int32_t* __restrict__ partial, int64_t n, 
     const int64_t j = i + (p - tri_index(i, i, n));
     const int4 q = reinterpret_cast<const int4*>(partial)[p];
     const int4 v = make_int4(q.x, q.y, q.w - q.x - q.y, q.w);
-    double d = q.w == 0 ? __longlong_as_double(0x7ff8000000000000LL) : (double)(q.y + 2 * q.x) / (2.0 * (double)q.w);
+    double d = ibs_dist(q.x, q.y, q.w);
     if (!square) {
       reinterpret_cast<int4*>(out_counts)[p] = v;
       if (out_dist) out_dist[p] = d;
@@ -387,8 +386,7 @@ __global__ void finalize_batch_kernel(const SubsetDev* __restrict__ subsets, con
     const int4 q = reinterpret_cast<const int4*>(sd.partial)[p];
     reinterpret_cast<int4*>(sd.out_counts)[p] = make_int4(q.x, q.y, q.w - q.x - q.y, q.w);
     if (sd.out_dist)
-      sd.out_dist[p] =
-          q.w == 0 ? __longlong_as_double(0x7ff8000000000000LL) : (double)(q.y + 2 * q.x) / (2.0 * (double)q.w);
+      sd.out_dist[p] = ibs_dist(q.x, q.y, q.w);
   }
 }
 

@@ -409,8 +409,7 @@ __global__ void __launch_bounds__(kTThreads, 1)
         }
         const int4 v = make_int4(i0, i1, nn - i0 - i1, nn);
         double d = 0.0;
-        if (out_dist) d = nn == 0 ? __longlong_as_double(0x7ff8000000000000LL)
-                                  : (double)(i1 + 2 * i0) / (2.0 * (double)nn);
+        if (out_dist) d = ibs_dist(i0, i1, nn);
         if (!square) {
           const int64_t p = tri_index(gi, gj, n);
           reinterpret_cast<int4*>(out_counts)[p] = v;
@@ -541,6 +540,8 @@ struct TriEpi {
   double* dist;
   int32_t* partial;
   bool split;
+  // Counts of accumulator columns 32*cg .. 32*cg+31 (run while the
+  // accumulators are read back).
   __device__ void store(int cg, const uint32_t (&vn)[32], const uint32_t (&vu)[32], const uint32_t (&v0)[32]) const {
     if (gi >= n) return;
 #pragma unroll
@@ -557,9 +558,18 @@ struct TriEpi {
         continue;
       }
       reinterpret_cast<int4*>(counts)[p] = make_int4(c.i0, c.i1, c.n - c.i0 - c.i1, c.n);
-      if (dist)
-        dist[p] = c.n == 0 ? __longlong_as_double(0x7ff8000000000000LL)
-                           : (double)(c.i1 + 2 * c.i0) / (2.0 * (double)c.n);
+    }
+  }
+  // Distances of the row, after the accumulators are handed back (so the
+  // FP64 work overlaps the next item's MMAs): each thread reads back the
+  // counts it stored itself.
+  __device__ void finish() const {
+    if (gi >= n || split || !dist) return;
+    const int64_t j1 = j0 + kTB < n ? j0 + kTB : n;
+    for (int64_t gj = gi > j0 ? gi : j0; gj < j1; ++gj) {
+      const int64_t p = tri_index(gi, gj, n);
+      const int4 c = reinterpret_cast<const int4*>(counts)[p];
+      dist[p] = ibs_dist(c.x, c.y, c.w);
     }
   }
 };
@@ -622,6 +632,7 @@ struct CrossWork {
         reinterpret_cast<int4*>(out)[gj] = make_int4(c.i0, c.i1, c.n - c.i0 - c.i1, c.n);
       }
     }
+    __device__ void finish() const {}
   };
   __device__ Epi epi(int64_t it, int row) const {
     const CrossItem ci = items[it];
@@ -825,6 +836,7 @@ __global__ void __launch_bounds__(256, 1)
         }
         ep.store(cg, vn, vu, v0);
       }
+      ep.finish();
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -868,8 +880,7 @@ __global__ void __launch_bounds__(256) tc_finalize_tiles_kernel(const int2* __re
     const int4 v = reinterpret_cast<const int4*>(partial)[q];
     reinterpret_cast<int4*>(out_counts)[q] = make_int4(v.x, v.y, v.w - v.x - v.y, v.w);
     if (out_dist)
-      out_dist[q] = v.w == 0 ? __longlong_as_double(0x7ff8000000000000LL)
-                             : (double)(v.y + 2 * v.x) / (2.0 * (double)v.w);
+      out_dist[q] = ibs_dist(v.x, v.y, v.w);
   }
 }
 
