@@ -140,6 +140,15 @@ def hbm_peak_gbs() -> float:
         return 6800.0
 
 
+def kernel_dtype(ibs, ctx) -> str:
+    """Arithmetic of a context's pair kernel: indicator products in E2M1 or E4M3
+    accumulated in FP32 (exact integer counts), or int32 for the integer form."""
+    k = ibs.ibs_kernel_info(ctx)
+    if k["family"] != "tensor-core":
+        return "int32"
+    return "e2m1xe2m1->f32" if k["tc_format"] == "e2m1" else "e4m3xe4m3->f32"
+
+
 def kernel_source_hash(files=("ibs_pairs.cu", "ibs_device.cuh")) -> str:
     h = hashlib.sha256()
     for f in files:
@@ -355,7 +364,9 @@ def run_plain(args, rank, world, local):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "int32",
+        # arithmetic of the pair kernel: E2M1 (or E4M3) indicator products accumulated
+        # in FP32, exact integer counts; the integer form computes in int32
+        "dtype": ("e2m1xe2m1->f32" if fp4 else "e4m3xe4m3->f32") if use_tc else "int32",
         "data": "synthetic",
         "config": {"workload": w.name + " (MAF U(0.01,0.5), 2% missing + 0.5% of variants at 30%), seed 1"
                    if args.workload == "plain" else w.name,
@@ -365,7 +376,7 @@ def run_plain(args, rank, world, local):
                    "parallelism": f"replicas x{world}", "kernel_mode": mode},
         "roofline": ({"bound": "alu", "achieved": achieved, "peak": roof["peak"], "unit": UNIT,
                       "frac": achieved / roof["peak"],
-                      "traffic": profiled_traffic(f"pair_kernel_{args.workload}.md"),
+                      "traffic": profiled_traffic(f"popc_tri_kernel_{args.workload}.md"),
                       "kernel": "tri_kernel (pair counts)", "kernel_ms": pairs_ms,
                       "peak_basis": f"{roof['comps_per_clk_sm']:.1f} comparisons/clk/SM x {probe['sms']} SMs x "
                                     f"{roof['sm_mhz']:.0f} MHz (median SM clock in the timed region); pipe rates "
@@ -376,7 +387,7 @@ def run_plain(args, rank, world, local):
                       "frac": 8.0 * achieved / 1e12 / tc_tflops,
                       "traffic": profiled_traffic(f"tc_kernel_{'fp4' if fp4 else 'fp8'}_{args.workload}.md",
                                                   ("ibs_tc.cu", "ibs_device.cuh")),
-                      "kernel": f"tc_tri_kernel (tcgen05 {'E2M1 kind::mxf4' if fp4 else 'E4M3 kind::f8f6f4'} "
+                      "kernel": f"tc_persistent_kernel (tcgen05 {'E2M1 kind::mxf4' if fp4 else 'E4M3 kind::f8f6f4'} "
                                 f"indicator GEMMs)", "kernel_ms": pairs_ms,
                       "peak_basis": f"measured bf16 burst TFLOP/s (MEASURED_PEAKS.json) x {tc_ratio:.0f}, the nominal "
                                     f"{'FP4' if fp4 else 'FP8'}/bf16 dense ratio; algorithmic flops = 8 per comparison "
@@ -458,8 +469,8 @@ def subset_packed_device(pool_dev, idx_dev, vb: int, vl: int):
 
 def run_batch(args, rank, world, local):
     """64 cohort subsets of a 30,000 x 600,000 pool: one batched call (gather
-    transpose + one persistent launch, graph-captured, autotuned) against the
-    plain path run once per subset."""
+    transpose from the pool and persistent pair launches in stages, graph-captured,
+    autotuned) against the plain path run once per subset."""
     import numpy as np
     import torch
     import oracle
@@ -556,13 +567,14 @@ def run_batch(args, rank, world, local):
             for b in range(a, rows.size):
                 if (got[oracle.tri_index(rows[a], rows[b], s.n)] != oc[a, b]).any():
                     oracle_ok = False
+    dtype_b = kernel_dtype(ibs, ctx_b)
     ibs.ibs_shutdown(ctx_b)
     ibs.ibs_shutdown(ctx_p)
     mb, mp = statistics.mean(ms_b), statistics.mean(ms_p)
     return {
         "metric": METRIC, "value": comps / (mb * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": mb, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "vs_baseline": None, "dtype": dtype_b, "data": "synthetic",
         "config": {"workload": f"batched: {len(subs)} subsets of pool n={w.n} m={w.m} "
                                f"(n ~ U[200, 8000], windows ~ U[10k, 200k]), seed 3",
                    "comparisons_per_step": comps, "plan": plan, "first_call_s_incl_autotune": first_call_s,
@@ -681,13 +693,14 @@ def run_serve(args, rank, world, local):
         results.append({"lambda_per_s": lam if lam > 0 else "saturation", "engine": eng, "plain": pln})
     clocks = clk.stop()
     stats = ibs.ibs_serve_stats_get(ctx)
+    dtype_s = kernel_dtype(ibs, ctx)
     ibs.ibs_shutdown(ctx)
     sat = [r for r in results if r["lambda_per_s"] == "saturation"]
     head = sat[0] if sat else results[-1]
     return {
         "metric": METRIC, "value": head["engine"]["throughput"], "unit": UNIT, "n_gpus": 1,
         "steps": len(results), "warmup": 1, "ms_per_step": head["engine"]["mean_ms"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": dtype_s, "data": "synthetic",
         "config": {"workload": f"serving: panel n={panel.n} m={panel.m} resident; requests of q = "
                                f"floor(exp(U(0, ln 512))) + 1 samples, Poisson arrivals; counts [q][n][4] and "
                                f"top-{k} to pinned host buffers", "distinct_payloads": n_payload,

@@ -558,19 +558,23 @@ ibs_status plan_build(ibs_ctx* ctx, BatchPlan& plan, const std::vector<SubsetSha
     plan.stage_item_off.assign(1, 0);
     plan.stage_job_off.assign(1, 0);
     plan.stage_ctas.clear();
+    plan.stage_max_chunks.clear();
     double acc = 0;
-    int64_t ctas = 0;
+    int64_t ctas = 0, max_chunks = 0;
     int b = 0;
     for (size_t q = 0; q < plan.order.size(); ++q) {
       const SubsetShape& sh = shapes[plan.order[q]];
       acc += (double)sh.n * (double)sh.n * (double)sh.m;
       ctas += tc_gather_ctas(sh.n, item_geom(sh, mode).nc);
+      max_chunks = std::max<int64_t>(max_chunks, item_geom(sh, mode).nc);
       const bool last = q + 1 == plan.order.size();
       if (last || acc >= bounds[b] * total) {
         plan.stage_item_off.push_back(subset_item_off[q + 1]);
         plan.stage_job_off.push_back((int64_t)q + 1);
         plan.stage_ctas.push_back(ctas);
+        plan.stage_max_chunks.push_back(max_chunks);
         ctas = 0;
+        max_chunks = 0;
         while (b < 3 && acc >= bounds[b] * total) ++b;
       }
     }
@@ -692,7 +696,7 @@ ibs_status plan_enqueue(ibs_ctx* ctx, BatchPlan& plan, int n_subsets, cudaStream
       if (g > 0) IBS_CUDA_TRY(cudaStreamWaitEvent(st, plan.stage_ev[g], 0));  // joins the side stream
       const int64_t n_items = plan.stage_item_off[g + 1] - plan.stage_item_off[g];
       IBS_CUDA_TRY(launch_tc_batch(static_cast<const SubsetDev*>(plan.subsets.p), items + plan.stage_item_off[g],
-                                   n_items, (int)std::min<int64_t>(plan.grid, n_items), fmt,
+                                   n_items, (int)std::min<int64_t>(plan.grid, n_items), fmt, plan.stage_max_chunks[g],
                                    static_cast<int*>(plan.counter.p), ctx->status_dev, st));
     }
   } else {

@@ -57,6 +57,7 @@ struct BatchPlan {
   // pair kernel of stage g runs.
   std::vector<int64_t> order;           // subset processing order
   std::vector<int64_t> stage_item_off, stage_job_off, stage_ctas;  // per stage (+1 end entry for offsets)
+  std::vector<int64_t> stage_max_chunks;  // longest item of a stage, in chunks (picks the ring depth)
   cudaStream_t side = nullptr;
   std::vector<cudaEvent_t> stage_ev;
   int64_t n_items = 0, total_ctas = 0, max_split_pairs = 0, tc_ctas = 0;

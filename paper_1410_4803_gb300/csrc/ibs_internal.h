@@ -144,7 +144,7 @@ cudaError_t launch_tc_gather(const TcGatherJob* jobs_dev, int n_jobs, int64_t to
 // n_chunks count 128-sample blocks and chunks, and WorkItem tiles and K ranges
 // are in those units.
 cudaError_t launch_tc_batch(const SubsetDev* subs, const WorkItem* items, int64_t n_items, int grid, int fmt,
-                            int* counter, int* status, cudaStream_t st);
+                            int64_t max_chunks, int* counter, int* status, cudaStream_t st);
 // One matrix through the persistent kernel (ibs_compute): work list, launch,
 // and the finalisation of the split tiles.
 void tc_single_items(int64_t n, int64_t m, int fmt, int num_sms, int group, std::vector<WorkItem>& items,

@@ -563,13 +563,24 @@ struct TriEpi {
   // Distances of the row, after the accumulators are handed back (so the
   // FP64 work overlaps the next item's MMAs): each thread reads back the
   // counts it stored itself.
+  // The row's pairs are consecutive in the triangle, so the reads are batched
+  // 16 at a time: the loop is bound by the FP64 rate, not by one L2 round
+  // trip per pair.
   __device__ void finish() const {
     if (gi >= n || split || !dist) return;
     const int64_t j1 = j0 + kTB < n ? j0 + kTB : n;
-    for (int64_t gj = gi > j0 ? gi : j0; gj < j1; ++gj) {
-      const int64_t p = tri_index(gi, gj, n);
-      const int4 c = reinterpret_cast<const int4*>(counts)[p];
-      dist[p] = ibs_dist(c.x, c.y, c.w);
+    const int64_t jb = gi > j0 ? gi : j0;
+    const int64_t p0 = tri_index(gi, jb, n), len = j1 - jb;
+    const int4* cnt = reinterpret_cast<const int4*>(counts) + p0;
+    double* dst = dist + p0;
+    for (int64_t u0 = 0; u0 < len; u0 += 16) {
+      int4 c[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u)
+        if (u0 + u < len) c[u] = cnt[u0 + u];
+#pragma unroll
+      for (int u = 0; u < 16; ++u)
+        if (u0 + u < len) dst[u0 + u] = ibs_dist(c[u].x, c[u].y, c[u].w);
     }
   }
 };
@@ -653,7 +664,7 @@ struct CrossWork {
 // the epilogue runs.
 constexpr int kQueue = 8;
 
-template <int F, class W>
+template <int F, class W, int kTStages>
 __global__ void __launch_bounds__(256, 1)
     tc_persistent_kernel(const W work, int64_t n_items, int* counter, int* status) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -991,28 +1002,56 @@ cudaError_t launch_tc_gather(const TcGatherJob* jobs_dev, int n_jobs, int64_t to
   return cudaGetLastError();
 }
 
-template <class W>
-cudaError_t launch_persistent(const W& work, int64_t n_items, int grid, int fmt, int* counter, int* status,
-                              cudaStream_t st) {
-  if (n_items <= 0) return cudaSuccess;
-  if (grid < 1 || n_items > 2147483647LL - grid) return cudaErrorInvalidValue;  // the claim counter is an int
-  auto kern = fmt == kTcFp4 ? tc_persistent_kernel<kTcFp4, W> : tc_persistent_kernel<kTcFp8, W>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+// Ring depth of the persistent kernel: 4 stages (128 KiB), or 6 (192 KiB)
+// when an item streams at least kLongK chunks.  Measured: 6 stages are 20%
+// faster at m = 500,000 (7,813 chunks per tile, where the CTAs drift apart
+// over a tile and miss L2 more) and 1-5% slower at m <= 100,000.
+// IBS_TC_STAGES=4|6 overrides the choice.
+constexpr int64_t kLongK = 4096;
+int persistent_stages(int64_t chunks_per_item) {
+  static const int forced = [] {
+    const char* e = getenv("IBS_TC_STAGES");
+    const int v = e ? atoi(e) : 0;
+    return v == 4 || v == 6 ? v : 0;
+  }();
+  if (forced) return forced;
+  return chunks_per_item >= kLongK ? 6 : 4;
+}
+
+template <int F, class W, int S>
+cudaError_t launch_persistent_s(const W& work, int64_t n_items, int grid, int* counter, int* status,
+                                cudaStream_t st) {
+  constexpr size_t smem = (size_t)S * 2 * kTChunkBytes + 1024;
+  cudaError_t e = cudaFuncSetAttribute(tc_persistent_kernel<F, W, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
-  kern<<<grid, 256, kTcSmem, st>>>(work, n_items, counter, status);
+  tc_persistent_kernel<F, W, S><<<grid, 256, smem, st>>>(work, n_items, counter, status);
   return cudaGetLastError();
 }
 
+template <class W>
+cudaError_t launch_persistent(const W& work, int64_t n_items, int grid, int fmt, int64_t chunks_per_item,
+                              int* counter, int* status, cudaStream_t st) {
+  if (n_items <= 0) return cudaSuccess;
+  if (grid < 1 || n_items > 2147483647LL - grid) return cudaErrorInvalidValue;  // the claim counter is an int
+  const bool six = persistent_stages(chunks_per_item) == 6;
+  if (fmt == kTcFp4)
+    return six ? launch_persistent_s<kTcFp4, W, 6>(work, n_items, grid, counter, status, st)
+               : launch_persistent_s<kTcFp4, W, 4>(work, n_items, grid, counter, status, st);
+  return six ? launch_persistent_s<kTcFp8, W, 6>(work, n_items, grid, counter, status, st)
+             : launch_persistent_s<kTcFp8, W, 4>(work, n_items, grid, counter, status, st);
+}
+
 cudaError_t launch_tc_batch(const SubsetDev* subs, const WorkItem* items, int64_t n_items, int grid, int fmt,
-                            int* counter, int* status, cudaStream_t st) {
-  return launch_persistent(BatchWork{subs, items}, n_items, grid, fmt, counter, status, st);
+                            int64_t max_chunks, int* counter, int* status, cudaStream_t st) {
+  return launch_persistent(BatchWork{subs, items}, n_items, grid, fmt, max_chunks, counter, status, st);
 }
 
 cudaError_t launch_tc_single(const SubsetDev& sd, const WorkItem* items, int64_t n_items, int grid, int fmt,
                              int* counter, int* status, cudaStream_t st) {
-  return launch_persistent(SingleWork{sd, items}, n_items, grid, fmt, counter, status, st);
+  return launch_persistent(SingleWork{sd, items}, n_items, grid, fmt, sd.n_chunks, counter, status, st);
 }
 
 cudaError_t launch_tc_finalize_tiles(const int2* tiles, int64_t n_tiles, const int32_t* partial, int64_t n,
@@ -1070,7 +1109,8 @@ void tc_single_items(int64_t n, int64_t m, int fmt, int num_sms, int group, std:
 
 cudaError_t launch_tc_cross(const uint8_t* panel, int64_t n_panel, int64_t n_chunks, const CrossItem* items,
                             int64_t n_items, int grid, int fmt, int* counter, int* status, cudaStream_t st) {
-  return launch_persistent(CrossWork{items, panel, n_panel, n_chunks}, n_items, grid, fmt, counter, status, st);
+  return launch_persistent(CrossWork{items, panel, n_panel, n_chunks}, n_items, grid, fmt, n_chunks, counter, status,
+                           st);
 }
 
 cudaError_t launch_tc_gather_rows(const RowSrc* rows, int64_t n_rows, int64_t n_chunks, uint8_t* dst,
