@@ -252,6 +252,7 @@ def run_plain(args, rank, world, local):
     ctx = ibs.ibs_init(local, flags=ibs.IBS_TIMING | (ibs.IBS_KERNEL_TC if use_tc else ibs.IBS_KERNEL_CSA))
     probe = ibs.ibs_probe_int_pipes(ctx)
     kinfo = ibs.ibs_kernel_info(ctx)
+    mma_probe = ibs.ibs_probe_mma(ctx) if use_tc else None
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -391,7 +392,12 @@ def run_plain(args, rank, world, local):
                                 f"indicator GEMMs)", "kernel_ms": pairs_ms,
                       "peak_basis": f"measured bf16 burst TFLOP/s (MEASURED_PEAKS.json) x {tc_ratio:.0f}, the nominal "
                                     f"{'FP4' if fp4 else 'FP8'}/bf16 dense ratio; algorithmic flops = 8 per comparison "
-                                    "(4 MACs: VV^T, UU^T, QR^T, RQ^T)"}),
+                                    "(4 MACs: VV^T, UU^T, QR^T, RQ^T)",
+                      "mma_probe": {"unit": "TFLOP/s",
+                                    "measured": mma_probe["e2m1_tflops" if fp4 else "e4m3_tflops"],
+                                    "frac": 8.0 * achieved / 1e12 / mma_probe["e2m1_tflops" if fp4 else "e4m3_tflops"],
+                                    "basis": "ibs_probe_mma: back-to-back 128x128 MMAs of this kind from "
+                                             "shared-memory tiles on all SMs, measured live"}}),
         "integer_kernel": None if popc is None else {
             "kernel": "tri_kernel, carry-save LOP3/POPC over bit planes (IBS_KERNEL_CSA)",
             "kernel_ms": popc, "value": comps / (popc * 1e-3), "unit": UNIT,

@@ -205,6 +205,13 @@ const char* ibs_last_error(void);
  * Synchronous.  Used to derive the integer-pipe roofline. */
 ibs_status ibs_probe_int_pipes(ibs_ctx* ctx, double out[5]);
 
+/* Measure the sustained tensor-core rate of the MMA kinds the tensor-core
+ * form issues, with an all-SM microbenchmark on the context's device (back-to-
+ * back 128 x 128 MMAs from shared-memory tiles): out[0] = E4M3
+ * (kind::f8f6f4, K = 32), out[1] = E2M1 (kind::mxf4 with unit scale factors,
+ * K = 64), in TFLOP/s.  Synchronous. */
+ibs_status ibs_probe_mma(ibs_ctx* ctx, double out[2]);
+
 /* The largest cached batched-launch plan: out[0] = kernel mode (0 plain,
  * 1 carry-save 2 CTAs/SM, 2 carry-save 1 CTA/SM, 3 tensor core E4M3, 4 tensor
  * core E2M1), out[1] =

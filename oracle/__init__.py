@@ -14,6 +14,8 @@ the number of markers not skipped.  The derived distance is
 IBS similarity the paper's ``--distance ibs`` command prints.
 
 The arithmetic lives in ``ibs_oracle.c`` (plain C, one byte per genotype).
+``ld_r`` is the linkage-disequilibrium correlation of marker pairs from the
+same file (paper, "Bitwise parallelism", the example of r with missing calls).
 ``topk`` below is the one rule written in Python: rank panel samples by
 ascending distance, break ties by ascending index, put NaN (N == 0) last, and
 pad with (-1, NaN) when k exceeds the panel size.
@@ -67,6 +69,8 @@ def _load():
             lib.oracle_ibs_block.restype = ctypes.c_int
             lib.oracle_ibs_triangle.argtypes = [p, i64, i64, p, p, ctypes.c_int]
             lib.oracle_ibs_triangle.restype = ctypes.c_int
+            lib.oracle_ld_r.argtypes = [p, i64, i64, i64, p, p, ctypes.c_int]
+            lib.oracle_ld_r.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -148,6 +152,22 @@ def ibs_rows(packed: np.ndarray, n: int, m: int, rows, threads: int = 0):
     """Counts of the listed samples against every sample: [len(rows)][n][4], dist [len(rows)][n]."""
     G = unpack(packed, n, m)
     return ibs_block(G, G, rows=rows, threads=threads)
+
+
+def ld_r(G: np.ndarray, window: int, threads: int = 0):
+    """LD correlation r of marker pairs (a, a+1 .. a+window) from sample-major
+    codes G [n][m] (paper, "Bitwise parallelism", the correlation coefficient
+    with missing calls; x = +1 hom major, -1 hom minor, 0 het or missing, means
+    over the samples where both calls are present).  Returns (r [m][window]
+    float64, N [m][window] int32); slots past the last marker are NaN and 0."""
+    G = np.ascontiguousarray(G, dtype=np.uint8)
+    n, m = G.shape
+    r = np.empty((m, window), dtype=np.float64)
+    cnt = np.empty((m, window), dtype=np.int32)
+    used = _load().oracle_ld_r(_ptr(G), n, m, int(window), _ptr(r), _ptr(cnt), int(threads))
+    if used <= 0:
+        raise ValueError("oracle_ld_r rejected its arguments")
+    return r, cnt
 
 
 def topk(dist_row: np.ndarray, k: int):

@@ -232,3 +232,120 @@ int oracle_ibs_triangle(const uint8_t* G, int64_t n, int64_t m,
   pthread_mutex_destroy(&job.lock);
   return started;
 }
+
+/* ------------------------------------------------------------------------
+ * Linkage disequilibrium: the correlation coefficient r between two markers
+ * (paper, "Improvements in PLINK 1.9 / Bitwise parallelism", the example of
+ * r with missing data).  For markers x and y and samples i:
+ *   x_i = -1 for a homozygous minor call, 0 for a heterozygous or missing call,
+ *         +1 for a homozygous major call (y likewise);
+ *   S_xy = the samples where neither x nor y is missing;
+ *   r = (|S_xy|^-1 sum_{i in S} x_i y_i - xbar ybar)
+ *       / sqrt((x2bar - xbar^2) (y2bar - ybar^2)),
+ * with xbar, x2bar, ybar, y2bar the means of x, x^2, y, y^2 over S_xy.
+ * Multiplying numerator and denominator by |S_xy|^2 gives the same value from
+ * integer sums, which is what is computed here (exactly, then one square root
+ * and one division in double):
+ *   r = (N Sxy - Sx Sy) / sqrt((N Sxx - Sx^2) (N Syy - Sy^2)),  N = |S_xy|.
+ * Readings where the paper is silent:
+ *   - major allele: A1 is major when its frequency among the marker's
+ *     non-missing calls is at least 1/2, i.e. when #hom A1 >= #hom A2 (ties
+ *     orient to A1);
+ *   - r is NaN when N = 0 or either variance term is 0.
+ * Output: pairs (a, b) with 1 <= b - a <= window, at r_out[a * window + (b - a - 1)]
+ * (and |S_xy| at n_out, which may be NULL); slots with b >= m hold NaN and 0.
+ * G is sample-major, one byte per genotype: G[s * m + k].  Threads split the
+ * markers a only.
+ */
+typedef struct {
+  const uint8_t* G;
+  int64_t n, m, window;
+  const int8_t* major_a1;  /* per marker: 1 when A1 is the major allele */
+  double* r_out;
+  int32_t* n_out;
+  int64_t next;
+  pthread_mutex_t lock;
+} oracle_ld_job;
+
+/* x value of one call of marker k: +1 homozygous major, -1 homozygous minor, 0 otherwise. */
+static int oracle_ld_value(uint8_t code, int major_a1) {
+  if (code == 0) return major_a1 ? 1 : -1; /* homozygous A1 */
+  if (code == 3) return major_a1 ? -1 : 1; /* homozygous A2 */
+  return 0;                                /* heterozygous (missing calls are skipped) */
+}
+
+static void* oracle_ld_worker(void* arg) {
+  oracle_ld_job* job = (oracle_ld_job*)arg;
+  for (;;) {
+    pthread_mutex_lock(&job->lock);
+    const int64_t a = job->next++;
+    pthread_mutex_unlock(&job->lock);
+    if (a >= job->m) break;
+    for (int64_t d = 0; d < job->window; ++d) {
+      const int64_t b = a + 1 + d, slot = a * job->window + d;
+      if (b >= job->m) {
+        job->r_out[slot] = NAN;
+        if (job->n_out) job->n_out[slot] = 0;
+        continue;
+      }
+      int64_t N = 0, Sx = 0, Sy = 0, Sxx = 0, Syy = 0, Sxy = 0;
+      for (int64_t s = 0; s < job->n; ++s) {
+        const uint8_t ca = job->G[s * job->m + a], cb = job->G[s * job->m + b];
+        if (ca == ORACLE_MISSING || cb == ORACLE_MISSING) continue;
+        const int x = oracle_ld_value(ca, job->major_a1[a]), y = oracle_ld_value(cb, job->major_a1[b]);
+        N += 1;
+        Sx += x;
+        Sy += y;
+        Sxx += x * x;
+        Syy += y * y;
+        Sxy += x * y;
+      }
+      const int64_t vx = N * Sxx - Sx * Sx, vy = N * Syy - Sy * Sy;
+      job->r_out[slot] = (N == 0 || vx == 0 || vy == 0)
+                             ? NAN
+                             : (double)(N * Sxy - Sx * Sy) / sqrt((double)vx * (double)vy);
+      if (job->n_out) job->n_out[slot] = (int32_t)N;
+    }
+  }
+  return NULL;
+}
+
+int oracle_ld_r(const uint8_t* G, int64_t n, int64_t m, int64_t window, double* r_out, int32_t* n_out,
+                int threads) {
+  if (!G || n <= 0 || m <= 0 || window <= 0 || !r_out) return -1;
+  int8_t* major_a1 = (int8_t*)malloc((size_t)m);
+  if (!major_a1) return -1;
+  for (int64_t k = 0; k < m; ++k) {
+    int64_t hom_a1 = 0, hom_a2 = 0;
+    for (int64_t s = 0; s < n; ++s) {
+      const uint8_t c = G[s * m + k];
+      hom_a1 += c == 0;
+      hom_a2 += c == 3;
+    }
+    major_a1[k] = hom_a1 >= hom_a2 ? 1 : 0;
+  }
+  if (threads <= 0) {
+    long c = sysconf(_SC_NPROCESSORS_ONLN);
+    threads = c > 0 ? (int)c : 1;
+  }
+  if (threads > 1024) threads = 1024;
+  if (m < threads) threads = (int)m;
+  oracle_ld_job job;
+  job.G = G; job.n = n; job.m = m; job.window = window; job.major_a1 = major_a1;
+  job.r_out = r_out; job.n_out = n_out; job.next = 0;
+  pthread_mutex_init(&job.lock, NULL);
+  int started = 0;
+  if (threads > 1) {
+    pthread_t* tids = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)threads);
+    for (int t = 0; t < threads; ++t) {
+      if (pthread_create(&tids[t], NULL, oracle_ld_worker, &job) == 0) started++;
+      else break;
+    }
+    for (int t = 0; t < started; ++t) pthread_join(tids[t], NULL);
+    free(tids);
+  }
+  if (started == 0) { oracle_ld_worker(&job); started = 1; }
+  pthread_mutex_destroy(&job.lock);
+  free(major_a1);
+  return started;
+}

@@ -248,7 +248,9 @@ ibs_status ibs_compute(ibs_ctx* ctx, const uint8_t* packed, int64_t n, int64_t m
     }
     splits = ctx->single_n_split > 0 ? 2 : 1;  // > 1: partial counts and a finalisation pass
   } else if (tc) {
-    splits = tc_splits_for(tiles, tc_chunks(m, fmt), ctx->num_sms);
+    const int64_t nc = tc_chunks(m, fmt);
+    splits = (int)std::max<int64_t>(tc_splits_for(tiles, nc, ctx->num_sms),
+                                    (nc + tc_max_chunks(fmt) - 1) / tc_max_chunks(fmt));
   } else {
     splits = tri_splits_for(tiles, geo.n_chunks, ctx->num_sms);
   }
@@ -374,6 +376,17 @@ ibs_status ibs_last_launch_info(ibs_ctx* ctx, int64_t out[3]) {
   return IBS_OK;
 }
 
+ibs_status ibs_probe_mma(ibs_ctx* ctx, double out[2]) {
+  clear_error();
+  if (ibs_status s = check_ctx(ctx)) return s;
+  if (!out) return fail(IBS_EINVAL, "out is NULL");
+  DeviceGuard g(ctx->device);
+  IBS_CUDA_TRY(probe_tc_mma(ctx->device, ctx->num_sms, ctx->status_dev, out));
+  if (__atomic_exchange_n(ctx->status_host, 0, __ATOMIC_SEQ_CST) == kDevTimeout)
+    return fail(IBS_ETIMEOUT, "the MMA probe's bounded wait timed out");
+  return IBS_OK;
+}
+
 ibs_status ibs_probe_int_pipes(ibs_ctx* ctx, double out[5]) {
   clear_error();
   if (ibs_status s = check_ctx(ctx)) return s;
@@ -436,6 +449,10 @@ void build_items(const std::vector<SubsetShape>& shapes, int mode, int split_pol
       int pieces = (int)std::ceil(item / std::max(1.0, share / 4.0));
       pieces = std::max(1, std::min<int>(pieces, (int)std::min<int64_t>(ig.nc, 64)));
       subset_split[k] = pieces;
+    }
+    if (is_tc_mode(mode)) {  // exact FP32 accumulation: at most 2^21 markers per item
+      const int64_t maxc = tc_max_chunks(tc_fmt_of(mode));
+      subset_split[k] = std::max<int>(subset_split[k], (int)((ig.nc + maxc - 1) / maxc));
     }
   }
   if (is_tc_mode(mode)) {

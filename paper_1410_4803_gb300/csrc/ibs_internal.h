@@ -131,6 +131,7 @@ size_t tc_planes_bytes(int64_t n, int64_t m, int fmt);
 int tc_splits_for(int64_t tiles, int64_t n_chunks, int num_sms);
 int64_t tc_tiles(int64_t n);
 int64_t tc_chunks(int64_t m, int fmt);
+int64_t tc_max_chunks(int fmt);  // longest K range of one accumulation (2^21 markers)
 cudaError_t launch_tc_planes(const uint8_t* packed, int64_t n, int64_t m, uint8_t* planes, int fmt,
                              cudaStream_t st);
 cudaError_t launch_tc_pairs(const uint8_t* planes, int64_t n, int64_t m, int fmt, int splits, int32_t* out_counts,
@@ -160,6 +161,9 @@ cudaError_t launch_tc_cross(const uint8_t* panel, int64_t n_panel, int64_t n_chu
 cudaError_t launch_tc_gather_rows(const RowSrc* rows, int64_t n_rows, int64_t n_chunks, uint8_t* dst,
                                   cudaStream_t st);
 int tc_block_samples();  // 128
+// MMA-rate probe: out[0] = E4M3 (kind::f8f6f4), out[1] = E2M1 (kind::mxf4)
+// TFLOP/s of 128 x 128 MMAs from shared memory, all SMs.
+cudaError_t probe_tc_mma(int device, int num_sms, int* status_dev, double out[2]);
 size_t pair_kernel_smem_bytes();
 
 // Integer-pipe microbenchmark (ibs_probe.cu).

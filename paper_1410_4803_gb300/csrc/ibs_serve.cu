@@ -467,8 +467,11 @@ ibs_status serve_panel_load(ibs_ctx* ctx, const uint8_t* panel, int64_t n_panel,
   serve_stop(ctx);
   auto eng = std::make_shared<ServeEngine>(ctx);
   eng->pg = PlaneGeom::make(n_panel, m);
-  eng->tc = ctx_use_tc(ctx);
   eng->fmt = ctx_tc_format(ctx);
+  // The tensor-core form covers a panel's whole marker range in one
+  // accumulation, exact up to 2^21 markers; longer panels are served by the
+  // integer-pipe kernels.
+  eng->tc = ctx_use_tc(ctx) && tc_chunks(m, eng->fmt) <= tc_max_chunks(eng->fmt);
   eng->blk = eng->tc ? kTcBlock : kSB;
   eng->pgeo = eng->geo(n_panel);
   IBS_CUDA_TRY(cudaStreamCreateWithFlags(&eng->stream, cudaStreamNonBlocking));

@@ -12,8 +12,10 @@
 //   IBS0  = Q R^T + R Q^T          (opposite homozygotes)
 // so IBS1 = (N - UU^T) / 2 and IBS2 = N - IBS0 - IBS1.  The values -1, 0, +1
 // are exact in every float format used here, every product is exact, and every
-// partial sum is an integer of magnitude at most the marker count, far below
-// 2^24, so FP32 accumulation is exact.  Four 128 x 128 MMAs per marker chunk.
+// partial sum is an integer of magnitude at most the marker count of the
+// accumulation; items are kept to at most 2^21 markers (longer tiles are split
+// over K and their pieces added as integers), below 2^24, so FP32
+// accumulation is exact.  Four 128 x 128 MMAs per marker chunk.
 //
 // Two operand formats share everything but the MMA kind and the packing:
 //   FP8  E4M3, kind::f8f6f4, one byte per indicator, 32 markers per chunk;
@@ -895,6 +897,59 @@ __global__ void __launch_bounds__(256) tc_finalize_tiles_kernel(const int2* __re
   }
 }
 
+// ---------------------------------------------------------------------------
+// MMA-rate probe: every CTA (one per SM) issues back-to-back 128 x 128 MMAs of
+// one kind from operand tiles resident in shared memory, into one TMEM
+// accumulator (the tile contents are irrelevant to the rate).  The launch time
+// gives the sustained MMA throughput the pair kernels are bound by.
+template <int F>
+__global__ void __launch_bounds__(128) tc_mma_probe_kernel(int n_mma, int* status) {
+  __shared__ __align__(1024) uint8_t sa[kTileBytes];
+  __shared__ __align__(1024) uint8_t sb[kTileBytes];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_slot;
+  const uint8_t fill = F == kTcFp4 ? 0x22 : kFp8One;  // 1.0 in every element
+  for (int i = threadIdx.x; i < kTileBytes; i += blockDim.x) {
+    sa[i] = fill;
+    sb[i] = fill;
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic-proxy writes seen by the MMA
+  const int warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  if constexpr (F == kTcFp4) {
+    tmem_fill_unit_scales(tmem, warp);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+  if (threadIdx.x == 0) {
+    const uint64_t da = umma_desc(smem_addr(sa)), db = umma_desc(smem_addr(sb));
+    for (int i = 0; i < n_mma; ++i) umma<F>(tmem, da, db, i > 0 ? 1u : 0u, tmem + kSfCol);
+    umma_commit(&bar);
+  }
+  __syncwarp();
+  const bool ok = mbar_wait_bounded(&bar, 0);
+  if (!ok && (threadIdx.x & 31) == 0) atomicExch(status, kDevTimeout);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
 }  // namespace
 
 int tc_default_format() {
@@ -906,6 +961,12 @@ int tc_default_format() {
   }();
   return f;
 }
+
+// Longest K range one accumulation may cover: 2^21 markers.  Every partial
+// sum of the three accumulators is at most one per marker, so this keeps them
+// far below 2^24, where FP32 accumulation stops being exact; longer tiles are
+// split over K and their pieces added as integers.
+int64_t tc_max_chunks(int fmt) { return ((int64_t)1 << 21) / (fmt == kTcFp4 ? kMarkers<kTcFp4> : kMarkers<kTcFp8>); }
 
 int64_t tc_chunks(int64_t m, int fmt) {
   const int64_t k = fmt == kTcFp4 ? kMarkers<kTcFp4> : kMarkers<kTcFp8>;
@@ -1091,8 +1152,9 @@ void tc_single_items(int64_t n, int64_t m, int fmt, int num_sms, int group, std:
     }
   }
   pieces = std::max<int64_t>(1, std::min<int64_t>(pieces, std::min<int64_t>(64, nc)));
+  const int64_t min_pieces = (nc + tc_max_chunks(fmt) - 1) / tc_max_chunks(fmt);  // exact FP32 accumulation
   for (int64_t t = 0; t < W; ++t) {
-    const int64_t np = t < whole ? 1 : pieces;
+    const int64_t np = std::max<int64_t>(min_pieces, t < whole ? 1 : pieces);
     if (np > 1) split_tiles.push_back(order[t]);
     for (int64_t p = 0; p < np; ++p) {
       WorkItem w;
@@ -1123,5 +1185,31 @@ cudaError_t launch_tc_gather_rows(const RowSrc* rows, int64_t n_rows, int64_t n_
 }
 
 int tc_block_samples() { return kTB; }
+
+cudaError_t probe_tc_mma(int device, int num_sms, int* status_dev, double out[2]) {
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) return e;
+  const int n_mma = 20000;
+  for (int f = 0; f < 2; ++f) {
+    auto kern = f == kTcFp4 ? tc_mma_probe_kernel<kTcFp4> : tc_mma_probe_kernel<kTcFp8>;
+    kern<<<num_sms, 128>>>(200, status_dev);  // warm-up
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return e;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0);
+    kern<<<num_sms, 128>>>(n_mma, status_dev);
+    cudaEventRecord(e1);
+    e = cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return e;
+    const double k = f == kTcFp4 ? 64.0 : 32.0;
+    out[f == kTcFp4 ? 1 : 0] = 2.0 * num_sms * (double)n_mma * 128.0 * 128.0 * k / (ms * 1e-3) / 1e12;
+  }
+  return cudaGetLastError();
+}
 
 }  // namespace ibs

@@ -87,6 +87,7 @@ def load():
             "ibs_serve_stats_get": [p, ctypes.POINTER(ibs_serve_stats)],
             "ibs_shutdown": [p],
             "ibs_probe_int_pipes": [p, ctypes.POINTER(ctypes.c_double)],
+            "ibs_probe_mma": [p, ctypes.POINTER(ctypes.c_double)],
             "ibs_batch_plan_info": [p, ctypes.POINTER(ctypes.c_int64)],
             "ibs_kernel_info": [p, ctypes.POINTER(ctypes.c_int64)],
             "ibs_last_launch_info": [p, ctypes.POINTER(ctypes.c_int64)],
@@ -231,6 +232,12 @@ def ibs_shutdown(ctx: Context):
     if ctx.handle is not None:
         _check(load().ibs_shutdown(ctx.handle), "ibs_shutdown")
         ctx.handle = None
+
+
+def ibs_probe_mma(ctx: Context) -> dict:
+    out = (ctypes.c_double * 2)()
+    _check(load().ibs_probe_mma(ctx._h, out), "ibs_probe_mma")
+    return {"e4m3_tflops": out[0], "e2m1_tflops": out[1]}
 
 
 def ibs_probe_int_pipes(ctx: Context) -> dict:

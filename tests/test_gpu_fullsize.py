@@ -107,3 +107,36 @@ def test_structured_n20000_m500000_sampled_pairs(kernel):
         del pos
     finally:
         ibs.ibs_shutdown(ctx)
+
+
+@pytest.mark.parametrize("kernel", ["tc8", "tc4"])
+def test_tensor_core_long_marker_range_is_split(kernel):
+    """m = 2,200,000 markers: one FP32 accumulation would exceed 2^24 (its
+    third accumulator grows by up to 6 per marker), so every tile is split over
+    K into pieces of at most 2^21 markers whose counts are added as integers.
+    The counts reach 2.2e6 and must equal the oracle on sampled rows."""
+    import torch
+    from paper_1410_4803_gb300 import ibs
+    from helpers import pack_codes, random_codes
+    rng = np.random.default_rng(31)
+    n, m = 130, 2_200_000
+    codes = random_codes(rng, n, m, miss=0.01)
+    codes[5] = 3          # hom A2 everywhere: IBS0 = N against sample 6
+    codes[6] = 0
+    packed = pack_codes(codes)
+    ctx = ibs.ibs_init(0, flags=_flags(ibs, kernel))
+    try:
+        counts, dist = ibs.compute(ctx, torch.from_numpy(packed).cuda(), n, m)
+        ibs.ibs_synchronize(ctx)
+        assert ibs.ibs_last_launch_info(ctx)["splits"] > 1
+        rows = np.array([0, 5, 6, 64, 127, 129])
+        wc, wd = oracle.ibs_block(codes, codes, rows=rows)
+        c_host, d_host = counts.cpu().numpy(), dist.cpu().numpy()
+        for t, i in enumerate(rows):
+            j = np.arange(i, n)
+            p = oracle.tri_index(i, j, n)
+            assert (c_host[p] == wc[t, i:]).all(), f"row {i} differs"
+            assert_dist_close(d_host[p], wd[t, i:])
+        assert c_host[oracle.tri_index(5, 6, n), 0] == m
+    finally:
+        ibs.ibs_shutdown(ctx)

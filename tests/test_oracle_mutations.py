@@ -28,10 +28,21 @@ MUTATIONS = {
     "no_diagonal": ("for (int64_t j = i; j < job->n; ++j) {", "for (int64_t j = i + 1; j < job->n; ++j) {"),
 }
 
+# Planted mistakes in the linkage-disequilibrium function, run against its own pins.
+LD_MUTATIONS = {
+    "ld_product_sign": ("(double)(N * Sxy - Sx * Sy)", "(double)(N * Sxy + Sx * Sy)"),
+    "ld_missing_not_skipped": ("if (ca == ORACLE_MISSING || cb == ORACLE_MISSING) continue;",
+                               "if (ca == ORACLE_MISSING && cb == ORACLE_MISSING) continue;"),
+    "ld_fixed_orientation": ("major_a1[k] = hom_a1 >= hom_a2 ? 1 : 0;", "major_a1[k] = 1;"),
+    "ld_window_offset": ("const int64_t b = a + 1 + d, slot", "const int64_t b = a + d, slot"),
+    "ld_variance_term": ("vx = N * Sxx - Sx * Sx", "vx = N * Sxx - Sx"),
+}
 
-@pytest.mark.parametrize("name", sorted(MUTATIONS))
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS) + sorted(LD_MUTATIONS))
 def test_planted_mistake_fails_pins(name, tmp_path):
-    old, new = MUTATIONS[name]
+    old, new = MUTATIONS[name] if name in MUTATIONS else LD_MUTATIONS[name]
+    pins = "test_oracle_pins.py" if name in MUTATIONS else "test_oracle_ld.py"
     src = open(SRC).read()
     assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
     mutant = tmp_path / "mutant.c"
@@ -41,6 +52,6 @@ def test_planted_mistake_fails_pins(name, tmp_path):
                            str(mutant), "-o", str(lib), "-lm"])
     env = dict(os.environ, IBS_ORACLE_LIB=str(lib))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", pins)],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant {name} passed every pin:\n{r.stdout[-2000:]}"
