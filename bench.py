@@ -717,13 +717,103 @@ def run_serve(args, rank, world, local):
     }
 
 
+def run_ld(args, rank, world, local):
+    """LD correlation r of every marker pair within a window (paper, "Bitwise
+    parallelism", r with missing calls) on the plain workload's genotypes:
+    n = 4,096 samples, m = 100,000 markers.  Unit: marker pair x sample."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_1410_4803_gb300 import ibs
+
+    torch.cuda.set_device(local)
+    w = make_workload("plain")
+    n, m, W = w.n, w.m, args.window
+    pairs = m * W - W * (W + 1) // 2 if W < m else m * (m - 1) // 2
+    comps = pairs * n
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    packed = torch.from_numpy(w.packed).to(dev)
+    r = torch.empty((m, W), dtype=torch.float64, device=dev)
+    cnt = torch.empty((m, W), dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    ctx = ibs.ibs_init(local)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            ibs.ibs_ld_r(ctx, packed, n, m, W, r, cnt, stream)
+        ibs.ibs_synchronize(ctx, stream)
+        launches = ibs.ibs_last_launch_info(ctx)["launches"]
+        clk = ClockSampler(local)
+        clk.start()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            ibs.ibs_ld_r(ctx, packed, n, m, W, r, cnt, stream)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        clocks = clk.stop()
+        ibs.ibs_synchronize(ctx, stream)
+        ms = [a.elapsed_time(b) for a, b in ev]
+        # end to end: pinned host input, r and N copied back each step
+        h_in = torch.from_numpy(w.packed).pin_memory()
+        h_r = torch.empty((m, W), dtype=torch.float64).pin_memory()
+        h_n = torch.empty((m, W), dtype=torch.int32).pin_memory()
+        d_in = torch.empty_like(packed)
+        e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.zero_()
+            e2e_ev[i][0].record(stream)
+            d_in.copy_(h_in, non_blocking=True)
+            ibs.ibs_ld_r(ctx, d_in, n, m, W, r, cnt, stream)
+            h_r.copy_(r, non_blocking=True)
+            h_n.copy_(cnt, non_blocking=True)
+            e2e_ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms = [a.elapsed_time(b) for a, b in e2e_ev]
+    # spot check against the oracle on a marker range
+    G = oracle.unpack(w.packed, n, m)
+    lo, hi = 50_000, 50_000 + 64
+    want_r, want_n = oracle.ld_r(np.ascontiguousarray(G[:, lo:hi + W]), W)
+    got_r, got_n = r[lo:hi].cpu().numpy(), cnt[lo:hi].cpu().numpy()
+    ok = bool((got_n == want_n[:hi - lo]).all()) and bool(
+        np.allclose(got_r, want_r[:hi - lo], rtol=1e-12, atol=0, equal_nan=True))
+    ibs.ibs_shutdown(ctx)
+    mean_ms = statistics.mean(ms)
+    line = {
+        "metric": "marker-pair x sample comparisons/s (LD r within a window)", "value": comps / (mean_ms * 1e-3),
+        "unit": "comparisons/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "e2m1xe2m1->f32",
+        "data": "synthetic",
+        "config": {"workload": f"LD r, plain workload genotypes n={n} m={m}, window {W}", "pairs": pairs,
+                   "l2": "flushed between steps (256 MiB write, outside the step events)"},
+        "e2e": {"value": comps / (statistics.mean(e2e_ms) * 1e-3), "unit": "comparisons/s",
+                "h2d_bytes_per_step": int(w.packed.nbytes), "d2h_bytes_per_step": int(m * W * 12)},
+        "exact": {"oracle_markers_50000_50063": ok},
+        "gpu_launches": int(launches * args.steps),
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        t = time.perf_counter()
+        Gs = np.ascontiguousarray(G[:, :200 + W])
+        oracle.ld_r(Gs, W)
+        dt = time.perf_counter() - t
+        sample_pairs = sum(min(W, Gs.shape[1] - 1 - a) for a in range(Gs.shape[1]))
+        line["cpu_baseline"] = {"value": sample_pairs * n / dt, "unit": "comparisons/s", "cores": os.cpu_count(),
+                                "kind": "oracle", "sample": f"markers 0..{199 + W} (all their pairs within the "
+                                                            f"window) x {n} samples ({dt:.1f} s)"}
+    return line
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="plain", choices=["plain", "structured", "batch", "serve"])
+    ap.add_argument("--workload", default="plain", choices=["plain", "structured", "batch", "serve", "ld"])
+    ap.add_argument("--window", type=int, default=1000, help="ld: marker window")
     ap.add_argument("--rates", type=float, nargs="*", default=[4.0, 12.0, 24.0, 0.0],
                     help="serving: Poisson arrival rates per second (0 = all at once)")
     ap.add_argument("--requests", type=int, default=60, help="serving: requests per rate")
@@ -745,6 +835,8 @@ def main():
         line = run_batch(args, rank, world, local)
     elif args.workload == "serve":
         line = run_serve(args, rank, world, local)
+    elif args.workload == "ld":
+        line = run_ld(args, rank, world, local)
     else:
         line = run_plain(args, rank, world, local)
     if line is not None:

@@ -224,6 +224,24 @@ ibs_status ibs_batch_plan_info(ibs_ctx* ctx, int64_t out[4]);
  * finalisation, out[3] = number of calls.  Resets the sums. */
 ibs_status ibs_kernel_times(ibs_ctx* ctx, double out[4]);
 
+/* Linkage disequilibrium between markers (paper, "Improvements in PLINK 1.9 /
+ * Bitwise parallelism", the example of the correlation coefficient r with
+ * missing calls).  For markers a < b <= a + window:
+ *   x = +1 homozygous major, -1 homozygous minor, 0 heterozygous or missing;
+ *   S_ab = samples where neither call is missing, N = |S_ab|;
+ *   r = (N Sxy - Sx Sy) / sqrt((N Sxx - Sx^2) (N Syy - Sy^2)), sums over S_ab
+ * (the paper's mean form multiplied through by N^2).  The major allele of a
+ * marker is A1 when #hom A1 >= #hom A2 over its calls.  r is NaN when N = 0 or
+ * either variance term is 0.  The sums are exact (tensor-core indicator
+ * products); r is within 1e-12 relative of the exactly rounded value.
+ * packed: DEVICE uint8 [n_variants][ceil(n_samples/4)] (.bed layout, as for
+ * ibs_compute).  out_r: DEVICE double [n_variants][window], pair (a, a+1+d) at
+ * out_r[a * window + d]; slots with a+1+d >= n_variants hold NaN.  out_n
+ * (optional, DEVICE int32, same shape) receives N, 0 past the last marker.
+ * 1 <= n_samples < 2^24, window >= 1.  Asynchronous on `stream`. */
+ibs_status ibs_ld_r(ibs_ctx* ctx, const uint8_t* packed, int64_t n_samples, int64_t n_variants, int64_t window,
+                    double* out_r, int32_t* out_n, void* stream);
+
 /* The kernels this context's ibs_compute uses: out[0] = pair kernel family
  * (0 POPC plain, 1 POPC carry-save, 2 tensor core), out[1] = tensor-core
  * operand format (0 E4M3, 1 E2M1), out[2] = SMs of the device, out[3] = device. */

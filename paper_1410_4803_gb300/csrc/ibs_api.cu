@@ -881,6 +881,44 @@ extern "C" ibs_status ibs_compute_batch(ibs_ctx* ctx, const uint8_t* pool, int64
   return IBS_OK;
 }
 
+extern "C" ibs_status ibs_ld_r(ibs_ctx* ctx, const uint8_t* packed, int64_t n, int64_t m, int64_t window,
+                               double* out_r, int32_t* out_n, void* stream) {
+  clear_error();
+  if (ibs_status s = check_ctx(ctx)) return s;
+  if (!packed || !out_r) return fail(IBS_EINVAL, "packed and out_r must be non-NULL");
+  if (n < 1 || n >= ((int64_t)1 << 24)) return fail(IBS_EINVAL, "n_samples %lld out of range [1, 2^24)", (long long)n);
+  if (m < 1 || m > 2147483647LL) return fail(IBS_EINVAL, "n_variants %lld out of range [1, 2^31)", (long long)m);
+  if (window < 1 || window > 2147483647LL / 2) return fail(IBS_EINVAL, "window %lld out of range", (long long)window);
+  if (reinterpret_cast<uintptr_t>(out_r) % 8) return fail(IBS_EINVAL, "out_r must be 8-byte aligned");
+  if (out_n && reinterpret_cast<uintptr_t>(out_n) % 4) return fail(IBS_EINVAL, "out_n must be 4-byte aligned");
+  DeviceGuard g(ctx->device);
+  if (!is_device_ptr(packed) || !is_device_ptr(out_r) || (out_n && !is_device_ptr(out_n)))
+    return fail(IBS_EINVAL, "packed, out_r and out_n must be device memory");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (ibs_status s = ensure_buf(ctx, ctx->ld_planes, ld_planes_bytes(n, m))) return s;
+  if (ibs_status s = ensure_buf(ctx, ctx->ld_diff, (size_t)m * sizeof(int32_t))) return s;
+  if (ibs_status s = ensure_buf(ctx, ctx->ld_counter, 256)) return s;
+  const std::vector<int64_t> key = {m, window};
+  if (ctx->ld_key != key) {
+    std::vector<int2> items;
+    ld_items(m, window, items);
+    if (ibs_status s = ensure_buf(ctx, ctx->ld_items, std::max<size_t>(1, items.size()) * sizeof(int2))) return s;
+    if (!items.empty())  // pageable source: the copy is staged before return
+      IBS_CUDA_TRY(cudaMemcpyAsync(ctx->ld_items.p, items.data(), items.size() * sizeof(int2),
+                                   cudaMemcpyHostToDevice, st));
+    ctx->ld_n_items = (int64_t)items.size();
+    ctx->ld_key = key;
+  }
+  IBS_CUDA_TRY(launch_ld(packed, n, m, window, static_cast<uint8_t*>(ctx->ld_planes.p),
+                         static_cast<int32_t*>(ctx->ld_diff.p), static_cast<const int2*>(ctx->ld_items.p),
+                         ctx->ld_n_items, static_cast<int*>(ctx->ld_counter.p), out_r, out_n, ctx->status_dev,
+                         ctx->num_sms, st));
+  ctx->last_info[0] = ctx->ld_n_items > 0 ? 3 : 2;
+  ctx->last_info[1] = ctx->ld_n_items;
+  ctx->last_info[2] = 1;
+  return IBS_OK;
+}
+
 extern "C" ibs_status ibs_kernel_info(ibs_ctx* ctx, int64_t out[4]) {
   clear_error();
   if (ibs_status s = check_ctx(ctx)) return s;
@@ -920,7 +958,9 @@ extern "C" ibs_status ibs_shutdown(ibs_ctx* ctx) {
     free_buf(ctx, ctx->planes);
     free_buf(ctx, ctx->partial);
     free_buf(ctx, ctx->tile_list);
-    for (DevBuf* b : {&ctx->single_items, &ctx->single_split, &ctx->single_counter}) free_buf(ctx, *b);
+    for (DevBuf* b : {&ctx->single_items, &ctx->single_split, &ctx->single_counter, &ctx->ld_planes, &ctx->ld_diff,
+                      &ctx->ld_items, &ctx->ld_counter})
+      free_buf(ctx, *b);
     for (auto* v : {&ctx->timing_used, &ctx->timing_free})
       for (auto& r : *v)
         for (auto& e : r.ev)

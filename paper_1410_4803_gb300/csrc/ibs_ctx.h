@@ -95,6 +95,10 @@ struct ibs_ctx {
   ibs::DevBuf planes, partial;
   ibs::DevBuf tile_list;          // tensor-core grouped tile order, for tile_list_T tiles per side
   int64_t tile_list_T = -1;
+  // LD correlation: operand planes, per-marker allele balance, band items of the last (m, window)
+  ibs::DevBuf ld_planes, ld_diff, ld_items, ld_counter;
+  std::vector<int64_t> ld_key;
+  int64_t ld_n_items = 0;
   // persistent tensor-core work list of the last (n, m, format, SMs, group)
   std::vector<int64_t> single_key;
   ibs::DevBuf single_items, single_split, single_counter;

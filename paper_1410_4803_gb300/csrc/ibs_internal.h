@@ -161,6 +161,16 @@ cudaError_t launch_tc_cross(const uint8_t* panel, int64_t n_panel, int64_t n_chu
 cudaError_t launch_tc_gather_rows(const RowSrc* rows, int64_t n_rows, int64_t n_chunks, uint8_t* dst,
                                   cudaStream_t st);
 int tc_block_samples();  // 128
+// LD correlation (ibs_ld.cu): operand planes of the markers (128-marker
+// blocks, 64-sample chunks, planes X, V, H), the band's work items and the
+// launch sequence (operand builder with per-marker allele balance, persistent
+// tensor-core kernel, fill of the slots past the last marker).
+size_t ld_planes_bytes(int64_t n, int64_t m);
+void ld_items(int64_t m, int64_t window, std::vector<int2>& items);
+cudaError_t launch_ld(const uint8_t* packed, int64_t n, int64_t m, int64_t window, uint8_t* planes, int32_t* diff,
+                      const int2* items, int64_t n_items, int* counter, double* out_r, int32_t* out_n,
+                      int* status, int num_sms, cudaStream_t st);
+
 // MMA-rate probe: out[0] = E4M3 (kind::f8f6f4), out[1] = E2M1 (kind::mxf4)
 // TFLOP/s of 128 x 128 MMAs from shared memory, all SMs.
 cudaError_t probe_tc_mma(int device, int num_sms, int* status_dev, double out[2]);

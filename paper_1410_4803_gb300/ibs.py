@@ -90,6 +90,7 @@ def load():
             "ibs_probe_mma": [p, ctypes.POINTER(ctypes.c_double)],
             "ibs_batch_plan_info": [p, ctypes.POINTER(ctypes.c_int64)],
             "ibs_kernel_info": [p, ctypes.POINTER(ctypes.c_int64)],
+            "ibs_ld_r": [p, p, i64, i64, i64, p, p, p],
             "ibs_last_launch_info": [p, ctypes.POINTER(ctypes.c_int64)],
             "ibs_kernel_times": [p, ctypes.POINTER(ctypes.c_double)],
             "ibs_compute_noalloc": [p, i64, i64, p, p, p],
@@ -257,6 +258,23 @@ def ibs_kernel_times(ctx: Context) -> dict:
     out = (ctypes.c_double * 4)()
     _check(load().ibs_kernel_times(ctx._h, out), "ibs_kernel_times")
     return {"planes_ms": out[0], "pairs_ms": out[1], "finalize_ms": out[2], "calls": int(out[3])}
+
+
+def ibs_ld_r(ctx: Context, packed, n_samples: int, n_variants: int, window: int, out_r, out_n=None,
+             stream=None) -> None:
+    _check(load().ibs_ld_r(ctx._h, _addr(packed), n_samples, n_variants, window, _addr(out_r), _addr(out_n),
+                           _stream(stream)), "ibs_ld_r")
+
+
+def ld_r(ctx: Context, packed, n_samples: int, n_variants: int, window: int, stream=None):
+    """Allocate the outputs on the packed tensor's device and run ibs_ld_r:
+    returns (r float64 [n_variants][window], N int32 [n_variants][window])."""
+    import torch
+    dev = packed.device
+    r = torch.empty((n_variants, window), dtype=torch.float64, device=dev)
+    cnt = torch.empty((n_variants, window), dtype=torch.int32, device=dev)
+    ibs_ld_r(ctx, packed, n_samples, n_variants, window, r, cnt, stream)
+    return r, cnt
 
 
 def ibs_kernel_info(ctx: Context) -> dict:
