@@ -15,7 +15,10 @@ IBS similarity the paper's ``--distance ibs`` command prints.
 
 The arithmetic lives in ``ibs_oracle.c`` (plain C, one byte per genotype).
 ``ld_r`` is the linkage-disequilibrium correlation of marker pairs from the
-same file (paper, "Bitwise parallelism", the example of r with missing calls).
+same file (paper, "Bitwise parallelism", the example of r with missing calls),
+and ``complete_linkage`` the complete-linkage clustering of the samples under
+the distance matrix (paper, "Identity-by-state matrices, complete linkage
+clustering").
 ``topk`` below is the one rule written in Python: rank panel samples by
 ascending distance, break ties by ascending index, put NaN (N == 0) last, and
 pad with (-1, NaN) when k exceeds the panel size.
@@ -71,6 +74,8 @@ def _load():
             lib.oracle_ibs_triangle.restype = ctypes.c_int
             lib.oracle_ld_r.argtypes = [p, i64, i64, i64, p, p, ctypes.c_int]
             lib.oracle_ld_r.restype = ctypes.c_int
+            lib.oracle_complete_linkage.argtypes = [p, i64, p]
+            lib.oracle_complete_linkage.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -168,6 +173,22 @@ def ld_r(G: np.ndarray, window: int, threads: int = 0):
     if used <= 0:
         raise ValueError("oracle_ld_r rejected its arguments")
     return r, cnt
+
+
+def complete_linkage(tri: np.ndarray, n: int) -> np.ndarray:
+    """Complete-linkage clustering (paper, "Identity-by-state matrices,
+    complete linkage clustering") of n samples under the distance triangle
+    (upper triangle with diagonal, as the library writes it; NaN = +inf).
+    Greedy: merge the closest active pair; ties to the smallest (rep A, rep B),
+    a cluster's rep being its smallest member.  Returns Z [n-1][4] = (id1, id2,
+    height, size), ids in scipy's convention."""
+    tri = np.ascontiguousarray(tri, dtype=np.float64)
+    if tri.size != n * (n + 1) // 2:
+        raise ValueError("triangle size does not match n")
+    Z = np.empty((max(n - 1, 0), 4), dtype=np.float64)
+    if _load().oracle_complete_linkage(_ptr(tri), n, _ptr(Z)) != 0:
+        raise ValueError("oracle_complete_linkage rejected its arguments")
+    return Z
 
 
 def topk(dist_row: np.ndarray, k: int):

@@ -349,3 +349,79 @@ int oracle_ld_r(const uint8_t* G, int64_t n, int64_t m, int64_t window, double* 
   free(major_a1);
   return started;
 }
+
+/* ------------------------------------------------------------------------
+ * Complete-linkage clustering of the samples under a distance matrix (paper,
+ * "Identity-by-state matrices, complete linkage clustering": PLINK's
+ * --cluster runs complete linkage on the IBS matrix), in the textbook greedy
+ * form: start from n singleton clusters; at every step merge the two active
+ * clusters at the smallest complete-linkage distance
+ *   D(A, B) = max over a in A, b in B of d(a, b),
+ * maintained by D(A u B, C) = max(D(A, C), D(B, C)).
+ * Readings where the paper is silent:
+ *   - the input is the distance (IBS1 + 2 IBS0) / (2N) as the library writes
+ *     it: the upper triangle including the diagonal, row-major, diagonal
+ *     ignored; NaN (no common non-missing marker) counts as +infinity;
+ *   - ties: a cluster is represented by its smallest member; among equal
+ *     distances the pair with the smallest (representative of A,
+ *     representative of B), A's representative below B's, merges first;
+ *   - output Z[n-1][4] = (id1, id2, height, size), id1 < id2, with singletons
+ *     numbered 0..n-1 and the cluster formed at step s numbered n + s (the
+ *     convention of scipy's linkage).
+ * O(n^3): the whole active triangle is searched at every step.
+ */
+int oracle_complete_linkage(const double* tri, int64_t n, double* Z) {
+  if (!tri || n <= 0 || !Z) return -1;
+  if (n == 1) return 0;
+  double* D = (double*)malloc(sizeof(double) * (size_t)n * (size_t)n);
+  int64_t* id = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+  int64_t* size = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+  char* active = (char*)malloc((size_t)n);
+  if (!D || !id || !size || !active) {
+    free(D); free(id); free(size); free(active);
+    return -1;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t j = i; j < n; ++j) {
+      double d = tri[i * n - i * (i - 1) / 2 + (j - i)];
+      if (d != d) d = INFINITY;
+      D[i * n + j] = d;
+      D[j * n + i] = d;
+    }
+    id[i] = i;
+    size[i] = 1;
+    active[i] = 1;
+  }
+  for (int64_t step = 0; step < n - 1; ++step) {
+    int64_t bi = -1, bj = -1;
+    double best = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      if (!active[i]) continue;
+      for (int64_t j = i + 1; j < n; ++j) {
+        if (!active[j]) continue;
+        const double d = D[i * n + j];
+        if (bi < 0 || d < best) { /* strict: the first (smallest i, then j) minimum wins */
+          best = d;
+          bi = i;
+          bj = j;
+        }
+      }
+    }
+    const int64_t a = id[bi] < id[bj] ? id[bi] : id[bj], b = id[bi] < id[bj] ? id[bj] : id[bi];
+    Z[step * 4 + 0] = (double)a;
+    Z[step * 4 + 1] = (double)b;
+    Z[step * 4 + 2] = best;
+    Z[step * 4 + 3] = (double)(size[bi] + size[bj]);
+    for (int64_t k = 0; k < n; ++k) {
+      if (!active[k] || k == bi || k == bj) continue;
+      const double d = D[bi * n + k] > D[bj * n + k] ? D[bi * n + k] : D[bj * n + k];
+      D[bi * n + k] = d;
+      D[k * n + bi] = d;
+    }
+    active[bj] = 0;
+    id[bi] = n + step;
+    size[bi] += size[bj];
+  }
+  free(D); free(id); free(size); free(active);
+  return 0;
+}

@@ -39,10 +39,24 @@ LD_MUTATIONS = {
 }
 
 
-@pytest.mark.parametrize("name", sorted(MUTATIONS) + sorted(LD_MUTATIONS))
+# Planted mistakes in the complete-linkage clustering, run against its pins.
+CLUSTER_MUTATIONS = {
+    "cluster_single_linkage": ("const double d = D[bi * n + k] > D[bj * n + k] ? D[bi * n + k] : D[bj * n + k];",
+                               "const double d = D[bi * n + k] < D[bj * n + k] ? D[bi * n + k] : D[bj * n + k];"),
+    "cluster_last_tie_wins": ("if (bi < 0 || d < best) {", "if (bi < 0 || d <= best) {"),
+    "cluster_id_offset": ("id[bi] = n + step;", "id[bi] = n + step + 1;"),
+    "cluster_size_not_added": ("size[bi] += size[bj];", "size[bi] = size[bj];"),
+}
+
+PINS = {**{k: "test_oracle_pins.py" for k in MUTATIONS}, **{k: "test_oracle_ld.py" for k in LD_MUTATIONS},
+        **{k: "test_oracle_cluster.py" for k in CLUSTER_MUTATIONS}}
+ALL = {**MUTATIONS, **LD_MUTATIONS, **CLUSTER_MUTATIONS}
+
+
+@pytest.mark.parametrize("name", sorted(ALL))
 def test_planted_mistake_fails_pins(name, tmp_path):
-    old, new = MUTATIONS[name] if name in MUTATIONS else LD_MUTATIONS[name]
-    pins = "test_oracle_pins.py" if name in MUTATIONS else "test_oracle_ld.py"
+    old, new = ALL[name]
+    pins = PINS[name]
     src = open(SRC).read()
     assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
     mutant = tmp_path / "mutant.c"
