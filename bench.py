@@ -806,13 +806,88 @@ def run_ld(args, rank, world, local):
     return line
 
 
+def run_cluster(args, rank, world, local):
+    """Complete-linkage clustering (paper, "Identity-by-state matrices, complete
+    linkage clustering") of the plain workload's 4,096 samples under their IBS
+    distances: ibs_compute once, then ibs_cluster_complete timed per step."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_1410_4803_gb300 import ibs
+
+    torch.cuda.set_device(local)
+    w = make_workload("plain")
+    n, m = w.n, w.m
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    ctx = ibs.ibs_init(local)
+    z = torch.empty((n - 1, 4), dtype=torch.float64, device=dev)
+    with torch.cuda.stream(stream):
+        _, dist = ibs.compute(ctx, torch.from_numpy(w.packed).to(dev), n, m, stream=stream)
+        for _ in range(args.warmup):
+            ibs.ibs_cluster_complete(ctx, dist, n, z, stream)
+        ibs.ibs_synchronize(ctx, stream)
+        launches = ibs.ibs_last_launch_info(ctx)["launches"]
+        clk = ClockSampler(local)
+        clk.start()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            ibs.ibs_cluster_complete(ctx, dist, n, z, stream)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        clocks = clk.stop()
+        ibs.ibs_synchronize(ctx, stream)
+        ms = [a.elapsed_time(b) for a, b in ev]
+        # end to end: the distance triangle from pinned host memory, the linkage back
+        h_d = dist.cpu().pin_memory()
+        h_z = torch.empty((n - 1, 4), dtype=torch.float64).pin_memory()
+        d_in = torch.empty_like(dist)
+        e2e = []
+        for i in range(max(1, args.steps // 2)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            d_in.copy_(h_d, non_blocking=True)
+            ibs.ibs_cluster_complete(ctx, d_in, n, z, stream)
+            h_z.copy_(z, non_blocking=True)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            e2e.append(e0.elapsed_time(e1))
+    tri = h_d.numpy()
+    want = oracle.complete_linkage(tri, n)
+    exact = bool(np.array_equal(h_z.numpy(), want))
+    ibs.ibs_shutdown(ctx)
+    mean_ms = statistics.mean(ms)
+    line = {
+        "metric": "complete-linkage merges/s (IBS distance matrix)", "value": (n - 1) / (mean_ms * 1e-3),
+        "unit": "merges/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"complete linkage of the plain workload's n={n} samples (IBS distances, m={m})"},
+        "e2e": {"value": (n - 1) / (statistics.mean(e2e) * 1e-3), "unit": "merges/s",
+                "h2d_bytes_per_step": int(tri.nbytes), "d2h_bytes_per_step": int((n - 1) * 32)},
+        "exact": {"linkage_equals_oracle": exact},
+        "gpu_launches": int(launches * args.steps),
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        k = 1500
+        tri_k = np.concatenate([tri[i * n - i * (i - 1) // 2: i * n - i * (i - 1) // 2 + (k - i)] for i in range(k)])
+        t = time.perf_counter()
+        oracle.complete_linkage(tri_k, k)
+        dt = time.perf_counter() - t
+        line["cpu_baseline"] = {"value": (k - 1) / dt, "unit": "merges/s", "cores": 1, "kind": "oracle",
+                                "sample": f"the first {k} samples' distances, O(n^3) greedy ({dt:.1f} s)"}
+    return line
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="plain", choices=["plain", "structured", "batch", "serve", "ld"])
+    ap.add_argument("--workload", default="plain",
+                    choices=["plain", "structured", "batch", "serve", "ld", "cluster"])
     ap.add_argument("--window", type=int, default=1000, help="ld: marker window")
     ap.add_argument("--rates", type=float, nargs="*", default=[4.0, 12.0, 24.0, 0.0],
                     help="serving: Poisson arrival rates per second (0 = all at once)")
@@ -837,6 +912,8 @@ def main():
         line = run_serve(args, rank, world, local)
     elif args.workload == "ld":
         line = run_ld(args, rank, world, local)
+    elif args.workload == "cluster":
+        line = run_cluster(args, rank, world, local)
     else:
         line = run_plain(args, rank, world, local)
     if line is not None:

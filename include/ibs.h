@@ -224,6 +224,22 @@ ibs_status ibs_batch_plan_info(ibs_ctx* ctx, int64_t out[4]);
  * finalisation, out[3] = number of calls.  Resets the sums. */
 ibs_status ibs_kernel_times(ibs_ctx* ctx, double out[4]);
 
+/* Complete-linkage clustering of the samples under the IBS distance (paper,
+ * "Identity-by-state matrices, complete linkage clustering": PLINK's
+ * --cluster merges by complete linkage on the IBS matrix).  Greedy
+ * agglomeration: the two active clusters at the smallest complete-linkage
+ * distance (the largest distance between their members) merge first; ties go
+ * to the smallest (representative, representative) pair, a cluster being
+ * represented by its smallest member; NaN distances count as +infinity.
+ * dist: DEVICE double [n(n+1)/2], the upper triangle with diagonal as
+ * ibs_compute writes it (diagonal ignored).  out_linkage: DEVICE double
+ * [n-1][4], rows (id1, id2, height, size) with id1 < id2, singletons 0..n-1 and
+ * the cluster formed at step s numbered n + s (scipy's linkage convention).
+ * Merge heights are input distances, exactly.  1 <= n <= 131072 (the working
+ * matrix holds n*n doubles in library workspace).  Asynchronous on `stream`. */
+ibs_status ibs_cluster_complete(ibs_ctx* ctx, const double* dist, int64_t n_samples, double* out_linkage,
+                                void* stream);
+
 /* Linkage disequilibrium between markers (paper, "Improvements in PLINK 1.9 /
  * Bitwise parallelism", the example of the correlation coefficient r with
  * missing calls).  For markers a < b <= a + window:

@@ -881,6 +881,27 @@ extern "C" ibs_status ibs_compute_batch(ibs_ctx* ctx, const uint8_t* pool, int64
   return IBS_OK;
 }
 
+extern "C" ibs_status ibs_cluster_complete(ibs_ctx* ctx, const double* dist, int64_t n, double* out_z,
+                                           void* stream) {
+  clear_error();
+  if (ibs_status s = check_ctx(ctx)) return s;
+  if (!dist || (!out_z && n > 1)) return fail(IBS_EINVAL, "dist and out_linkage must be non-NULL");
+  if (n < 1 || n > ((int64_t)1 << 17)) return fail(IBS_EINVAL, "n_samples %lld out of range [1, 131072]", (long long)n);
+  if (reinterpret_cast<uintptr_t>(dist) % 8 || (out_z && reinterpret_cast<uintptr_t>(out_z) % 8))
+    return fail(IBS_EINVAL, "dist and out_linkage must be 8-byte aligned");
+  DeviceGuard g(ctx->device);
+  if (!is_device_ptr(dist) || (out_z && !is_device_ptr(out_z)))
+    return fail(IBS_EINVAL, "dist and out_linkage must be device memory");
+  if (n == 1) return IBS_OK;
+  if (ibs_status s = ensure_buf(ctx, ctx->cluster_work, cluster_workspace_bytes(n))) return s;
+  IBS_CUDA_TRY(launch_cluster_complete(dist, n, out_z, ctx->cluster_work.p, ctx->num_sms,
+                                       static_cast<cudaStream_t>(stream)));
+  ctx->last_info[0] = 4;
+  ctx->last_info[1] = n - 1;
+  ctx->last_info[2] = 1;
+  return IBS_OK;
+}
+
 extern "C" ibs_status ibs_ld_r(ibs_ctx* ctx, const uint8_t* packed, int64_t n, int64_t m, int64_t window,
                                double* out_r, int32_t* out_n, void* stream) {
   clear_error();
@@ -959,7 +980,7 @@ extern "C" ibs_status ibs_shutdown(ibs_ctx* ctx) {
     free_buf(ctx, ctx->partial);
     free_buf(ctx, ctx->tile_list);
     for (DevBuf* b : {&ctx->single_items, &ctx->single_split, &ctx->single_counter, &ctx->ld_planes, &ctx->ld_diff,
-                      &ctx->ld_items, &ctx->ld_counter})
+                      &ctx->ld_items, &ctx->ld_counter, &ctx->cluster_work})
       free_buf(ctx, *b);
     for (auto* v : {&ctx->timing_used, &ctx->timing_free})
       for (auto& r : *v)

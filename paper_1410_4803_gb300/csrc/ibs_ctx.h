@@ -95,6 +95,7 @@ struct ibs_ctx {
   ibs::DevBuf planes, partial;
   ibs::DevBuf tile_list;          // tensor-core grouped tile order, for tile_list_T tiles per side
   int64_t tile_list_T = -1;
+  ibs::DevBuf cluster_work;  // complete-linkage working matrix and row minima
   // LD correlation: operand planes, per-marker allele balance, band items of the last (m, window)
   ibs::DevBuf ld_planes, ld_diff, ld_items, ld_counter;
   std::vector<int64_t> ld_key;

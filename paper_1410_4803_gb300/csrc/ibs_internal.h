@@ -171,6 +171,13 @@ cudaError_t launch_ld(const uint8_t* packed, int64_t n, int64_t m, int64_t windo
                       const int2* items, int64_t n_items, int* counter, double* out_r, int32_t* out_n,
                       int* status, int num_sms, cudaStream_t st);
 
+// Complete-linkage clustering (ibs_cluster.cu) of n samples under a distance
+// triangle (ibs_compute's layout), into Z [n-1][4] on the device; `work` holds
+// cluster_workspace_bytes(n).
+size_t cluster_workspace_bytes(int64_t n);
+cudaError_t launch_cluster_complete(const double* tri, int64_t n, double* Z, void* work, int num_sms,
+                                    cudaStream_t st);
+
 // MMA-rate probe: out[0] = E4M3 (kind::f8f6f4), out[1] = E2M1 (kind::mxf4)
 // TFLOP/s of 128 x 128 MMAs from shared memory, all SMs.
 cudaError_t probe_tc_mma(int device, int num_sms, int* status_dev, double out[2]);

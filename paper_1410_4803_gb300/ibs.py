@@ -91,6 +91,7 @@ def load():
             "ibs_batch_plan_info": [p, ctypes.POINTER(ctypes.c_int64)],
             "ibs_kernel_info": [p, ctypes.POINTER(ctypes.c_int64)],
             "ibs_ld_r": [p, p, i64, i64, i64, p, p, p],
+            "ibs_cluster_complete": [p, p, i64, p, p],
             "ibs_last_launch_info": [p, ctypes.POINTER(ctypes.c_int64)],
             "ibs_kernel_times": [p, ctypes.POINTER(ctypes.c_double)],
             "ibs_compute_noalloc": [p, i64, i64, p, p, p],
@@ -264,6 +265,19 @@ def ibs_ld_r(ctx: Context, packed, n_samples: int, n_variants: int, window: int,
              stream=None) -> None:
     _check(load().ibs_ld_r(ctx._h, _addr(packed), n_samples, n_variants, window, _addr(out_r), _addr(out_n),
                            _stream(stream)), "ibs_ld_r")
+
+
+def ibs_cluster_complete(ctx: Context, dist, n_samples: int, out_linkage, stream=None) -> None:
+    _check(load().ibs_cluster_complete(ctx._h, _addr(dist), n_samples, _addr(out_linkage), _stream(stream)),
+           "ibs_cluster_complete")
+
+
+def cluster_complete(ctx: Context, dist, n_samples: int, stream=None):
+    """Allocate the linkage [n-1][4] on dist's device and run ibs_cluster_complete."""
+    import torch
+    z = torch.empty((max(n_samples - 1, 0), 4), dtype=torch.float64, device=dist.device)
+    ibs_cluster_complete(ctx, dist, n_samples, z, stream)
+    return z
 
 
 def ld_r(ctx: Context, packed, n_samples: int, n_variants: int, window: int, stream=None):
