@@ -16,9 +16,10 @@ IBS similarity the paper's ``--distance ibs`` command prints.
 The arithmetic lives in ``ibs_oracle.c`` (plain C, one byte per genotype).
 ``ld_r`` is the linkage-disequilibrium correlation of marker pairs from the
 same file (paper, "Bitwise parallelism", the example of r with missing calls),
-and ``complete_linkage`` the complete-linkage clustering of the samples under
+``complete_linkage`` the complete-linkage clustering of the samples under
 the distance matrix (paper, "Identity-by-state matrices, complete linkage
-clustering").
+clustering"), and ``grm`` the GCTA genomic relationship matrix (paper,
+"Partial sum lookup").
 ``topk`` below is the one rule written in Python: rank panel samples by
 ascending distance, break ties by ascending index, put NaN (N == 0) last, and
 pad with (-1, NaN) when k exceeds the panel size.
@@ -76,6 +77,8 @@ def _load():
             lib.oracle_ld_r.restype = ctypes.c_int
             lib.oracle_complete_linkage.argtypes = [p, i64, p]
             lib.oracle_complete_linkage.restype = ctypes.c_int
+            lib.oracle_grm.argtypes = [p, i64, i64, p, ctypes.c_int]
+            lib.oracle_grm.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -189,6 +192,21 @@ def complete_linkage(tri: np.ndarray, n: int) -> np.ndarray:
     if _load().oracle_complete_linkage(_ptr(tri), n, _ptr(Z)) != 0:
         raise ValueError("oracle_complete_linkage rejected its arguments")
     return Z
+
+
+def grm(G: np.ndarray, threads: int = 0) -> np.ndarray:
+    """GCTA genomic relationship matrix (paper, "Partial sum lookup") of the
+    samples of G [n][m]: per marker a table of the increments
+    (x_j - 2p)(x_k - 2p) / (2p(1-p)) (x = A1 count, p its frequency over the
+    marker's calls), summed over the markers where both calls are present and
+    divided by their number; monomorphic markers left out; NaN when none is
+    left.  Returns the upper triangle with diagonal (float64)."""
+    G = np.ascontiguousarray(G, dtype=np.uint8)
+    n, m = G.shape
+    out = np.empty(n * (n + 1) // 2, dtype=np.float64)
+    if _load().oracle_grm(_ptr(G), n, m, _ptr(out), int(threads)) <= 0:
+        raise ValueError("oracle_grm rejected its arguments")
+    return out
 
 
 def topk(dist_row: np.ndarray, k: int):

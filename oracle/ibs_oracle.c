@@ -425,3 +425,114 @@ int oracle_complete_linkage(const double* tri, int64_t n, double* Z) {
   free(D); free(id); free(size); free(active);
   return 0;
 }
+
+/* ------------------------------------------------------------------------
+ * Genomic relationship matrix (paper, "Other noteworthy algorithms / Partial
+ * sum lookup": the GCTA relationship matrix as a weighted sum over markers of
+ * seven per-marker cases).  For marker i, with p the frequency of the counted
+ * allele over the marker's non-missing calls and x its count in a call (2 hom
+ * A1, 1 het, 0 hom A2), a pair of samples with both calls present adds
+ *   (x_j - 2p)(x_k - 2p) / (2p(1 - p)),
+ * and a pair with a missing call adds nothing and is left out of the pair's
+ * denominator ("subtract 1 from the final denominator").  So
+ *   A_jk = (sum of the increments) / (number of markers where both are present).
+ * Readings where the paper is silent or garbled:
+ *   - the counted allele: A1.  The paper's table counts the major allele while
+ *     naming q the minor allele frequency; the value does not depend on the
+ *     choice, since counting the other allele negates both factors;
+ *   - markers with p = 0 or 1 (monomorphic, or without calls) would divide by
+ *     zero and are left out of both the sums and the denominators;
+ *   - A_jk = NaN when no marker is left for the pair.
+ * The algorithm follows the paper's first draft: per marker, a table of the
+ * increments of the six cases without a missing call, then one lookup and one
+ * addition per pair and marker (in double).
+ * Output: upper triangle with diagonal, row-major over j <= k (the IBS layout).
+ */
+typedef struct {
+  const uint8_t* G;
+  int64_t n, m;
+  const double* table; /* per marker 16 entries: [code_j * 4 + code_k], 0 where a call is missing */
+  const char* used;    /* per marker: 1 when polymorphic */
+  double* out;
+  int64_t next;
+  pthread_mutex_t lock;
+} oracle_grm_job;
+
+static void* oracle_grm_worker(void* arg) {
+  oracle_grm_job* job = (oracle_grm_job*)arg;
+  const int64_t n = job->n, m = job->m;
+  for (;;) {
+    pthread_mutex_lock(&job->lock);
+    const int64_t j = job->next++;
+    pthread_mutex_unlock(&job->lock);
+    if (j >= n) break;
+    const int64_t base = j * n - j * (j - 1) / 2;
+    for (int64_t k = j; k < n; ++k) {
+      double sum = 0.0;
+      int64_t cnt = 0;
+      for (int64_t i = 0; i < m; ++i) {
+        if (!job->used[i]) continue;
+        const uint8_t a = job->G[j * m + i], b = job->G[k * m + i];
+        if (a == ORACLE_MISSING || b == ORACLE_MISSING) continue;
+        sum += job->table[i * 16 + a * 4 + b];
+        cnt += 1;
+      }
+      job->out[base + (k - j)] = cnt == 0 ? NAN : sum / (double)cnt;
+    }
+  }
+  return NULL;
+}
+
+int oracle_grm(const uint8_t* G, int64_t n, int64_t m, double* out, int threads) {
+  if (!G || n <= 0 || m <= 0 || !out) return -1;
+  double* table = (double*)calloc((size_t)m * 16, sizeof(double));
+  char* used = (char*)calloc((size_t)m, 1);
+  if (!table || !used) {
+    free(table);
+    free(used);
+    return -1;
+  }
+  for (int64_t i = 0; i < m; ++i) {
+    int64_t alleles = 0, calls = 0;
+    for (int64_t s = 0; s < n; ++s) {
+      const uint8_t c = G[s * m + i];
+      if (c == ORACLE_MISSING) continue;
+      calls += 1;
+      alleles += c == 0 ? 2 : (c == 2 ? 1 : 0);
+    }
+    if (calls == 0) continue;
+    const double p = (double)alleles / (2.0 * (double)calls);
+    if (p <= 0.0 || p >= 1.0) continue;
+    used[i] = 1;
+    const double x_of[4] = {2.0, 0.0, 1.0, 0.0}; /* A1 count by code; code 1 (missing) unused */
+    const double denom = 2.0 * p * (1.0 - p);
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b)
+        if (a != ORACLE_MISSING && b != ORACLE_MISSING)
+          table[i * 16 + a * 4 + b] = (x_of[a] - 2.0 * p) * (x_of[b] - 2.0 * p) / denom;
+  }
+  if (threads <= 0) {
+    long c = sysconf(_SC_NPROCESSORS_ONLN);
+    threads = c > 0 ? (int)c : 1;
+  }
+  if (threads > 1024) threads = 1024;
+  if (n < threads) threads = (int)n;
+  oracle_grm_job job;
+  job.G = G; job.n = n; job.m = m; job.table = table; job.used = used; job.out = out; job.next = 0;
+  pthread_mutex_init(&job.lock, NULL);
+  int started = 0;
+  if (threads > 1) {
+    pthread_t* tids = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)threads);
+    for (int t = 0; t < threads; ++t) {
+      if (pthread_create(&tids[t], NULL, oracle_grm_worker, &job) == 0) started++;
+      else break;
+    }
+    for (int t = 0; t < started; ++t) pthread_join(tids[t], NULL);
+    free(tids);
+  }
+  if (started == 0) { oracle_grm_worker(&job); started = 1; }
+  pthread_mutex_destroy(&job.lock);
+  free(table);
+  free(used);
+  return started;
+}

@@ -18,7 +18,8 @@
 //      and the merged row itself, rescan their row.  A distance to the merged
 //      cluster only grows, so no other row's minimum can change.
 // The steps form one persistent CTA of 1,024 threads (32 warps); phases are
-// separated by block barriers, which also order the global-memory updates.
+// separated by block barriers, which also order the memory updates.  Up to
+// 12,000 samples the row minima and activity flags sit in shared memory.
 // The working matrix is square and symmetric in HBM (8 bytes per entry).
 #include <cstdint>
 
@@ -96,12 +97,33 @@ struct ClArgs {
   double* Z;  // [n-1][4]
 };
 
-__global__ void __launch_bounds__(kClThreads, 1) cl_main_kernel(const ClArgs a) {
+// Row minima and activity flags live in shared memory when they fit (13 bytes
+// per sample, up to kClSmemRows samples), so that the per-step argmin and the
+// rescan checks touch no global memory.
+constexpr int64_t kClSmemRows = 12000;
+constexpr size_t cl_smem_bytes(int64_t n) { return n <= kClSmemRows ? (size_t)n * 13 + 16 : 0; }
+
+__global__ void __launch_bounds__(kClThreads, 1) cl_main_kernel(ClArgs a) {
+  extern __shared__ __align__(16) uint8_t cl_smem[];
   __shared__ double s_v[kClThreads / 32];
   __shared__ int32_t s_i[kClThreads / 32];
   __shared__ int64_t s_bi, s_bj;
   const int64_t n = a.n;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (n <= kClSmemRows) {
+    double* sv = reinterpret_cast<double*>(cl_smem);
+    int32_t* sj = reinterpret_cast<int32_t*>(cl_smem + (size_t)n * 8);
+    uint8_t* sa = cl_smem + (size_t)n * 12;
+    for (int64_t r = threadIdx.x; r < n; r += kClThreads) {
+      sv[r] = a.rmin_v[r];
+      sj[r] = a.rmin_j[r];
+      sa[r] = a.active[r];
+    }
+    __syncthreads();
+    a.rmin_v = sv;
+    a.rmin_j = sj;
+    a.active = sa;
+  }
   for (int64_t step = 0; step + 1 < n; ++step) {
     // 1. global minimum over the row minima: (value, row) lexicographic
     double v = 0;
@@ -165,18 +187,27 @@ __global__ void __launch_bounds__(kClThreads, 1) cl_main_kernel(const ClArgs a) 
       a.size[i0] += a.size[j0];
     }
     __syncthreads();
-    // 3. rows whose minimum pointed at either merged cluster, and the merged row
-    for (int64_t r = warp; r < n; r += kClThreads / 32) {
-      if (!a.active[r]) continue;
-      const int32_t rj = a.rmin_j[r];
-      const bool redo = r == i0 || (r < i0 && rj == i0) || (r < j0 && rj == j0);
-      if (!redo) continue;
-      double rv;
-      int32_t nj;
-      row_min_warp(a.D, a.active, n, r, rv, nj);
-      if (lane == 0) {
-        a.rmin_v[r] = rv;
-        a.rmin_j[r] = nj;
+    // 3. rows whose minimum pointed at either merged cluster, and the merged
+    // row: each warp checks 32 rows at a time and rescans the flagged ones
+    for (int64_t base = (int64_t)warp * 32; base < n; base += kClThreads) {
+      const int64_t r = base + lane;
+      bool redo = false;
+      if (r < n && a.active[r]) {
+        const int32_t rj = a.rmin_j[r];
+        redo = r == i0 || (r < i0 && rj == i0) || (r < j0 && rj == j0);
+      }
+      unsigned flagged = __ballot_sync(0xffffffffu, redo);
+      while (flagged) {
+        const int l = __ffs(flagged) - 1;
+        flagged &= flagged - 1;
+        const int64_t rr = base + l;
+        double rv;
+        int32_t nj;
+        row_min_warp(a.D, a.active, n, rr, rv, nj);
+        if (lane == 0) {
+          a.rmin_v[rr] = rv;
+          a.rmin_j[rr] = nj;
+        }
       }
     }
     __syncthreads();
@@ -221,7 +252,12 @@ cudaError_t launch_cluster_complete(const double* tri, int64_t n, double* Z, voi
   cl_rowmin_kernel<<<grid, 256, 0, st>>>(D, active, n, rmin_v, rmin_j);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   ClArgs args{D, n, rmin_v, rmin_j, active, id, size, Z};
-  cl_main_kernel<<<1, kClThreads, 0, st>>>(args);
+  const size_t smem = cl_smem_bytes(n);
+  if (smem > 48 * 1024 &&
+      (e = cudaFuncSetAttribute(cl_main_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+          cudaSuccess)
+    return e;
+  cl_main_kernel<<<1, kClThreads, smem, st>>>(args);
   return cudaGetLastError();
 }
 

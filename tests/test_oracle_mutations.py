@@ -48,9 +48,20 @@ CLUSTER_MUTATIONS = {
     "cluster_size_not_added": ("size[bi] += size[bj];", "size[bi] = size[bj];"),
 }
 
+# Planted mistakes in the relationship matrix, run against its pins.
+GRM_MUTATIONS = {
+    "grm_centre_at_p": ("(x_of[a] - 2.0 * p) * (x_of[b] - 2.0 * p) / denom",
+                        "(x_of[a] - p) * (x_of[b] - p) / denom"),
+    "grm_missing_counted": ("cnt += 1;\n      }\n      job->out[base + (k - j)]",
+                            "}\n      cnt = job->m;\n      job->out[base + (k - j)]"),
+    "grm_het_count": ("const double x_of[4] = {2.0, 0.0, 1.0, 0.0};", "const double x_of[4] = {2.0, 0.0, 2.0, 0.0};"),
+    "grm_keep_monomorphic": ("if (p <= 0.0 || p >= 1.0) continue;", "if (p < 0.0 || p > 1.0) continue;"),
+}
+
 PINS = {**{k: "test_oracle_pins.py" for k in MUTATIONS}, **{k: "test_oracle_ld.py" for k in LD_MUTATIONS},
-        **{k: "test_oracle_cluster.py" for k in CLUSTER_MUTATIONS}}
-ALL = {**MUTATIONS, **LD_MUTATIONS, **CLUSTER_MUTATIONS}
+        **{k: "test_oracle_cluster.py" for k in CLUSTER_MUTATIONS},
+        **{k: "test_oracle_grm.py" for k in GRM_MUTATIONS}}
+ALL = {**MUTATIONS, **LD_MUTATIONS, **CLUSTER_MUTATIONS, **GRM_MUTATIONS}
 
 
 @pytest.mark.parametrize("name", sorted(ALL))
