@@ -472,9 +472,9 @@ static void* oracle_grm_worker(void* arg) {
       int64_t cnt = 0;
       for (int64_t i = 0; i < m; ++i) {
         if (!job->used[i]) continue;
-        const uint8_t a = job->G[j * m + i], b = job->G[k * m + i];
-        if (a == ORACLE_MISSING || b == ORACLE_MISSING) continue;
-        sum += job->table[i * 16 + a * 4 + b];
+        const uint8_t gj = job->G[j * m + i], gk = job->G[k * m + i];
+        if (gj == ORACLE_MISSING || gk == ORACLE_MISSING) continue;
+        sum += job->table[i * 16 + gj * 4 + gk];
         cnt += 1;
       }
       job->out[base + (k - j)] = cnt == 0 ? NAN : sum / (double)cnt;
