@@ -806,6 +806,101 @@ def run_ld(args, rank, world, local):
     return line
 
 
+def run_grm(args, rank, world, local):
+    """GCTA genomic relationship matrix (paper, "Partial sum lookup") of the
+    plain workload's genotypes, n = 4,096 samples x m = 100,000 markers, on the
+    tensor cores (FP16 hi/lo operands, FP32 segments, float-float sums).
+    Unit: sample pair (with the diagonal) x marker."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_1410_4803_gb300 import ibs
+
+    torch.cuda.set_device(local)
+    from paper_1410_4803_gb300 import synth
+    w = synth.plain_config2(m=args.markers)
+    n, m = w.n, w.m
+    P = n * (n + 1) // 2
+    comps = P * m
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    packed = torch.from_numpy(w.packed).to(dev)
+    out = torch.empty(P, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    ctx = ibs.ibs_init(local)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            ibs.ibs_grm(ctx, packed, n, m, out, stream)
+        ibs.ibs_synchronize(ctx, stream)
+        launches = ibs.ibs_last_launch_info(ctx)["launches"]
+        clk = ClockSampler(local)
+        clk.start()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            ibs.ibs_grm(ctx, packed, n, m, out, stream)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        clocks = clk.stop()
+        ibs.ibs_synchronize(ctx, stream)
+        ms = [a.elapsed_time(b) for a, b in ev]
+        # end to end: pinned host input, the matrix copied back each step
+        h_in = torch.from_numpy(w.packed).pin_memory()
+        h_out = torch.empty(P, dtype=torch.float64).pin_memory()
+        d_in = torch.empty_like(packed)
+        e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.zero_()
+            e2e_ev[i][0].record(stream)
+            d_in.copy_(h_in, non_blocking=True)
+            ibs.ibs_grm(ctx, d_in, n, m, out, stream)
+            h_out.copy_(out, non_blocking=True)
+            e2e_ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms = [a.elapsed_time(b) for a, b in e2e_ev]
+    got = h_out.numpy()
+    # spot check: sampled rows against the oracle's row sampler
+    G = oracle.unpack(w.packed, n, m)
+    rows = np.array([0, 2047, 4095])
+    want = oracle.grm_rows(G, rows)
+    k = np.arange(n)
+    got_rows = np.stack([got[oracle.tri_index(np.minimum(j, k), np.maximum(j, k), n)] for j in rows])
+    err = float(np.nanmax(np.abs(got_rows - want)))
+    ibs.ibs_shutdown(ctx)
+    mean_ms = statistics.mean(ms)
+    tflops = 8.0 * comps / (mean_ms * 1e-3) / 1e12
+    peak = measured_peak("bf16_tflops", 1900.0)
+    line = {
+        "metric": "sample-pair x marker terms/s (GCTA relationship matrix)", "value": comps / (mean_ms * 1e-3),
+        "unit": "terms/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16xf16->f32 (hi/lo split)",
+        "data": "synthetic",
+        "config": {"workload": f"GCTA relationship matrix, plain workload genotypes n={n} m={m}",
+                   "pairs_incl_diagonal": P,
+                   "l2": "flushed between steps (256 MiB write, outside the step events)"},
+        "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
+                     "traffic": None, "kernel": "whole ibs_grm call (frequency and operand kernels included)",
+                     "kernel_ms": mean_ms,
+                     "peak_basis": "measured bf16 burst TFLOP/s (MEASURED_PEAKS.json; FP16 runs at the bf16 rate); "
+                                   "algorithmic flops = 8 per term (4 MACs: hi hi, hi lo, lo hi, V'V')"},
+        "e2e": {"value": comps / (statistics.mean(e2e_ms) * 1e-3), "unit": "terms/s",
+                "h2d_bytes_per_step": int(w.packed.nbytes), "d2h_bytes_per_step": int(P * 8)},
+        "accuracy": {"max_abs_err_rows_0_2047_4095": err},
+        "gpu_launches": int(launches * args.steps),
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        R = 8
+        t = time.perf_counter()
+        oracle.grm_rows(G, np.linspace(0, n - 1, R).astype(np.int64))
+        dt = time.perf_counter() - t
+        line["cpu_baseline"] = {"value": R * n * m / dt, "unit": "terms/s", "cores": os.cpu_count(),
+                                "kind": "oracle", "sample": f"{R} rows x all {n} columns x {m} markers ({dt:.1f} s)"}
+    return line
+
+
 def run_cluster(args, rank, world, local):
     """Complete-linkage clustering (paper, "Identity-by-state matrices, complete
     linkage clustering") of the plain workload's 4,096 samples under their IBS
@@ -887,8 +982,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="plain",
-                    choices=["plain", "structured", "batch", "serve", "ld", "cluster"])
+                    choices=["plain", "structured", "batch", "serve", "ld", "cluster", "grm"])
     ap.add_argument("--window", type=int, default=1000, help="ld: marker window")
+    ap.add_argument("--markers", type=int, default=100_000,
+                    help="grm: markers of the plain genotypes (100,000 is the benchmarked size)")
     ap.add_argument("--rates", type=float, nargs="*", default=[4.0, 12.0, 24.0, 0.0],
                     help="serving: Poisson arrival rates per second (0 = all at once)")
     ap.add_argument("--requests", type=int, default=60, help="serving: requests per rate")
@@ -914,6 +1011,8 @@ def main():
         line = run_ld(args, rank, world, local)
     elif args.workload == "cluster":
         line = run_cluster(args, rank, world, local)
+    elif args.workload == "grm":
+        line = run_grm(args, rank, world, local)
     else:
         line = run_plain(args, rank, world, local)
     if line is not None:

@@ -258,6 +258,31 @@ ibs_status ibs_cluster_complete(ibs_ctx* ctx, const double* dist, int64_t n_samp
 ibs_status ibs_ld_r(ibs_ctx* ctx, const uint8_t* packed, int64_t n_samples, int64_t n_variants, int64_t window,
                     double* out_r, int32_t* out_n, void* stream);
 
+/* GCTA genomic relationship matrix of the samples (paper, "Partial sum
+ * lookup", the weighted-distance example).  Per marker, p = frequency of A1
+ * over the marker's non-missing calls, x = number of A1 copies in a call;
+ * markers with p = 0 or p = 1 are left out.  For samples j <= k:
+ *   A_jk = (1 / N_jk) * sum over markers where both calls are present of
+ *          (x_j - 2p)(x_k - 2p) / (2p(1 - p)),
+ * N_jk = the number of such markers (the diagonal uses the same formula with
+ * j = k).  A_jk is NaN when N_jk = 0.
+ * packed: DEVICE uint8 [n_variants][ceil(n_samples/4)] (.bed layout, as for
+ * ibs_compute).  out_grm: DEVICE double [n(n+1)/2], the upper triangle with
+ * diagonal in ibs_compute's order (pair (j, k), j <= k, at
+ * j*n - j*(j-1)/2 + (k - j)).
+ * Precision: the standardised values z = (x - 2p) / sqrt(2p(1-p)) are formed
+ * in FP64 and carried as FP16 pairs hi + lo; the products run on the tensor
+ * cores in FP32, restarted every 128 markers and summed across segments
+ * without rounding loss (float-float).  With S = sum over the shared markers
+ * of |z_j z_k|, the result is within (3 + 24) * 2^-22 * S / N_jk
+ * + 2^-25 * sum(|z_j| + |z_k|) / N_jk of the exact value, for any number of
+ * markers (3 * 2^-22 from the FP16 split, 24 MMA accumulations per segment
+ * at 2^-22 each); N_jk is exact.
+ * 1 <= n_samples <= 8388480, 1 <= n_variants < 2^24.  Workspace: 12 KiB per
+ * (128 samples, 16 markers) of library memory.  Asynchronous on `stream`. */
+ibs_status ibs_grm(ibs_ctx* ctx, const uint8_t* packed, int64_t n_samples, int64_t n_variants, double* out_grm,
+                   void* stream);
+
 /* The kernels this context's ibs_compute uses: out[0] = pair kernel family
  * (0 POPC plain, 1 POPC carry-save, 2 tensor core), out[1] = tensor-core
  * operand format (0 E4M3, 1 E2M1), out[2] = SMs of the device, out[3] = device. */

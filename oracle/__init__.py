@@ -79,6 +79,8 @@ def _load():
             lib.oracle_complete_linkage.restype = ctypes.c_int
             lib.oracle_grm.argtypes = [p, i64, i64, p, ctypes.c_int]
             lib.oracle_grm.restype = ctypes.c_int
+            lib.oracle_grm_rows.argtypes = [p, i64, i64, p, i64, p, ctypes.c_int]
+            lib.oracle_grm_rows.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -206,6 +208,18 @@ def grm(G: np.ndarray, threads: int = 0) -> np.ndarray:
     out = np.empty(n * (n + 1) // 2, dtype=np.float64)
     if _load().oracle_grm(_ptr(G), n, m, _ptr(out), int(threads)) <= 0:
         raise ValueError("oracle_grm rejected its arguments")
+    return out
+
+
+def grm_rows(G: np.ndarray, rows, threads: int = 0) -> np.ndarray:
+    """Rows of the full symmetric relationship matrix of grm(): out[r][k] =
+    A_{rows[r], k}, with the marker frequencies taken over all samples of G."""
+    G = np.ascontiguousarray(G, dtype=np.uint8)
+    n, m = G.shape
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    out = np.empty((rows.size, n), dtype=np.float64)
+    if _load().oracle_grm_rows(_ptr(G), n, m, _ptr(rows), rows.size, _ptr(out), int(threads)) <= 0:
+        raise ValueError("oracle_grm_rows rejected its arguments")
     return out
 
 

@@ -453,38 +453,54 @@ typedef struct {
   int64_t n, m;
   const double* table; /* per marker 16 entries: [code_j * 4 + code_k], 0 where a call is missing */
   const char* used;    /* per marker: 1 when polymorphic */
+  const int64_t* rows; /* NULL: the whole upper triangle; else these rows, every column */
+  int64_t n_rows;
   double* out;
   int64_t next;
   pthread_mutex_t lock;
 } oracle_grm_job;
 
+/* A_jk: the pair's increments summed over the used markers where both calls
+ * are present, divided by their number. */
+static double oracle_grm_pair(const oracle_grm_job* job, int64_t j, int64_t k) {
+  const int64_t m = job->m;
+  double sum = 0.0;
+  int64_t cnt = 0;
+  for (int64_t i = 0; i < m; ++i) {
+    if (!job->used[i]) continue;
+    const uint8_t gj = job->G[j * m + i], gk = job->G[k * m + i];
+    if (gj == ORACLE_MISSING || gk == ORACLE_MISSING) continue;
+    sum += job->table[i * 16 + gj * 4 + gk];
+    cnt += 1;
+  }
+  return cnt == 0 ? NAN : sum / (double)cnt;
+}
+
 static void* oracle_grm_worker(void* arg) {
   oracle_grm_job* job = (oracle_grm_job*)arg;
-  const int64_t n = job->n, m = job->m;
+  const int64_t n = job->n;
+  const int64_t units = job->rows ? job->n_rows : n;
   for (;;) {
     pthread_mutex_lock(&job->lock);
-    const int64_t j = job->next++;
+    const int64_t u = job->next++;
     pthread_mutex_unlock(&job->lock);
-    if (j >= n) break;
-    const int64_t base = j * n - j * (j - 1) / 2;
-    for (int64_t k = j; k < n; ++k) {
-      double sum = 0.0;
-      int64_t cnt = 0;
-      for (int64_t i = 0; i < m; ++i) {
-        if (!job->used[i]) continue;
-        const uint8_t gj = job->G[j * m + i], gk = job->G[k * m + i];
-        if (gj == ORACLE_MISSING || gk == ORACLE_MISSING) continue;
-        sum += job->table[i * 16 + gj * 4 + gk];
-        cnt += 1;
-      }
-      job->out[base + (k - j)] = cnt == 0 ? NAN : sum / (double)cnt;
+    if (u >= units) break;
+    if (job->rows) {
+      const int64_t j = job->rows[u];
+      for (int64_t k = 0; k < n; ++k) job->out[u * n + k] = oracle_grm_pair(job, j, k);
+    } else {
+      const int64_t base = u * n - u * (u - 1) / 2;
+      for (int64_t k = u; k < n; ++k) job->out[base + (k - u)] = oracle_grm_pair(job, u, k);
     }
   }
   return NULL;
 }
 
-int oracle_grm(const uint8_t* G, int64_t n, int64_t m, double* out, int threads) {
-  if (!G || n <= 0 || m <= 0 || !out) return -1;
+static int oracle_grm_run(const uint8_t* G, int64_t n, int64_t m, const int64_t* rows, int64_t n_rows, double* out,
+                          int threads) {
+  if (!G || n <= 0 || m <= 0 || !out || (rows && n_rows <= 0)) return -1;
+  for (int64_t r = 0; rows && r < n_rows; ++r)
+    if (rows[r] < 0 || rows[r] >= n) return -1;
   double* table = (double*)calloc((size_t)m * 16, sizeof(double));
   char* used = (char*)calloc((size_t)m, 1);
   if (!table || !used) {
@@ -511,14 +527,16 @@ int oracle_grm(const uint8_t* G, int64_t n, int64_t m, double* out, int threads)
         if (a != ORACLE_MISSING && b != ORACLE_MISSING)
           table[i * 16 + a * 4 + b] = (x_of[a] - 2.0 * p) * (x_of[b] - 2.0 * p) / denom;
   }
+  const int64_t units = rows ? n_rows : n;
   if (threads <= 0) {
     long c = sysconf(_SC_NPROCESSORS_ONLN);
     threads = c > 0 ? (int)c : 1;
   }
   if (threads > 1024) threads = 1024;
-  if (n < threads) threads = (int)n;
+  if (units < threads) threads = (int)units;
   oracle_grm_job job;
-  job.G = G; job.n = n; job.m = m; job.table = table; job.used = used; job.out = out; job.next = 0;
+  job.G = G; job.n = n; job.m = m; job.table = table; job.used = used; job.rows = rows; job.n_rows = n_rows;
+  job.out = out; job.next = 0;
   pthread_mutex_init(&job.lock, NULL);
   int started = 0;
   if (threads > 1) {
@@ -535,4 +553,15 @@ int oracle_grm(const uint8_t* G, int64_t n, int64_t m, double* out, int threads)
   free(table);
   free(used);
   return started;
+}
+
+int oracle_grm(const uint8_t* G, int64_t n, int64_t m, double* out, int threads) {
+  return oracle_grm_run(G, n, m, NULL, 0, out, threads);
+}
+
+/* Rows rows[0..n_rows) of the full symmetric matrix: out[r * n + k] = A_{rows[r], k}
+ * (the frequencies still come from all n samples). */
+int oracle_grm_rows(const uint8_t* G, int64_t n, int64_t m, const int64_t* rows, int64_t n_rows, double* out,
+                    int threads) {
+  return oracle_grm_run(G, n, m, rows, n_rows, out, threads);
 }

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libibs.so")
-SOURCES = ["ibs_planes.cu", "ibs_pairs.cu", "ibs_tc.cu", "ibs_ld.cu", "ibs_cluster.cu", "ibs_misc.cu", "ibs_api.cu",
+SOURCES = ["ibs_planes.cu", "ibs_pairs.cu", "ibs_tc.cu", "ibs_ld.cu", "ibs_grm.cu", "ibs_cluster.cu", "ibs_misc.cu", "ibs_api.cu",
            "ibs_serve.cu", "ibs_noalloc.cu"]
 HEADERS = ["ibs_device.cuh", "ibs_internal.h", "ibs_ctx.h", "ibs_tc_common.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -940,6 +940,40 @@ extern "C" ibs_status ibs_ld_r(ibs_ctx* ctx, const uint8_t* packed, int64_t n, i
   return IBS_OK;
 }
 
+extern "C" ibs_status ibs_grm(ibs_ctx* ctx, const uint8_t* packed, int64_t n, int64_t m, double* out_grm,
+                              void* stream) {
+  clear_error();
+  if (ibs_status s = check_ctx(ctx)) return s;
+  if (!packed || !out_grm) return fail(IBS_EINVAL, "packed and out_grm must be non-NULL");
+  if (n < 1 || n > 65535LL * 128) return fail(IBS_EINVAL, "n_samples %lld out of range [1, 8388480]", (long long)n);
+  if (m < 1 || m >= ((int64_t)1 << 24))
+    return fail(IBS_EINVAL, "n_variants %lld out of range [1, 2^24)", (long long)m);
+  if (reinterpret_cast<uintptr_t>(out_grm) % 8) return fail(IBS_EINVAL, "out_grm must be 8-byte aligned");
+  DeviceGuard g(ctx->device);
+  if (!is_device_ptr(packed) || !is_device_ptr(out_grm))
+    return fail(IBS_EINVAL, "packed and out_grm must be device memory");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (ibs_status s = ensure_buf(ctx, ctx->grm_work, grm_planes_bytes(n, m))) return s;
+  if (ibs_status s = ensure_buf(ctx, ctx->grm_counter, 256)) return s;
+  if (ctx->grm_tiles_n != n) {
+    std::vector<int2> tiles;
+    grm_tiles(n, tiles);
+    if (ibs_status s = ensure_buf(ctx, ctx->grm_tiles, tiles.size() * sizeof(int2))) return s;
+    // pageable source: the copy is staged before return
+    IBS_CUDA_TRY(cudaMemcpyAsync(ctx->grm_tiles.p, tiles.data(), tiles.size() * sizeof(int2),
+                                 cudaMemcpyHostToDevice, st));
+    ctx->grm_n_tiles = (int64_t)tiles.size();
+    ctx->grm_tiles_n = n;
+  }
+  IBS_CUDA_TRY(launch_grm(packed, n, m, out_grm, static_cast<uint8_t*>(ctx->grm_work.p),
+                          static_cast<const int2*>(ctx->grm_tiles.p), ctx->grm_n_tiles,
+                          static_cast<int*>(ctx->grm_counter.p), ctx->status_dev, ctx->num_sms, st));
+  ctx->last_info[0] = 3;  // frequencies, operand builder, pair kernel
+  ctx->last_info[1] = ctx->grm_n_tiles;
+  ctx->last_info[2] = 1;
+  return IBS_OK;
+}
+
 extern "C" ibs_status ibs_kernel_info(ibs_ctx* ctx, int64_t out[4]) {
   clear_error();
   if (ibs_status s = check_ctx(ctx)) return s;
@@ -980,7 +1014,8 @@ extern "C" ibs_status ibs_shutdown(ibs_ctx* ctx) {
     free_buf(ctx, ctx->partial);
     free_buf(ctx, ctx->tile_list);
     for (DevBuf* b : {&ctx->single_items, &ctx->single_split, &ctx->single_counter, &ctx->ld_planes, &ctx->ld_diff,
-                      &ctx->ld_items, &ctx->ld_counter, &ctx->cluster_work})
+                      &ctx->ld_items, &ctx->ld_counter, &ctx->cluster_work, &ctx->grm_work,
+                      &ctx->grm_tiles, &ctx->grm_counter})
       free_buf(ctx, *b);
     for (auto* v : {&ctx->timing_used, &ctx->timing_free})
       for (auto& r : *v)

@@ -171,6 +171,15 @@ cudaError_t launch_ld(const uint8_t* packed, int64_t n, int64_t m, int64_t windo
                       const int2* items, int64_t n_items, int* counter, double* out_r, int32_t* out_n,
                       int* status, int num_sms, cudaStream_t st);
 
+// Genomic relationship matrix (ibs_grm.cu): per-marker frequency table and
+// FP16 hi/lo/V' operand planes (128-sample blocks, 16-marker chunks) in one
+// workspace of grm_planes_bytes(n, m), the grouped triangle tile order, and
+// the launch sequence (frequencies, operand builder, persistent kernel).
+size_t grm_planes_bytes(int64_t n, int64_t m);
+void grm_tiles(int64_t n, std::vector<int2>& out);
+cudaError_t launch_grm(const uint8_t* packed, int64_t n, int64_t m, double* out, uint8_t* work, const int2* tiles,
+                       int64_t n_tiles, int* counter, int* status, int num_sms, cudaStream_t st);
+
 // Complete-linkage clustering (ibs_cluster.cu) of n samples under a distance
 // triangle (ibs_compute's layout), into Z [n-1][4] on the device; `work` holds
 // cluster_workspace_bytes(n).

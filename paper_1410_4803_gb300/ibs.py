@@ -92,6 +92,7 @@ def load():
             "ibs_kernel_info": [p, ctypes.POINTER(ctypes.c_int64)],
             "ibs_ld_r": [p, p, i64, i64, i64, p, p, p],
             "ibs_cluster_complete": [p, p, i64, p, p],
+            "ibs_grm": [p, p, i64, i64, p, p],
             "ibs_last_launch_info": [p, ctypes.POINTER(ctypes.c_int64)],
             "ibs_kernel_times": [p, ctypes.POINTER(ctypes.c_double)],
             "ibs_compute_noalloc": [p, i64, i64, p, p, p],
@@ -265,6 +266,19 @@ def ibs_ld_r(ctx: Context, packed, n_samples: int, n_variants: int, window: int,
              stream=None) -> None:
     _check(load().ibs_ld_r(ctx._h, _addr(packed), n_samples, n_variants, window, _addr(out_r), _addr(out_n),
                            _stream(stream)), "ibs_ld_r")
+
+
+def ibs_grm(ctx: Context, packed, n_samples: int, n_variants: int, out_grm, stream=None) -> None:
+    _check(load().ibs_grm(ctx._h, _addr(packed), n_samples, n_variants, _addr(out_grm), _stream(stream)), "ibs_grm")
+
+
+def grm(ctx: Context, packed, n_samples: int, n_variants: int, stream=None):
+    """Allocate the upper triangle (with diagonal, float64) on the packed
+    tensor's device and run ibs_grm."""
+    import torch
+    out = torch.empty(n_samples * (n_samples + 1) // 2, dtype=torch.float64, device=packed.device)
+    ibs_grm(ctx, packed, n_samples, n_variants, out, stream)
+    return out
 
 
 def ibs_cluster_complete(ctx: Context, dist, n_samples: int, out_linkage, stream=None) -> None:

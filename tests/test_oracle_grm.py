@@ -97,3 +97,25 @@ def test_no_shared_markers_is_nan():
     G[1, 2] = 1
     A = oracle.grm(G)
     assert np.isnan(A[oracle.tri_index(0, 1, 3)])
+
+
+def test_rows_match_triangle():
+    """grm_rows gives the rows of the same symmetric matrix, in any order and
+    with repeats, bit for bit (same arithmetic per pair), and rejects rows
+    outside [0, n)."""
+    rng = np.random.default_rng(33)
+    n, m = 45, 260
+    G = _random(rng, n, m, miss=0.1)
+    G[7, :] = 1                          # a sample without calls: NaN row
+    A = oracle.grm(G)
+    full = np.empty((n, n))
+    full[np.triu_indices(n)] = A
+    full = np.triu(full) + np.triu(full, 1).T
+    rows = np.array([44, 0, 7, 13, 13, 30])
+    got = oracle.grm_rows(G, rows, threads=3)
+    np.testing.assert_array_equal(got, full[rows])
+    assert np.isnan(got[2]).all()
+    with pytest.raises(ValueError):
+        oracle.grm_rows(G, [n])
+    with pytest.raises(ValueError):
+        oracle.grm_rows(G, [-1])

@@ -52,8 +52,9 @@ CLUSTER_MUTATIONS = {
 GRM_MUTATIONS = {
     "grm_centre_at_p": ("(x_of[a] - 2.0 * p) * (x_of[b] - 2.0 * p) / denom",
                         "(x_of[a] - p) * (x_of[b] - p) / denom"),
-    "grm_missing_counted": ("cnt += 1;\n      }\n      job->out[base + (k - j)]",
-                            "}\n      cnt = job->m;\n      job->out[base + (k - j)]"),
+    "grm_missing_counted": ("cnt += 1;\n  }\n  return cnt == 0", "}\n  cnt = m;\n  return cnt == 0"),
+    "grm_rows_transposed": ("job->out[u * n + k] = oracle_grm_pair(job, j, k);",
+                            "job->out[u * n + k] = oracle_grm_pair(job, k, k);"),
     "grm_het_count": ("const double x_of[4] = {2.0, 0.0, 1.0, 0.0};", "const double x_of[4] = {2.0, 0.0, 2.0, 0.0};"),
     "grm_keep_monomorphic": ("if (p <= 0.0 || p >= 1.0) continue;", "if (p < 0.0 || p > 1.0) continue;"),
 }
