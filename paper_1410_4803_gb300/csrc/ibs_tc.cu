@@ -40,6 +40,7 @@
 // set, and the CTA still waits (bounded) for its MMAs and frees its tensor
 // memory before returning.
 #include <algorithm>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <vector>
@@ -565,9 +566,10 @@ struct CrossWork {
 // the epilogue runs.
 constexpr int kQueue = 8;
 
-template <int F, class W, int kTStages>
+template <int F, class W, int kTStages, int kPer>
 __global__ void __launch_bounds__(256, 1)
     tc_persistent_kernel(const W work, int64_t n_items, int* counter, int* status) {
+  constexpr int kBlockBytes = kPer * kTChunkBytes;  // one block's share of a ring stage
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* ring = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ __align__(8) uint64_t full[kTStages], empty[kTStages], tfull, tempty, drain;
@@ -649,7 +651,8 @@ __global__ void __launch_bounds__(256, 1)
       if (last) break;
       const TcTile t = work.tile(it);
       bool stop = false;
-      for (int64_t k = t.c0; k < t.c1; ++k, ++g) {
+      for (int64_t k = t.c0; k < t.c1; k += kPer, ++g) {
+        const uint32_t bytes = (uint32_t)(t.c1 - k < kPer ? t.c1 - k : kPer) * kTChunkBytes;
         const int s = (int)(g % kTStages);
         const bool ok = g < (uint32_t)kTStages || mbar_wait_bounded(&empty[s], ((g / kTStages) - 1) & 1u);
         if (__any_sync(0xffffffffu, !ok)) {
@@ -662,10 +665,10 @@ __global__ void __launch_bounds__(256, 1)
           break;
         }
         if (lane == 0) {
-          uint8_t* dst = ring + (size_t)s * 2 * kTChunkBytes;
-          mbar_arrive_expect_tx(&full[s], t.same ? kTChunkBytes : 2 * kTChunkBytes);
-          bulk_g2s(dst, t.a + (size_t)k * kTChunkBytes, kTChunkBytes, &full[s]);
-          if (!t.same) bulk_g2s(dst + kTChunkBytes, t.b + (size_t)k * kTChunkBytes, kTChunkBytes, &full[s]);
+          uint8_t* dst = ring + (size_t)s * 2 * kBlockBytes;
+          mbar_arrive_expect_tx(&full[s], t.same ? bytes : 2 * bytes);
+          bulk_g2s(dst, t.a + (size_t)k * kTChunkBytes, bytes, &full[s]);
+          if (!t.same) bulk_g2s(dst + kBlockBytes, t.b + (size_t)k * kTChunkBytes, bytes, &full[s]);
         }
         __syncwarp();
       }
@@ -686,7 +689,8 @@ __global__ void __launch_bounds__(256, 1)
       bool stop = __any_sync(0xffffffffu, !free_ok);
       if (!stop) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        for (int64_t k = t.c0; k < t.c1; ++k, ++g) {
+        for (int64_t k = t.c0; k < t.c1; k += kPer, ++g) {
+          const int cnt = (int)(t.c1 - k < kPer ? t.c1 - k : kPer);
           const int s = (int)(g % kTStages);
           const bool ok = mbar_wait_bounded(&full[s], (g / kTStages) & 1u);
           if (__any_sync(0xffffffffu, !ok)) {
@@ -695,9 +699,15 @@ __global__ void __launch_bounds__(256, 1)
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           if (lane == 0) {
-            const uint32_t a0 = smem_addr(ring + (size_t)s * 2 * kTChunkBytes);
-            const uint32_t b0 = t.same ? a0 : a0 + kTChunkBytes;
-            chunk_mmas<F>(tmem, a0, b0, k > t.c0 ? 1u : 0u);
+            const uint32_t st0 = smem_addr(ring + (size_t)s * 2 * kBlockBytes);
+#pragma unroll
+            for (int c = 0; c < kPer; ++c) {
+              if (c < cnt) {
+                const uint32_t a0 = st0 + c * kTChunkBytes;
+                const uint32_t b0 = t.same ? a0 : a0 + kBlockBytes;
+                chunk_mmas<F>(tmem, a0, b0, k + c > t.c0 ? 1u : 0u);
+              }
+            }
             umma_commit(&empty[s]);
           }
           __syncwarp();
@@ -962,33 +972,59 @@ cudaError_t launch_tc_gather(const TcGatherJob* jobs_dev, int n_jobs, int64_t to
   return cudaGetLastError();
 }
 
-// Ring depth of the persistent kernel: 4 stages (128 KiB), or 6 (192 KiB)
-// when an item streams at least kLongK chunks.  Measured: 6 stages are 20%
-// faster at m = 500,000 (7,813 chunks per tile, where the CTAs drift apart
-// over a tile and miss L2 more) and 1-5% slower at m <= 100,000.
-// IBS_TC_STAGES=4|6 overrides the choice.
+// Ring of the persistent kernel: kPer chunks per stage (one bulk copy per
+// block and stage) and the stage count, 192 KiB either way.  The copy engine
+// spends a fixed time per bulk copy, so two-chunk stages stream faster while
+// the operands mostly hit L2 (n = 4,096, m = 100,000: pair kernel 1.74 ->
+// 1.39 ms); for items of at least kLongK chunks the CTAs drift apart over a
+// tile and miss L2 more, and six one-chunk stages (more copies in flight)
+// win (n = 20,000, m = 500,000: 198 ms against 252 ms with two-chunk stages).
+// IBS_TC_RING=per,stages overrides (1,4 / 1,6 / 2,3 / 3,2).
 constexpr int64_t kLongK = 4096;
-int persistent_stages(int64_t chunks_per_item) {
-  static const int forced = [] {
-    const char* e = getenv("IBS_TC_STAGES");
-    const int v = e ? atoi(e) : 0;
-    return v == 4 || v == 6 ? v : 0;
+struct Ring {
+  int per, stages;
+};
+Ring persistent_ring(int64_t chunks_per_item) {
+  static const Ring forced = [] {
+    Ring r{0, 0};
+    if (const char* e = getenv("IBS_TC_RING")) {
+      const bool known = sscanf(e, "%d,%d", &r.per, &r.stages) == 2 &&
+                         ((r.per == 1 && (r.stages == 4 || r.stages == 6)) || (r.per == 2 && r.stages == 3) ||
+                          (r.per == 3 && r.stages == 2));
+      if (!known) r = Ring{0, 0};
+    } else if (const char* e2 = getenv("IBS_TC_STAGES")) {
+      const int v = atoi(e2);
+      if (v == 4 || v == 6) r = Ring{1, v};
+    }
+    return r;
   }();
-  if (forced) return forced;
-  return chunks_per_item >= kLongK ? 6 : 4;
+  if (forced.per > 0) return forced;
+  return chunks_per_item >= kLongK ? Ring{1, 6} : Ring{2, 3};
 }
+int persistent_stages(int64_t chunks_per_item) { return persistent_ring(chunks_per_item).stages; }
 
-template <int F, class W, int S>
+template <int F, class W, int S, int P>
 cudaError_t launch_persistent_s(const W& work, int64_t n_items, int grid, int* counter, int* status,
                                 cudaStream_t st) {
-  constexpr size_t smem = (size_t)S * 2 * kTChunkBytes + 1024;
-  cudaError_t e = cudaFuncSetAttribute(tc_persistent_kernel<F, W, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  constexpr size_t smem = (size_t)S * 2 * P * kTChunkBytes + 1024;
+  static_assert(smem <= 227 * 1024, "ring exceeds shared memory");
+  cudaError_t e = cudaFuncSetAttribute(tc_persistent_kernel<F, W, S, P>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
-  tc_persistent_kernel<F, W, S><<<grid, 256, smem, st>>>(work, n_items, counter, status);
+  tc_persistent_kernel<F, W, S, P><<<grid, 256, smem, st>>>(work, n_items, counter, status);
   return cudaGetLastError();
+}
+
+template <int F, class W>
+cudaError_t launch_persistent_f(const W& work, int64_t n_items, int grid, Ring r, int* counter, int* status,
+                                cudaStream_t st) {
+  if (r.per == 1 && r.stages == 4) return launch_persistent_s<F, W, 4, 1>(work, n_items, grid, counter, status, st);
+  if (r.per == 1 && r.stages == 6) return launch_persistent_s<F, W, 6, 1>(work, n_items, grid, counter, status, st);
+  if (r.per == 2 && r.stages == 3) return launch_persistent_s<F, W, 3, 2>(work, n_items, grid, counter, status, st);
+  if (r.per == 3 && r.stages == 2) return launch_persistent_s<F, W, 2, 3>(work, n_items, grid, counter, status, st);
+  return cudaErrorInvalidValue;
 }
 
 template <class W>
@@ -996,12 +1032,9 @@ cudaError_t launch_persistent(const W& work, int64_t n_items, int grid, int fmt,
                               int* counter, int* status, cudaStream_t st) {
   if (n_items <= 0) return cudaSuccess;
   if (grid < 1 || n_items > 2147483647LL - grid) return cudaErrorInvalidValue;  // the claim counter is an int
-  const bool six = persistent_stages(chunks_per_item) == 6;
-  if (fmt == kTcFp4)
-    return six ? launch_persistent_s<kTcFp4, W, 6>(work, n_items, grid, counter, status, st)
-               : launch_persistent_s<kTcFp4, W, 4>(work, n_items, grid, counter, status, st);
-  return six ? launch_persistent_s<kTcFp8, W, 6>(work, n_items, grid, counter, status, st)
-             : launch_persistent_s<kTcFp8, W, 4>(work, n_items, grid, counter, status, st);
+  const Ring r = persistent_ring(chunks_per_item);
+  if (fmt == kTcFp4) return launch_persistent_f<kTcFp4>(work, n_items, grid, r, counter, status, st);
+  return launch_persistent_f<kTcFp8>(work, n_items, grid, r, counter, status, st);
 }
 
 cudaError_t launch_tc_batch(const SubsetDev* subs, const WorkItem* items, int64_t n_items, int grid, int fmt,
