@@ -131,17 +131,26 @@ typedef struct {
 } ibs_subset;
 
 /* Batched all-pairs IBS of many subsets of one pool (paper "Multicore and
- * cluster parallelism": independent pieces of sample x sample matrices).  All
- * subsets' bit planes are built by one gather-transpose launch and all their
- * pair tiles run in ONE persistent launch over a (subset, tile, K range) work
- * list sorted longest first.  The pair kernel follows ibs_compute's choice:
- * the tensor-core form by default (one more launch expands every subset's bit
- * planes to FP8 indicator planes, 4 bytes per genotype, held for the call),
- * the POPC kernels under IBS_KERNEL_PLAIN / IBS_KERNEL_CSA.  The launch
- * sequence is captured into a CUDA graph per batch shape and replayed; tile
- * splitting (and, for POPC, the kernel variant) is chosen by the autotuner.
- * pool_packed is DEVICE [pool_m][ceil(pool_n/4)].  Results are
- * bit-identical to ibs_compute on each subset alone. */
+ * cluster parallelism": independent pieces of sample x sample matrices).
+ * Tensor-core form (the default, as ibs_compute): each subset's samples and
+ * variant window are gathered from the pool straight into operand planes, in
+ * four stages (about 10/30/30/30% of the comparisons, subsets by decreasing
+ * variant count); the gathers of later stages run on a second stream while the
+ * pair work of earlier stages runs.  Pair work, by split policy:
+ *   0  one persistent launch per stage over (subset, tile) items;
+ *   1  the same, the marker axis of large subsets split into K ranges that add
+ *      into a partial triangle (finalised at the end);
+ *   2  one persistent launch per subset over ibs_compute's own work list
+ *      (a subset with fewer tiles than SMs, and the tiles of a final partial
+ *      wave, split over K; their tiles finalised at the end).
+ * POPC form (IBS_KERNEL_PLAIN / IBS_KERNEL_CSA): one gather-transpose launch
+ * and one persistent launch over all subsets (policies 0 and 1).  The launch
+ * sequence is captured into a CUDA graph per batch shape and replayed; the
+ * policy (and, for POPC, the kernel variant) is chosen by timing the
+ * candidates on the first call of a shape, or fixed by the environment
+ * variable IBS_BATCH_POLICY=0|1|2.  pool_packed is DEVICE
+ * [pool_m][ceil(pool_n/4)].  Results are bit-identical to ibs_compute on each
+ * subset alone. */
 ibs_status ibs_compute_batch(ibs_ctx* ctx, const uint8_t* pool_packed, int64_t pool_n, int64_t pool_m,
                              const ibs_subset* subsets, int n_subsets, void* stream);
 

@@ -428,9 +428,13 @@ ItemGeom item_geom(const SubsetShape& s, int mode) {
 // Build the work list for a batch: every (subset, tile) item, K-split for
 // subsets whose tiles would be too large relative to one CTA's fair share
 // (split_policy 1), sorted by descending cost (longest processing time first).
+// Tensor-core split_policy 2: each subset's own single-matrix list (its final
+// partial wave, or all of it when it has fewer tiles than CTAs, split over K;
+// the split tiles go to split_tiles_out), for one launch per subset.
 void build_items(const std::vector<SubsetShape>& shapes, int mode, int split_policy, int grid,
                  std::vector<WorkItem>& items, std::vector<int>& subset_split, int64_t& tiles_total,
-                 std::vector<int64_t>* order_out = nullptr, std::vector<int64_t>* item_off_out = nullptr) {
+                 std::vector<int64_t>* order_out = nullptr, std::vector<int64_t>* item_off_out = nullptr,
+                 std::vector<int4>* split_tiles_out = nullptr) {
   items.clear();
   subset_split.assign(shapes.size(), 1);
   double total = 0;
@@ -467,10 +471,24 @@ void build_items(const std::vector<SubsetShape>& shapes, int mode, int split_pol
     std::vector<int2> tiles;
     if (order_out) order_out->assign(order.begin(), order.end());
     if (item_off_out) item_off_out->clear();
+    if (split_tiles_out) split_tiles_out->clear();
     for (size_t k : order) {
       const ItemGeom ig = item_geom(shapes[k], mode);
-      const int pieces = subset_split[k];
       if (item_off_out) item_off_out->push_back((int64_t)items.size());
+      if (split_policy == 2) {
+        std::vector<WorkItem> own;
+        std::vector<int2> own_split;
+        tc_single_items(shapes[k].n, shapes[k].m, tc_fmt_of(mode), grid, kTcBatchGroup, own, own_split);
+        for (WorkItem w : own) {
+          w.subset = (int32_t)k;
+          items.push_back(w);
+        }
+        subset_split[k] = own_split.empty() ? 1 : 2;
+        if (split_tiles_out)
+          for (const int2& t : own_split) split_tiles_out->push_back(make_int4((int)k, t.x, t.y, 0));
+        continue;
+      }
+      const int pieces = subset_split[k];
       tc_tile_order(ig.T, kTcBatchGroup, tiles);
       for (const int2& t : tiles)
         for (int p = 0; p < pieces; ++p) {
@@ -533,7 +551,13 @@ ibs_status plan_build(ibs_ctx* ctx, BatchPlan& plan, const std::vector<SubsetSha
   std::vector<WorkItem> items;
   std::vector<int> split;
   std::vector<int64_t> subset_item_off;
-  build_items(shapes, mode, split_policy, plan.grid, items, split, plan.tiles, &plan.order, &subset_item_off);
+  std::vector<int4> split_tiles;
+  build_items(shapes, mode, split_policy, plan.grid, items, split, plan.tiles, &plan.order, &subset_item_off,
+              &split_tiles);
+  plan.q_item_off = subset_item_off;
+  plan.q_chunks.clear();
+  for (int64_t q : plan.order) plan.q_chunks.push_back(item_geom(shapes[(size_t)q], mode).nc);
+  plan.n_split_tiles = (int64_t)split_tiles.size();
   plan.n_items = (int64_t)items.size();
   if (plan.grid > plan.n_items) plan.grid = (int)std::max<int64_t>(1, plan.n_items);
   // planes and partial offsets
@@ -613,6 +637,11 @@ ibs_status plan_build(ibs_ctx* ctx, BatchPlan& plan, const std::vector<SubsetSha
     return s;
   if (ibs_status s = ensure_buf(ctx, plan.counter, 256)) return s;
   IBS_CUDA_TRY(cudaMemcpy(plan.items.p, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice));
+  if (!split_tiles.empty()) {
+    if (ibs_status s = ensure_buf(ctx, plan.split_tiles, sizeof(int4) * split_tiles.size())) return s;
+    IBS_CUDA_TRY(cudaMemcpy(plan.split_tiles.p, split_tiles.data(), sizeof(int4) * split_tiles.size(),
+                            cudaMemcpyHostToDevice));
+  }
   if (!split_ids.empty())
     IBS_CUDA_TRY(cudaMemcpy(plan.split_ids.p, split_ids.data(), sizeof(int32_t) * split_ids.size(),
                             cudaMemcpyHostToDevice));
@@ -711,10 +740,26 @@ ibs_status plan_enqueue(ibs_ctx* ctx, BatchPlan& plan, int n_subsets, cudaStream
         IBS_CUDA_TRY(cudaEventRecord(plan.stage_ev[g + 1], plan.side));
       }
       if (g > 0) IBS_CUDA_TRY(cudaStreamWaitEvent(st, plan.stage_ev[g], 0));  // joins the side stream
+      if (plan.split_policy == 2) {
+        // one launch per subset of the stage, over its own work list
+        for (int64_t q = plan.stage_job_off[g]; q < plan.stage_job_off[g + 1]; ++q) {
+          const int64_t n_items = plan.q_item_off[q + 1] - plan.q_item_off[q];
+          IBS_CUDA_TRY(launch_tc_batch(static_cast<const SubsetDev*>(plan.subsets.p), items + plan.q_item_off[q],
+                                       n_items, (int)std::min<int64_t>(plan.grid, n_items), fmt, plan.q_chunks[q],
+                                       static_cast<int*>(plan.counter.p), ctx->status_dev, st));
+        }
+        continue;
+      }
       const int64_t n_items = plan.stage_item_off[g + 1] - plan.stage_item_off[g];
       IBS_CUDA_TRY(launch_tc_batch(static_cast<const SubsetDev*>(plan.subsets.p), items + plan.stage_item_off[g],
                                    n_items, (int)std::min<int64_t>(plan.grid, n_items), fmt, plan.stage_max_chunks[g],
                                    static_cast<int*>(plan.counter.p), ctx->status_dev, st));
+    }
+    if (plan.split_policy == 2) {
+      IBS_CUDA_TRY(launch_tc_finalize_batch_tiles(static_cast<const SubsetDev*>(plan.subsets.p),
+                                                  static_cast<const int4*>(plan.split_tiles.p), plan.n_split_tiles,
+                                                  st));
+      return IBS_OK;
     }
   } else {
     IBS_CUDA_TRY(launch_planes_batch(static_cast<const PlaneJob*>(plan.jobs.p), n_subsets, plan.total_ctas,
@@ -742,7 +787,7 @@ void plan_free(ibs_ctx* ctx, BatchPlan& plan) {
   plan.exec = nullptr;
   plan.graph = nullptr;
   for (DevBuf* b : {&plan.planes, &plan.partial, &plan.subsets, &plan.jobs, &plan.items, &plan.split_ids,
-                    &plan.counter, &plan.tc_planes, &plan.tc_jobs})
+                    &plan.counter, &plan.tc_planes, &plan.tc_jobs, &plan.split_tiles})
     free_buf(ctx, *b);
 }
 
@@ -800,7 +845,12 @@ extern "C" ibs_status ibs_compute_batch(ibs_ctx* ctx, const uint8_t* pool, int64
     const std::string tk = tune_key(ctx, shapes) + (tc ? "_tc" : "");
     int mode = forced >= 0 ? forced : (tc ? kBatchModeTc : ctx->default_mode), policy = 0;
     auto te = ctx->tune.find(tk);
-    if (te != ctx->tune.end()) {
+    // IBS_BATCH_POLICY=0|1|2 fixes the split policy (2: tensor-core modes only)
+    const char* pe = getenv("IBS_BATCH_POLICY");
+    const int fixed_policy = pe && (atoi(pe) == 0 || atoi(pe) == 1 || (atoi(pe) == 2 && tc)) ? atoi(pe) : -1;
+    if (fixed_policy >= 0) {
+      policy = fixed_policy;
+    } else if (te != ctx->tune.end()) {
       if (forced < 0) mode = te->second.mode;
       policy = te->second.split_policy;
     } else if (!getenv("IBS_NO_AUTOTUNE")) {
@@ -808,7 +858,7 @@ extern "C" ibs_status ibs_compute_batch(ibs_ctx* ctx, const uint8_t* pool, int64
       for (int cm = 0; cm <= kBatchModeTc + kTcFp4; ++cm) {
         if (forced >= 0 && cm != forced) continue;
         if (is_tc_mode(cm) != tc) continue;
-        for (int cp = 0; cp < 2; ++cp) {
+        for (int cp = 0; cp < (is_tc_mode(cm) ? 3 : 2); ++cp) {
           BatchPlan trial;
           if (ibs_status s = plan_build(ctx, trial, shapes, cm, cp)) {
             plan_free(ctx, trial);
@@ -875,7 +925,10 @@ extern "C" ibs_status ibs_compute_batch(ibs_ctx* ctx, const uint8_t* pool, int64
   BatchPlan& plan = *it->second;
   if (ibs_status s = plan_upload(ctx, plan, pool, pool_n, subs, shapes, st)) return s;
   IBS_CUDA_TRY(cudaGraphLaunch(plan.exec, st));
-  ctx->last_info[0] = (is_tc_mode(plan.mode) ? 2 * (int64_t)plan.stage_ctas.size() : 3) + (plan.n_split > 0 ? 1 : 0);
+  ctx->last_info[0] = !is_tc_mode(plan.mode) ? 3 + (plan.n_split > 0 ? 1 : 0)
+                      : plan.split_policy == 2
+                          ? (int64_t)plan.stage_ctas.size() + n_subsets + (plan.n_split_tiles > 0 ? 1 : 0)
+                          : 2 * (int64_t)plan.stage_ctas.size() + (plan.n_split > 0 ? 1 : 0);
   ctx->last_info[1] = plan.tiles;
   ctx->last_info[2] = plan.split_policy;
   return IBS_OK;

@@ -58,6 +58,13 @@ struct BatchPlan {
   std::vector<int64_t> order;           // subset processing order
   std::vector<int64_t> stage_item_off, stage_job_off, stage_ctas;  // per stage (+1 end entry for offsets)
   std::vector<int64_t> stage_max_chunks;  // longest item of a stage, in chunks (picks the ring depth)
+  // split policy 2 (tensor-core modes): one launch per subset over its own
+  // work list (the single-matrix list: small subsets and tail waves split over
+  // K); q_item_off / q_chunks per position of `order`, split tiles
+  // {subset, I, J, -} finalised after the last launch
+  std::vector<int64_t> q_item_off, q_chunks;
+  DevBuf split_tiles;
+  int64_t n_split_tiles = 0;
   cudaStream_t side = nullptr;
   std::vector<cudaEvent_t> stage_ev;
   int64_t n_items = 0, total_ctas = 0, max_split_pairs = 0, tc_ctas = 0;

@@ -83,24 +83,42 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16
 // Per marker: the A1 frequency and, for the three called codes, hi and lo of
 // z; table[i] = {hi, lo} of hom A1 (x = 2), het (x = 1), hom A2 (x = 0), then
 // V' (1.0 when 0 < p < 1) and a pad, as FP16 bit patterns.  One warp per
-// marker row; p and z in FP64.
+// marker row; the codes are counted by population counts over 16 genotypes
+// per 32-bit word (codes 0 hom A1, 1 missing, 2 het, 3 hom A2 in bit pairs);
+// p and z in FP64.
+__device__ __forceinline__ void count_codes(uint32_t w, uint32_t valid, int& hom1, int& het, int& miss) {
+  const uint32_t lo = w & 0x55555555u, hi = (w >> 1) & 0x55555555u;
+  hom1 += __popc(~(lo | hi) & valid);
+  het += __popc(hi & ~lo & valid);
+  miss += __popc(lo & ~hi & valid);
+}
+
 __global__ void grm_freq_kernel(const uint8_t* __restrict__ packed, int64_t row_bytes, int64_t n, int64_t m,
                                 uint16_t* __restrict__ table) {
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
   const int lane = threadIdx.x & 31;
+  // rows are 16-byte aligned when the row length is (the buffer base is)
+  const bool vec = (row_bytes & 15) == 0 && (reinterpret_cast<uintptr_t>(packed) & 15) == 0;
   for (int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); i < m; i += warps) {
     const uint8_t* row = packed + i * row_bytes;
-    int64_t hom1 = 0, het = 0, miss = 0;
-    for (int64_t byte = lane; byte < row_bytes; byte += 32) {
-      const uint32_t v = row[byte];
+    int hom1 = 0, het = 0, miss = 0;
+    if (vec) {
+      const uint4* r4 = reinterpret_cast<const uint4*>(row);
+      for (int64_t q = lane; q < row_bytes / 16; q += 32) {
+        const uint4 v = __ldg(r4 + q);
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        if (byte * 4 + q < n) {
-          const uint32_t c = (v >> (2 * q)) & 3u;
-          hom1 += c == 0;
-          het += c == 2;
-          miss += c == 1;
+        for (int t = 0; t < 4; ++t) {
+          const int64_t s0 = q * 64 + t * 16;  // first sample of the word
+          const uint32_t valid = s0 + 16 <= n ? 0x55555555u : (s0 >= n ? 0u : 0x55555555u >> (2 * (s0 + 16 - n)));
+          count_codes(w[t], valid, hom1, het, miss);
         }
+      }
+    } else {
+      for (int64_t q = lane; q < row_bytes; q += 32) {
+        const int64_t s0 = q * 4;
+        const uint32_t valid = s0 + 4 <= n ? 0x55u : 0x55u >> (2 * (s0 + 4 - n));
+        count_codes(__ldg(row + q), valid, hom1, het, miss);
       }
     }
 #pragma unroll
@@ -111,50 +129,61 @@ __global__ void grm_freq_kernel(const uint8_t* __restrict__ packed, int64_t row_
     }
     if (lane == 0) {
       const int64_t calls = n - miss;
-      const double p = calls > 0 ? (double)(2 * hom1 + het) / (2.0 * (double)calls) : 0.0;
+      const double p = calls > 0 ? (double)(2 * (int64_t)hom1 + het) / (2.0 * (double)calls) : 0.0;
       const bool used = p > 0.0 && p < 1.0;
-      const double s = used ? 1.0 / sqrt(2.0 * p * (1.0 - p)) : 0.0;
-      uint16_t* t = table + i * 8;
+      const double sc = used ? 1.0 / sqrt(2.0 * p * (1.0 - p)) : 0.0;
+      uint16_t t[8];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const double z = used ? ((double)(2 - c) - 2.0 * p) * s : 0.0;
-        const __half hi = __double2half(z);
-        const __half lo = __double2half(z - (double)__half2float(hi));
-        t[2 * c] = __half_as_ushort(hi);
-        t[2 * c + 1] = __half_as_ushort(lo);
+        const double z = used ? ((double)(2 - c) - 2.0 * p) * sc : 0.0;
+        const __half zh = __double2half(z);
+        const __half zl = __double2half(z - (double)__half2float(zh));
+        t[2 * c] = __half_as_ushort(zh);
+        t[2 * c + 1] = __half_as_ushort(zl);
       }
       t[6] = __half_as_ushort(__float2half(used ? 1.0f : 0.0f));
       t[7] = 0;
+      *reinterpret_cast<uint4*>(table + i * 8) = make_uint4(t[0] | ((uint32_t)t[1] << 16), t[2] | ((uint32_t)t[3] << 16),
+                                                            t[4] | ((uint32_t)t[5] << 16), t[6] | ((uint32_t)t[7] << 16));
     }
   }
 }
 
 // Operand rows: CTA = (marker chunk c, sample block b), thread = sample row r.
-// The thread reads its sample's codes at the chunk's 16 markers and writes 32
-// bytes (16 FP16 values) of each of hi, lo and V'.
+// The chunk's 16 table entries are staged in shared memory; the thread reads
+// its sample's codes at the 16 markers and writes 32 bytes (16 FP16 values)
+// of each of hi, lo and V'.
 __global__ void __launch_bounds__(128) grm_planes_kernel(const uint8_t* __restrict__ packed, int64_t row_bytes,
                                                          int64_t n, int64_t m, const uint16_t* __restrict__ table,
                                                          uint8_t* __restrict__ planes, int64_t n_chunks) {
+  __shared__ uint4 tab[kGrmK];
   const int64_t c = blockIdx.x, b = blockIdx.y;
   const int r = threadIdx.x;
+  if (r < kGrmK) {
+    const int64_t i = c * kGrmK + r;
+    tab[r] = i < m ? __ldg(reinterpret_cast<const uint4*>(table) + i) : make_uint4(0, 0, 0, 0);
+  }
   const int64_t s = b * kTB + r;
+  uint32_t code[kGrmK];
+#pragma unroll
+  for (int k = 0; k < kGrmK; ++k) {
+    const int64_t i = c * kGrmK + k;
+    code[k] = s < n && i < m ? (__ldg(packed + i * row_bytes + (s >> 2)) >> (2 * (s & 3))) & 3u : 1u;
+  }
+  __syncthreads();
+  const uint16_t* t16 = reinterpret_cast<const uint16_t*>(tab);
   uint32_t hi[kGrmK / 2], lo[kGrmK / 2], vp[kGrmK / 2];
 #pragma unroll
   for (int k = 0; k < kGrmK / 2; ++k) hi[k] = lo[k] = vp[k] = 0;
 #pragma unroll
   for (int k = 0; k < kGrmK; ++k) {
-    const int64_t i = c * kGrmK + k;
-    if (s < n && i < m) {
-      const uint32_t code = (__ldg(packed + i * row_bytes + (s >> 2)) >> (2 * (s & 3))) & 3u;
-      if (code != 1) {
-        // code 0 = hom A1 (slot 0), 2 = het (slot 1), 3 = hom A2 (slot 2)
-        const uint32_t slot = code == 0 ? 0u : code - 1u;
-        const uint16_t* t = table + i * 8;
-        const int sh = 16 * (k & 1);
-        hi[k >> 1] |= (uint32_t)__ldg(t + 2 * slot) << sh;
-        lo[k >> 1] |= (uint32_t)__ldg(t + 2 * slot + 1) << sh;
-        vp[k >> 1] |= (uint32_t)__ldg(t + 6) << sh;
-      }
+    if (code[k] != 1) {  // missing (and padding) stays 0
+      // code 0 = hom A1 (slot 0), 2 = het (slot 1), 3 = hom A2 (slot 2)
+      const uint32_t slot = code[k] == 0 ? 0u : code[k] - 1u;
+      const int sh = 16 * (k & 1);
+      hi[k >> 1] |= (uint32_t)t16[k * 8 + 2 * slot] << sh;
+      lo[k >> 1] |= (uint32_t)t16[k * 8 + 2 * slot + 1] << sh;
+      vp[k >> 1] |= (uint32_t)t16[k * 8 + 6] << sh;
     }
   }
   uint8_t* base = planes + (size_t)(b * n_chunks + c) * kGrmChunkBytes;

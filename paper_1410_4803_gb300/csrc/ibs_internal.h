@@ -154,6 +154,9 @@ cudaError_t launch_tc_single(const SubsetDev& sd, const WorkItem* items, int64_t
                              int* counter, int* status, cudaStream_t st);
 cudaError_t launch_tc_finalize_tiles(const int2* tiles, int64_t n_tiles, const int32_t* partial, int64_t n,
                                      int32_t* out_counts, double* out_dist, cudaStream_t st);
+// Batch form: tiles {subset, I, J, -}, outputs from the subsets' descriptors.
+cudaError_t launch_tc_finalize_batch_tiles(const SubsetDev* subs, const int4* tiles, int64_t n_tiles,
+                                           cudaStream_t st);
 // Serving, tensor-core form: CrossItem.qplanes points at a 128-row query block
 // of operand planes, row_out has 128 entries, pb is a 128-sample panel block.
 cudaError_t launch_tc_cross(const uint8_t* panel, int64_t n_panel, int64_t n_chunks, const CrossItem* items,

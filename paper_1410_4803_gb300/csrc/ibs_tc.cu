@@ -806,6 +806,23 @@ __global__ void __launch_bounds__(256) tc_finalize_tiles_kernel(const int2* __re
   }
 }
 
+// The same for a batch: one CTA per listed (subset, tile), the subset's
+// outputs and partial triangle read from its descriptor (so a captured graph
+// serves calls with new output pointers).
+__global__ void __launch_bounds__(256) tc_finalize_batch_tiles_kernel(const SubsetDev* __restrict__ subs,
+                                                                      const int4* __restrict__ tiles) {
+  const int4 t = tiles[blockIdx.x];  // {subset, I, J, -}
+  const SubsetDev sd = subs[t.x];
+  for (int p = threadIdx.x; p < kTB * kTB; p += blockDim.x) {
+    const int64_t gi = (int64_t)t.y * kTB + p / kTB, gj = (int64_t)t.z * kTB + p % kTB;
+    if (gi >= sd.n || gj >= sd.n || gj < gi) continue;
+    const int64_t q = tri_index(gi, gj, sd.n);
+    const int4 v = reinterpret_cast<const int4*>(sd.partial)[q];
+    reinterpret_cast<int4*>(sd.out_counts)[q] = make_int4(v.x, v.y, v.w - v.x - v.y, v.w);
+    if (sd.out_dist) sd.out_dist[q] = ibs_dist(v.x, v.y, v.w);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // MMA-rate probe: every CTA (one per SM) issues back-to-back 128 x 128 MMAs of
 // one kind from operand tiles resident in shared memory, into one TMEM
@@ -979,7 +996,7 @@ cudaError_t launch_tc_gather(const TcGatherJob* jobs_dev, int n_jobs, int64_t to
 // 1.39 ms); for items of at least kLongK chunks the CTAs drift apart over a
 // tile and miss L2 more, and six one-chunk stages (more copies in flight)
 // win (n = 20,000, m = 500,000: 198 ms against 252 ms with two-chunk stages).
-// IBS_TC_RING=per,stages overrides (1,4 / 1,6 / 2,3 / 3,2).
+// IBS_TC_RING=per,stages overrides (1,4 / 1,6 / 2,2 / 2,3 / 3,2).
 constexpr int64_t kLongK = 4096;
 struct Ring {
   int per, stages;
@@ -989,8 +1006,8 @@ Ring persistent_ring(int64_t chunks_per_item) {
     Ring r{0, 0};
     if (const char* e = getenv("IBS_TC_RING")) {
       const bool known = sscanf(e, "%d,%d", &r.per, &r.stages) == 2 &&
-                         ((r.per == 1 && (r.stages == 4 || r.stages == 6)) || (r.per == 2 && r.stages == 3) ||
-                          (r.per == 3 && r.stages == 2));
+                         ((r.per == 1 && (r.stages == 4 || r.stages == 6)) ||
+                          (r.per == 2 && (r.stages == 2 || r.stages == 3)) || (r.per == 3 && r.stages == 2));
       if (!known) r = Ring{0, 0};
     } else if (const char* e2 = getenv("IBS_TC_STAGES")) {
       const int v = atoi(e2);
@@ -1022,6 +1039,7 @@ cudaError_t launch_persistent_f(const W& work, int64_t n_items, int grid, Ring r
                                 cudaStream_t st) {
   if (r.per == 1 && r.stages == 4) return launch_persistent_s<F, W, 4, 1>(work, n_items, grid, counter, status, st);
   if (r.per == 1 && r.stages == 6) return launch_persistent_s<F, W, 6, 1>(work, n_items, grid, counter, status, st);
+  if (r.per == 2 && r.stages == 2) return launch_persistent_s<F, W, 2, 2>(work, n_items, grid, counter, status, st);
   if (r.per == 2 && r.stages == 3) return launch_persistent_s<F, W, 3, 2>(work, n_items, grid, counter, status, st);
   if (r.per == 3 && r.stages == 2) return launch_persistent_s<F, W, 2, 3>(work, n_items, grid, counter, status, st);
   return cudaErrorInvalidValue;
@@ -1052,6 +1070,14 @@ cudaError_t launch_tc_finalize_tiles(const int2* tiles, int64_t n_tiles, const i
   if (n_tiles <= 0) return cudaSuccess;
   if (n_tiles > 2147483647LL) return cudaErrorInvalidValue;
   tc_finalize_tiles_kernel<<<(unsigned)n_tiles, 256, 0, st>>>(tiles, partial, n, out_counts, out_dist);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_finalize_batch_tiles(const SubsetDev* subs, const int4* tiles, int64_t n_tiles,
+                                           cudaStream_t st) {
+  if (n_tiles <= 0) return cudaSuccess;
+  if (n_tiles > 2147483647LL) return cudaErrorInvalidValue;
+  tc_finalize_batch_tiles_kernel<<<(unsigned)n_tiles, 256, 0, st>>>(subs, tiles);
   return cudaGetLastError();
 }
 

@@ -123,12 +123,45 @@ def test_batch_split_items(pool, flags_name):
     ctx = ibs.ibs_init(0, flags=_flags(ibs, flags_name))
     try:
         (c, d), = _run_batch(ctx, w, subs, torch.from_numpy(w.packed).cuda())
-        assert ibs.ibs_batch_plan_info(ctx)["split_policy"] == 1
+        # tensor-core modes may also pick the per-subset launches (policy 2),
+        # which split this subset's few tiles over K as ibs_compute does
+        assert ibs.ibs_batch_plan_info(ctx)["split_policy"] in ((1, 2) if "TC" in flags_name else (1,))
         idx, vb, vl = subs[0]
         G = oracle.unpack_subset(w.packed, w.n, w.m, idx, vb, vl)
         oc, od, _ = oracle.ibs_triangle_from_codes(G)
         assert (c == oc).all()
         assert_dist_close(d, od)
+    finally:
+        ibs.ibs_shutdown(ctx)
+
+
+@pytest.mark.parametrize("policy", [0, 1, 2])
+@pytest.mark.parametrize("fmt", ["IBS_TC_FP8", "IBS_TC_FP4"])
+def test_batch_each_policy(pool, policy, fmt, monkeypatch):
+    """Every split policy of the tensor-core batch, fixed by IBS_BATCH_POLICY:
+    0 whole tiles in one launch per stage, 1 K-split large subsets, 2 one
+    launch per subset over its own work list (small subsets and tail waves
+    split over K, split tiles finalised from the subset descriptors).  Counts
+    equal the oracle for all twelve subsets, twice (graph replay)."""
+    import torch
+    from paper_1410_4803_gb300 import ibs
+    monkeypatch.setenv("IBS_BATCH_POLICY", str(policy))
+    w, codes = pool
+    rng = np.random.default_rng(9)
+    subs = _make_subsets(rng, w.n, w.m)
+    ctx = ibs.ibs_init(0, flags=_flags(ibs, "IBS_KERNEL_TC|" + fmt))
+    try:
+        dev = torch.from_numpy(w.packed).cuda()
+        first = _run_batch(ctx, w, subs, dev)
+        second = _run_batch(ctx, w, subs, dev)
+        assert ibs.ibs_batch_plan_info(ctx)["split_policy"] == policy
+        for (idx, vb, vl), (c1, d1), (c2, d2) in zip(subs, first, second):
+            G = oracle.unpack_subset(w.packed, w.n, w.m, idx, vb, vl)
+            oc, od, _ = oracle.ibs_triangle_from_codes(G)
+            assert (c1 == oc).all(), f"policy {policy}: n={idx.size} window={vb}+{vl}"
+            assert (c2 == oc).all()
+            assert_dist_close(d1, od)
+            np.testing.assert_array_equal(d1, d2)
     finally:
         ibs.ibs_shutdown(ctx)
 
