@@ -881,7 +881,9 @@ def run_grm(args, rank, world, local):
                    "pairs_incl_diagonal": P,
                    "l2": "flushed between steps (256 MiB write, outside the step events)"},
         "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
-                     "traffic": None, "kernel": "whole ibs_grm call (frequency and operand kernels included)",
+                     "traffic": profiled_traffic("tc_grm_kernel_plain.md",
+                                                 ("ibs_grm.cu", "ibs_tc_common.cuh", "ibs_device.cuh")),
+                     "kernel": "whole ibs_grm call (frequency and operand kernels included)",
                      "kernel_ms": mean_ms,
                      "peak_basis": "measured bf16 burst TFLOP/s (MEASURED_PEAKS.json; FP16 runs at the bf16 rate); "
                                    "algorithmic flops = 8 per term (4 MACs: hi hi, hi lo, lo hi, V'V')"},

@@ -1008,21 +1008,34 @@ extern "C" ibs_status ibs_grm(ibs_ctx* ctx, const uint8_t* packed, int64_t n, in
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (ibs_status s = ensure_buf(ctx, ctx->grm_work, grm_planes_bytes(n, m))) return s;
   if (ibs_status s = ensure_buf(ctx, ctx->grm_counter, 256)) return s;
-  if (ctx->grm_tiles_n != n) {
-    std::vector<int2> tiles;
-    grm_tiles(n, tiles);
-    if (ibs_status s = ensure_buf(ctx, ctx->grm_tiles, tiles.size() * sizeof(int2))) return s;
-    // pageable source: the copy is staged before return
-    IBS_CUDA_TRY(cudaMemcpyAsync(ctx->grm_tiles.p, tiles.data(), tiles.size() * sizeof(int2),
+  const std::vector<int64_t> key = {n, m};
+  if (ctx->grm_key != key) {
+    std::vector<GrmItem> items;
+    std::vector<int4> splits;
+    int64_t parts = 0;
+    grm_items(n, m, ctx->num_sms, items, splits, parts);
+    if (ibs_status s = ensure_buf(ctx, ctx->grm_items, items.size() * sizeof(GrmItem))) return s;
+    if (ibs_status s = ensure_buf(ctx, ctx->grm_splits, std::max<size_t>(1, splits.size()) * sizeof(int4))) return s;
+    if (ibs_status s = ensure_buf(ctx, ctx->grm_part, std::max<int64_t>(1, parts) * 128 * 128 * 12)) return s;
+    // pageable sources: the copies are staged before return
+    IBS_CUDA_TRY(cudaMemcpyAsync(ctx->grm_items.p, items.data(), items.size() * sizeof(GrmItem),
                                  cudaMemcpyHostToDevice, st));
-    ctx->grm_n_tiles = (int64_t)tiles.size();
-    ctx->grm_tiles_n = n;
+    if (!splits.empty())
+      IBS_CUDA_TRY(cudaMemcpyAsync(ctx->grm_splits.p, splits.data(), splits.size() * sizeof(int4),
+                                   cudaMemcpyHostToDevice, st));
+    ctx->grm_n_items = (int64_t)items.size();
+    ctx->grm_n_splits = (int64_t)splits.size();
+    ctx->grm_parts = parts;
+    ctx->grm_key = key;
   }
+  double* part_num = static_cast<double*>(ctx->grm_part.p);
+  float* part_cnt = reinterpret_cast<float*>(part_num + std::max<int64_t>(1, ctx->grm_parts) * 128 * 128);
   IBS_CUDA_TRY(launch_grm(packed, n, m, out_grm, static_cast<uint8_t*>(ctx->grm_work.p),
-                          static_cast<const int2*>(ctx->grm_tiles.p), ctx->grm_n_tiles,
+                          static_cast<const GrmItem*>(ctx->grm_items.p), ctx->grm_n_items,
+                          static_cast<const int4*>(ctx->grm_splits.p), ctx->grm_n_splits, part_num, part_cnt,
                           static_cast<int*>(ctx->grm_counter.p), ctx->status_dev, ctx->num_sms, st));
-  ctx->last_info[0] = 3;  // frequencies, operand builder, pair kernel
-  ctx->last_info[1] = ctx->grm_n_tiles;
+  ctx->last_info[0] = ctx->grm_n_splits > 0 ? 4 : 3;  // frequencies, operands, pairs (, finalisation)
+  ctx->last_info[1] = ctx->grm_n_items;
   ctx->last_info[2] = 1;
   return IBS_OK;
 }
@@ -1068,7 +1081,7 @@ extern "C" ibs_status ibs_shutdown(ibs_ctx* ctx) {
     free_buf(ctx, ctx->tile_list);
     for (DevBuf* b : {&ctx->single_items, &ctx->single_split, &ctx->single_counter, &ctx->ld_planes, &ctx->ld_diff,
                       &ctx->ld_items, &ctx->ld_counter, &ctx->cluster_work, &ctx->grm_work,
-                      &ctx->grm_tiles, &ctx->grm_counter})
+                      &ctx->grm_items, &ctx->grm_splits, &ctx->grm_part, &ctx->grm_counter})
       free_buf(ctx, *b);
     for (auto* v : {&ctx->timing_used, &ctx->timing_free})
       for (auto& r : *v)

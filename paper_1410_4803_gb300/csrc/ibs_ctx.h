@@ -107,9 +107,11 @@ struct ibs_ctx {
   ibs::DevBuf ld_planes, ld_diff, ld_items, ld_counter;
   std::vector<int64_t> ld_key;
   int64_t ld_n_items = 0;
-  // GCTA relationship matrix: operand planes and frequency table, tile order of the last n
-  ibs::DevBuf grm_work, grm_tiles, grm_counter;
-  int64_t grm_tiles_n = -1, grm_n_tiles = 0;
+  // GCTA relationship matrix: operand planes and frequency table; work list,
+  // split tiles and their part sums for the last (n, m)
+  ibs::DevBuf grm_work, grm_items, grm_splits, grm_part, grm_counter;
+  std::vector<int64_t> grm_key;
+  int64_t grm_n_items = 0, grm_n_splits = 0, grm_parts = 0;
   // persistent tensor-core work list of the last (n, m, format, SMs, group)
   std::vector<int64_t> single_key;
   ibs::DevBuf single_items, single_split, single_counter;

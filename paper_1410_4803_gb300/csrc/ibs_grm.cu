@@ -82,10 +82,9 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16
 
 // Per marker: the A1 frequency and, for the three called codes, hi and lo of
 // z; table[i] = {hi, lo} of hom A1 (x = 2), het (x = 1), hom A2 (x = 0), then
-// V' (1.0 when 0 < p < 1) and a pad, as FP16 bit patterns.  One warp per
-// marker row; the codes are counted by population counts over 16 genotypes
-// per 32-bit word (codes 0 hom A1, 1 missing, 2 het, 3 hom A2 in bit pairs);
-// p and z in FP64.
+// V' (1.0 when 0 < p < 1) and a pad, as FP16 bit patterns.  The codes are
+// counted by population counts over 16 genotypes per 32-bit word (codes 0 hom
+// A1, 1 missing, 2 het, 3 hom A2 in bit pairs); p and z in FP64.
 __device__ __forceinline__ void count_codes(uint32_t w, uint32_t valid, int& hom1, int& het, int& miss) {
   const uint32_t lo = w & 0x55555555u, hi = (w >> 1) & 0x55555555u;
   hom1 += __popc(~(lo | hi) & valid);
@@ -93,43 +92,58 @@ __device__ __forceinline__ void count_codes(uint32_t w, uint32_t valid, int& hom
   miss += __popc(lo & ~hi & valid);
 }
 
+// A warp takes 32 consecutive markers: it counts each row with all lanes,
+// lane j keeps marker j's totals, and the 32 lanes then form p and z in FP64
+// side by side (GB300's FP64 rate is low, so the arithmetic is spread over
+// the lanes rather than left to one).
 __global__ void grm_freq_kernel(const uint8_t* __restrict__ packed, int64_t row_bytes, int64_t n, int64_t m,
                                 uint16_t* __restrict__ table) {
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
   const int lane = threadIdx.x & 31;
   // rows are 16-byte aligned when the row length is (the buffer base is)
   const bool vec = (row_bytes & 15) == 0 && (reinterpret_cast<uintptr_t>(packed) & 15) == 0;
-  for (int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); i < m; i += warps) {
-    const uint8_t* row = packed + i * row_bytes;
-    int hom1 = 0, het = 0, miss = 0;
-    if (vec) {
-      const uint4* r4 = reinterpret_cast<const uint4*>(row);
-      for (int64_t q = lane; q < row_bytes / 16; q += 32) {
-        const uint4 v = __ldg(r4 + q);
-        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+  for (int64_t i0 = ((int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5)) * 32; i0 < m; i0 += warps * 32) {
+    int my_hom1 = 0, my_het = 0, my_miss = 0;
+    const int rows = (int)(m - i0 < 32 ? m - i0 : 32);
+    for (int j = 0; j < rows; ++j) {
+      const uint8_t* row = packed + (i0 + j) * row_bytes;
+      int hom1 = 0, het = 0, miss = 0;
+      if (vec) {
+        const uint4* r4 = reinterpret_cast<const uint4*>(row);
+        for (int64_t q = lane; q < row_bytes / 16; q += 32) {
+          const uint4 v = __ldg(r4 + q);
+          const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const int64_t s0 = q * 64 + t * 16;  // first sample of the word
-          const uint32_t valid = s0 + 16 <= n ? 0x55555555u : (s0 >= n ? 0u : 0x55555555u >> (2 * (s0 + 16 - n)));
-          count_codes(w[t], valid, hom1, het, miss);
+          for (int t = 0; t < 4; ++t) {
+            const int64_t s0 = q * 64 + t * 16;  // first sample of the word
+            const uint32_t valid =
+                s0 + 16 <= n ? 0x55555555u : (s0 >= n ? 0u : 0x55555555u >> (2 * (s0 + 16 - n)));
+            count_codes(w[t], valid, hom1, het, miss);
+          }
+        }
+      } else {
+        for (int64_t q = lane; q < row_bytes; q += 32) {
+          const int64_t s0 = q * 4;
+          const uint32_t valid = s0 + 4 <= n ? 0x55u : 0x55u >> (2 * (s0 + 4 - n));
+          count_codes(__ldg(row + q), valid, hom1, het, miss);
         }
       }
-    } else {
-      for (int64_t q = lane; q < row_bytes; q += 32) {
-        const int64_t s0 = q * 4;
-        const uint32_t valid = s0 + 4 <= n ? 0x55u : 0x55u >> (2 * (s0 + 4 - n));
-        count_codes(__ldg(row + q), valid, hom1, het, miss);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        hom1 += __shfl_xor_sync(0xffffffffu, hom1, o);
+        het += __shfl_xor_sync(0xffffffffu, het, o);
+        miss += __shfl_xor_sync(0xffffffffu, miss, o);
+      }
+      if (lane == j) {
+        my_hom1 = hom1;
+        my_het = het;
+        my_miss = miss;
       }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      hom1 += __shfl_xor_sync(0xffffffffu, hom1, o);
-      het += __shfl_xor_sync(0xffffffffu, het, o);
-      miss += __shfl_xor_sync(0xffffffffu, miss, o);
-    }
-    if (lane == 0) {
-      const int64_t calls = n - miss;
-      const double p = calls > 0 ? (double)(2 * (int64_t)hom1 + het) / (2.0 * (double)calls) : 0.0;
+    if (lane < rows) {
+      const int64_t i = i0 + lane;
+      const int64_t calls = n - my_miss;
+      const double p = calls > 0 ? (double)(2 * (int64_t)my_hom1 + my_het) / (2.0 * (double)calls) : 0.0;
       const bool used = p > 0.0 && p < 1.0;
       const double sc = used ? 1.0 / sqrt(2.0 * p * (1.0 - p)) : 0.0;
       uint16_t t[8];
@@ -201,9 +215,11 @@ __global__ void __launch_bounds__(128) grm_planes_kernel(const uint8_t* __restri
 struct GrmArgs {
   const uint8_t* planes;
   int64_t n, n_chunks;
-  const int2* tiles;
-  int64_t n_tiles;
-  double* out;  // upper triangle with diagonal
+  const GrmItem* items;
+  int64_t n_items;
+  double* out;       // upper triangle with diagonal
+  double* part_num;  // split items: [part][128][128] numerators and counts
+  float* part_cnt;
   int* counter;
   int* status;
 };
@@ -291,8 +307,6 @@ __global__ void __launch_bounds__(kGrmThreads, 1) tc_grm_kernel(const GrmArgs ar
     if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
   };
   const int64_t nk = args.n_chunks;  // a multiple of kGrmPad
-  const int64_t nq = nk / kPer;
-  const int64_t nseg = (nk + kGrmSeg - 1) / kGrmSeg;
 
   if (warp == kGrmCopyWarp) {
     uint32_t g = 0;
@@ -300,7 +314,7 @@ __global__ void __launch_bounds__(kGrmThreads, 1) tc_grm_kernel(const GrmArgs ar
       int64_t it = 0;
       if (lane == 0) it = atomicAdd(args.counter, 1);
       it = __shfl_sync(0xffffffffu, it, 0);
-      const bool last = it >= args.n_tiles;
+      const bool last = it >= args.n_items;
       const int qs = (int)(e % kGrmQueue);
       const bool qok = e < (uint32_t)kGrmQueue || mbar_wait_bounded(&qempty[qs], ((e / kGrmQueue) - 1) & 1u);
       if (__any_sync(0xffffffffu, !qok)) {
@@ -314,12 +328,12 @@ __global__ void __launch_bounds__(kGrmThreads, 1) tc_grm_kernel(const GrmArgs ar
       }
       __syncwarp();
       if (last) break;
-      const int2 t = args.tiles[it];
-      const bool same = t.x == t.y;
-      const uint8_t* ablk = args.planes + (size_t)t.x * nk * kGrmChunkBytes;
-      const uint8_t* bblk = args.planes + (size_t)t.y * nk * kGrmChunkBytes;
+      const GrmItem t = args.items[it];
+      const bool same = t.I == t.J;
+      const uint8_t* ablk = args.planes + (size_t)t.I * nk * kGrmChunkBytes;
+      const uint8_t* bblk = args.planes + (size_t)t.J * nk * kGrmChunkBytes;
       bool stop = false;
-      for (int64_t q = 0; q < nq; ++q, ++g) {
+      for (int64_t q = t.c0 / kPer; q < t.c1 / kPer; ++q, ++g) {
         const int s = (int)(g % kGrmStages);
         const bool ok = g < (uint32_t)kGrmStages || mbar_wait_bounded(&empty[s], ((g / kGrmStages) - 1) & 1u);
         if (__any_sync(0xffffffffu, !ok)) {
@@ -351,18 +365,19 @@ __global__ void __launch_bounds__(kGrmThreads, 1) tc_grm_kernel(const GrmArgs ar
         break;
       }
       if (it < 0) break;
-      const int2 t = args.tiles[it];
-      const bool same = t.x == t.y;
-      for (int64_t q = 0; q < nq && !stop; ++q, ++g) {
-        const int64_t k0 = q * kPer;
+      const GrmItem t = args.items[it];
+      const bool same = t.I == t.J;
+      const int64_t q1 = t.c1 / kPer;
+      for (int64_t q = t.c0 / kPer; q < q1 && !stop; ++q, ++g) {
+        const int64_t k0 = q * kPer, r0 = k0 - t.c0;  // r0: chunks into the item
         const uint32_t b = gs & 1u;
-        const bool seg_end = (k0 + kPer) % kGrmSeg == 0 || q == nq - 1;
-        if (k0 % kGrmSeg == 0) {
+        const bool seg_end = (r0 + kPer) % kGrmSeg == 0 || q == q1 - 1;
+        if (r0 % kGrmSeg == 0) {
           // the numerator bank is free once the epilogue has read the segment
           // two back; the previous tile's count must be read before the first
           // count MMA of this one
           bool ok = gs < 2 || mbar_wait_bounded(&seg_free[b], ((gs >> 1) - 1) & 1u);
-          if (ok && k0 == 0 && e > 0) ok = mbar_wait_bounded(&cnt_free, (e - 1) & 1u);
+          if (ok && r0 == 0 && e > 0) ok = mbar_wait_bounded(&cnt_free, (e - 1) & 1u);
           if (__any_sync(0xffffffffu, !ok)) {
             stop = true;
             break;
@@ -381,12 +396,12 @@ __global__ void __launch_bounds__(kGrmThreads, 1) tc_grm_kernel(const GrmArgs ar
           const uint32_t num = tmem + kColNum + 128u * b;
 #pragma unroll
           for (int c = 0; c < kPer; ++c) {
-            const int64_t k = k0 + c;
+            const int64_t k = k0 + c - t.c0;  // chunk index within the item
             const uint32_t a0 = st0 + c * kGrmChunkBytes;
             const uint32_t b0 = same ? a0 : a0 + kBlockBytes;
             const uint64_t ah = umma_desc(a0), al = umma_desc(a0 + kTileBytes), av = umma_desc(a0 + 2 * kTileBytes);
             const uint64_t bh = umma_desc(b0), bl = umma_desc(b0 + kTileBytes), bv = umma_desc(b0 + 2 * kTileBytes);
-            umma_f16(num, ah, bh, k % kGrmSeg != 0 ? 1u : 0u);  // hi hi^T
+            umma_f16(num, ah, bh, k % kGrmSeg != 0 ? 1u : 0u);  // hi hi^T (restarts every segment)
             umma_f16(num, ah, bl, 1u);                          // + hi lo^T
             umma_f16(num, al, bh, 1u);                          // + lo hi^T
             umma_f16(tmem + kColCnt, av, bv, k > 0 ? 1u : 0u);  // pair counts
@@ -419,6 +434,8 @@ __global__ void __launch_bounds__(kGrmThreads, 1) tc_grm_kernel(const GrmArgs ar
         break;
       }
       if (it < 0) break;
+      const GrmItem t = args.items[it];
+      const int64_t nseg = (t.c1 - t.c0 + kGrmSeg - 1) / kGrmSeg;
       float lo[64];
       for (int64_t sg = 0; sg < nseg; ++sg, ++gs) {
         const uint32_t b = gs & 1u;
@@ -457,11 +474,10 @@ __global__ void __launch_bounds__(kGrmThreads, 1) tc_grm_kernel(const GrmArgs ar
         fail(true);
         break;
       }
-      // the tile's last segment is folded: read the counts, hand the count
-      // accumulator back, divide and store
-      const int2 t = args.tiles[it];
-      const int64_t gi = (int64_t)t.x * kTB + row;
-      const int64_t j0 = (int64_t)t.y * kTB + 64 * half;
+      // the item's last segment is folded: read the counts, hand the count
+      // accumulator back, then divide and store (a split item stores its sums)
+      const int64_t gi = (int64_t)t.I * kTB + row;
+      const int64_t j0 = (int64_t)t.J * kTB + 64 * half;
 #pragma unroll
       for (int h = 0; h < 4; ++h) {
         uint32_t vc[16], vh[16];
@@ -469,7 +485,14 @@ __global__ void __launch_bounds__(kGrmThreads, 1) tc_grm_kernel(const GrmArgs ar
         tmem_ld16(tl + kColHi + 16 * h, vh);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (h == 3) arrive(&cnt_free);
-        if (gi < args.n) {
+        if (t.part >= 0) {
+          const size_t base = (size_t)t.part * kTB * kTB + (size_t)row * kTB + 64 * half + 16 * h;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            args.part_num[base + j] = (double)__uint_as_float(vh[j]) + (double)lo[16 * h + j];
+            args.part_cnt[base + j] = __uint_as_float(vc[j]);
+          }
+        } else if (gi < args.n) {
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int64_t gj = j0 + 16 * h + j;
@@ -490,21 +513,27 @@ __global__ void __launch_bounds__(kGrmThreads, 1) tc_grm_kernel(const GrmArgs ar
   }
 }
 
-}  // namespace
-
-// Chunks per sample block: ceil(m / 16), padded to a multiple of kGrmPad with
-// zero chunks (no contribution to either product).
-static int64_t grm_chunks(int64_t m) { return ((m + kGrmK - 1) / kGrmK + kGrmPad - 1) / kGrmPad * kGrmPad; }
-
-size_t grm_planes_bytes(int64_t n, int64_t m) {
-  const int64_t nb = (n + kTB - 1) / kTB;
-  return (size_t)nb * grm_chunks(m) * kGrmChunkBytes + (size_t)m * 16;
+// Split items: the pieces of a tile, added in piece order (deterministic),
+// divided by the count and stored.  One CTA per split tile.
+__global__ void __launch_bounds__(256) grm_finalize_kernel(const int4* __restrict__ splits, const double* part_num,
+                                                           const float* part_cnt, int64_t n, double* __restrict__ out) {
+  const int4 sp = splits[blockIdx.x];  // {I, J, first part, pieces}
+  for (int e = threadIdx.x; e < kTB * kTB; e += blockDim.x) {
+    const int64_t gi = (int64_t)sp.x * kTB + e / kTB, gj = (int64_t)sp.y * kTB + e % kTB;
+    if (gi >= n || gj >= n || gj < gi) continue;
+    double num = 0.0;
+    float cnt = 0.0f;
+    for (int p = 0; p < sp.w; ++p) {
+      const size_t q = (size_t)(sp.z + p) * kTB * kTB + e;
+      num += part_num[q];
+      cnt += part_cnt[q];  // integers below 2^24: exact
+    }
+    out[tri_index(gi, gj, n)] = cnt == 0.0f ? __longlong_as_double(0x7ff8000000000000LL) : div_count(num, cnt);
+  }
 }
 
-void grm_tiles(int64_t n, std::vector<int2>& out) { tc_tile_order((n + kTB - 1) / kTB, 16, out); }
-
 template <int kPer, int kStages>
-static cudaError_t launch_grm_pairs(const GrmArgs& args, int grid, cudaStream_t st) {
+cudaError_t launch_grm_pairs(const GrmArgs& args, int grid, cudaStream_t st) {
   constexpr size_t smem = (size_t)kStages * 2 * kPer * kGrmChunkBytes + 1024;
   cudaError_t e = cudaFuncSetAttribute(tc_grm_kernel<kPer, kStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
@@ -513,23 +542,84 @@ static cudaError_t launch_grm_pairs(const GrmArgs& args, int grid, cudaStream_t 
   return cudaGetLastError();
 }
 
-cudaError_t launch_grm(const uint8_t* packed, int64_t n, int64_t m, double* out, uint8_t* work, const int2* tiles,
-                       int64_t n_tiles, int* counter, int* status, int num_sms, cudaStream_t st) {
+// Chunks per sample block: ceil(m / 16), padded to a multiple of kGrmPad with
+// zero chunks (no contribution to either product).
+int64_t grm_chunks(int64_t m) { return ((m + kGrmK - 1) / kGrmK + kGrmPad - 1) / kGrmPad * kGrmPad; }
+
+}  // namespace
+
+size_t grm_planes_bytes(int64_t n, int64_t m) {
+  const int64_t nb = (n + kTB - 1) / kTB;
+  return (size_t)nb * grm_chunks(m) * kGrmChunkBytes + (size_t)m * 16;
+}
+
+
+// Work list: the triangle's tiles in the grouped order, whole, except the
+// tiles of a final wave at most 3/4 full (or every tile, when there are fewer
+// tiles than SMs), which are split over the marker axis into pieces of whole
+// 128-marker segments; each piece's sums go to a part slot of their own.
+void grm_items(int64_t n, int64_t m, int num_sms, std::vector<GrmItem>& items, std::vector<int4>& splits,
+               int64_t& parts) {
+  std::vector<int2> order;
+  tc_tile_order((n + kTB - 1) / kTB, 16, order);
+  const int64_t W = (int64_t)order.size(), nc = grm_chunks(m), nsegs = (nc + kGrmSeg - 1) / kGrmSeg;
+  int64_t whole = W, pieces = 1;
+  if (W < num_sms) {
+    whole = 0;
+    pieces = (num_sms + W - 1) / W;
+  } else {
+    const int64_t R = W % num_sms;
+    if (R > 0 && R * 4 <= (int64_t)num_sms * 3) {
+      whole = W - R;
+      pieces = std::max<int64_t>(2, (num_sms + R / 2) / R);
+    }
+  }
+  pieces = std::max<int64_t>(1, std::min<int64_t>(pieces, std::min<int64_t>(nsegs, 16)));
+  items.clear();
+  splits.clear();
+  parts = 0;
+  for (int64_t t = 0; t < W; ++t) {
+    const int np = t < whole ? 1 : (int)pieces;
+    if (np > 1) splits.push_back(make_int4(order[t].x, order[t].y, (int)parts, np));
+    for (int p = 0; p < np; ++p) {
+      GrmItem w{};
+      w.I = order[t].x;
+      w.J = order[t].y;
+      w.c0 = (int32_t)(nsegs * p / np * kGrmSeg);
+      w.c1 = p + 1 == np ? (int32_t)nc : (int32_t)(nsegs * (p + 1) / np * kGrmSeg);
+      w.part = np > 1 ? (int32_t)(parts + p) : -1;
+      items.push_back(w);
+    }
+    if (np > 1) parts += np;
+  }
+}
+
+cudaError_t launch_grm(const uint8_t* packed, int64_t n, int64_t m, double* out, uint8_t* work, const GrmItem* items,
+                       int64_t n_items, const int4* splits, int64_t n_splits, double* part_num, float* part_cnt,
+                       int* counter, int* status, int num_sms, cudaStream_t st) {
   const int64_t nb = (n + kTB - 1) / kTB, nc = grm_chunks(m);
-  if (nc > 2147483647LL || nb > 65535 || n_tiles < 1 || n_tiles > 2147483647LL - num_sms)
+  if (nc > 2147483647LL || nb > 65535 || n_items < 1 || n_items > 2147483647LL - num_sms ||
+      n_splits > 2147483647LL)
     return cudaErrorInvalidValue;
   uint8_t* planes = work;
   uint16_t* table = reinterpret_cast<uint16_t*>(planes + (size_t)nb * nc * kGrmChunkBytes);
   const int64_t row_bytes = (n + 3) / 4;
-  grm_freq_kernel<<<num_sms * 4, 256, 0, st>>>(packed, row_bytes, n, m, table);
+  const int64_t freq_warps = (m + 31) / 32;
+  grm_freq_kernel<<<(unsigned)std::min<int64_t>((freq_warps + 7) / 8, (int64_t)num_sms * 8), 256, 0, st>>>(
+      packed, row_bytes, n, m, table);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   grm_planes_kernel<<<dim3((unsigned)nc, (unsigned)nb), 128, 0, st>>>(packed, row_bytes, n, m, table, planes, nc);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(counter, 0, sizeof(int), st)) != cudaSuccess) return e;
-  const GrmArgs args{planes, n, nc, tiles, n_tiles, out, counter, status};
-  const int grid = (int)std::min<int64_t>(num_sms, n_tiles);
-  return launch_grm_pairs<4, 2>(args, grid, st);
+  const GrmArgs args{planes, n, nc, items, n_items, out, part_num, part_cnt, counter, status};
+  const int grid = (int)std::min<int64_t>(num_sms, n_items);
+  if ((e = launch_grm_pairs<4, 2>(args, grid, st)) != cudaSuccess) return e;
+  if (n_splits > 0) {
+    grm_finalize_kernel<<<(unsigned)n_splits, 256, 0, st>>>(splits, part_num, part_cnt, n, out);
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 }  // namespace ibs

@@ -176,12 +176,22 @@ cudaError_t launch_ld(const uint8_t* packed, int64_t n, int64_t m, int64_t windo
 
 // Genomic relationship matrix (ibs_grm.cu): per-marker frequency table and
 // FP16 hi/lo/V' operand planes (128-sample blocks, 16-marker chunks) in one
-// workspace of grm_planes_bytes(n, m), the grouped triangle tile order, and
-// the launch sequence (frequencies, operand builder, persistent kernel).
+// workspace of grm_planes_bytes(n, m); the work list (grouped triangle tile
+// order, the tiles of a final partial wave split over the marker axis into
+// parts whose sums a finalisation pass adds); the launch sequence
+// (frequencies, operand builder, persistent kernel, finalisation).
+struct GrmItem {
+  int32_t I, J;    // tile: row block, column block (I <= J)
+  int32_t c0, c1;  // chunk range (c0 a multiple of the 128-marker segment)
+  int32_t part;    // part slot of a split tile's piece, -1 for a whole tile
+  int32_t pad[3];
+};
 size_t grm_planes_bytes(int64_t n, int64_t m);
-void grm_tiles(int64_t n, std::vector<int2>& out);
-cudaError_t launch_grm(const uint8_t* packed, int64_t n, int64_t m, double* out, uint8_t* work, const int2* tiles,
-                       int64_t n_tiles, int* counter, int* status, int num_sms, cudaStream_t st);
+void grm_items(int64_t n, int64_t m, int num_sms, std::vector<GrmItem>& items, std::vector<int4>& splits,
+               int64_t& parts);
+cudaError_t launch_grm(const uint8_t* packed, int64_t n, int64_t m, double* out, uint8_t* work, const GrmItem* items,
+                       int64_t n_items, const int4* splits, int64_t n_splits, double* part_num, float* part_cnt,
+                       int* counter, int* status, int num_sms, cudaStream_t st);
 
 // Complete-linkage clustering (ibs_cluster.cu) of n samples under a distance
 // triangle (ibs_compute's layout), into Z [n-1][4] on the device; `work` holds
