@@ -24,8 +24,8 @@
 // E2M1 values.  Every value is 0 or +-1 and every partial sum an integer of
 // magnitude at most the sample count (kept below 2^24), so FP32 accumulation
 // is exact.  The numerator and variance terms are formed in int64.  Only the
-// reciprocal square root and the product are rounded: an FP32 seed refined by
-// two Newton-Raphson steps in FP64.
+// reciprocal square root and the products are rounded, in float-float
+// arithmetic on the FP32 pipe (see ld_r_value).
 //
 // One persistent CTA per SM, 8 warps: the copy warp claims (A block, B
 // half-block) items of the band |b - a| <= window from a counter and streams
@@ -106,20 +106,56 @@ __global__ void __launch_bounds__(256) ld_planes_kernel(const uint8_t* __restric
 }
 
 // r from the six exact sums, oriented by the two markers' signs; NaN when N = 0
-// or a variance term is 0.  1/sqrt(va vb) is seeded in FP32 and refined by two
-// Newton-Raphson steps y <- y (3 - P y^2) / 2 in FP64, which leaves about 2^-52
-// relative error from a 2^-22 seed.
+// or a variance term is 0.  The numerator and the variance terms are exact
+// int64 values below 2^48 (N < 2^24); they are split exactly into float-float
+// pairs, and r = num / sqrt(va vb) is formed in float-float arithmetic on the
+// FP32 pipe (GB300 runs FP32 at 64x its FP64 rate): the product va vb, an
+// rsqrtf seed (relative error near 2^-22) refined by one Newton step whose
+// residual 1 - P y^2 is taken in float-float, and the product with the
+// numerator.  Error: about 1.5 * 2^-44 from the Newton step plus a few 2^-46
+// from the float-float operations, well under 1e-12 relative.
+struct FF {
+  float hi, lo;
+};
+
+// Error-free sum (Knuth): s + e == a + b.
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+
+// x (|x| < 2^48) as an exact float-float: x = h 2^24 + l with 0 <= l < 2^24.
+__device__ __forceinline__ FF ff_from_i48(long long x) {
+  const long long h = x >> 24;  // floor: |h| < 2^24
+  const int l = (int)(x - (h << 24));
+  return ff_two_sum(__fmul_rn((float)(int)h, 16777216.0f), (float)l);
+}
+
+// a * b in float-float (products exact by FMA, cross terms added once).
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const float s = __fadd_rn(p, e);
+  return {s, __fsub_rn(e, __fsub_rn(s, p))};
+}
+
 __device__ __forceinline__ double ld_r_value(int32_t N, int32_t sx, int32_t sy, int32_t sxx, int32_t syy,
                                              int32_t sxy, int sign) {
   const long long n = N;
   const long long va = n * sxx - (long long)sx * sx, vb = n * syy - (long long)sy * sy;
   if (N == 0 || va == 0 || vb == 0) return __longlong_as_double(0x7ff8000000000000LL);
   const long long num = n * sxy - (long long)sx * sy;
-  const double P = (double)va * (double)vb;
-  double y = (double)rsqrtf((float)P);
-  y = y * fma(-0.5 * P, y * y, 1.5);
-  y = y * fma(-0.5 * P, y * y, 1.5);
-  return (double)(sign * num) * y;
+  const FF P = ff_mul(ff_from_i48(va), ff_from_i48(vb));
+  const float y0 = rsqrtf(P.hi);
+  const float q = __fmul_rn(y0, y0);
+  const FF w = ff_mul(P, FF{q, __fmaf_rn(y0, y0, -q)});  // P y0^2, near 1
+  const float t = __fsub_rn(__fsub_rn(1.0f, w.hi), w.lo);  // 1 - P y0^2 (the first difference is exact)
+  const FF y = ff_two_sum(y0, __fmul_rn(__fmul_rn(y0, t), 0.5f));  // one Newton step
+  const FF r = ff_mul(ff_from_i48(sign * num), y);
+  return (double)r.hi + (double)r.lo;
 }
 
 struct LdArgs {
