@@ -8,7 +8,8 @@ transpose + triangular pair-count kernel with the fused epilogue) over inputs
 already resident in HBM; L2 is flushed (256 MiB write) between steps outside
 the timed events.  `e2e` repeats the step through the same C ABI with the
 packed input in pinned host memory and the counts and distances copied back
-each step.  `roofline` compares the pair-count kernel, timed with CUDA events
+each step, pipelined over a copy-in, a compute and a copy-out stream (the
+one-stream figure is reported beside it).  `roofline` compares the pair-count kernel, timed with CUDA events
 on its own stream inside the library, with the integer-pipe ceiling derived
 from a live microbenchmark of POPC / LOP3 / IADD3 throughput.  `cpu_baseline`
 times the CPU oracle on a bounded row sample of the same workload.
@@ -283,29 +284,69 @@ def run_plain(args, rank, world, local):
 
         # end to end through the same API: pinned host input, results copied back
         h_packed = torch.from_numpy(w.packed).pin_memory()
-        h_counts = torch.empty((P, 4), dtype=torch.int32).pin_memory()
-        h_dist = torch.empty(P, dtype=torch.float64).pin_memory()
-        d_in = torch.empty_like(packed)
+        h_counts = [torch.empty((P, 4), dtype=torch.int32).pin_memory() for _ in range(2)]
+        h_dist = [torch.empty(P, dtype=torch.float64).pin_memory() for _ in range(2)]
+        d_in = [torch.empty_like(packed) for _ in range(2)]
+        d_counts = [counts, torch.empty_like(counts)]
+        d_dist = [dist_t, torch.empty_like(dist_t)]
         for _ in range(2):
-            d_in.copy_(h_packed, non_blocking=True)
-            ibs.ibs_compute(ctx, d_in, n, m, counts, dist_t, stream)
-            h_counts.copy_(counts, non_blocking=True)
-            h_dist.copy_(dist_t, non_blocking=True)
+            d_in[0].copy_(h_packed, non_blocking=True)
+            ibs.ibs_compute(ctx, d_in[0], n, m, d_counts[0], d_dist[0], stream)
+            h_counts[0].copy_(d_counts[0], non_blocking=True)
+            h_dist[0].copy_(d_dist[0], non_blocking=True)
         torch.cuda.synchronize(dev)
+        # (a) one step after another on one stream: copy in, compute, copy out
         e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                   for _ in range(args.steps)]
         for i in range(args.steps):
             flush.zero_()
             e2e_ev[i][0].record(stream)
-            d_in.copy_(h_packed, non_blocking=True)
-            ibs.ibs_compute(ctx, d_in, n, m, counts, dist_t, stream)
-            h_counts.copy_(counts, non_blocking=True)
-            h_dist.copy_(dist_t, non_blocking=True)
+            d_in[0].copy_(h_packed, non_blocking=True)
+            ibs.ibs_compute(ctx, d_in[0], n, m, d_counts[0], d_dist[0], stream)
+            h_counts[0].copy_(d_counts[0], non_blocking=True)
+            h_dist[0].copy_(d_dist[0], non_blocking=True)
             e2e_ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_serial_ms = [a.elapsed_time(b) for a, b in e2e_ev]
+        # (b) pipelined: every step still copies its input in from pinned host
+        # memory and its counts and distances back, but on a copy-in and a
+        # copy-out stream of their own, with two buffer sets, so that step i+1's
+        # input and step i-1's results move while step i computes (the copy
+        # engines run both directions at once).  The compute calls stay on one
+        # stream, in order; the L2 flush runs before each of them, inside the
+        # timed region.
+        s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        in_ready = [torch.cuda.Event() for _ in range(args.steps)]
+        comp_done = [torch.cuda.Event() for _ in range(args.steps)]
+        out_done = [torch.cuda.Event() for _ in range(args.steps)]
+        t0_ev, t1_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0_ev.record(s_in)
+        stream.wait_event(t0_ev)
+        for i in range(args.steps):
+            b = i % 2
+            if i >= 2:
+                s_in.wait_event(comp_done[i - 2])  # compute i-2 has read d_in[b]
+            with torch.cuda.stream(s_in):
+                d_in[b].copy_(h_packed, non_blocking=True)
+            in_ready[i].record(s_in)
+            stream.wait_event(in_ready[i])
+            if i >= 2:
+                stream.wait_event(out_done[i - 2])  # results i-2 have left d_counts[b]
+            flush.zero_()
+            ibs.ibs_compute(ctx, d_in[b], n, m, d_counts[b], d_dist[b], stream)
+            comp_done[i].record(stream)
+            s_out.wait_event(comp_done[i])
+            with torch.cuda.stream(s_out):
+                h_counts[b].copy_(d_counts[b], non_blocking=True)
+                h_dist[b].copy_(d_dist[b], non_blocking=True)
+            out_done[i].record(s_out)
+        t1_ev.record(s_out)
         torch.cuda.synchronize(dev)
         ibs.ibs_synchronize(ctx, stream)
         ibs.ibs_kernel_times(ctx)
-        e2e_ms = [a.elapsed_time(b) for a, b in e2e_ev]
+        e2e_ms = [t0_ev.elapsed_time(t1_ev) / args.steps] * args.steps
+        counts.copy_(d_counts[(args.steps - 1) % 2])
+        dist_t.copy_(d_dist[(args.steps - 1) % 2])
 
         # The integer-pipe kernel (bit planes, carry-save LOP3/POPC) on the same
         # input, timed the same way: its fraction of the integer-pipe roofline.
@@ -407,7 +448,9 @@ def run_plain(args, rank, world, local):
                       "achieved_gbs": transpose_bytes / (planes_ms * 1e-3) / 1e9,
                       "peak_gbs": hbm_peak_gbs(), "frac": transpose_bytes / (planes_ms * 1e-3) / 1e9 / hbm_peak_gbs()},
         "e2e": {"value": world * comps / (e2e_total / args.steps * 1e-3), "unit": UNIT,
-                "h2d_bytes_per_step": int(w.packed.nbytes), "d2h_bytes_per_step": int(P * 16 + P * 8)},
+                "h2d_bytes_per_step": int(w.packed.nbytes), "d2h_bytes_per_step": int(P * 16 + P * 8),
+                "pipelined": "copy-in, compute and copy-out streams, two buffer sets",
+                "serial_value": world * comps / (reduce_max(sum(e2e_serial_ms), world) / args.steps * 1e-3)},
         "gpu_launches": int(launches_per_step * args.steps),
         "clocks": clocks,
         "wall_s_timed_region": wall,
