@@ -844,7 +844,7 @@ def run_ld(args, rank, world, local):
         dt = time.perf_counter() - t
         sample_pairs = sum(min(W, Gs.shape[1] - 1 - a) for a in range(Gs.shape[1]))
         line["cpu_baseline"] = {"value": sample_pairs * n / dt, "unit": "comparisons/s", "cores": os.cpu_count(),
-                                "kind": "oracle", "sample": f"markers 0..{199 + W} (all their pairs within the "
+                                "kind": "oracle", "sample": f"markers 0..{Gs.shape[1] - 1} (all their pairs within the "
                                                             f"window) x {n} samples ({dt:.1f} s)"}
     return line
 

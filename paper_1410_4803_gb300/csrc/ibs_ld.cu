@@ -27,13 +27,16 @@
 // reciprocal square root and the products are rounded, in float-float
 // arithmetic on the FP32 pipe (see ld_r_value).
 //
-// One persistent CTA per SM, 8 warps: the copy warp claims (A block, B
+// One persistent CTA per SM, 12 warps: the copy warp claims (A block, B
 // half-block) items of the band |b - a| <= window from a counter and streams
-// each item's sample chunks (A: 3 planes x 4 KiB, B: 3 planes x 2 KiB) through
-// a ring; the MMA warp issues 6 MMAs (M = 128, N = 64, K = 64) per chunk into
-// six FP32 accumulators (tensor-memory columns 0, 64, ..., 320; unit scale
-// factors at 384..511); warps 4..7 read the accumulators back and store r.
-// Every wait is bounded (2 s of %globaltimer), as in the IBS kernels.
+// each item's sample chunks through a ring of 3 stages x 4 chunks (one copy of
+// the A block's 3 planes x 4 KiB per chunk, one of the B half-block's 3 planes
+// x 2 KiB per chunk, from a second copy of the planes laid out for it); the
+// MMA warp issues 6 MMAs (M = 128, N = 64, K = 64) per chunk into six FP32
+// accumulators (tensor-memory columns 0, 64, ..., 320; unit scale factors at
+// 384..511); warps 4..11 read the accumulators back (two warps per lane
+// quarter, 32 columns each) and store r.  Every wait is bounded (2 s of
+// %globaltimer), as in the IBS kernels.
 #include <algorithm>
 #include <vector>
 
@@ -46,11 +49,19 @@ namespace {
 constexpr int kLdPlanes = 3;                         // X, V, H
 constexpr int kLdChunkBytes = kLdPlanes * kTileBytes;  // 12 KiB per (marker block, sample chunk)
 constexpr int kLdHalfBytes = kTileBytes / 2;         // 64 rows of a plane tile
-constexpr int kLdStageBytes = kLdChunkBytes + kLdPlanes * kLdHalfBytes;  // A 12 KiB + B 6 KiB
-constexpr int kLdStages = 6;
+constexpr int kLdHalfChunkBytes = kLdPlanes * kLdHalfBytes;  // 6 KiB per (half-block, sample chunk)
+// A ring stage holds kLdPer chunks of the A block and of the B half-block, one
+// bulk copy each (the copy engine spends a fixed time per copy).
+constexpr int kLdPer = 4;
+constexpr int kLdStageBytes = kLdPer * (kLdChunkBytes + kLdHalfChunkBytes);  // 72 KiB
+constexpr int kLdStages = 3;
 constexpr size_t kLdSmem = (size_t)kLdStages * kLdStageBytes + 1024;
 constexpr int kLdN = 64;                             // B rows (markers) per item
 constexpr int kLdQueue = 8;
+// warps 0 (copies), 1 (MMAs), 2-3 idle, 4..11 epilogue: two warps per TMEM lane
+// quarter, each reading 32 of the item's 64 accumulator columns
+constexpr int kLdEpiWarps = 8;
+constexpr int kLdThreads = (4 + kLdEpiWarps) * 32;
 
 // Even bits of a 64-bit word packed into 32 bits (bit 2i -> bit i).
 __device__ __forceinline__ uint32_t even_bits(uint64_t x) {
@@ -65,11 +76,15 @@ __device__ __forceinline__ uint32_t even_bits(uint64_t x) {
 
 // Operand rows: CTA = (sample chunk c, marker block b), thread (row r, half):
 // marker b*128 + r, samples c*64 + 32*half .. +31 (8 bytes of the .bed row).
-// Writes 16 bytes of each of X, V, H (E2M1: +1 = 0x2, -1 = 0xA) and adds the
-// marker's #hom A1 - #hom A2 over these samples to diff.
+// Writes 16 bytes of each of X, V, H (E2M1: +1 = 0x2, -1 = 0xA) twice: into
+// the A layout [block][chunk][plane][128 rows] and into the B layout
+// [half-block][chunk][plane][64 rows], so that an item's B operand for a run
+// of chunks is one contiguous copy; adds the marker's #hom A1 - #hom A2 over
+// these samples to diff.
 __global__ void __launch_bounds__(256) ld_planes_kernel(const uint8_t* __restrict__ packed, int64_t row_bytes,
                                                         int64_t n, int64_t m, uint8_t* __restrict__ planes,
-                                                        int64_t n_chunks, int32_t* __restrict__ diff) {
+                                                        uint8_t* __restrict__ planes_b, int64_t n_chunks,
+                                                        int32_t* __restrict__ diff) {
   const int64_t c = blockIdx.x, b = blockIdx.y;
   const int r = threadIdx.x >> 1, half = threadIdx.x & 1;
   const int64_t k = b * kTB + r;
@@ -103,6 +118,10 @@ __global__ void __launch_bounds__(256) ld_planes_kernel(const uint8_t* __restric
   *reinterpret_cast<uint4*>(base + 0 * kTileBytes) = make_uint4(wx[0], wx[1], wx[2], wx[3]);
   *reinterpret_cast<uint4*>(base + 1 * kTileBytes) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
   *reinterpret_cast<uint4*>(base + 2 * kTileBytes) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+  uint8_t* bb = planes_b + (size_t)((b * 2 + (r >> 6)) * n_chunks + c) * kLdHalfChunkBytes + tile_off(r & 63, 16 * half);
+  *reinterpret_cast<uint4*>(bb + 0 * kLdHalfBytes) = make_uint4(wx[0], wx[1], wx[2], wx[3]);
+  *reinterpret_cast<uint4*>(bb + 1 * kLdHalfBytes) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+  *reinterpret_cast<uint4*>(bb + 2 * kLdHalfBytes) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
 }
 
 // r from the six exact sums, oriented by the two markers' signs; NaN when N = 0
@@ -159,7 +178,8 @@ __device__ __forceinline__ double ld_r_value(int32_t N, int32_t sx, int32_t sy, 
 }
 
 struct LdArgs {
-  const uint8_t* planes;
+  const uint8_t* planes;    // A layout
+  const uint8_t* planes_b;  // B layout
   int64_t n_chunks, m, window;
   const int2* items;  // (A marker block, B half-block)
   int64_t n_items;
@@ -170,7 +190,7 @@ struct LdArgs {
   int* status;
 };
 
-__global__ void __launch_bounds__(256, 1) tc_ld_kernel(const LdArgs args) {
+__global__ void __launch_bounds__(kLdThreads, 1) tc_ld_kernel(const LdArgs args) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* ring = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ __align__(8) uint64_t full[kLdStages], empty[kLdStages], tfull, tempty, drain;
@@ -187,10 +207,10 @@ __global__ void __launch_bounds__(256, 1) tc_ld_kernel(const LdArgs args) {
     }
     for (int s = 0; s < kLdQueue; ++s) {
       mbar_init(&qfull[s], 1);
-      mbar_init(&qempty[s], 5);  // the MMA warp and the four epilogue warps
+      mbar_init(&qempty[s], 1 + kLdEpiWarps);  // the MMA warp and the epilogue warps
     }
     mbar_init(&tfull, 1);
-    mbar_init(&tempty, 4);
+    mbar_init(&tempty, kLdEpiWarps);
     mbar_init(&drain, 1);
     mbar_fence_init();
     abort_flag = 0;
@@ -205,7 +225,7 @@ __global__ void __launch_bounds__(256, 1) tc_ld_kernel(const LdArgs args) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
-  if (warp >= 4) tmem_fill_unit_scales(tmem, warp - 4);
+  if (warp >= 4 && warp < 8) tmem_fill_unit_scales(tmem, warp - 4);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -250,9 +270,9 @@ __global__ void __launch_bounds__(256, 1) tc_ld_kernel(const LdArgs args) {
       if (last) break;
       const int2 item = args.items[it];
       const uint8_t* ablk = args.planes + (size_t)item.x * nk * kLdChunkBytes;
-      const uint8_t* bblk = args.planes + (size_t)(item.y >> 1) * nk * kLdChunkBytes + (item.y & 1) * kLdHalfBytes;
+      const uint8_t* bblk = args.planes_b + (size_t)item.y * nk * kLdHalfChunkBytes;
       bool stop = false;
-      for (int64_t k = 0; k < nk; ++k, ++g) {
+      for (int64_t k = 0; k < nk; k += kLdPer, ++g) {
         const int s = (int)(g % kLdStages);
         const bool ok = g < (uint32_t)kLdStages || mbar_wait_bounded(&empty[s], ((g / kLdStages) - 1) & 1u);
         if (__any_sync(0xffffffffu, !ok)) {
@@ -267,11 +287,9 @@ __global__ void __launch_bounds__(256, 1) tc_ld_kernel(const LdArgs args) {
         if (lane == 0) {
           uint8_t* dst = ring + (size_t)s * kLdStageBytes;
           mbar_arrive_expect_tx(&full[s], kLdStageBytes);
-          bulk_g2s(dst, ablk + (size_t)k * kLdChunkBytes, kLdChunkBytes, &full[s]);
-#pragma unroll
-          for (int p = 0; p < kLdPlanes; ++p)
-            bulk_g2s(dst + kLdChunkBytes + p * kLdHalfBytes, bblk + (size_t)k * kLdChunkBytes + p * kTileBytes,
-                     kLdHalfBytes, &full[s]);
+          bulk_g2s(dst, ablk + (size_t)k * kLdChunkBytes, kLdPer * kLdChunkBytes, &full[s]);
+          bulk_g2s(dst + kLdPer * kLdChunkBytes, bblk + (size_t)k * kLdHalfChunkBytes, kLdPer * kLdHalfChunkBytes,
+                   &full[s]);
         }
         __syncwarp();
       }
@@ -291,7 +309,7 @@ __global__ void __launch_bounds__(256, 1) tc_ld_kernel(const LdArgs args) {
       bool stop = __any_sync(0xffffffffu, !free_ok);
       if (!stop) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        for (int64_t k = 0; k < nk; ++k, ++g) {
+        for (int64_t k0 = 0; k0 < nk; k0 += kLdPer, ++g) {
           const int s = (int)(g % kLdStages);
           const bool ok = mbar_wait_bounded(&full[s], (g / kLdStages) & 1u);
           if (__any_sync(0xffffffffu, !ok)) {
@@ -300,17 +318,21 @@ __global__ void __launch_bounds__(256, 1) tc_ld_kernel(const LdArgs args) {
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           if (lane == 0) {
-            const uint32_t a0 = smem_addr(ring + (size_t)s * kLdStageBytes), b0 = a0 + kLdChunkBytes;
-            const uint64_t aX = umma_desc(a0), aV = umma_desc(a0 + kTileBytes), aH = umma_desc(a0 + 2 * kTileBytes);
-            const uint64_t bX = umma_desc(b0), bV = umma_desc(b0 + kLdHalfBytes),
-                           bH = umma_desc(b0 + 2 * kLdHalfBytes);
-            const uint32_t acc = k > 0 ? 1u : 0u;
-            umma<kTcFp4, kLdN>(tmem + 0 * kLdN, aV, bV, acc, sf);  // N
-            umma<kTcFp4, kLdN>(tmem + 1 * kLdN, aX, bV, acc, sf);  // Sx
-            umma<kTcFp4, kLdN>(tmem + 2 * kLdN, aV, bX, acc, sf);  // Sy
-            umma<kTcFp4, kLdN>(tmem + 3 * kLdN, aH, bV, acc, sf);  // Sxx
-            umma<kTcFp4, kLdN>(tmem + 4 * kLdN, aV, bH, acc, sf);  // Syy
-            umma<kTcFp4, kLdN>(tmem + 5 * kLdN, aX, bX, acc, sf);  // Sxy
+            const uint32_t st0 = smem_addr(ring + (size_t)s * kLdStageBytes);
+#pragma unroll
+            for (int c = 0; c < kLdPer; ++c) {
+              const uint32_t a0 = st0 + c * kLdChunkBytes, b0 = st0 + kLdPer * kLdChunkBytes + c * kLdHalfChunkBytes;
+              const uint64_t aX = umma_desc(a0), aV = umma_desc(a0 + kTileBytes), aH = umma_desc(a0 + 2 * kTileBytes);
+              const uint64_t bX = umma_desc(b0), bV = umma_desc(b0 + kLdHalfBytes),
+                             bH = umma_desc(b0 + 2 * kLdHalfBytes);
+              const uint32_t acc = k0 + c > 0 ? 1u : 0u;
+              umma<kTcFp4, kLdN>(tmem + 0 * kLdN, aV, bV, acc, sf);  // N
+              umma<kTcFp4, kLdN>(tmem + 1 * kLdN, aX, bV, acc, sf);  // Sx
+              umma<kTcFp4, kLdN>(tmem + 2 * kLdN, aV, bX, acc, sf);  // Sy
+              umma<kTcFp4, kLdN>(tmem + 3 * kLdN, aH, bV, acc, sf);  // Sxx
+              umma<kTcFp4, kLdN>(tmem + 4 * kLdN, aV, bH, acc, sf);  // Syy
+              umma<kTcFp4, kLdN>(tmem + 5 * kLdN, aX, bX, acc, sf);  // Sxy
+            }
             umma_commit(&empty[s]);
           }
           __syncwarp();
@@ -328,7 +350,7 @@ __global__ void __launch_bounds__(256, 1) tc_ld_kernel(const LdArgs args) {
     const bool drained = mbar_wait_bounded(&drain, 0);
     if (lane == 0 && !drained) atomicExch(status, kDevTimeout);
   } else if (warp >= 4) {
-    const int quarter = warp - 4;
+    const int quarter = warp & 3, colhalf = (warp - 4) >> 2;
     const int row = quarter * 32 + lane;
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
     for (uint32_t e = 0;; ++e) {
@@ -348,12 +370,12 @@ __global__ void __launch_bounds__(256, 1) tc_ld_kernel(const LdArgs args) {
       const int64_t a = (int64_t)item.x * kTB + row;
       const int sa = a < args.m ? (args.diff[a] >= 0 ? 1 : -1) : 1;
 #pragma unroll 1
-      for (int cg = 0; cg < kLdN / 16; ++cg) {
+      for (int cg = 2 * colhalf; cg < 2 * colhalf + 2; ++cg) {
         uint32_t v[6][16];
 #pragma unroll
         for (int q = 0; q < 6; ++q) tmem_ld16(lane_base + q * kLdN + cg * 16, v[q]);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (cg == kLdN / 16 - 1) {
+        if (cg == 2 * colhalf + 1) {
           asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
           __syncwarp();
           if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&tempty)) : "memory");
@@ -399,8 +421,11 @@ __global__ void ld_fill_tail_kernel(int64_t m, int64_t window, double* __restric
 
 }  // namespace
 
-size_t ld_planes_bytes(int64_t n, int64_t m) {
-  return (size_t)((m + kTB - 1) / kTB) * (size_t)((n + 63) / 64) * kLdChunkBytes;
+// Sample chunks: ceil(n / 64), padded to a multiple of kLdPer with zero chunks.
+static int64_t ld_chunks(int64_t n) { return ((n + 63) / 64 + kLdPer - 1) / kLdPer * kLdPer; }
+
+size_t ld_planes_bytes(int64_t n, int64_t m) {  // A layout, then B layout
+  return (size_t)((m + kTB - 1) / kTB) * (size_t)ld_chunks(n) * (kLdChunkBytes + 2 * kLdHalfChunkBytes);
 }
 
 // Items of the band: (A block I of 128 markers, B half-block j of 64 markers)
@@ -419,19 +444,21 @@ void ld_items(int64_t m, int64_t window, std::vector<int2>& items) {
 cudaError_t launch_ld(const uint8_t* packed, int64_t n, int64_t m, int64_t window, uint8_t* planes, int32_t* diff,
                       const int2* items, int64_t n_items, int* counter, double* out_r, int32_t* out_n,
                       int* status, int num_sms, cudaStream_t st) {
-  const int64_t nc = (n + 63) / 64, nb = (m + kTB - 1) / kTB;
+  const int64_t nc = ld_chunks(n), nb = (m + kTB - 1) / kTB;
   if (nc > 2147483647LL || nb > 65535 || n_items > 2147483647LL - num_sms) return cudaErrorInvalidValue;
+  uint8_t* planes_b = planes + (size_t)nb * nc * kLdChunkBytes;
   cudaError_t e = cudaMemsetAsync(diff, 0, (size_t)m * sizeof(int32_t), st);
   if (e != cudaSuccess) return e;
-  ld_planes_kernel<<<dim3((unsigned)nc, (unsigned)nb), 256, 0, st>>>(packed, (n + 3) / 4, n, m, planes, nc, diff);
+  ld_planes_kernel<<<dim3((unsigned)nc, (unsigned)nb), 256, 0, st>>>(packed, (n + 3) / 4, n, m, planes, planes_b, nc,
+                                                                      diff);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(counter, 0, sizeof(int), st)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(tc_ld_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLdSmem)) !=
       cudaSuccess)
     return e;
-  LdArgs args{planes, nc, m, window, items, n_items, diff, out_r, out_n, counter, status};
+  LdArgs args{planes, planes_b, nc, m, window, items, n_items, diff, out_r, out_n, counter, status};
   if (n_items > 0) {
-    tc_ld_kernel<<<(int)std::min<int64_t>(num_sms, n_items), 256, kLdSmem, st>>>(args);
+    tc_ld_kernel<<<(int)std::min<int64_t>(num_sms, n_items), kLdThreads, kLdSmem, st>>>(args);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   ld_fill_tail_kernel<<<64, 256, 0, st>>>(m, window, out_r, out_n);
