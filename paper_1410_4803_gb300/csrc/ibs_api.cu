@@ -626,6 +626,10 @@ ibs_status plan_build(ibs_ctx* ctx, BatchPlan& plan, const std::vector<SubsetSha
     }
     if (ibs_status s = ensure_buf(ctx, plan.tc_planes, tb)) return s;
     if (ibs_status s = ensure_buf(ctx, plan.tc_jobs, sizeof(TcGatherJob) * shapes.size())) return s;
+    if (ibs_status s = ensure_buf(ctx, plan.gather_map, sizeof(int4) * std::max<int64_t>(1, plan.tc_ctas))) return s;
+    plan.stage_map_off.assign(1, 0);
+    for (int64_t c : plan.stage_ctas) plan.stage_map_off.push_back(plan.stage_map_off.back() + c);
+    plan.map_key.clear();
     pb = 0;
   }
   if (ibs_status s = ensure_buf(ctx, plan.planes, pb)) return s;
@@ -708,6 +712,42 @@ ibs_status plan_upload(ibs_ctx* ctx, BatchPlan& plan, const uint8_t* pool, int64
       tcta += tc_gather_ctas(shapes[i].n, ig.nc);
     }
     IBS_CUDA_TRY(cudaMemcpyAsync(plan.tc_jobs.p, tj.data(), sizeof(TcGatherJob) * k, cudaMemcpyHostToDevice, st));
+    // Gather CTA order within each stage: by the pool variant a CTA starts at
+    // (a counting sort over chunk-group-sized buckets), then job, block.
+    std::vector<int64_t> key(k);
+    for (size_t i = 0; i < k; ++i) key[i] = subs[i].var_begin;
+    if (plan.map_key != key) {
+      const int64_t span = (int64_t)tc_gather_chunks() * (tc_fmt_of(plan.mode) == kTcFp4 ? 64 : 32);
+      int64_t vend = 0;
+      for (size_t i = 0; i < k; ++i) vend = std::max<int64_t>(vend, subs[i].var_begin + shapes[i].m);
+      const int64_t buckets = (vend + span - 1) / span + 1;
+      std::vector<int4> map((size_t)std::max<int64_t>(1, plan.tc_ctas));
+      std::vector<int64_t> count((size_t)buckets + 1);
+      for (size_t g = 0; g + 1 < plan.stage_job_off.size(); ++g) {
+        std::fill(count.begin(), count.end(), 0);
+        auto each = [&](auto&& f) {
+          for (int64_t q = plan.stage_job_off[g]; q < plan.stage_job_off[g + 1]; ++q) {
+            const size_t i = (size_t)plan.order[(size_t)q];
+            const ItemGeom ig = item_geom(shapes[i], plan.mode);
+            const int64_t groups = (ig.nc + tc_gather_chunks() - 1) / tc_gather_chunks();
+            for (int64_t cg = 0; cg < groups; ++cg) {
+              const int64_t bucket = (subs[i].var_begin + cg * span) / span;
+              for (int64_t bl = 0; bl < ig.T; ++bl) f(q, bl, cg, bucket);
+            }
+          }
+        };
+        each([&](int64_t, int64_t, int64_t, int64_t bucket) { ++count[(size_t)bucket + 1]; });
+        for (size_t u = 1; u < count.size(); ++u) count[u] += count[u - 1];
+        int4* out = map.data() + plan.stage_map_off[g];
+        each([&](int64_t q, int64_t bl, int64_t cg, int64_t bucket) {
+          out[count[(size_t)bucket]++] = make_int4((int)q, (int)bl, (int)cg, 0);
+        });
+      }
+      // pageable source: the copy is staged before return
+      IBS_CUDA_TRY(cudaMemcpyAsync(plan.gather_map.p, map.data(), sizeof(int4) * (size_t)plan.tc_ctas,
+                                   cudaMemcpyHostToDevice, st));
+      plan.map_key = key;
+    }
   }
   // Pageable sources: the copy is staged before return, so the vectors may go.
   IBS_CUDA_TRY(cudaMemcpyAsync(plan.subsets.p, sd.data(), sizeof(SubsetDev) * k, cudaMemcpyHostToDevice, st));
@@ -725,7 +765,7 @@ ibs_status plan_enqueue(ibs_ctx* ctx, BatchPlan& plan, int n_subsets, cudaStream
     const WorkItem* items = static_cast<const WorkItem*>(plan.items.p);
     const int G = (int)plan.stage_ctas.size();
     auto gather = [&](int g, cudaStream_t s) {
-      return launch_tc_gather(jobs + plan.stage_job_off[g], (int)(plan.stage_job_off[g + 1] - plan.stage_job_off[g]),
+      return launch_tc_gather(jobs, static_cast<const int4*>(plan.gather_map.p) + plan.stage_map_off[g],
                               plan.stage_ctas[g], fmt, ctx->status_dev, s);
     };
     IBS_CUDA_TRY(gather(0, st));
@@ -787,7 +827,7 @@ void plan_free(ibs_ctx* ctx, BatchPlan& plan) {
   plan.exec = nullptr;
   plan.graph = nullptr;
   for (DevBuf* b : {&plan.planes, &plan.partial, &plan.subsets, &plan.jobs, &plan.items, &plan.split_ids,
-                    &plan.counter, &plan.tc_planes, &plan.tc_jobs, &plan.split_tiles})
+                    &plan.counter, &plan.tc_planes, &plan.tc_jobs, &plan.split_tiles, &plan.gather_map})
     free_buf(ctx, *b);
 }
 

@@ -63,6 +63,10 @@ struct BatchPlan {
   // K); q_item_off / q_chunks per position of `order`, split tiles
   // {subset, I, J, -} finalised after the last launch
   std::vector<int64_t> q_item_off, q_chunks;
+  // gather CTA map {job, sample block, chunk group, -} per stage (offsets into
+  // it per stage), ordered by pool variant; rebuilt when the windows change
+  DevBuf gather_map;
+  std::vector<int64_t> stage_map_off, map_key;
   DevBuf split_tiles;
   int64_t n_split_tiles = 0;
   cudaStream_t side = nullptr;

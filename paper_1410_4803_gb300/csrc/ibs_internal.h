@@ -139,8 +139,11 @@ cudaError_t launch_tc_pairs(const uint8_t* planes, int64_t n, int64_t m, int fmt
                             cudaStream_t st);
 void tc_tile_order(int64_t T, int G, std::vector<int2>& out);
 int64_t tc_gather_ctas(int64_t n, int64_t nc);  // CTAs of one job of the gather launch
-cudaError_t launch_tc_gather(const TcGatherJob* jobs_dev, int n_jobs, int64_t total_ctas, int fmt, int* status,
-                             cudaStream_t st);
+// map_dev[c] = {job, sample block, chunk group, -} of gather CTA c; chunk groups
+// hold tc_gather_chunks() chunks.
+cudaError_t launch_tc_gather(const TcGatherJob* jobs_dev, const int4* map_dev, int64_t total_ctas, int fmt,
+                             int* status, cudaStream_t st);
+int tc_gather_chunks();
 // Batched tensor-core pairs: SubsetDev.planes holds operand planes, n_blocks and
 // n_chunks count 128-sample blocks and chunks, and WorkItem tiles and K ranges
 // are in those units.

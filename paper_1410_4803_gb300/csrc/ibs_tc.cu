@@ -347,20 +347,17 @@ __global__ void __launch_bounds__(kTThreads, 1)
 // status word reports it.
 constexpr int kGatherChunks = 8;
 
+// CTA blockIdx.x takes the (job, sample block, chunk group) of map[blockIdx.x]:
+// the host orders a stage's CTAs by the pool variant they start at, so that
+// subsets whose windows overlap read the same pool rows at about the same
+// time and share them through L2.
 template <int F>
-__global__ void __launch_bounds__(kTB) tc_gather_kernel(const TcGatherJob* __restrict__ jobs, int n_jobs, int* status) {
+__global__ void __launch_bounds__(kTB) tc_gather_kernel(const TcGatherJob* __restrict__ jobs,
+                                                        const int4* __restrict__ map, int* status) {
   constexpr int K = kMarkers<F>;
-  const int64_t cta = blockIdx.x;
-  int lo = 0, hi = n_jobs - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (jobs[mid].cta_begin <= cta) lo = mid;
-    else hi = mid - 1;
-  }
-  const TcGatherJob j = jobs[lo];
-  const int64_t groups = (j.nc + kGatherChunks - 1) / kGatherChunks;
-  const int64_t local = cta - j.cta_begin;
-  const int64_t b = local / groups, cg = local % groups;
+  const int4 e = map[blockIdx.x];  // {job, sample block, chunk group, -}
+  const TcGatherJob j = jobs[e.x];
+  const int64_t b = e.y, cg = e.z;
   const int r = threadIdx.x;
   const int64_t s = b * kTB + r;
   int64_t ps = -1;
@@ -978,14 +975,14 @@ int64_t tc_tiles(int64_t n) {
   return nb * (nb + 1) / 2;
 }
 
-cudaError_t launch_tc_gather(const TcGatherJob* jobs_dev, int n_jobs, int64_t total_ctas, int fmt, int* status,
-                             cudaStream_t st) {
+cudaError_t launch_tc_gather(const TcGatherJob* jobs_dev, const int4* map_dev, int64_t total_ctas, int fmt,
+                             int* status, cudaStream_t st) {
   if (total_ctas <= 0) return cudaSuccess;
   if (total_ctas > 2147483647LL) return cudaErrorInvalidValue;
   if (fmt == kTcFp4)
-    tc_gather_kernel<kTcFp4><<<(unsigned)total_ctas, kTB, 0, st>>>(jobs_dev, n_jobs, status);
+    tc_gather_kernel<kTcFp4><<<(unsigned)total_ctas, kTB, 0, st>>>(jobs_dev, map_dev, status);
   else
-    tc_gather_kernel<kTcFp8><<<(unsigned)total_ctas, kTB, 0, st>>>(jobs_dev, n_jobs, status);
+    tc_gather_kernel<kTcFp8><<<(unsigned)total_ctas, kTB, 0, st>>>(jobs_dev, map_dev, status);
   return cudaGetLastError();
 }
 
@@ -1080,6 +1077,8 @@ cudaError_t launch_tc_finalize_batch_tiles(const SubsetDev* subs, const int4* ti
   tc_finalize_batch_tiles_kernel<<<(unsigned)n_tiles, 256, 0, st>>>(subs, tiles);
   return cudaGetLastError();
 }
+
+int tc_gather_chunks() { return kGatherChunks; }
 
 int64_t tc_gather_ctas(int64_t n, int64_t nc) {
   return (n + kTB - 1) / kTB * ((nc + kGatherChunks - 1) / kGatherChunks);
