@@ -40,7 +40,8 @@ constexpr int kMaxQuery = 4096;     // rows per request
 constexpr int kMaxK = 64;           // top-k limit of the kernel
 constexpr int64_t kMaxRows = 4096;  // query rows admitted at once (slot limit)
 constexpr int64_t kStepWaves = 16;  // a step aims at this many waves of (query block, panel block) tiles
-constexpr int64_t kStepWavesTc = 4; // ... of the tensor-core form's 4x larger tiles
+constexpr int64_t kStepWavesTc = 8; // ... of the tensor-core form (a request of one query block then takes
+                                    // one step over a 100,000-sample panel; two steps cost it about 3 ms)
 constexpr int64_t kMinStepDiv = 32; // ... and covers at least 1/32 of the panel
 constexpr size_t kMemMargin = (size_t)1 << 30;
 constexpr int64_t kTcBlock = 128;          // samples per tensor-core block
