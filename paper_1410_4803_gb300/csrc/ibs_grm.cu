@@ -514,11 +514,12 @@ __global__ void __launch_bounds__(kGrmThreads, 1) tc_grm_kernel(const GrmArgs ar
 }
 
 // Split items: the pieces of a tile, added in piece order (deterministic),
-// divided by the count and stored.  One CTA per split tile.
+// divided by the count and stored.  CTA (x, y) takes split tile x, its entries
+// y, y + gridDim.y, ... in units of blockDim.x.
 __global__ void __launch_bounds__(256) grm_finalize_kernel(const int4* __restrict__ splits, const double* part_num,
                                                            const float* part_cnt, int64_t n, double* __restrict__ out) {
   const int4 sp = splits[blockIdx.x];  // {I, J, first part, pieces}
-  for (int e = threadIdx.x; e < kTB * kTB; e += blockDim.x) {
+  for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < kTB * kTB; e += gridDim.y * blockDim.x) {
     const int64_t gi = (int64_t)sp.x * kTB + e / kTB, gj = (int64_t)sp.y * kTB + e % kTB;
     if (gi >= n || gj >= n || gj < gi) continue;
     double num = 0.0;
@@ -616,7 +617,7 @@ cudaError_t launch_grm(const uint8_t* packed, int64_t n, int64_t m, double* out,
   const int grid = (int)std::min<int64_t>(num_sms, n_items);
   if ((e = launch_grm_pairs<4, 2>(args, grid, st)) != cudaSuccess) return e;
   if (n_splits > 0) {
-    grm_finalize_kernel<<<(unsigned)n_splits, 256, 0, st>>>(splits, part_num, part_cnt, n, out);
+    grm_finalize_kernel<<<dim3((unsigned)n_splits, 8), 256, 0, st>>>(splits, part_num, part_cnt, n, out);
     e = cudaGetLastError();
   }
   return e;
