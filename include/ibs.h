@@ -287,7 +287,7 @@ ibs_status ibs_ld_r(ibs_ctx* ctx, const uint8_t* packed, int64_t n_samples, int6
  * + 2^-25 * sum(|z_j| + |z_k|) / N_jk of the exact value, for any number of
  * markers (3 * 2^-22 from the FP16 split, 24 MMA accumulations per segment
  * at 2^-22 each); N_jk is exact.
- * 1 <= n_samples <= 8388480, 1 <= n_variants < 2^24.  Workspace: 12 KiB per
+ * 1 <= n_samples <= 8388480, 1 <= n_variants < 2^24.  Workspace: 10 KiB per
  * (128 samples, 16 markers) of library memory.  Asynchronous on `stream`. */
 ibs_status ibs_grm(ibs_ctx* ctx, const uint8_t* packed, int64_t n_samples, int64_t n_variants, double* out_grm,
                    void* stream);

@@ -26,16 +26,18 @@
 // accumulations plus the FP16 split, independent of m.
 //
 // Layout: samples are the MMA rows (128 per block), markers the K axis (16 per
-// chunk); one (block, chunk) holds three 128 x 32-byte tiles, hi, lo and V',
-// in the canonical K-major layout (12 KiB).  Tensor memory: numerator banks at
+// FP16 chunk); a pair of chunks of one block holds hi and lo of each chunk
+// (128 x 32-byte FP16 tiles) and V' of its 32 markers as one E4M3 tile, in
+// the canonical K-major layout (20 KiB).  Tensor memory: numerator banks at
 // columns 0 and 128, the count at 256, the float-float high words at 384.
 // One persistent CTA per SM, 10 warps: warp 8 claims triangle tiles in the
 // grouped order and streams both blocks' chunks through a ring of two stages
-// of four chunks (one 48 KiB bulk copy per block and stage: the copy engine
+// of four chunks (one 40 KiB bulk copy per block and stage: the copy engine
 // spends a fixed time per copy, measured near 340 cycles, so one chunk per
-// stage ran 1.6x slower); warp 9 issues 4 MMAs per chunk; warps 0..7 fold
-// segments (warp w: TMEM lanes of quarter w % 4, columns 64 (w / 4) .. +63) and
-// store A.  Every wait is bounded (2 s of %globaltimer).
+// stage ran 1.6x slower); warp 9 issues 3 kind::f16 MMAs per chunk and one
+// kind::f8f6f4 MMA (the counts) per pair; warps 0..7 fold segments (warp w:
+// TMEM lanes of quarter w % 4, columns 64 (w / 4) .. +63) and store A.  Every
+// wait is bounded (2 s of %globaltimer).
 #include <algorithm>
 #include <cuda_fp16.h>
 #include <vector>
@@ -47,8 +49,13 @@ namespace ibs {
 namespace {
 
 constexpr int kGrmK = 16;                                // markers per FP16 chunk
-constexpr int kGrmPlanes = 3;                            // hi, lo, V'
-constexpr int kGrmChunkBytes = kGrmPlanes * kTileBytes;  // 12 KiB
+// Operand unit: a pair of chunks (32 markers) of one 128-sample block, 20 KiB:
+// hi and lo of the first chunk, hi and lo of the second (FP16, 4 KiB tiles),
+// then V' for all 32 markers as one E4M3 tile (1.0 = 0x38; kind::f8f6f4 takes
+// 32 markers per MMA, so the pair counts cost one MMA and 4 KiB per pair).
+constexpr int kGrmPairBytes = 5 * kTileBytes;            // 20 KiB
+constexpr int kGrmChunkBytes = kGrmPairBytes / 2;        // 10 KiB per chunk on average
+constexpr int kGrmVpOff = 4 * kTileBytes;                // V' tile within a pair
 constexpr int kGrmPad = 4;                               // chunk count padded to a multiple of this
 constexpr int kGrmQueue = 8;
 constexpr int kGrmSeg = 8;                               // chunks per numerator segment
@@ -166,7 +173,7 @@ __global__ void grm_freq_kernel(const uint8_t* __restrict__ packed, int64_t row_
 // Operand rows: CTA = (marker chunk c, sample block b), thread = sample row r.
 // The chunk's 16 table entries are staged in shared memory; the thread reads
 // its sample's codes at the 16 markers and writes 32 bytes (16 FP16 values)
-// of each of hi, lo and V'.
+// of each of hi and lo, and its 16 bytes of the pair's E4M3 V' row.
 __global__ void __launch_bounds__(128) grm_planes_kernel(const uint8_t* __restrict__ packed, int64_t row_bytes,
                                                          int64_t n, int64_t m, const uint16_t* __restrict__ table,
                                                          uint8_t* __restrict__ planes, int64_t n_chunks) {
@@ -186,9 +193,11 @@ __global__ void __launch_bounds__(128) grm_planes_kernel(const uint8_t* __restri
   }
   __syncthreads();
   const uint16_t* t16 = reinterpret_cast<const uint16_t*>(tab);
-  uint32_t hi[kGrmK / 2], lo[kGrmK / 2], vp[kGrmK / 2];
+  uint32_t hi[kGrmK / 2], lo[kGrmK / 2], vp[kGrmK / 4];
 #pragma unroll
-  for (int k = 0; k < kGrmK / 2; ++k) hi[k] = lo[k] = vp[k] = 0;
+  for (int k = 0; k < kGrmK / 2; ++k) hi[k] = lo[k] = 0;
+#pragma unroll
+  for (int k = 0; k < kGrmK / 4; ++k) vp[k] = 0;
 #pragma unroll
   for (int k = 0; k < kGrmK; ++k) {
     if (code[k] != 1) {  // missing (and padding) stays 0
@@ -197,19 +206,22 @@ __global__ void __launch_bounds__(128) grm_planes_kernel(const uint8_t* __restri
       const int sh = 16 * (k & 1);
       hi[k >> 1] |= (uint32_t)t16[k * 8 + 2 * slot] << sh;
       lo[k >> 1] |= (uint32_t)t16[k * 8 + 2 * slot + 1] << sh;
-      vp[k >> 1] |= (uint32_t)t16[k * 8 + 6] << sh;
+      if (t16[k * 8 + 6] != 0) vp[k >> 2] |= (uint32_t)kFp8One << (8 * (k & 3));  // used marker
     }
   }
-  uint8_t* base = planes + (size_t)(b * n_chunks + c) * kGrmChunkBytes;
+  // the pair unit of chunks (c & ~1, c | 1)
+  uint8_t* unit = planes + ((size_t)b * n_chunks + (c & ~(int64_t)1)) * kGrmChunkBytes;
+  uint8_t* base = unit + (c & 1) * 2 * kTileBytes;
 #pragma unroll
   for (int h = 0; h < 2; ++h) {  // K core matrices: markers 0..7 and 8..15
     *reinterpret_cast<uint4*>(base + 0 * kTileBytes + tile_off(r, 16 * h)) =
         make_uint4(hi[4 * h], hi[4 * h + 1], hi[4 * h + 2], hi[4 * h + 3]);
     *reinterpret_cast<uint4*>(base + 1 * kTileBytes + tile_off(r, 16 * h)) =
         make_uint4(lo[4 * h], lo[4 * h + 1], lo[4 * h + 2], lo[4 * h + 3]);
-    *reinterpret_cast<uint4*>(base + 2 * kTileBytes + tile_off(r, 16 * h)) =
-        make_uint4(vp[4 * h], vp[4 * h + 1], vp[4 * h + 2], vp[4 * h + 3]);
   }
+  // E4M3 V': markers 0..15 of the pair in byte columns 0..15, 16..31 in 16..31
+  *reinterpret_cast<uint4*>(unit + kGrmVpOff + tile_off(r, 16 * (int)(c & 1))) =
+      make_uint4(vp[0], vp[1], vp[2], vp[3]);
 }
 
 struct GrmArgs {
@@ -243,7 +255,7 @@ __device__ __forceinline__ double div_count(double x, float c) {
 // kPer chunks per ring stage (one bulk copy per block), kStages stages.
 template <int kPer, int kStages>
 __global__ void __launch_bounds__(kGrmThreads, 1) tc_grm_kernel(const GrmArgs args) {
-  static_assert(kGrmSeg % kPer == 0 && kGrmPad % kPer == 0, "stage size");
+  static_assert(kGrmSeg % kPer == 0 && kGrmPad % kPer == 0 && kPer % 2 == 0, "stage size: whole chunk pairs");
   constexpr int kBlockBytes = kPer * kGrmChunkBytes;  // one block's share of a stage
   constexpr int kGrmStages = kStages;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -397,14 +409,16 @@ __global__ void __launch_bounds__(kGrmThreads, 1) tc_grm_kernel(const GrmArgs ar
 #pragma unroll
           for (int c = 0; c < kPer; ++c) {
             const int64_t k = k0 + c - t.c0;  // chunk index within the item
-            const uint32_t a0 = st0 + c * kGrmChunkBytes;
-            const uint32_t b0 = same ? a0 : a0 + kBlockBytes;
-            const uint64_t ah = umma_desc(a0), al = umma_desc(a0 + kTileBytes), av = umma_desc(a0 + 2 * kTileBytes);
-            const uint64_t bh = umma_desc(b0), bl = umma_desc(b0 + kTileBytes), bv = umma_desc(b0 + 2 * kTileBytes);
+            const uint32_t ua = st0 + (c >> 1) * kGrmPairBytes;  // pair unit of A
+            const uint32_t ub = same ? ua : ua + kBlockBytes;
+            const uint32_t a0 = ua + (c & 1) * 2 * kTileBytes, b0 = ub + (c & 1) * 2 * kTileBytes;
+            const uint64_t ah = umma_desc(a0), al = umma_desc(a0 + kTileBytes);
+            const uint64_t bh = umma_desc(b0), bl = umma_desc(b0 + kTileBytes);
             umma_f16(num, ah, bh, k % kGrmSeg != 0 ? 1u : 0u);  // hi hi^T (restarts every segment)
             umma_f16(num, ah, bl, 1u);                          // + hi lo^T
             umma_f16(num, al, bh, 1u);                          // + lo hi^T
-            umma_f16(tmem + kColCnt, av, bv, k > 0 ? 1u : 0u);  // pair counts
+            if (c & 1)  // pair counts over the pair's 32 markers
+              umma<kTcFp8>(tmem + kColCnt, umma_desc(ua + kGrmVpOff), umma_desc(ub + kGrmVpOff), k > 1 ? 1u : 0u, 0u);
           }
           umma_commit(&empty[s]);
           if (seg_end) umma_commit(&seg_full[b]);
