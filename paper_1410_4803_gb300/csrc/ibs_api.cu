@@ -686,16 +686,10 @@ ibs_status plan_upload(ibs_ctx* ctx, BatchPlan& plan, const uint8_t* pool, int64
     cta += shapes[i].g.n_chunks * jobs[i].groups;
   }
   if (is_tc_mode(plan.mode)) {
-    // the pair kernel reads operand planes, in 128-sample blocks and MMA-K chunks
-    // gather jobs in processing order; CTA numbering restarts at every stage
+    // the pair kernel reads operand planes, in 128-sample blocks and MMA-K
+    // chunks; gather jobs in processing order (the CTA map below refers to them)
     std::vector<TcGatherJob> tj(k);
-    int64_t tcta = 0;
-    size_t stage = 0;
     for (size_t q = 0; q < k; ++q) {
-      if ((int64_t)q == plan.stage_job_off[stage + 1]) {
-        ++stage;
-        tcta = 0;
-      }
       const size_t i = (size_t)plan.order[q];
       const ItemGeom ig = item_geom(shapes[i], plan.mode);
       uint8_t* tcp = static_cast<uint8_t*>(plan.tc_planes.p) + plan.tc_offsets[i];
@@ -708,8 +702,6 @@ ibs_status plan_upload(ibs_ctx* ctx, BatchPlan& plan, const uint8_t* pool, int64
       tj[q].tc = tcp;
       tj[q].nb = ig.T;
       tj[q].nc = ig.nc;
-      tj[q].cta_begin = tcta;
-      tcta += tc_gather_ctas(shapes[i].n, ig.nc);
     }
     IBS_CUDA_TRY(cudaMemcpyAsync(plan.tc_jobs.p, tj.data(), sizeof(TcGatherJob) * k, cudaMemcpyHostToDevice, st));
     // Gather CTA order within each stage: by the pool variant a CTA starts at

@@ -119,7 +119,6 @@ struct TcGatherJob {
   int64_t m, n;           // markers in the window, samples
   uint8_t* tc;            // operand planes of the subset
   int64_t nb, nc;         // 128-sample blocks, chunks
-  int64_t cta_begin;      // first CTA of this job in the flattened grid
 };
 
 // Tensor-core form (ibs_tc.cu): indicator planes and tcgen05 pair tiles, in
