@@ -1016,7 +1016,6 @@ Ring persistent_ring(int64_t chunks_per_item) {
   if (forced.per > 0) return forced;
   return chunks_per_item >= kLongK ? Ring{1, 6} : Ring{2, 3};
 }
-int persistent_stages(int64_t chunks_per_item) { return persistent_ring(chunks_per_item).stages; }
 
 template <int F, class W, int S, int P>
 cudaError_t launch_persistent_s(const W& work, int64_t n_items, int grid, int* counter, int* status,

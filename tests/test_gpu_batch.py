@@ -200,3 +200,30 @@ def test_batch_validation_errors(pool):
         assert ei.value.status == ibs.IBS_EINVAL
     finally:
         ibs.ibs_shutdown(ctx)
+
+
+def test_batch_windows_move_between_calls(pool):
+    """Same subset shapes (n, window length) on two calls, but the windows
+    start elsewhere on the second: the cached plan is reused and the gather's
+    CTA map (ordered by pool variant) is rebuilt; both calls equal the oracle."""
+    import torch
+    from paper_1410_4803_gb300 import ibs
+    w, _ = pool
+    rng = np.random.default_rng(12)
+    subs = _make_subsets(rng, w.n, w.m)[:8]
+    moved = []
+    for idx, vb, vl in subs:
+        vb2 = int(rng.integers(0, w.m - vl + 1))
+        moved.append((idx, vb2, vl))
+    ctx = ibs.ibs_init(0)
+    try:
+        dev = torch.from_numpy(w.packed).cuda()
+        for case in (subs, moved, subs):
+            res = _run_batch(ctx, w, case, dev)
+            for (idx, vb, vl), (c, d) in zip(case, res):
+                G = oracle.unpack_subset(w.packed, w.n, w.m, idx, vb, vl)
+                oc, od, _ = oracle.ibs_triangle_from_codes(G)
+                assert (c == oc).all(), f"n={idx.size} window={vb}+{vl}"
+                assert_dist_close(d, od)
+    finally:
+        ibs.ibs_shutdown(ctx)
