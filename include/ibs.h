@@ -93,6 +93,15 @@ ibs_status ibs_init(const ibs_config* cfg, ibs_ctx** out_ctx);
 ibs_status ibs_compute(ibs_ctx* ctx, const uint8_t* packed, int64_t n_samples, int64_t n_variants,
                        int32_t* out_counts, double* out_dist, void* stream);
 
+/* ibs_compute with the caller's buffer sizes in bytes, checked before any
+ * work: packed_bytes >= n_variants * ceil(n_samples/4), counts_bytes >= P * 16
+ * and, when out_dist is used, dist_bytes >= P * 8 (P = n(n+1)/2, or n*n with
+ * IBS_OUT_SQUARE); a smaller buffer is refused with IBS_EINVAL and nothing is
+ * enqueued.  Otherwise identical to ibs_compute. */
+ibs_status ibs_compute_sz(ibs_ctx* ctx, const uint8_t* packed, size_t packed_bytes, int64_t n_samples,
+                          int64_t n_variants, int32_t* out_counts, size_t counts_bytes, double* out_dist,
+                          size_t dist_bytes, void* stream);
+
 /* Allocation-free variant of ibs_compute (the paper has no counterpart; it
  * exists for callers that may not allocate device memory when they call in:
  * code running during CUDA graph capture, applications whose memory pool owns

@@ -833,6 +833,27 @@ void save_tune(const ibs_ctx* ctx) {
 
 }  // namespace
 
+extern "C" ibs_status ibs_compute_sz(ibs_ctx* ctx, const uint8_t* packed, size_t packed_bytes, int64_t n, int64_t m,
+                                     int32_t* out_counts, size_t counts_bytes, double* out_dist, size_t dist_bytes,
+                                     void* stream) {
+  clear_error();
+  if (ibs_status s = check_ctx(ctx)) return s;
+  if (n < 1 || n > 2147483647LL) return fail(IBS_EINVAL, "n_samples %lld out of range [1, 2^31)", (long long)n);
+  if (m < 1 || m > 2147483647LL) return fail(IBS_EINVAL, "n_variants %lld out of range [1, 2^31)", (long long)m);
+  using u128 = unsigned __int128;
+  const u128 need_packed = (u128)m * (u128)((n + 3) / 4);
+  const u128 pairs = (ctx->flags & IBS_OUT_SQUARE) ? (u128)n * (u128)n : (u128)n * (u128)(n + 1) / 2;
+  if ((u128)packed_bytes < need_packed)
+    return fail(IBS_EINVAL, "packed holds %zu bytes, n_variants * ceil(n_samples/4) = %llu needed", packed_bytes,
+                (unsigned long long)need_packed);
+  if ((u128)counts_bytes < pairs * 16)
+    return fail(IBS_EINVAL, "out_counts holds %zu bytes, %llu needed", counts_bytes,
+                (unsigned long long)(pairs * 16));
+  if (out_dist && !(ctx->flags & IBS_NO_DIST) && (u128)dist_bytes < pairs * 8)
+    return fail(IBS_EINVAL, "out_dist holds %zu bytes, %llu needed", dist_bytes, (unsigned long long)(pairs * 8));
+  return ibs_compute(ctx, packed, n, m, out_counts, out_dist, stream);
+}
+
 extern "C" ibs_status ibs_compute_batch(ibs_ctx* ctx, const uint8_t* pool, int64_t pool_n, int64_t pool_m,
                                         const ibs_subset* subs, int n_subsets, void* stream) {
   clear_error();

@@ -77,6 +77,7 @@ def load():
         sig = {
             "ibs_init": [ctypes.POINTER(ibs_config), ctypes.POINTER(p)],
             "ibs_compute": [p, p, i64, i64, p, p, p],
+            "ibs_compute_sz": [p, p, ctypes.c_size_t, i64, i64, p, ctypes.c_size_t, p, ctypes.c_size_t, p],
             "ibs_synchronize": [p, p],
             "ibs_compute_batch": [p, p, i64, i64, ctypes.POINTER(ibs_subset), i32, p],
             "ibs_panel_load": [p, p, i64, i64],
@@ -175,6 +176,14 @@ def ibs_init(device: int = 0, workspace_bytes: int = 0, flags: int = 0, autotune
 def ibs_compute(ctx: Context, packed, n_samples: int, n_variants: int, out_counts, out_dist=None, stream=None):
     _check(load().ibs_compute(ctx._h, _addr(packed), n_samples, n_variants, _addr(out_counts), _addr(out_dist),
                               _stream(stream, ctx.device)), "ibs_compute")
+
+
+def ibs_compute_sz(ctx: Context, packed, packed_bytes: int, n_samples: int, n_variants: int, out_counts,
+                   counts_bytes: int, out_dist=None, dist_bytes: int = 0, stream=None):
+    """ibs_compute with the buffers' byte sizes checked first (see include/ibs.h)."""
+    _check(load().ibs_compute_sz(ctx._h, _addr(packed), packed_bytes, n_samples, n_variants, _addr(out_counts),
+                                 counts_bytes, _addr(out_dist), dist_bytes, _stream(stream, ctx.device)),
+           "ibs_compute_sz")
 
 
 def ibs_compute_noalloc(packed, n_samples: int, n_variants: int, out_counts, out_dist=None, stream=None):
