@@ -182,19 +182,17 @@ def oracle_rate(packed, n, m, target_s: float, threads: int = 0):
     import oracle
     G = oracle.unpack(packed, n, m)
     cores = os.cpu_count() or 1
-    rows0 = np.arange(min(n, cores), dtype=np.int64)
+    used = threads if threads > 0 else cores
+    rows0 = np.arange(min(n, used), dtype=np.int64)  # one row per thread to calibrate
     t = time.perf_counter()
     oracle.ibs_block(G, G, rows=rows0, threads=threads)
     dt0 = time.perf_counter() - t
-    per_row = dt0 / rows0.size * min(cores, rows0.size)  # seconds per row-wave
     R = int(max(rows0.size, min(n, rows0.size * target_s / max(dt0, 1e-6))))
     rows = np.linspace(0, n - 1, R).astype(np.int64)
     t = time.perf_counter()
     _, _ = oracle.ibs_block(G, G, rows=rows, threads=threads)
     dt = time.perf_counter() - t
     comps = R * (n - 1) * m
-    used = threads if threads > 0 else cores
-    del per_row
     return comps / dt, used, f"{R} rows x all {n} columns x {m} variants", dt
 
 
@@ -459,6 +457,10 @@ def run_plain(args, rank, world, local):
         rate, cores, sample, dt = oracle_rate(w.packed, n, m, target_s=args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": sample + f" ({dt:.1f} s)"}
+        # the same oracle on one core, for the per-core figure
+        rate1, _, sample1, dt1 = oracle_rate(w.packed, n, m, target_s=args.cpu_seconds / 2, threads=1)
+        line["cpu_baseline_1core"] = {"value": rate1, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                      "sample": sample1 + f" ({dt1:.1f} s)"}
     return line
 
 
