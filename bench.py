@@ -425,10 +425,13 @@ def run_plain(args, rank, world, local):
                      if not use_tc else
                      {"bound": "tensor", "achieved": 8.0 * achieved / 1e12, "peak": tc_tflops, "unit": "TFLOP/s",
                       "frac": 8.0 * achieved / 1e12 / tc_tflops,
-                      "traffic": profiled_traffic(f"tc_kernel_{'fp4' if fp4 else 'fp8'}_{args.workload}.md",
-                                                  ("ibs_tc.cu", "ibs_device.cuh")),
-                      "kernel": f"tc_persistent_kernel (tcgen05 {'E2M1 kind::mxf4' if fp4 else 'E4M3 kind::f8f6f4'} "
-                                f"indicator GEMMs)", "kernel_ms": pairs_ms,
+                      "traffic": None if kinfo["two_sm"] else
+                      profiled_traffic(f"tc_kernel_{'fp4' if fp4 else 'fp8'}_{args.workload}.md",
+                                       ("ibs_tc.cu", "ibs_device.cuh")),
+                      "kernel": ("tc_pair_kernel (tcgen05 cta_group::2, M = 256 over two SMs, E2M1 kind::mxf4 "
+                                 "indicator GEMMs)" if kinfo["two_sm"] else
+                                 f"tc_persistent_kernel (tcgen05 {'E2M1 kind::mxf4' if fp4 else 'E4M3 kind::f8f6f4'} "
+                                 f"indicator GEMMs)"), "kernel_ms": pairs_ms,
                       "peak_basis": f"measured bf16 burst TFLOP/s (MEASURED_PEAKS.json) x {tc_ratio:.0f}, the nominal "
                                     f"{'FP4' if fp4 else 'FP8'}/bf16 dense ratio; algorithmic flops = 8 per comparison "
                                     "(4 MACs: VV^T, UU^T, QR^T, RQ^T)",

@@ -302,7 +302,9 @@ ibs_status ibs_grm(ibs_ctx* ctx, const uint8_t* packed, int64_t n_samples, int64
                    void* stream);
 
 /* The kernels this context's ibs_compute uses: out[0] = pair kernel family
- * (0 POPC plain, 1 POPC carry-save, 2 tensor core), out[1] = tensor-core
+ * (0 POPC plain, 1 POPC carry-save, 2 tensor core, 3 tensor core with the
+ * two-SM pair kernel: opted in by IBS_TC_PAIR=1 in the environment, E2M1
+ * operands, triangle output, 129 or more samples), out[1] = tensor-core
  * operand format (0 E4M3, 1 E2M1), out[2] = SMs of the device, out[3] = device. */
 ibs_status ibs_kernel_info(ibs_ctx* ctx, int64_t out[4]);
 

@@ -227,22 +227,31 @@ ibs_status ibs_compute(ibs_ctx* ctx, const uint8_t* packed, int64_t n, int64_t m
   const int64_t tiles = tc ? tc_tiles(n) : geo.n_blocks * (geo.n_blocks + 1) / 2;
   int splits = 1;
   if (persistent) {
-    const std::vector<int64_t> key = {n, m, fmt, ctx->num_sms, group};
+    // the two-SM kernel where it applies (E2M1, at least two blocks); its
+    // work list depends on how many clusters of two fit at once
+    const int pair_clusters = tc_pair_usable(n, m, fmt) ? tc_pair_clusters(tc_chunks(m, fmt)) : 0;
+    const std::vector<int64_t> key = {n, m, fmt, ctx->num_sms, group, pair_clusters};
     if (ctx->single_key != key) {
       std::vector<WorkItem> items;
+      std::vector<PairItem> pitems;
       std::vector<int2> split_tiles;
-      tc_single_items(n, m, fmt, ctx->num_sms, group, items, split_tiles);
-      if (ibs_status s = ensure_buf(ctx, ctx->single_items, items.size() * sizeof(WorkItem))) return s;
+      if (pair_clusters > 0)
+        tc_pair_items(n, m, fmt, pair_clusters, group, pitems, split_tiles);
+      else
+        tc_single_items(n, m, fmt, ctx->num_sms, group, items, split_tiles);
+      const void* src = pair_clusters > 0 ? static_cast<const void*>(pitems.data()) : items.data();
+      const size_t bytes = pair_clusters > 0 ? pitems.size() * sizeof(PairItem) : items.size() * sizeof(WorkItem);
+      if (ibs_status s = ensure_buf(ctx, ctx->single_items, bytes)) return s;
       if (ibs_status s = ensure_buf(ctx, ctx->single_split, std::max<size_t>(1, split_tiles.size()) * sizeof(int2)))
         return s;
       if (ibs_status s = ensure_buf(ctx, ctx->single_counter, 256)) return s;
       // pageable sources: the copies are staged before return
-      IBS_CUDA_TRY(cudaMemcpyAsync(ctx->single_items.p, items.data(), items.size() * sizeof(WorkItem),
-                                   cudaMemcpyHostToDevice, st));
+      IBS_CUDA_TRY(cudaMemcpyAsync(ctx->single_items.p, src, bytes, cudaMemcpyHostToDevice, st));
+      ctx->single_pair = pair_clusters > 0;
       if (!split_tiles.empty())
         IBS_CUDA_TRY(cudaMemcpyAsync(ctx->single_split.p, split_tiles.data(), split_tiles.size() * sizeof(int2),
                                      cudaMemcpyHostToDevice, st));
-      ctx->single_n_items = (int64_t)items.size();
+      ctx->single_n_items = (int64_t)(pair_clusters > 0 ? pitems.size() : items.size());
       ctx->single_n_split = (int64_t)split_tiles.size();
       ctx->single_key = key;
     }
@@ -287,9 +296,14 @@ ibs_status ibs_compute(ibs_ctx* ctx, const uint8_t* packed, int64_t n, int64_t m
     sd.out_dist = out_dist;
     sd.partial = splits > 1 ? static_cast<int32_t*>(ctx->partial.p) : nullptr;
     sd.pad = 0;
-    const int grid = (int)std::min<int64_t>(ctx->num_sms, ctx->single_n_items);
-    IBS_CUDA_TRY(launch_tc_single(sd, static_cast<const WorkItem*>(ctx->single_items.p), ctx->single_n_items, grid,
-                                  fmt, static_cast<int*>(ctx->single_counter.p), ctx->status_dev, st));
+    if (ctx->single_pair) {
+      IBS_CUDA_TRY(launch_tc_pair(sd, static_cast<const PairItem*>(ctx->single_items.p), ctx->single_n_items,
+                                  ctx->status_dev, st));
+    } else {
+      const int grid = (int)std::min<int64_t>(ctx->num_sms, ctx->single_n_items);
+      IBS_CUDA_TRY(launch_tc_single(sd, static_cast<const WorkItem*>(ctx->single_items.p), ctx->single_n_items,
+                                    grid, fmt, static_cast<int*>(ctx->single_counter.p), ctx->status_dev, st));
+    }
   } else if (tc) {
     const int64_t T = (n + 127) / 128;
     if (ctx->tile_list_T != T) {
@@ -1097,7 +1111,7 @@ extern "C" ibs_status ibs_kernel_info(ibs_ctx* ctx, int64_t out[4]) {
   clear_error();
   if (ibs_status s = check_ctx(ctx)) return s;
   if (!out) return fail(IBS_EINVAL, "out is NULL");
-  out[0] = use_tc(ctx) ? 2 : mode_for(ctx) == 0 ? 0 : 1;
+  out[0] = use_tc(ctx) ? (tc_pair_enabled() && tc_format_for(ctx) == kTcFp4 ? 3 : 2) : mode_for(ctx) == 0 ? 0 : 1;
   out[1] = tc_format_for(ctx);
   out[2] = ctx->num_sms;
   out[3] = ctx->device;

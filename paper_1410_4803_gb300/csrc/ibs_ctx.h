@@ -120,6 +120,7 @@ struct ibs_ctx {
   std::vector<int64_t> single_key;
   ibs::DevBuf single_items, single_split, single_counter;
   int64_t single_n_items = 0, single_n_split = 0;
+  bool single_pair = false;  // single_items holds PairItem (two-SM kernel), else WorkItem
   int* status_host = nullptr;     // mapped pinned status word
   int* status_dev = nullptr;
 

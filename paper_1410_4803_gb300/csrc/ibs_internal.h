@@ -59,6 +59,15 @@ struct WorkItem {
   int32_t split;  // 1 when the tile is split over K (accumulate into partial)
 };
 
+// A work item of the two-SM pair kernel: two tiles (I0, J) and (I1, J) that
+// share their column block J, one per CTA of the pair (I1 < 0: the second CTA
+// has no tile and stores nothing), over chunks c0 .. c1-1.
+struct PairItem {
+  int32_t I0, I1, J;
+  int32_t c0, c1;
+  int32_t split;  // 1 when the tiles are split over K (accumulate into partial)
+};
+
 // Per-subset plane-build job for the batched gather-transpose.
 struct PlaneJob {
   BedSource src;
@@ -154,6 +163,19 @@ void tc_single_items(int64_t n, int64_t m, int fmt, int num_sms, int group, std:
                      std::vector<int2>& split_tiles);
 cudaError_t launch_tc_single(const SubsetDev& sd, const WorkItem* items, int64_t n_items, int grid, int fmt,
                              int* counter, int* status, cudaStream_t st);
+// Two-SM form of the same (tcgen05 cta_group::2, E2M1 only): clusters of two
+// CTAs, each pair item two tiles sharing their column block.  tc_pair_clusters
+// is the number of clusters the launch runs (0 when the kernel cannot run);
+// tc_pair_usable says whether it runs for an n x m matrix (opt-in:
+// tc_pair_enabled, IBS_TC_PAIR=1; E2M1; two or more blocks; within its
+// tensor map's coordinate range).
+bool tc_pair_enabled();
+int tc_pair_clusters(int64_t chunks_per_item);
+bool tc_pair_usable(int64_t n, int64_t m, int fmt);
+void tc_pair_items(int64_t n, int64_t m, int fmt, int n_clusters, int group, std::vector<PairItem>& items,
+                   std::vector<int2>& split_tiles);
+cudaError_t launch_tc_pair(const SubsetDev& sd, const PairItem* items, int64_t n_items, int* status,
+                           cudaStream_t st);
 cudaError_t launch_tc_finalize_tiles(const int2* tiles, int64_t n_tiles, const int32_t* partial, int64_t n,
                                      int32_t* out_counts, double* out_dist, cudaStream_t st);
 // Batch form: tiles {subset, I, J, -}, outputs from the subsets' descriptors.

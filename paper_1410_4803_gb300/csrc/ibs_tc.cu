@@ -45,6 +45,8 @@
 #include <cstring>
 #include <vector>
 
+#include <cuda.h>
+
 #include "ibs_tc_common.cuh"
 
 namespace ibs {
@@ -765,6 +767,324 @@ __global__ void __launch_bounds__(256, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Two-SM form of the persistent kernel (tcgen05 cta_group::2).  A cluster of
+// two CTAs on two SMs computes a 256 x 128 piece of the triangle per item:
+// CTA r holds the 128-sample row block I_r (the MMA's A rows 128r ..) and rows
+// 64r .. 64r+63 of the shared column block J (half of the MMA's B), and the
+// even CTA issues M = 256, N = 128 MMAs over both CTAs' shared memory; CTA r's
+// tensor memory receives its 128 x 128 tile.  Per SM and chunk, L2 streams 24
+// KiB instead of 32 KiB for the same 128 x 128 results.  Shared memory saves
+// less: it takes 24 KiB of copies and 32 KiB of MMA reads (A 16 KiB, and the B
+// half 8 KiB for each of the two tensor cores) against 32 + 32 KiB, 12.5% less,
+// and half of the B reads come from the peer SM.
+//
+// The B half of a chunk run is strided in the plane layout (rows 64..127 of a
+// plane are its second 2 KiB), so one 4-D TMA tensor copy per stage gathers it:
+// the planes as 64-bit elements [block * chunk][plane][half][256], a box of
+// {256, 1 half, 4 planes, kPer chunks} landing as [chunk][plane][64 rows].
+//
+// Roles per CTA: warp 0 streams its own A block and B half into its ring
+// with cta_group::2 tensor copies that complete on the even CTA's `full`
+// barrier (the even CTA expects both CTAs' bytes), so no thread relays
+// anything per stage; warp 1 of the even CTA issues the MMAs (4 per chunk) and
+// commits each stage to both CTAs' `empty` barriers and each item to both
+// CTAs' `tfull`; warps 4..7 of both read their accumulators back and arrive on
+// the even CTA's `tempty` (count 8, one cluster-scope release per item).  Both
+// CTAs walk the same items (cluster c takes items c, c + clusters, ...).
+// Every wait is bounded.
+//
+// Measured on n = 4,096, m = 100,000: 1.50 ms against 1.38 ms for the one-SM
+// kernel (tensor pipe 49% against 52% active, L2 hit rate 78% against 75%), so
+// it is opt-in (IBS_TC_PAIR=1).  A relay warp that forwarded each stage of the
+// odd CTA with a cluster-scope release arrive cost about 1.7 us per stage
+// (2.8 ms).
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_index() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_total() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+  return r;
+}
+// Every thread of both CTAs: release this CTA's prior writes, acquire the peer's.
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Address of the same shared variable in cluster CTA `rank`.
+__device__ __forceinline__ uint32_t cluster_addr(const void* p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_addr(p)), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(addr) : "memory");
+}
+// Waits on a barrier that the peer CTA also arrives on (acquire at cluster scope).
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_cluster_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait_cluster(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  for (;;) {
+    for (int i = 0; i < 64; ++i)
+      if (mbar_try_wait_cluster(bar, parity)) return true;
+    if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
+  }
+}
+// The same loads issued by either CTA of the pair, completing on the barrier
+// at `bar` (a shared::cluster address: the even CTA's barrier), so the even
+// CTA's MMA warp sees both CTAs' operands land on one barrier.
+__device__ __forceinline__ void tma_load_3d_pair(void* dst, const CUtensorMap* map, int x0, int x1, int x2,
+                                                 uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.cta_group::2 [%0], [%1, {%2, "
+      "%3, %4}], [%5];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x0), "r"(x1), "r"(x2), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_4d_pair(void* dst, const CUtensorMap* map, int x0, int x1, int x2, int x3,
+                                                 uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.cta_group::2 [%0], [%1, {%2, "
+      "%3, %4, %5}], [%6];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x0), "r"(x1), "r"(x2), "r"(x3), "r"(bar)
+      : "memory");
+}
+
+// Block-scaled E2M1 x E2M1 -> F32, M = 256 over the CTA pair, N = 128.
+constexpr uint32_t kIdescFp4Pair =
+    (1u << 7) | (1u << 10) | ((uint32_t)(128 >> 3) << 17) | (1u << 23) | ((uint32_t)(256 >> 4) << 24);
+__device__ __forceinline__ void umma_pair(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc, uint32_t sf) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%5], [%6], p;\n\t}" ::"r"(
+          tmem),
+      "l"(a), "l"(b), "r"(kIdescFp4Pair), "r"(acc), "r"(sf), "r"(sf + 64u)
+      : "memory");
+}
+// Arrives on the barrier at this offset in both CTAs once the MMAs issued so far are done.
+__device__ __forceinline__ void umma_commit_both(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_addr(bar)),
+      "h"((uint16_t)3)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit_local2(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+               : "memory");
+}
+// The four MMAs of one chunk; b0 is this CTA's B half: [plane][64 rows].
+__device__ __forceinline__ void chunk_mmas_pair(uint32_t tmem, uint32_t a0, uint32_t b0, uint32_t acc) {
+  constexpr uint32_t kHalf = kTileBytes / 2;
+  const uint32_t sf = tmem + kSfCol;
+  umma_pair(tmem + 0, umma_desc(a0 + 0 * kTileBytes), umma_desc(b0 + 0 * kHalf), acc, sf);    // V V^T
+  umma_pair(tmem + 128, umma_desc(a0 + 1 * kTileBytes), umma_desc(b0 + 1 * kHalf), acc, sf);  // U U^T
+  umma_pair(tmem + 256, umma_desc(a0 + 2 * kTileBytes), umma_desc(b0 + 3 * kHalf), acc, sf);  // Q R^T
+  umma_pair(tmem + 256, umma_desc(a0 + 3 * kTileBytes), umma_desc(b0 + 2 * kHalf), 1u, sf);   // + R Q^T
+}
+
+struct PairWork {
+  SubsetDev sd;
+  const PairItem* items;
+};
+
+// Shared memory of one ring stage: kPer chunks of the A block, then kPer
+// chunks of the B half; 4 KiB of slack after the ring.
+template <int kPer>
+constexpr int kPairStageBytes = kPer * (kTChunkBytes + kTChunkBytes / 2);
+template <int kStages, int kPer>
+constexpr size_t kPairSmem = (size_t)kStages * kPairStageBytes<kPer> + 1024 + 4096;
+
+template <int kStages, int kPer>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
+    tc_pair_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap,
+                   const PairWork work, int64_t n_items, int* status) {
+  constexpr int kABytes = kPer * kTChunkBytes;
+  constexpr int kStageBytes = kPairStageBytes<kPer>;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* ring = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], tfull, tempty, drain;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const int64_t first = cluster_index(), step = cluster_total();
+  const int64_t nc = work.sd.n_chunks;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);  // the even CTA's: both CTAs' copies complete on it
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&tfull, 1);
+    mbar_init(&tempty, 8);  // four epilogue warps per CTA
+    mbar_init(&drain, 1);
+    mbar_fence_init();
+    abort_flag = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  if (warp >= 4) tmem_fill_unit_scales(tmem, warp - 4);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  cluster_sync_all();  // both CTAs' barriers initialised and scale factors stored
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+  auto fail = [&](bool cond) {
+    if (lane == 0 && cond) {
+      atomicExch(status, kDevTimeout);
+      atomicExch(&abort_flag, 1);
+    }
+  };
+  auto aborted = [&]() { return __any_sync(0xffffffffu, *(volatile int*)&abort_flag != 0); };
+
+  if (warp == 0) {
+    uint32_t g = 0;
+    bool stop = false;
+    const uint32_t full0 = cluster_addr(&full[0], 0);  // the even CTA's ring barriers
+    for (int64_t it = first; it < n_items && !stop; it += step) {
+      const PairItem pi = work.items[it];
+      const int32_t ib = rank == 0 ? pi.I0 : (pi.I1 >= 0 ? pi.I1 : pi.I0);
+      for (int64_t k = pi.c0; k < pi.c1; k += kPer, ++g) {
+        const int s = (int)(g % kStages);
+        const bool ok = g < (uint32_t)kStages || mbar_wait_bounded(&empty[s], ((g / kStages) - 1) & 1u);
+        if (__any_sync(0xffffffffu, !ok)) {
+          fail(true);
+          stop = true;
+          break;
+        }
+        if (aborted()) {
+          stop = true;
+          break;
+        }
+        if (lane == 0) {
+          // whole boxes always (past an item's last chunk they read the next
+          // block's chunks, or zeros past the end, which no MMA uses)
+          uint8_t* dst = ring + (size_t)s * kStageBytes;
+          const uint32_t bar = full0 + (uint32_t)s * 8u;
+          if (rank == 0) mbar_arrive_expect_tx(&full[s], 2u * kStageBytes);
+          tma_load_3d_pair(dst, &amap, 0, 0, (int)((int64_t)ib * nc + k), bar);
+          tma_load_4d_pair(dst + kABytes, &bmap, 0, (int)rank, 0, (int)((int64_t)pi.J * nc + k), bar);
+        }
+        __syncwarp();
+      }
+    }
+    // the last stages' releases (commits of the even CTA) have landed here
+    for (uint32_t j = g > (uint32_t)kStages ? g - kStages : 0; j < g && !stop; ++j) {
+      const bool ok = mbar_wait_bounded(&empty[j % kStages], (j / kStages) & 1u);
+      if (__any_sync(0xffffffffu, !ok)) {
+        fail(true);
+        break;
+      }
+    }
+  } else if (warp == 1 && rank == 0) {
+    uint32_t g = 0, e = 0;
+    for (int64_t it = first; it < n_items; it += step, ++e) {
+      const PairItem pi = work.items[it];
+      const bool free_ok = e == 0 || mbar_wait_cluster_bounded(&tempty, (e - 1) & 1u);
+      bool stop = __any_sync(0xffffffffu, !free_ok);
+      if (!stop) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (int64_t k = pi.c0; k < pi.c1; k += kPer, ++g) {
+          const int cnt = (int)(pi.c1 - k < kPer ? pi.c1 - k : kPer);
+          const int s = (int)(g % kStages);
+          const bool ok = mbar_wait_bounded(&full[s], (g / kStages) & 1u);
+          if (__any_sync(0xffffffffu, !ok)) {
+            stop = true;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          if (lane == 0) {
+            const uint32_t st0 = smem_addr(ring + (size_t)s * kStageBytes);
+#pragma unroll
+            for (int c = 0; c < kPer; ++c)
+              if (c < cnt)
+                chunk_mmas_pair(tmem, st0 + c * kTChunkBytes, st0 + kABytes + c * (kTChunkBytes / 2),
+                                k + c > pi.c0 ? 1u : 0u);
+            umma_commit_both(&empty[s]);
+          }
+          __syncwarp();
+        }
+      }
+      if (stop || aborted()) {
+        fail(stop);
+        break;
+      }
+      if (lane == 0) umma_commit_both(&tfull);
+      __syncwarp();
+    }
+    if (lane == 0) umma_commit_local2(&drain);
+    __syncwarp();
+    const bool drained = mbar_wait_bounded(&drain, 0);
+    if (lane == 0 && !drained) atomicExch(status, kDevTimeout);
+  } else if (warp >= 4) {
+    const int quarter = warp - 4;
+    const int row = quarter * 32 + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+    const uint32_t tempty_addr = cluster_addr(&tempty, 0);
+    uint32_t e = 0;
+    for (int64_t it = first; it < n_items; it += step, ++e) {
+      const PairItem pi = work.items[it];
+      const bool ok = mbar_wait_bounded(&tfull, e & 1u);
+      if (__any_sync(0xffffffffu, !ok) || aborted()) {
+        fail(!ok);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int32_t ib = rank == 0 ? pi.I0 : pi.I1;
+      const TriEpi ep{ib >= 0 ? (int64_t)ib * kTB + row : work.sd.n, (int64_t)pi.J * kTB, work.sd.n,
+                      work.sd.out_counts, work.sd.out_dist, work.sd.partial, pi.split != 0};
+#pragma unroll 1
+      for (int cg = 0; cg < kTB / 32; ++cg) {
+        uint32_t vn[32], vu[32], v0[32];
+        tmem_ld32(lane_base + 0 + cg * 32, vn);
+        tmem_ld32(lane_base + 128 + cg * 32, vu);
+        tmem_ld32(lane_base + 256 + cg * 32, v0);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (cg == kTB / 32 - 1) {
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive_cluster(tempty_addr);
+        }
+        ep.store(cg, vn, vu, v0);
+      }
+      ep.finish();
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  cluster_sync_all();  // the even CTA's MMAs are drained and no arrival to either CTA is outstanding
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
 // Serving: copy dense query rows (each a row of some request's operand
 // planes) into 128-row step blocks.  CTA = (step block, chunk); each thread
 // moves 16-byte pieces (row, plane, K half).
@@ -1060,6 +1380,216 @@ cudaError_t launch_tc_batch(const SubsetDev* subs, const WorkItem* items, int64_
 cudaError_t launch_tc_single(const SubsetDev& sd, const WorkItem* items, int64_t n_items, int grid, int fmt,
                              int* counter, int* status, cudaStream_t st) {
   return launch_persistent(SingleWork{sd, items}, n_items, grid, fmt, sd.n_chunks, counter, status, st);
+}
+
+// ---------------------------------------------------------------------------
+// Two-SM pair kernel, host side.
+
+// Ring of the pair kernel: kPer chunks per stage.  Three stages of three
+// chunks (216 KiB) measured fastest on n = 4,096, m = 100,000 (1.50 ms; 2 x 4:
+// 1.60 ms, 4 x 2: 1.51 ms).  IBS_TC_PAIR_RING=per,stages overrides (2,4 / 1,8 /
+// 4,2 / 3,3).
+struct PairRing {
+  int per, stages;
+};
+PairRing pair_ring(int64_t chunks_per_item) {
+  static const PairRing forced = [] {
+    PairRing r{0, 0};
+    if (const char* e = getenv("IBS_TC_PAIR_RING")) {
+      const bool known = sscanf(e, "%d,%d", &r.per, &r.stages) == 2 &&
+                         ((r.per == 2 && r.stages == 4) || (r.per == 1 && r.stages == 8) ||
+                          (r.per == 4 && r.stages == 2) || (r.per == 3 && r.stages == 3));
+      if (!known) r = PairRing{0, 0};
+    }
+    return r;
+  }();
+  (void)chunks_per_item;
+  return forced.per > 0 ? forced : PairRing{3, 3};
+}
+
+// Clusters of two that fit at once (one CTA per SM; a GPC with an odd number
+// of free SMs leaves one out).
+template <int S, int P>
+int pair_clusters_s() {
+  static const int v = [] {
+    constexpr size_t smem = kPairSmem<S, P>;
+    if (cudaFuncSetAttribute(tc_pair_kernel<S, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)std::max(2, sms & ~1));
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, tc_pair_kernel<S, P>, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    return n;
+  }();
+  return v;
+}
+
+int tc_pair_clusters(int64_t chunks_per_item) {
+  const PairRing r = pair_ring(chunks_per_item);
+  if (r.per == 2 && r.stages == 4) return pair_clusters_s<4, 2>();
+  if (r.per == 1 && r.stages == 8) return pair_clusters_s<8, 1>();
+  if (r.per == 4 && r.stages == 2) return pair_clusters_s<2, 4>();
+  if (r.per == 3 && r.stages == 3) return pair_clusters_s<3, 3>();
+  return 0;
+}
+
+// cuTensorMapEncodeTiled, from the driver through the runtime (no link-time
+// dependency on libcuda).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled_fn() {
+  static const EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return (EncodeTiledFn) nullptr;
+    }
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+// Two views of the operand planes as 64-bit elements.  A: [block * chunk]
+// [8][256], a box is `per` whole block-chunks (16 KiB each).  B half:
+// [block * chunk][plane][half][256], a box is one half of all four planes
+// over `per` chunks, landing as [chunk][plane][64 rows].
+bool encode_a_map(CUtensorMap* map, const void* planes, int64_t nb, int64_t nc, int per) {
+  const EncodeTiledFn fn = encode_tiled_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[3] = {256, 8, (cuuint64_t)(nb * nc)};
+  const cuuint64_t strides[2] = {(cuuint64_t)kTileBytes / 2, (cuuint64_t)kTChunkBytes};
+  const cuuint32_t box[3] = {256, 8, (cuuint32_t)per};
+  const cuuint32_t elem[3] = {1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<void*>(planes), dims, strides, box, elem,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+bool encode_bhalf_map(CUtensorMap* map, const void* planes, int64_t nb, int64_t nc, int per) {
+  const EncodeTiledFn fn = encode_tiled_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[4] = {256, 2, 4, (cuuint64_t)(nb * nc)};
+  const cuuint64_t strides[3] = {(cuuint64_t)kTileBytes / 2, (cuuint64_t)kTileBytes, (cuuint64_t)kTChunkBytes};
+  const cuuint32_t box[4] = {256, 1, 4, (cuuint32_t)per};
+  const cuuint32_t elem[4] = {1, 1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, const_cast<void*>(planes), dims, strides, box, elem,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool tc_pair_enabled() {
+  static const bool on = [] {
+    const char* e = getenv("IBS_TC_PAIR");
+    return e && strcmp(e, "1") == 0;
+  }();
+  return on;
+}
+
+bool tc_pair_usable(int64_t n, int64_t m, int fmt) {
+  if (!tc_pair_enabled() || fmt != kTcFp4) return false;
+  const int64_t nb = (n + kTB - 1) / kTB, nc = tc_chunks(m, fmt);
+  if (nb < 2 || nb * nc + 8 > 2147483647LL) return false;  // the tensor map's chunk coordinate is an int
+  if (!encode_tiled_fn()) return false;
+  return tc_pair_clusters(nc) > 0;
+}
+
+// Work list of the pair kernel: pair items in the grouped order (bands of
+// `group` tile rows, rounded up to even; inside a band, column by column, the
+// rows (I, I+1) of a column as one item, a lone row where I+1 is past the band
+// or the diagonal).  The clusters take items round-robin, so the items of the
+// final partial wave are split over K where that shortens the tail.
+void tc_pair_items(int64_t n, int64_t m, int fmt, int n_clusters, int group, std::vector<PairItem>& items,
+                   std::vector<int2>& split_tiles) {
+  items.clear();
+  split_tiles.clear();
+  const int64_t T = (n + kTB - 1) / kTB, nc = tc_chunks(m, fmt);
+  const int64_t G = group + (group & 1);
+  std::vector<int4> order;  // {I0, I1, J, -}
+  for (int64_t g0 = 0; g0 < T; g0 += G) {
+    const int64_t g1 = g0 + G < T ? g0 + G : T;
+    for (int64_t J = g0; J < T; ++J)
+      for (int64_t I = g0; I < g1 && I <= J; I += 2) {
+        const int64_t I1 = I + 1 < g1 && I + 1 <= J ? I + 1 : -1;
+        order.push_back(make_int4((int)I, (int)I1, (int)J, 0));
+      }
+  }
+  const int64_t W = (int64_t)order.size(), C = std::max(1, n_clusters);
+  int64_t whole = W, pieces = 1;
+  if (W < C) {
+    whole = 0;
+    pieces = tc_splits_for(W, nc, (int)C);
+  } else {
+    // the final partial wave's R items: pieces by the wave-cost rule (with a
+    // static schedule, R x pieces just above a multiple of the clusters gains
+    // nothing, which the rule accounts for)
+    const int64_t R = W % C;
+    const int64_t s = R > 0 ? tc_splits_for(R, nc, (int)C) : 1;
+    if (s > 1) {
+      whole = W - R;
+      pieces = s;
+    }
+  }
+  pieces = std::max<int64_t>(1, std::min<int64_t>(pieces, std::min<int64_t>(64, nc)));
+  const int64_t min_pieces = (nc + tc_max_chunks(fmt) - 1) / tc_max_chunks(fmt);  // exact FP32 accumulation
+  for (int64_t t = 0; t < W; ++t) {
+    const int4 o = order[t];
+    const int64_t np = std::max<int64_t>(min_pieces, t < whole ? 1 : pieces);
+    if (np > 1) {
+      split_tiles.push_back(make_int2(o.x, o.z));
+      if (o.y >= 0) split_tiles.push_back(make_int2(o.y, o.z));
+    }
+    for (int64_t p = 0; p < np; ++p) {
+      PairItem w;
+      w.I0 = o.x;
+      w.I1 = o.y;
+      w.J = o.z;
+      w.c0 = (int32_t)(nc * p / np);
+      w.c1 = (int32_t)(nc * (p + 1) / np);
+      w.split = np > 1 ? 1 : 0;
+      items.push_back(w);
+    }
+  }
+}
+
+template <int S, int P>
+cudaError_t launch_pair_s(const SubsetDev& sd, const PairItem* items, int64_t n_items, int* status,
+                          cudaStream_t st) {
+  constexpr size_t smem = kPairSmem<S, P>;
+  static_assert(smem <= 227 * 1024, "ring exceeds shared memory");
+  const int clusters = tc_pair_clusters(sd.n_chunks);
+  if (clusters < 1) return cudaErrorInvalidConfiguration;
+  CUtensorMap amap, bmap;
+  if (!encode_a_map(&amap, sd.planes, sd.n_blocks, sd.n_chunks, P) ||
+      !encode_bhalf_map(&bmap, sd.planes, sd.n_blocks, sd.n_chunks, P))
+    return cudaErrorInvalidValue;
+  const int grid = 2 * (int)std::min<int64_t>(clusters, n_items);
+  tc_pair_kernel<S, P><<<grid, 256, smem, st>>>(amap, bmap, PairWork{sd, items}, n_items, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_pair(const SubsetDev& sd, const PairItem* items, int64_t n_items, int* status,
+                           cudaStream_t st) {
+  if (n_items <= 0) return cudaSuccess;
+  if (n_items > 2147483647LL) return cudaErrorInvalidValue;
+  const PairRing r = pair_ring(sd.n_chunks);
+  if (r.per == 2 && r.stages == 4) return launch_pair_s<4, 2>(sd, items, n_items, status, st);
+  if (r.per == 1 && r.stages == 8) return launch_pair_s<8, 1>(sd, items, n_items, status, st);
+  if (r.per == 4 && r.stages == 2) return launch_pair_s<2, 4>(sd, items, n_items, status, st);
+  if (r.per == 3 && r.stages == 3) return launch_pair_s<3, 3>(sd, items, n_items, status, st);
+  return cudaErrorInvalidValue;
 }
 
 constexpr unsigned kFinalizeSplit = 8;  // CTAs per finalised tile (one CTA per tile reached ~0.8 TB/s)

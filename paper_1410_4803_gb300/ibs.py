@@ -317,8 +317,9 @@ def ld_r(ctx: Context, packed, n_samples: int, n_variants: int, window: int, str
 def ibs_kernel_info(ctx: Context) -> dict:
     out = (ctypes.c_int64 * 4)()
     _check(load().ibs_kernel_info(ctx._h, out), "ibs_kernel_info")
-    return {"family": ("popc-plain", "popc-csa", "tensor-core")[out[0]], "tc_format": ("e4m3", "e2m1")[out[1]],
-            "sms": out[2], "device": out[3]}
+    return {"family": ("popc-plain", "popc-csa", "tensor-core", "tensor-core")[out[0]],
+            "two_sm": out[0] == 3,  # the opt-in two-SM pair kernel (IBS_TC_PAIR=1)
+            "tc_format": ("e4m3", "e2m1")[out[1]], "sms": out[2], "device": out[3]}
 
 
 def ibs_batch_plan_info(ctx: Context) -> dict:

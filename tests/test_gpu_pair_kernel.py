@@ -1,0 +1,55 @@
+"""The opt-in two-SM pair kernel (tcgen05 cta_group::2, IBS_TC_PAIR=1) through
+ibs_compute: bit-exact counts and distances within 1e-12 against the oracle.
+The switch is read once per process, so each case runs in a child process.
+Shapes: two blocks with a ragged marker tail, a lone diagonal tile per column
+pair, garbage in the padding bits, every tile split over K (fewer pair items
+than clusters), and whole waves plus an unsplit tail; every ring variant."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+CHILD = r"""
+import sys
+import numpy as np
+sys.path.insert(0, {tests!r}); sys.path.insert(0, {root!r})
+import oracle
+from helpers import assert_dist_close, gpu_compute, pack_codes, random_codes
+from paper_1410_4803_gb300 import ibs
+ctx = ibs.ibs_init(0, flags=ibs.IBS_KERNEL_TC | ibs.IBS_TC_FP4)
+info = ibs.ibs_kernel_info(ctx)
+assert info["family"] == "tensor-core" and info["two_sm"], info
+rng = np.random.default_rng({seed})
+for n, m, miss, garbage in {shapes!r}:
+    codes = random_codes(rng, n, m, miss=miss)
+    packed = pack_codes(codes, garbage_rng=np.random.default_rng(7) if garbage else None)
+    want_c, want_d = oracle.ibs_triangle(packed, n, m)
+    got_c, got_d = gpu_compute(ctx, packed, n, m)
+    bad = np.flatnonzero((got_c != want_c).any(axis=1))
+    assert bad.size == 0, f"n={{n}} m={{m}}: {{bad.size}} pairs differ, first {{bad[:4]}}"
+    assert_dist_close(got_d, want_d)
+    print(f"ok n={{n}} m={{m}}")
+ibs.ibs_shutdown(ctx)
+"""
+
+SHAPES = {
+    "3,3": [(129, 65, 0.05, False), (256, 1, 0.0, False), (300, 1000, 0.3, True), (1500, 4000, 0.02, False),
+            (2200, 700, 0.02, True)],
+    "2,4": [(257, 1025, 0.05, True), (1100, 777, 0.1, False)],
+    "4,2": [(257, 1025, 0.05, False), (700, 3001, 0.02, True)],
+    "1,8": [(200, 130, 0.05, False), (640, 2000, 0.02, False)],
+}
+
+
+@pytest.mark.parametrize("ring", sorted(SHAPES))
+def test_pair_kernel_matches_oracle(ring):
+    code = CHILD.format(tests=os.path.join(ROOT, "tests"), root=ROOT, seed=11, shapes=SHAPES[ring])
+    env = dict(os.environ, IBS_TC_PAIR="1", IBS_TC_PAIR_RING=ring)
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.count("ok n=") == len(SHAPES[ring])
