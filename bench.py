@@ -251,6 +251,7 @@ def run_plain(args, rank, world, local):
     ctx = ibs.ibs_init(local, flags=ibs.IBS_TIMING | (ibs.IBS_KERNEL_TC if use_tc else ibs.IBS_KERNEL_CSA))
     probe = ibs.ibs_probe_int_pipes(ctx)
     kinfo = ibs.ibs_kernel_info(ctx)
+    two_sm = use_tc and ibs.ibs_compute_kernel(ctx, n, m) == "tc-pair"  # cta_group::2 kernel for long items
     mma_probe = ibs.ibs_probe_mma(ctx) if use_tc else None
 
     with torch.cuda.stream(stream):
@@ -425,11 +426,10 @@ def run_plain(args, rank, world, local):
                      if not use_tc else
                      {"bound": "tensor", "achieved": 8.0 * achieved / 1e12, "peak": tc_tflops, "unit": "TFLOP/s",
                       "frac": 8.0 * achieved / 1e12 / tc_tflops,
-                      "traffic": None if kinfo["two_sm"] else
-                      profiled_traffic(f"tc_kernel_{'fp4' if fp4 else 'fp8'}_{args.workload}.md",
-                                       ("ibs_tc.cu", "ibs_device.cuh")),
+                      "traffic": profiled_traffic(f"{'tc_pair_kernel' if two_sm else 'tc_kernel_fp4' if fp4 else 'tc_kernel_fp8'}"
+                                                  f"_{args.workload}.md", ("ibs_tc.cu", "ibs_device.cuh")),
                       "kernel": ("tc_pair_kernel (tcgen05 cta_group::2, M = 256 over two SMs, E2M1 kind::mxf4 "
-                                 "indicator GEMMs)" if kinfo["two_sm"] else
+                                 "indicator GEMMs)" if two_sm else
                                  f"tc_persistent_kernel (tcgen05 {'E2M1 kind::mxf4' if fp4 else 'E4M3 kind::f8f6f4'} "
                                  f"indicator GEMMs)"), "kernel_ms": pairs_ms,
                       "peak_basis": f"measured bf16 burst TFLOP/s (MEASURED_PEAKS.json) x {tc_ratio:.0f}, the nominal "

@@ -302,11 +302,21 @@ ibs_status ibs_grm(ibs_ctx* ctx, const uint8_t* packed, int64_t n_samples, int64
                    void* stream);
 
 /* The kernels this context's ibs_compute uses: out[0] = pair kernel family
- * (0 POPC plain, 1 POPC carry-save, 2 tensor core, 3 tensor core with the
- * two-SM pair kernel: opted in by IBS_TC_PAIR=1 in the environment, E2M1
- * operands, triangle output, 129 or more samples), out[1] = tensor-core
+ * (0 POPC plain, 1 POPC carry-save, 2 tensor core), out[1] = tensor-core
  * operand format (0 E4M3, 1 E2M1), out[2] = SMs of the device, out[3] = device. */
 ibs_status ibs_kernel_info(ibs_ctx* ctx, int64_t out[4]);
+
+/* The pair kernel ibs_compute runs on this context for an n_samples x
+ * n_variants matrix, written to *out: 0 POPC plain, 1 POPC carry-save,
+ * 2 tensor core with one persistent CTA per SM, 3 tensor core with the
+ * two-SM kernel (clusters of two CTAs, tcgen05 cta_group::2), 4 tensor core
+ * with one CTA per tile (square output).  The two-SM kernel runs for E2M1
+ * operands, triangle output and 129 or more samples when the matrix has at
+ * least 262,144 variants (4,096 chunks of 64), where it is the faster one;
+ * IBS_TC_PAIR=1 in the environment selects it for every size, IBS_TC_PAIR=0
+ * never.  Host only, no device work; IBS_EINVAL for sizes ibs_compute
+ * refuses or out == NULL. */
+ibs_status ibs_compute_kernel(ibs_ctx* ctx, int64_t n_samples, int64_t n_variants, int64_t* out);
 
 /* Counters of the last ibs_compute / ibs_compute_batch on this context:
  * out[0] = kernel launches enqueued, out[1] = pair tiles, out[2] = K splits. */

@@ -195,6 +195,13 @@ ibs_status ibs_init(const ibs_config* cfg, ibs_ctx** out_ctx) {
   return IBS_OK;
 }
 
+// IBS_TC_TILE_KERNEL set: the tensor-core form runs one CTA per tile (or tile
+// piece) instead of the persistent kernels.
+static bool tc_tile_kernel_forced() {
+  static const bool v = getenv("IBS_TC_TILE_KERNEL") != nullptr;
+  return v;
+}
+
 ibs_status ibs_compute(ibs_ctx* ctx, const uint8_t* packed, int64_t n, int64_t m, int32_t* out_counts,
                        double* out_dist, void* stream) {
   clear_error();
@@ -215,8 +222,7 @@ ibs_status ibs_compute(ibs_ctx* ctx, const uint8_t* packed, int64_t n, int64_t m
   // Tensor-core form, triangle output: the persistent kernel over a work list
   // (tail wave split over K).  Square output, or IBS_TC_TILE_KERNEL set: one
   // CTA per tile (or tile piece).
-  static const bool tile_kernel = getenv("IBS_TC_TILE_KERNEL") != nullptr;
-  const bool persistent = tc && !square && !tile_kernel;
+  const bool persistent = tc && !square && !tc_tile_kernel_forced();
   static const int group = [] {
     const char* e = getenv("IBS_TC_GROUP");
     const int v = e ? atoi(e) : 16;
@@ -227,8 +233,9 @@ ibs_status ibs_compute(ibs_ctx* ctx, const uint8_t* packed, int64_t n, int64_t m
   const int64_t tiles = tc ? tc_tiles(n) : geo.n_blocks * (geo.n_blocks + 1) / 2;
   int splits = 1;
   if (persistent) {
-    // the two-SM kernel where it applies (E2M1, at least two blocks); its
-    // work list depends on how many clusters of two fit at once
+    // the two-SM kernel where it applies (E2M1, at least two blocks, items of
+    // at least 4,096 chunks unless IBS_TC_PAIR says otherwise); its work list
+    // depends on how many clusters of two fit at once
     const int pair_clusters = tc_pair_usable(n, m, fmt) ? tc_pair_clusters(tc_chunks(m, fmt)) : 0;
     const std::vector<int64_t> key = {n, m, fmt, ctx->num_sms, group, pair_clusters};
     if (ctx->single_key != key) {
@@ -1111,10 +1118,27 @@ extern "C" ibs_status ibs_kernel_info(ibs_ctx* ctx, int64_t out[4]) {
   clear_error();
   if (ibs_status s = check_ctx(ctx)) return s;
   if (!out) return fail(IBS_EINVAL, "out is NULL");
-  out[0] = use_tc(ctx) ? (tc_pair_enabled() && tc_format_for(ctx) == kTcFp4 ? 3 : 2) : mode_for(ctx) == 0 ? 0 : 1;
+  out[0] = use_tc(ctx) ? 2 : mode_for(ctx) == 0 ? 0 : 1;
   out[1] = tc_format_for(ctx);
   out[2] = ctx->num_sms;
   out[3] = ctx->device;
+  return IBS_OK;
+}
+
+extern "C" ibs_status ibs_compute_kernel(ibs_ctx* ctx, int64_t n, int64_t m, int64_t* out) {
+  clear_error();
+  if (ibs_status s = check_ctx(ctx)) return s;
+  if (!out) return fail(IBS_EINVAL, "out is NULL");
+  if (n < 1 || n > 2147483647LL) return fail(IBS_EINVAL, "n_samples %lld out of range [1, 2^31)", (long long)n);
+  if (m < 1 || m > 2147483647LL) return fail(IBS_EINVAL, "n_variants %lld out of range [1, 2^31)", (long long)m);
+  DeviceGuard g(ctx->device);
+  if (!use_tc(ctx)) {
+    *out = mode_for(ctx) == 0 ? 0 : 1;
+  } else if ((ctx->flags & IBS_OUT_SQUARE) || tc_tile_kernel_forced()) {
+    *out = 4;
+  } else {
+    *out = tc_pair_usable(n, m, tc_format_for(ctx)) ? 3 : 2;
+  }
   return IBS_OK;
 }
 

@@ -166,10 +166,10 @@ cudaError_t launch_tc_single(const SubsetDev& sd, const WorkItem* items, int64_t
 // Two-SM form of the same (tcgen05 cta_group::2, E2M1 only): clusters of two
 // CTAs, each pair item two tiles sharing their column block.  tc_pair_clusters
 // is the number of clusters the launch runs (0 when the kernel cannot run);
-// tc_pair_usable says whether it runs for an n x m matrix (opt-in:
-// tc_pair_enabled, IBS_TC_PAIR=1; E2M1; two or more blocks; within its
-// tensor map's coordinate range).
-bool tc_pair_enabled();
+// tc_pair_usable says whether it runs for an n x m matrix (E2M1; two or more
+// blocks; within its tensor map's coordinate range; tc_pair_mode: 1 always,
+// -1 never, 0 for items of at least 4,096 chunks, from IBS_TC_PAIR).
+int tc_pair_mode();
 int tc_pair_clusters(int64_t chunks_per_item);
 bool tc_pair_usable(int64_t n, int64_t m, int fmt);
 void tc_pair_items(int64_t n, int64_t m, int fmt, int n_clusters, int group, std::vector<PairItem>& items,

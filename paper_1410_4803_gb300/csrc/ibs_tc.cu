@@ -794,11 +794,12 @@ __global__ void __launch_bounds__(256, 1)
 // CTAs walk the same items (cluster c takes items c, c + clusters, ...).
 // Every wait is bounded.
 //
-// Measured on n = 4,096, m = 100,000: 1.50 ms against 1.38 ms for the one-SM
-// kernel (tensor pipe 49% against 52% active, L2 hit rate 78% against 75%), so
-// it is opt-in (IBS_TC_PAIR=1).  A relay warp that forwarded each stage of the
-// odd CTA with a cluster-scope release arrive cost about 1.7 us per stage
-// (2.8 ms).
+// Measured: n = 20,000, m = 500,000 (7,813 chunks per item), 156 ms against
+// 198 ms for the one-SM kernel; n = 4,096, m = 100,000 (1,563 chunks), 1.50 ms
+// against 1.38 ms (tensor pipe 49% against 52% active, L2 hit rate 78%
+// against 75%).  So ibs_compute takes it for items of at least kLongK chunks
+// (tc_pair_mode).  A relay warp that forwarded each stage of the odd CTA with
+// a cluster-scope release arrive cost about 1.7 us per stage (2.8 ms).
 
 __device__ __forceinline__ uint32_t cluster_rank() {
   uint32_t r;
@@ -1490,17 +1491,25 @@ bool encode_bhalf_map(CUtensorMap* map, const void* planes, int64_t nb, int64_t 
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-bool tc_pair_enabled() {
-  static const bool on = [] {
+// IBS_TC_PAIR=1: the pair kernel wherever it can run; 0: never; unset: for
+// items of at least kLongK chunks, where the one-SM kernel's CTAs drift apart
+// along K and miss L2, and the pair's smaller L2 stream pays (n = 20,000,
+// m = 500,000: 156 ms against 198 ms; n = 4,096, m = 100,000: 1.50 ms
+// against 1.38 ms).
+int tc_pair_mode() {
+  static const int v = [] {
     const char* e = getenv("IBS_TC_PAIR");
-    return e && strcmp(e, "1") == 0;
+    if (e && strcmp(e, "1") == 0) return 1;
+    if (e && strcmp(e, "0") == 0) return -1;
+    return 0;
   }();
-  return on;
+  return v;
 }
 
 bool tc_pair_usable(int64_t n, int64_t m, int fmt) {
-  if (!tc_pair_enabled() || fmt != kTcFp4) return false;
+  if (tc_pair_mode() < 0 || fmt != kTcFp4) return false;
   const int64_t nb = (n + kTB - 1) / kTB, nc = tc_chunks(m, fmt);
+  if (tc_pair_mode() == 0 && nc < kLongK) return false;
   if (nb < 2 || nb * nc + 8 > 2147483647LL) return false;  // the tensor map's chunk coordinate is an int
   if (!encode_tiled_fn()) return false;
   return tc_pair_clusters(nc) > 0;

@@ -91,6 +91,7 @@ def load():
             "ibs_probe_mma": [p, ctypes.POINTER(ctypes.c_double)],
             "ibs_batch_plan_info": [p, ctypes.POINTER(ctypes.c_int64)],
             "ibs_kernel_info": [p, ctypes.POINTER(ctypes.c_int64)],
+            "ibs_compute_kernel": [p, i64, i64, ctypes.POINTER(ctypes.c_int64)],
             "ibs_ld_r": [p, p, i64, i64, i64, p, p, p],
             "ibs_cluster_complete": [p, p, i64, p, p],
             "ibs_grm": [p, p, i64, i64, p, p],
@@ -317,9 +318,19 @@ def ld_r(ctx: Context, packed, n_samples: int, n_variants: int, window: int, str
 def ibs_kernel_info(ctx: Context) -> dict:
     out = (ctypes.c_int64 * 4)()
     _check(load().ibs_kernel_info(ctx._h, out), "ibs_kernel_info")
-    return {"family": ("popc-plain", "popc-csa", "tensor-core", "tensor-core")[out[0]],
-            "two_sm": out[0] == 3,  # the opt-in two-SM pair kernel (IBS_TC_PAIR=1)
-            "tc_format": ("e4m3", "e2m1")[out[1]], "sms": out[2], "device": out[3]}
+    return {"family": ("popc-plain", "popc-csa", "tensor-core")[out[0]], "tc_format": ("e4m3", "e2m1")[out[1]],
+            "sms": out[2], "device": out[3]}
+
+
+COMPUTE_KERNELS = ("popc-plain", "popc-csa", "tc-persistent", "tc-pair", "tc-tile")
+
+
+def ibs_compute_kernel(ctx: Context, n_samples: int, n_variants: int) -> str:
+    """The pair kernel ibs_compute runs on this context for an n x m matrix:
+    one of COMPUTE_KERNELS ('tc-pair' is the two-SM cta_group::2 kernel)."""
+    out = ctypes.c_int64()
+    _check(load().ibs_compute_kernel(ctx._h, n_samples, n_variants, ctypes.byref(out)), "ibs_compute_kernel")
+    return COMPUTE_KERNELS[out.value]
 
 
 def ibs_batch_plan_info(ctx: Context) -> dict:

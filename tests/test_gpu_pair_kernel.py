@@ -1,6 +1,8 @@
-"""The opt-in two-SM pair kernel (tcgen05 cta_group::2, IBS_TC_PAIR=1) through
-ibs_compute: bit-exact counts and distances within 1e-12 against the oracle.
-The switch is read once per process, so each case runs in a child process.
+"""The two-SM pair kernel (tcgen05 cta_group::2) through ibs_compute, forced
+on for every size with IBS_TC_PAIR=1: bit-exact counts and distances within
+1e-12 against the oracle.  The switch is read once per process, so each case
+runs in a child process.  Also the default choice (ibs_compute_kernel): the
+pair kernel for 262,144 or more variants, the one-SM kernel otherwise.
 Shapes: two blocks with a ragged marker tail, a lone diagonal tile per column
 pair, garbage in the padding bits, every tile split over K (fewer pair items
 than clusters), and whole waves plus an unsplit tail; every ring variant."""
@@ -22,10 +24,9 @@ import oracle
 from helpers import assert_dist_close, gpu_compute, pack_codes, random_codes
 from paper_1410_4803_gb300 import ibs
 ctx = ibs.ibs_init(0, flags=ibs.IBS_KERNEL_TC | ibs.IBS_TC_FP4)
-info = ibs.ibs_kernel_info(ctx)
-assert info["family"] == "tensor-core" and info["two_sm"], info
 rng = np.random.default_rng({seed})
 for n, m, miss, garbage in {shapes!r}:
+    assert ibs.ibs_compute_kernel(ctx, n, m) == "tc-pair", (n, m)
     codes = random_codes(rng, n, m, miss=miss)
     packed = pack_codes(codes, garbage_rng=np.random.default_rng(7) if garbage else None)
     want_c, want_d = oracle.ibs_triangle(packed, n, m)
@@ -53,3 +54,34 @@ def test_pair_kernel_matches_oracle(ring):
     r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stdout + r.stderr
     assert r.stdout.count("ok n=") == len(SHAPES[ring])
+
+
+CHOICE = r"""
+import sys
+sys.path.insert(0, {root!r})
+from paper_1410_4803_gb300 import ibs
+want = {want!r}
+for flags, n, m, kern in want:
+    ctx = ibs.ibs_init(0, flags=flags)
+    got = ibs.ibs_compute_kernel(ctx, n, m)
+    ibs.ibs_shutdown(ctx)
+    assert got == kern, (flags, n, m, got, kern)
+print("ok")
+"""
+
+
+@pytest.mark.parametrize("mode", ["auto", "off"])
+def test_default_kernel_choice(mode):
+    from paper_1410_4803_gb300 import ibs
+    tc4, tc8 = ibs.IBS_KERNEL_TC | ibs.IBS_TC_FP4, ibs.IBS_KERNEL_TC | ibs.IBS_TC_FP8
+    long_k = "tc-pair" if mode == "auto" else "tc-persistent"
+    want = [(tc4, 4096, 100_000, "tc-persistent"), (tc4, 20_000, 500_000, long_k), (tc4, 300, 262_144, long_k),
+            (tc4, 300, 262_080, "tc-persistent"), (tc4, 128, 500_000, "tc-persistent"),
+            (tc8, 20_000, 500_000, "tc-persistent"), (tc4 | ibs.IBS_OUT_SQUARE, 20_000, 500_000, "tc-tile"),
+            (ibs.IBS_KERNEL_CSA, 20_000, 500_000, "popc-csa")]
+    env = {k: v for k, v in os.environ.items() if k not in ("IBS_TC_PAIR", "IBS_TC_TILE_KERNEL")}
+    if mode == "off":
+        env["IBS_TC_PAIR"] = "0"
+    r = subprocess.run([sys.executable, "-c", CHOICE.format(root=ROOT, want=want)], env=env, capture_output=True,
+                       text=True, timeout=300)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stdout + r.stderr
