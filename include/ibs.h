@@ -89,7 +89,8 @@ ibs_status ibs_init(const ibs_config* cfg, ibs_ctx** out_ctx);
  *   out_dist    DEVICE double [P] (8-byte aligned) or NULL.
  *   stream      cudaStream_t or NULL.
  * Transposes the matrix into library-owned sample-major bit planes, then runs
- * the triangular pair-count kernel with the fused count/distance epilogue. */
+ * the triangular pair-count kernel with the fused count/distance epilogue;
+ * which pair kernel a shape gets is given by ibs_compute_kernel. */
 ibs_status ibs_compute(ibs_ctx* ctx, const uint8_t* packed, int64_t n_samples, int64_t n_variants,
                        int32_t* out_counts, double* out_dist, void* stream);
 
