@@ -1580,6 +1580,9 @@ cudaError_t launch_pair_s(const SubsetDev& sd, const PairItem* items, int64_t n_
   static_assert(smem <= 227 * 1024, "ring exceeds shared memory");
   const int clusters = tc_pair_clusters(sd.n_chunks);
   if (clusters < 1) return cudaErrorInvalidConfiguration;
+  // per device: the cluster count above was taken once, on the first device used
+  cudaError_t e = cudaFuncSetAttribute(tc_pair_kernel<S, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   CUtensorMap amap, bmap;
   if (!encode_a_map(&amap, sd.planes, sd.n_blocks, sd.n_chunks, P) ||
       !encode_bhalf_map(&bmap, sd.planes, sd.n_blocks, sd.n_chunks, P))
