@@ -1,24 +1,36 @@
 #!/usr/bin/env python3
 """All-pairs IBS benchmark: sample-pair x variant comparisons per second.
 
-Default workload: the plain IBS matrix of n = 4,096 samples x m = 100,000
-variants (MAF ~ U(0.01, 0.5), 2% missing i.i.d. plus 0.5% of variants at 30%
-missing), synthetic, on one GB300.  One step = one ibs_compute call (bit-plane
-transpose + triangular pair-count kernel with the fused epilogue) over inputs
-already resident in HBM; L2 is flushed (256 MiB write) between steps outside
-the timed events.  `e2e` repeats the step through the same C ABI with the
-packed input in pinned host memory and the counts and distances copied back
-each step, pipelined over a copy-in, a compute and a copy-out stream (the
-one-stream figure is reported beside it).  `roofline` compares the pair-count kernel, timed with CUDA events
-on its own stream inside the library, with the integer-pipe ceiling derived
-from a live microbenchmark of POPC / LOP3 / IADD3 throughput.  `cpu_baseline`
-times the CPU oracle on a bounded row sample of the same workload.
+Default workload (the headline line): the structured cohort, n = 20,000
+samples x m = 500,000 variants (Balding-Nichols five subpopulations, Fst
+0.05; 200 parent-offspring pairs and 50 near-duplicates; 1% missing; seed 2),
+synthetic, on one GB300.  One step = one ibs_compute call (transpose into
+operand planes, the pair-count kernel with its fused epilogue, the split-tile
+finalisation) over an input already resident in HBM, timed with CUDA events
+on the launching stream; the planes (20 GB) exceed L2 many times over and a
+256 MiB L2 flush still runs before every step.
+
+The line carries:
+  roofline      the pair kernel (CUDA events inside the library) against the
+                tensor peak of its operand type (measured bf16 x nominal ratio);
+  e2e           the same calls through the C ABI from pinned host memory,
+                input copied in and counts and distances copied back every
+                step, pipelined over copy-in, compute and copy-out streams;
+  cpu_baseline  the CPU oracle on a bounded block (rows x 2,048 columns x all
+                variants) on this machine's cores; the same block spot-checks
+                the GPU result (`exact`);
+  plain_config2 the plain n = 4,096 x m = 100,000 matrix;
+  batched       64 cohort subsets of a 30,000 x 600,000 pool in one batched
+                call against the plain path once per subset;
+  served        the resident 100,000 x 200,000 panel, Poisson query arrivals,
+                engine against one request at a time (p50/p99, throughput).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload plain|structured|batch|serve]
+                    [--workload structured|plain|batch|serve|ld|cluster|grm] [--no-sub]
 
 With N > 1 (torchrun, one rank per GPU) every rank runs its own copy of the
-workload (replicas; weak scaling) and rank 0 prints one JSON line.
+workload (replicas; weak scaling) and rank 0 prints one JSON line; the
+sub-records run at N = 1 only.
 """
 from __future__ import annotations
 
@@ -173,27 +185,60 @@ def profiled_traffic(name: str, files=("ibs_pairs.cu", "ibs_device.cuh")):
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle baseline
+# CPU oracle baseline and spot check
 
-def oracle_rate(packed, n, m, target_s: float, threads: int = 0):
-    """Time the oracle on a row sample sized to about target_s seconds.
-    Returns (comparisons/s, threads, sample description, seconds)."""
+def oracle_block_rate(packed, n, m, rows, cols, threads: int = 0):
+    """Time the oracle on the block rows x cols of an n x m packed matrix (host
+    numpy): unpack only those samples, then the plain per-marker loop.  Returns
+    (counts [R][C][4], dist [R][C], comparisons/s, threads used, seconds)."""
     import numpy as np
     import oracle
-    G = oracle.unpack(packed, n, m)
-    cores = os.cpu_count() or 1
-    used = threads if threads > 0 else cores
-    rows0 = np.arange(min(n, used), dtype=np.int64)  # one row per thread to calibrate
+    rows = np.asarray(rows, dtype=np.int64)
+    cols = np.asarray(cols, dtype=np.int64)
+    GR = oracle.unpack_subset(packed, n, m, rows, 0, m)
+    GC = oracle.unpack_subset(packed, n, m, cols, 0, m)
+    used = threads if threads > 0 else (os.cpu_count() or 1)
     t = time.perf_counter()
-    oracle.ibs_block(G, G, rows=rows0, threads=threads)
-    dt0 = time.perf_counter() - t
-    R = int(max(rows0.size, min(n, rows0.size * target_s / max(dt0, 1e-6))))
-    rows = np.linspace(0, n - 1, R).astype(np.int64)
-    t = time.perf_counter()
-    _, _ = oracle.ibs_block(G, G, rows=rows, threads=threads)
+    counts, dist = oracle.ibs_block(GR, GC, threads=threads)
     dt = time.perf_counter() - t
-    comps = R * (n - 1) * m
-    return comps / dt, used, f"{R} rows x all {n} columns x {m} variants", dt
+    return counts, dist, rows.size * cols.size * m / dt, used, dt
+
+
+def calibrated_rows(packed, n, m, cols, target_s: float, threads: int = 0):
+    """Rows (evenly spaced) for an oracle block of about target_s seconds."""
+    import numpy as np
+    probe = np.linspace(0, n - 1, max(1, min(n, threads if threads > 0 else (os.cpu_count() or 1)))).astype(np.int64)
+    _, _, rate, _, _ = oracle_block_rate(packed, n, m, probe, cols[: max(1, min(len(cols), 256))], threads)
+    R = int(max(1, min(n, target_s * rate / (len(cols) * m))))
+    return np.linspace(0, n - 1, R).astype(np.int64)
+
+
+def gpu_block(counts_dev, dist_dev, n, rows, cols):
+    """Rows x cols of the device triangle (harness: gathered by torch indexing)."""
+    import numpy as np
+    import torch
+    r = np.asarray(rows, dtype=np.int64)[:, None]
+    c = np.asarray(cols, dtype=np.int64)[None, :]
+    lo, hi = np.minimum(r, c), np.maximum(r, c)
+    idx = torch.from_numpy((lo * n - lo * (lo - 1) // 2 + (hi - lo)).reshape(-1)).to(counts_dev.device)
+    got_c = counts_dev.index_select(0, idx).cpu().numpy().reshape(r.shape[0], c.shape[1], 4)
+    got_d = dist_dev.index_select(0, idx).cpu().numpy().reshape(r.shape[0], c.shape[1]) if dist_dev is not None else None
+    return got_c, got_d
+
+
+def same_block(got_c, got_d, want_c, want_d) -> bool:
+    """Counts bit for bit; distances within 1e-12 relative, NaN in the same places."""
+    import numpy as np
+    if not np.array_equal(got_c, want_c):
+        return False
+    if got_d is None:
+        return True
+    nan_g, nan_w = np.isnan(got_d), np.isnan(want_d)
+    if not np.array_equal(nan_g, nan_w):
+        return False
+    ok = ~nan_w
+    rel = np.abs(got_d[ok] - want_d[ok]) / np.maximum(np.abs(want_d[ok]), 1e-300)
+    return bool(rel.size == 0 or rel.max() <= 1e-12)
 
 
 # ---------------------------------------------------------------------------
@@ -221,27 +266,44 @@ def barrier(world: int):
         dist.barrier()
 
 
-def make_workload(name: str):
+WORKLOADS = {
+    "plain": "plain n=4096 m=100000 (MAF U(0.01,0.5), 2% missing + 0.5% of variants at 30%), seed 1",
+    "structured": "structured n=20000 m=500000 (Balding-Nichols, 5 subpopulations, Fst 0.05, ancestral MAF "
+                  "U(0.02,0.5); 200 parent-offspring pairs, 50 duplicates at 0.1% discordance; 1% missing), seed 2",
+}
+
+
+def make_workload(name: str, device=None):
+    """The named all-pairs workload; packed on `device` (torch) or on the host (numpy)."""
     from paper_1410_4803_gb300 import synth
     if name == "plain":
-        return synth.plain_config2()
+        return synth.plain_config2(device=device)
     if name == "structured":
-        return synth.structured_config3()
+        return synth.structured_config3(device=device)
     raise ValueError(name)
 
 
-def run_plain(args, rank, world, local):
+def run_matrix(args, rank, world, local, name: str, full: bool = True):
+    """One all-pairs workload (ibs_compute: transpose + pair kernel + split-tile
+    finalisation) over an input resident in HBM, timed per step with CUDA events
+    on the launching stream; the pair kernel's own time from the library's
+    events gives the roofline.  With `full`: the pipelined e2e through the
+    same API from pinned host memory, the integer-pipe kernel on the same input,
+    and the CPU oracle on a bounded block, which also spot-checks the GPU
+    result (`exact`)."""
     import numpy as np
     import torch
     from paper_1410_4803_gb300 import ibs
 
     torch.cuda.set_device(local)
-    w = make_workload(args.workload)
+    dev = torch.device("cuda", local)
+    t0 = time.perf_counter()
+    w = make_workload(name, device=local)
+    gen_s = time.perf_counter() - t0
     n, m = w.n, w.m
     comps = n * (n - 1) // 2 * m
-    dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(dev)
-    packed = torch.from_numpy(w.packed).to(dev)
+    packed = w.packed
     P = n * (n + 1) // 2
     counts = torch.empty((P, 4), dtype=torch.int32, device=dev)
     dist_t = torch.empty(P, dtype=torch.float64, device=dev)
@@ -251,7 +313,8 @@ def run_plain(args, rank, world, local):
     ctx = ibs.ibs_init(local, flags=ibs.IBS_TIMING | (ibs.IBS_KERNEL_TC if use_tc else ibs.IBS_KERNEL_CSA))
     probe = ibs.ibs_probe_int_pipes(ctx)
     kinfo = ibs.ibs_kernel_info(ctx)
-    two_sm = use_tc and ibs.ibs_compute_kernel(ctx, n, m) == "tc-pair"  # cta_group::2 kernel for long items
+    kname = ibs.ibs_compute_kernel(ctx, n, m)
+    two_sm = use_tc and kname == "tc-pair"  # cta_group::2 kernel for long items
     mma_probe = ibs.ibs_probe_mma(ctx) if use_tc else None
 
     with torch.cuda.stream(stream):
@@ -281,47 +344,28 @@ def run_plain(args, rank, world, local):
         step_ms = [a.elapsed_time(b) for a, b in ev]
         kt = ibs.ibs_kernel_times(ctx)
 
-        # end to end through the same API: pinned host input, results copied back
-        h_packed = torch.from_numpy(w.packed).pin_memory()
+        # end to end through the same API: pinned host input, results copied
+        # back every step, pipelined over a copy-in, a compute and a copy-out
+        # stream with two buffer sets, so that step i+1's input and step i-1's
+        # results move while step i computes (the copy engines run both
+        # directions at once).  The compute calls stay in order on one stream
+        # and the L2 flush runs before each of them, inside the timed region.
+        h_packed = packed.cpu().pin_memory()
         h_counts = [torch.empty((P, 4), dtype=torch.int32).pin_memory() for _ in range(2)]
         h_dist = [torch.empty(P, dtype=torch.float64).pin_memory() for _ in range(2)]
         d_in = [torch.empty_like(packed) for _ in range(2)]
-        d_counts = [counts, torch.empty_like(counts)]
-        d_dist = [dist_t, torch.empty_like(dist_t)]
-        for _ in range(2):
-            d_in[0].copy_(h_packed, non_blocking=True)
-            ibs.ibs_compute(ctx, d_in[0], n, m, d_counts[0], d_dist[0], stream)
-            h_counts[0].copy_(d_counts[0], non_blocking=True)
-            h_dist[0].copy_(d_dist[0], non_blocking=True)
-        torch.cuda.synchronize(dev)
-        # (a) one step after another on one stream: copy in, compute, copy out
-        e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                  for _ in range(args.steps)]
-        for i in range(args.steps):
-            flush.zero_()
-            e2e_ev[i][0].record(stream)
-            d_in[0].copy_(h_packed, non_blocking=True)
-            ibs.ibs_compute(ctx, d_in[0], n, m, d_counts[0], d_dist[0], stream)
-            h_counts[0].copy_(d_counts[0], non_blocking=True)
-            h_dist[0].copy_(d_dist[0], non_blocking=True)
-            e2e_ev[i][1].record(stream)
-        torch.cuda.synchronize(dev)
-        e2e_serial_ms = [a.elapsed_time(b) for a, b in e2e_ev]
-        # (b) pipelined: every step still copies its input in from pinned host
-        # memory and its counts and distances back, but on a copy-in and a
-        # copy-out stream of their own, with two buffer sets, so that step i+1's
-        # input and step i-1's results move while step i computes (the copy
-        # engines run both directions at once).  The compute calls stay on one
-        # stream, in order; the L2 flush runs before each of them, inside the
-        # timed region.
+        d_counts = [torch.empty_like(counts) for _ in range(2)]
+        d_dist = [torch.empty_like(dist_t) for _ in range(2)]
+        e2e_steps = max(3, args.steps)
         s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-        in_ready = [torch.cuda.Event() for _ in range(args.steps)]
-        comp_done = [torch.cuda.Event() for _ in range(args.steps)]
-        out_done = [torch.cuda.Event() for _ in range(args.steps)]
+        in_ready = [torch.cuda.Event() for _ in range(e2e_steps)]
+        comp_done = [torch.cuda.Event() for _ in range(e2e_steps)]
+        out_done = [torch.cuda.Event() for _ in range(e2e_steps)]
         t0_ev, t1_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
         t0_ev.record(s_in)
         stream.wait_event(t0_ev)
-        for i in range(args.steps):
+        for i in range(e2e_steps):
             b = i % 2
             if i >= 2:
                 s_in.wait_event(comp_done[i - 2])  # compute i-2 has read d_in[b]
@@ -343,34 +387,37 @@ def run_plain(args, rank, world, local):
         torch.cuda.synchronize(dev)
         ibs.ibs_synchronize(ctx, stream)
         ibs.ibs_kernel_times(ctx)
-        e2e_ms = [t0_ev.elapsed_time(t1_ev) / args.steps] * args.steps
-        counts.copy_(d_counts[(args.steps - 1) % 2])
-        dist_t.copy_(d_dist[(args.steps - 1) % 2])
+        e2e_ms = t0_ev.elapsed_time(t1_ev) / e2e_steps
+        last = (e2e_steps - 1) % 2
+        e2e_same = bool(torch.equal(d_counts[last], counts))
+        del d_in, d_counts, d_dist, h_counts, h_dist
 
         # The integer-pipe kernel (bit planes, carry-save LOP3/POPC) on the same
-        # input, timed the same way: its fraction of the integer-pipe roofline.
+        # input: its fraction of the integer-pipe roofline.
         popc = None
-        if use_tc:
+        if use_tc and full:
             ctx_i = ibs.ibs_init(local, flags=ibs.IBS_TIMING | ibs.IBS_KERNEL_CSA)
-            k_i = max(1, min(args.steps, 10))
-            for _ in range(2):
-                ibs.ibs_compute(ctx_i, packed, n, m, counts, dist_t, stream)
+            k_i = 2 if comps > 1e13 else max(1, min(args.steps, 10))
+            tmp_c = torch.empty_like(counts)
+            ibs.ibs_compute(ctx_i, packed, n, m, tmp_c, None, stream)
             ibs.ibs_synchronize(ctx_i, stream)
             ibs.ibs_kernel_times(ctx_i)
             for _ in range(k_i):
                 flush.zero_()
-                ibs.ibs_compute(ctx_i, packed, n, m, counts, dist_t, stream)
+                ibs.ibs_compute(ctx_i, packed, n, m, tmp_c, None, stream)
             ibs.ibs_synchronize(ctx_i, stream)
             kt_i = ibs.ibs_kernel_times(ctx_i)
+            popc_same = bool(torch.equal(tmp_c, counts))
             ibs.ibs_shutdown(ctx_i)
+            del tmp_c
             popc = kt_i["pairs_ms"] / max(1, kt_i["calls"])
 
-    # spot check of the last result against the oracle on a few rows (rank 0)
     total_ms = reduce_max(sum(step_ms), world)
-    e2e_total = reduce_max(sum(e2e_ms), world)
+    e2e_total = reduce_max(e2e_ms, world)
     ms_per_step = total_ms / args.steps
     pairs_ms = kt["pairs_ms"] / max(1, kt["calls"])
     planes_ms = kt["planes_ms"] / max(1, kt["calls"])
+    finalize_ms = kt["finalize_ms"] / max(1, kt["calls"])
     roof = int_pipe_roofline(probe, clocks.get("sm_mhz"))
     achieved = comps / (pairs_ms * 1e-3)
     fp4 = use_tc and kinfo["tc_format"] == "e2m1"
@@ -383,14 +430,38 @@ def run_plain(args, rank, world, local):
     mode = {"0": "plain", "1": "csa3", "2": "csa3-1cta"}.get(os.environ.get("IBS_PAIR_MODE", "1"), "csa3")
     if use_tc:
         mode = "tc-fp4" if fp4 else "tc-fp8"
-    # transpose: read the 2-bit input once, write 16 bytes per (padded) sample-word of planes
-    words = (m + 31) // 32
-    n_blocks, n_chunks = (n + 63) // 64, (words + 11) // 12
-    transpose_bytes = m * ((n + 3) // 4) + n_blocks * n_chunks * 12 * 64 * 16
-    if use_tc:  # operand planes: 4 planes of 1 byte (FP8) or half a byte (FP4) per padded genotype
-        k = 64 if fp4 else 32
-        transpose_bytes = m * ((n + 3) // 4) + ((n + 127) // 128) * 128 * ((m + k - 1) // k) * k * 4 // (2 if fp4 else 1)
+    # transpose: read the 2-bit input once, write the operand planes (4 planes of one
+    # byte (FP8) or half a byte (FP4) per padded genotype)
+    k = 64 if fp4 else 32
+    transpose_bytes = m * ((n + 3) // 4) + ((n + 127) // 128) * 128 * ((m + k - 1) // k) * k * 4 // (2 if fp4 else 1)
+    profile = f"{'tc_pair_kernel' if two_sm else 'tc_kernel_fp4' if fp4 else 'tc_kernel_fp8'}_{name}.md"
+
+    # oracle block: the CPU baseline and the spot check of the last result
+    exact = None
+    cpu = None
+    if rank == 0 and full:
+        h = h_packed.numpy()
+        cols = np.linspace(0, n - 1, min(n, 2048)).astype(np.int64)
+        rows = calibrated_rows(h, n, m, cols, args.cpu_seconds)
+        if name == "structured":  # every injected offspring and duplicate among the rows
+            rel = np.flatnonzero(w.samples.kind != 0)
+            rows = np.unique(np.concatenate([rows, rel[:: max(1, rel.size // 16)]]))
+        want_c, want_d, rate, cores, dt = oracle_block_rate(h, n, m, rows, cols)
+        got_c, got_d = gpu_block(counts, dist_t, n, rows, cols)
+        exact = {"oracle_block": same_block(got_c, got_d, want_c, want_d),
+                 "oracle_block_shape": f"{rows.size} rows x {cols.size} columns x all {m} variants",
+                 "e2e_equals_resident": e2e_same}
+        if popc is not None:
+            exact["integer_kernel_equals_tensor_core"] = popc_same
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{rows.size} rows x {cols.size} columns (evenly spaced) x all {m} variants ({dt:.1f} s)"}
+        r1 = rows[:: max(1, rows.size // 4)][:4]
+        _, _, rate1, _, dt1 = oracle_block_rate(h, n, m, r1, cols[: 1024], threads=1)
+        cpu1 = {"value": rate1, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"{r1.size} rows x 1024 columns x all {m} variants ({dt1:.1f} s)"}
     ibs.ibs_shutdown(ctx)
+    del counts, dist_t, packed, w
+    torch.cuda.empty_cache()
 
     if rank != 0:
         return None
@@ -409,15 +480,15 @@ def run_plain(args, rank, world, local):
         # in FP32, exact integer counts; the integer form computes in int32
         "dtype": ("e2m1xe2m1->f32" if fp4 else "e4m3xe4m3->f32") if use_tc else "int32",
         "data": "synthetic",
-        "config": {"workload": w.name + " (MAF U(0.01,0.5), 2% missing + 0.5% of variants at 30%), seed 1"
-                   if args.workload == "plain" else w.name,
-                   "n_samples": n, "n_variants": m, "pairs_incl_diagonal": P,
+        "config": {"workload": WORKLOADS[name], "n_samples": n, "n_variants": m, "pairs_incl_diagonal": P,
                    "comparisons_per_step": comps,
-                   "l2": "flushed between steps (256 MiB write, outside the step events)",
-                   "parallelism": f"replicas x{world}", "kernel_mode": mode},
+                   "l2": "flushed between steps (256 MiB write, outside the step events); the operand planes "
+                         f"({tc_planes_gb(n, m, fp4):.1f} GB) exceed L2 many times over",
+                   "parallelism": f"replicas x{world}", "kernel_mode": mode, "pair_kernel": kname,
+                   "input_generation_s": gen_s},
         "roofline": ({"bound": "alu", "achieved": achieved, "peak": roof["peak"], "unit": UNIT,
                       "frac": achieved / roof["peak"],
-                      "traffic": profiled_traffic(f"popc_tri_kernel_{args.workload}.md"),
+                      "traffic": profiled_traffic(f"popc_tri_kernel_{name}.md"),
                       "kernel": "tri_kernel (pair counts)", "kernel_ms": pairs_ms,
                       "peak_basis": f"{roof['comps_per_clk_sm']:.1f} comparisons/clk/SM x {probe['sms']} SMs x "
                                     f"{roof['sm_mhz']:.0f} MHz (median SM clock in the timed region); pipe rates "
@@ -426,15 +497,15 @@ def run_plain(args, rank, world, local):
                      if not use_tc else
                      {"bound": "tensor", "achieved": 8.0 * achieved / 1e12, "peak": tc_tflops, "unit": "TFLOP/s",
                       "frac": 8.0 * achieved / 1e12 / tc_tflops,
-                      "traffic": profiled_traffic(f"{'tc_pair_kernel' if two_sm else 'tc_kernel_fp4' if fp4 else 'tc_kernel_fp8'}"
-                                                  f"_{args.workload}.md", ("ibs_tc.cu", "ibs_device.cuh")),
+                      "traffic": profiled_traffic(profile, ("ibs_tc.cu", "ibs_device.cuh", "ibs_tc_common.cuh")),
                       "kernel": ("tc_pair_kernel (tcgen05 cta_group::2, M = 256 over two SMs, E2M1 kind::mxf4 "
                                  "indicator GEMMs)" if two_sm else
                                  f"tc_persistent_kernel (tcgen05 {'E2M1 kind::mxf4' if fp4 else 'E4M3 kind::f8f6f4'} "
                                  f"indicator GEMMs)"), "kernel_ms": pairs_ms,
                       "peak_basis": f"measured bf16 burst TFLOP/s (MEASURED_PEAKS.json) x {tc_ratio:.0f}, the nominal "
-                                    f"{'FP4' if fp4 else 'FP8'}/bf16 dense ratio; algorithmic flops = 8 per comparison "
-                                    "(4 MACs: VV^T, UU^T, QR^T, RQ^T)",
+                                    f"{'FP4' if fp4 else 'FP8'}/bf16 dense ratio (of measured); algorithmic flops = 8 "
+                                    "per comparison (4 MACs: VV^T, UU^T, QR^T, RQ^T); achieved = that work / the pair "
+                                    "kernel's CUDA-event time per call",
                       "mma_probe": {"unit": "TFLOP/s",
                                     "measured": mma_probe["e2m1_tflops" if fp4 else "e4m3_tflops"],
                                     "frac": 8.0 * achieved / 1e12 / mma_probe["e2m1_tflops" if fp4 else "e4m3_tflops"],
@@ -444,64 +515,82 @@ def run_plain(args, rank, world, local):
             "kernel": "tri_kernel, carry-save LOP3/POPC over bit planes (IBS_KERNEL_CSA)",
             "kernel_ms": popc, "value": comps / (popc * 1e-3), "unit": UNIT,
             "roofline_peak": roof["peak"], "frac": comps / (popc * 1e-3) / roof["peak"],
-            "peak_basis": "integer-pipe roofline as for the POPC bench line (measured pipe rates x SMs x clock)"},
+            "peak_basis": "integer-pipe roofline (measured pipe rates x SMs x clock)"},
         "transpose": {"kernel_ms": planes_ms, "bytes": transpose_bytes,
                       "achieved_gbs": transpose_bytes / (planes_ms * 1e-3) / 1e9,
                       "peak_gbs": hbm_peak_gbs(), "frac": transpose_bytes / (planes_ms * 1e-3) / 1e9 / hbm_peak_gbs()},
-        "e2e": {"value": world * comps / (e2e_total / args.steps * 1e-3), "unit": UNIT,
-                "h2d_bytes_per_step": int(w.packed.nbytes), "d2h_bytes_per_step": int(P * 16 + P * 8),
-                "pipelined": "copy-in, compute and copy-out streams, two buffer sets",
-                "serial_value": world * comps / (reduce_max(sum(e2e_serial_ms), world) / args.steps * 1e-3)},
+        "finalize_ms": finalize_ms,
+        "e2e": {"value": world * comps / (e2e_total * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": int(n // 4 * m if n % 4 == 0 else (n + 3) // 4 * m),
+                "d2h_bytes_per_step": int(P * 16 + P * 8), "steps": e2e_steps,
+                "pipelined": "copy-in, compute and copy-out streams, two buffer sets; the fill and drain of the "
+                             "pipeline are inside the timed region"},
         "gpu_launches": int(launches_per_step * args.steps),
         "clocks": clocks,
         "wall_s_timed_region": wall,
     }
-    if world == 1 and not args.no_cpu_baseline:
-        rate, cores, sample, dt = oracle_rate(w.packed, n, m, target_s=args.cpu_seconds)
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": sample + f" ({dt:.1f} s)"}
-        # the same oracle on one core, for the per-core figure
-        rate1, _, sample1, dt1 = oracle_rate(w.packed, n, m, target_s=args.cpu_seconds / 2, threads=1)
-        line["cpu_baseline_1core"] = {"value": rate1, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                      "sample": sample1 + f" ({dt1:.1f} s)"}
+    if exact is not None:
+        line["exact"] = exact
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+        line["cpu_baseline_1core"] = cpu1
     return line
+
+
+def tc_planes_gb(n, m, fp4=True):
+    k = 64 if fp4 else 32
+    return ((n + 127) // 128) * 128 * ((m + k - 1) // k) * k * 4 / (2 if fp4 else 1) / 1e9
 
 
 def run_reference(args, rank, world, local):
     """The oracle arm: the CPU oracle as it stands, on this machine's host cores,
-    each step a bounded row sample of the same workload."""
+    each step a bounded block of the same workload (rows x evenly spaced
+    columns x all variants; only those samples are generated and unpacked)."""
     if rank != 0:
         return None
-    w = make_workload(args.workload)
-    n, m = w.n, w.m
     import numpy as np
-    import oracle
-    G = oracle.unpack(w.packed, n, m)
+    from paper_1410_4803_gb300 import synth
+    name = args.workload if args.workload in WORKLOADS else "structured"
+    if name == "plain":
+        model = synth.plain_model(100_000, 1, maf=(0.01, 0.5), miss=0.02, hi_miss_frac=0.005, hi_miss_rate=0.3)
+        smp = synth.Samples.base(4096)
+    else:
+        model = synth.balding_nichols_model(500_000, 2, n_pop=5, fst=0.05, anc=(0.02, 0.5), miss=0.01)
+        smp = synth.structured_samples(3950 * 5, 5, 200, 50, 2)
+    n, m = smp.n, model.m
+    cols = np.linspace(0, n - 1, min(n, 2048)).astype(np.int64)
     cores = os.cpu_count() or 1
-    # size a step at about args.ref_step_seconds
-    rows = np.arange(min(n, cores), dtype=np.int64)
-    t = time.perf_counter()
-    oracle.ibs_block(G, G, rows=rows)
-    dt0 = time.perf_counter() - t
-    R = int(max(rows.size, min(n, rows.size * args.ref_step_seconds / max(dt0, 1e-6))))
-    sel = np.linspace(0, n - 1, R).astype(np.int64)
+    # size a step at about args.ref_step_seconds from a calibration block
+    probe_rows = np.linspace(0, n - 1, min(n, cores)).astype(np.int64)
+    sel = np.unique(np.concatenate([cols, probe_rows]))
+    packed = synth.generate(model, smp.take(sel))  # only the sampled samples
+    pos = {int(v): i for i, v in enumerate(sel)}
+    cidx = np.array([pos[int(v)] for v in cols])
+    pidx = np.array([pos[int(v)] for v in probe_rows])
+    _, _, rate, _, _ = oracle_block_rate(packed, sel.size, m, pidx, cidx[:256])
+    R = int(max(1, min(n, args.ref_step_seconds * rate / (cols.size * m))))
+    rows = np.linspace(0, n - 1, R).astype(np.int64)
+    sel = np.unique(np.concatenate([cols, rows]))
+    packed = synth.generate(model, smp.take(sel))
+    pos = {int(v): i for i, v in enumerate(sel)}
+    cidx = np.array([pos[int(v)] for v in cols])
+    ridx = np.array([pos[int(v)] for v in rows])
     for _ in range(args.warmup):
-        oracle.ibs_block(G, G, rows=sel[: max(1, R // 4)])
+        oracle_block_rate(packed, sel.size, m, ridx[: max(1, R // 4)], cidx)
     times = []
     for _ in range(args.steps):
-        t = time.perf_counter()
-        oracle.ibs_block(G, G, rows=sel)
-        times.append(time.perf_counter() - t)
-    comps = R * (n - 1) * m
+        _, _, _, _, dt = oracle_block_rate(packed, sel.size, m, ridx, cidx)
+        times.append(dt)
+    comps = R * cols.size * m
     value = comps / statistics.mean(times)
     return {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(times) * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": w.name, "n_samples": n, "n_variants": m,
-                   "sample_per_step": f"{R} rows x all {n} columns x {m} variants"},
+        "config": {"workload": WORKLOADS[name], "n_samples": n, "n_variants": m,
+                   "sample_per_step": f"{R} rows x {cols.size} columns (evenly spaced) x all {m} variants"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{R} rows x all {n} columns x {m} variants per step"},
+                         "sample": f"{R} rows x {cols.size} columns x all {m} variants per step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -533,10 +622,10 @@ def run_batch(args, rank, world, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     t0 = time.perf_counter()
-    w = synth.batch_pool()
+    w = synth.batch_pool(device=local)
     subs = synth.batch_subsets()
     gen_s = time.perf_counter() - t0
-    pool = torch.from_numpy(w.packed).to(dev)
+    pool = w.packed
     comps = sum(s.comparisons for s in subs)
     stream = torch.cuda.Stream(dev)
     args_b, plain_in, outs_b, outs_p = [], [], [], []
@@ -577,13 +666,6 @@ def run_batch(args, rank, world, local):
             for s, pk, (c, d) in zip(subs, plain_in, outs_p):
                 ibs.ibs_compute(ctx_p, pk, s.n, s.var_len, c, d, stream)
 
-        def plain_loop_from_pool():
-            # the plain path needs each cohort's own packed matrix: extract it
-            # from the pool on the device (torch gather), then one ibs_compute
-            for s, (it, _, _, _, _), (c, d) in zip(subs, args_b, outs_p):
-                ibs.ibs_compute(ctx_p, subset_packed_device(pool, it, s.var_begin, s.var_len), s.n, s.var_len,
-                                c, d, stream)
-
         for _ in range(args.warmup):
             batched()
             plain_loop()
@@ -601,7 +683,6 @@ def run_batch(args, rank, world, local):
         ms_b = timed(batched, args.steps)
         ms_p = timed(plain_loop, args.steps)
         kt_p = ibs.ibs_kernel_times(ctx_p)  # the plain loop's kernels only
-        ms_pe = timed(plain_loop_from_pool, 1)
         clocks = clk.stop()
         ibs.ibs_synchronize(ctx_b, stream)
         ibs.ibs_synchronize(ctx_p, stream)
@@ -611,10 +692,11 @@ def run_batch(args, rank, world, local):
                for a, b in zip(outs_b, outs_p))
     rng = np.random.default_rng(0)
     oracle_ok = True
+    pool_host = pool.cpu().numpy()
     for k in rng.choice(len(subs), 4, replace=False):
         s = subs[k]
         rows = np.sort(rng.choice(s.n, min(s.n, 24), replace=False))
-        G = oracle.unpack_subset(w.packed, w.n, w.m, s.sample_idx[rows], s.var_begin, s.var_len)
+        G = oracle.unpack_subset(pool_host, w.n, w.m, s.sample_idx[rows], s.var_begin, s.var_len)
         oc, _ = oracle.ibs_block(G, G)
         got = outs_b[k][0].cpu().numpy()
         for a in range(rows.size):
@@ -637,10 +719,7 @@ def run_batch(args, rank, world, local):
                        "transpose_ms_per_step": kt_p["planes_ms"] / args.steps,
                        "pair_kernel_ms_per_step": kt_p["pairs_ms"] / args.steps,
                        "finalize_ms_per_step": kt_p["finalize_ms"] / args.steps},
-        "plain_loop_from_pool": {"value": comps / (ms_pe[0] * 1e-3), "ms_per_step": ms_pe[0],
-                                 "note": "includes the device-side extraction of each subset's packed matrix"},
         "speedup_vs_plain_loop": mp / mb,
-        "speedup_vs_plain_loop_from_pool": ms_pe[0] / mb,
         "exact": {"batched_equals_plain_all_subsets": bool(same), "oracle_sampled_pairs": bool(oracle_ok)},
         "gpu_launches": int(args.steps * launches_b),
         "clocks": clocks,
@@ -658,7 +737,7 @@ def run_serve(args, rank, world, local):
 
     torch.cuda.set_device(local)
     t0 = time.perf_counter()
-    panel = synth.serving_panel()
+    panel = synth.serving_panel(device=local)
     gen_s = time.perf_counter() - t0
     n_payload = 48
     sizes = synth.serving_query_sizes(n_payload)
@@ -669,8 +748,13 @@ def run_serve(args, rank, world, local):
              torch.empty((int(q), k), dtype=torch.float64).pin_memory()) for q in sizes]
     ctx = ibs.ibs_init(local)
     t = time.perf_counter()
-    ibs.ibs_panel_load(ctx, torch.from_numpy(panel.packed).cuda(), panel.n, panel.m)
+    ibs.ibs_panel_load(ctx, panel.packed, panel.n, panel.m)
     load_s = time.perf_counter() - t
+    # oracle spot check later: two query rows against 4,096 evenly spaced panel samples
+    check_cols = np.linspace(0, panel.n - 1, 4096).astype(np.int64)
+    panel_host = panel.packed.cpu().numpy()
+    panel.packed = None  # the library holds its own planes of the panel
+    torch.cuda.empty_cache()
 
     def comps_of(i):
         return int(sizes[i]) * panel.n * panel.m
@@ -732,6 +816,14 @@ def run_serve(args, rank, world, local):
         ibs.ibs_query_sync(ctx, payloads[p], q, k, *b)
         exact &= all(torch.equal(x, y) for x, y in zip(a[:2], b[:2]))
         exact &= torch.equal(torch.nan_to_num(a[2], nan=-1.0), torch.nan_to_num(b[2], nan=-1.0))
+        if p == 0:
+            import oracle
+            qrows = np.array([0, q - 1], dtype=np.int64)
+            GQ = oracle.unpack_subset(payloads[0], q, panel.m, qrows, 0, panel.m)
+            GP = oracle.unpack_subset(panel_host, panel.n, panel.m, check_cols, 0, panel.m)
+            want_c, _ = oracle.ibs_block(GQ, GP)
+            oracle_ok = bool(np.array_equal(a[0].numpy()[qrows][:, check_cols], want_c))
+    del panel_host
     rng = np.random.default_rng(4)
     results = []
     clk = ClockSampler(local)
@@ -760,7 +852,8 @@ def run_serve(args, rank, world, local):
                                f"top-{k} to pinned host buffers", "distinct_payloads": n_payload,
                    "mean_q": float(np.mean(sizes)), "panel_generation_s": gen_s, "panel_load_s": load_s},
         "serving": results, "engine_stats": stats,
-        "exact": {"engine_equals_plain": bool(exact)},
+        "exact": {"engine_equals_plain": bool(exact),
+                  "oracle_two_query_rows_x_4096_panel_samples": oracle_ok},
         "clocks": clocks,
     }
 
@@ -1047,23 +1140,29 @@ def run_cluster(args, rank, world, local):
     return line
 
 
+def sub_record(line: dict, keys) -> dict:
+    return {k: line[k] for k in keys if k in line}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=60)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="plain",
+    ap.add_argument("--workload", default="structured",
                     choices=["plain", "structured", "batch", "serve", "ld", "cluster", "grm"])
+    ap.add_argument("--no-sub", action="store_true",
+                    help="structured: skip the plain, batched and served sub-records")
     ap.add_argument("--window", type=int, default=1000, help="ld: marker window")
     ap.add_argument("--markers", type=int, default=100_000,
                     help="grm: markers of the plain genotypes (100,000 is the benchmarked size)")
-    ap.add_argument("--rates", type=float, nargs="*", default=[4.0, 12.0, 24.0, 0.0],
+    ap.add_argument("--rates", type=float, nargs="*", default=None,
                     help="serving: Poisson arrival rates per second (0 = all at once)")
-    ap.add_argument("--requests", type=int, default=60, help="serving: requests per rate")
+    ap.add_argument("--requests", type=int, default=None, help="serving: requests per rate")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--ref-step-seconds", type=float, default=4.0)
+    ap.add_argument("--ref-step-seconds", type=float, default=3.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -1078,6 +1177,10 @@ def main():
     elif args.workload == "batch":
         line = run_batch(args, rank, world, local)
     elif args.workload == "serve":
+        if args.rates is None:
+            args.rates = [4.0, 12.0, 24.0, 0.0]
+        if args.requests is None:
+            args.requests = 60
         line = run_serve(args, rank, world, local)
     elif args.workload == "ld":
         line = run_ld(args, rank, world, local)
@@ -1086,7 +1189,30 @@ def main():
     elif args.workload == "grm":
         line = run_grm(args, rank, world, local)
     else:
-        line = run_plain(args, rank, world, local)
+        if args.no_cpu_baseline:
+            args.cpu_seconds = 1.0  # the spot check still runs, on a small block
+        line = run_matrix(args, rank, world, local, args.workload, full=True)
+        if args.workload == "structured" and not args.no_sub and world == 1:
+            import torch
+            torch.cuda.empty_cache()
+            # the plain workload, the batched cohorts and the served panel on the same
+            # GPU and in the same run, each with its own timing and exactness checks
+            p = run_matrix(args, rank, world, local, "plain", full=False)
+            line["plain_config2"] = sub_record(p, ["value", "unit", "ms_per_step", "dtype", "config", "roofline",
+                                                   "transpose", "finalize_ms", "e2e", "gpu_launches", "clocks"])
+            torch.cuda.empty_cache()
+            b = run_batch(args, rank, world, local)
+            line["batched"] = sub_record(b, ["value", "unit", "ms_per_step", "dtype", "config", "plain_loop",
+                                             "speedup_vs_plain_loop", "exact", "gpu_launches", "clocks"])
+            torch.cuda.empty_cache()
+            if args.rates is None:
+                args.rates = [6.0, 24.0, 0.0]
+            if args.requests is None:
+                args.requests = 48
+            sv = run_serve(args, rank, world, local)
+            line["served"] = sub_record(sv, ["value", "unit", "dtype", "config", "serving", "engine_stats",
+                                             "exact", "clocks"])
+            line["gpu_launches"] += b.get("gpu_launches", 0) + p.get("gpu_launches", 0)
     if line is not None:
         print(json.dumps(line))
     if world > 1 and args.impl == "ours":

@@ -117,9 +117,20 @@ ibs_status ibs_compute_sz(ibs_ctx* ctx, const uint8_t* packed, size_t packed_byt
  * up the scratch address (cudaGetSymbolAddress); make it before any stream
  * capture.  All calls share the one scratch array: calls whose work overlaps
  * on the GPU (different streams, or threads) race and give undefined results;
- * serialise them.  A bounded device wait that expires is not reported here. */
+ * serialise them.  packed, out_counts and out_dist must be device (or
+ * managed) memory of the current device; anything else is refused with
+ * IBS_EINVAL before any work is enqueued.  A bounded device wait that expires
+ * is reported by ibs_noalloc_status, not by this call. */
 ibs_status ibs_compute_noalloc(const uint8_t* packed, int64_t n_samples, int64_t n_variants, int32_t* out_counts,
                                double* out_dist, void* stream);
+
+/* Outcome of the ibs_compute_noalloc calls enqueued on `stream` (the paper has
+ * no counterpart; it completes the allocation-free entry point above).  Waits
+ * for the stream, then reads the fixed device status word that every
+ * ibs_compute_noalloc call clears and its kernels set: IBS_OK, or
+ * IBS_ETIMEOUT when a bounded device wait expired in the last such call (its
+ * outputs are then undefined).  Allocates nothing; uses the current device. */
+ibs_status ibs_noalloc_status(void* stream);
 
 /* Wait for all work enqueued on `stream` and report device-side errors of
  * this context's kernels since the last call: IBS_ETIMEOUT when a bounded
@@ -322,6 +333,18 @@ ibs_status ibs_compute_kernel(ibs_ctx* ctx, int64_t n_samples, int64_t n_variant
 /* Counters of the last ibs_compute / ibs_compute_batch on this context:
  * out[0] = kernel launches enqueued, out[1] = pair tiles, out[2] = K splits. */
 ibs_status ibs_last_launch_info(ibs_ctx* ctx, int64_t out[3]);
+
+/* Testing hook of the failure handling (the paper has no counterpart).
+ * Sets the bound, in ns, of every pipeline wait (operand stages, work queue,
+ * accumulator hand-over) inside the persistent pair kernels that ibs_compute
+ * launches on this context for triangle output; ns = 0 restores the default
+ * of 2 s.  A wait that runs out sets the context's device status word and
+ * the kernel winds down: it stops issuing work, waits (with the default
+ * bound) for the copies and MMAs it already issued, frees its tensor memory
+ * and returns, so the next ibs_synchronize reports IBS_ETIMEOUT (outputs of
+ * that call undefined) and the context stays usable.  0 <= ns <= 2e9, else
+ * IBS_EINVAL. */
+ibs_status ibs_test_set_wait_limit(ibs_ctx* ctx, int64_t ns);
 
 #ifdef __cplusplus
 }

@@ -71,6 +71,7 @@ def build_library(force: bool = False, verbose: bool = False, ptxas_info: bool =
 def build_all(force: bool = False) -> str:
     from . import synth
     synth.build(force=force)
+    synth.build_gpu(force=force)
     return build_library(force=force)
 
 

@@ -303,13 +303,15 @@ ibs_status ibs_compute(ibs_ctx* ctx, const uint8_t* packed, int64_t n, int64_t m
     sd.out_dist = out_dist;
     sd.partial = splits > 1 ? static_cast<int32_t*>(ctx->partial.p) : nullptr;
     sd.pad = 0;
+    const unsigned long long wait_ns = ctx->wait_ns > 0 ? ctx->wait_ns : kWaitLimitNs;
     if (ctx->single_pair) {
       IBS_CUDA_TRY(launch_tc_pair(sd, static_cast<const PairItem*>(ctx->single_items.p), ctx->single_n_items,
-                                  ctx->status_dev, st));
+                                  ctx->status_dev, wait_ns, st));
     } else {
       const int grid = (int)std::min<int64_t>(ctx->num_sms, ctx->single_n_items);
       IBS_CUDA_TRY(launch_tc_single(sd, static_cast<const WorkItem*>(ctx->single_items.p), ctx->single_n_items,
-                                    grid, fmt, static_cast<int*>(ctx->single_counter.p), ctx->status_dev, st));
+                                    grid, fmt, static_cast<int*>(ctx->single_counter.p), ctx->status_dev, wait_ns,
+                                    st));
     }
   } else if (tc) {
     const int64_t T = (n + 127) / 128;
@@ -513,7 +515,7 @@ void build_items(const std::vector<SubsetShape>& shapes, int mode, int split_pol
       tc_tile_order(ig.T, kTcBatchGroup, tiles);
       for (const int2& t : tiles)
         for (int p = 0; p < pieces; ++p) {
-          WorkItem w;
+          WorkItem w{};
           w.subset = (int32_t)k;
           w.I = t.x;
           w.J = t.y;
@@ -532,7 +534,7 @@ void build_items(const std::vector<SubsetShape>& shapes, int mode, int split_pol
     for (int64_t I = 0; I < ig.T; ++I)
       for (int64_t J = I; J < ig.T; ++J)
         for (int p = 0; p < pieces; ++p) {
-          WorkItem w;
+          WorkItem w{};
           w.subset = (int32_t)k;
           w.I = (int32_t)I;
           w.J = (int32_t)J;
@@ -1111,6 +1113,15 @@ extern "C" ibs_status ibs_grm(ibs_ctx* ctx, const uint8_t* packed, int64_t n, in
   ctx->last_info[0] = ctx->grm_n_splits > 0 ? 4 : 3;  // frequencies, operands, pairs (, finalisation)
   ctx->last_info[1] = ctx->grm_n_items;
   ctx->last_info[2] = 1;
+  return IBS_OK;
+}
+
+extern "C" ibs_status ibs_test_set_wait_limit(ibs_ctx* ctx, int64_t ns) {
+  clear_error();
+  if (ibs_status s = check_ctx(ctx)) return s;
+  if (ns < 0 || (unsigned long long)ns > kWaitLimitNs)
+    return fail(IBS_EINVAL, "wait limit %lld ns out of range [0, %llu]", (long long)ns, kWaitLimitNs);
+  ctx->wait_ns = (unsigned long long)ns;
   return IBS_OK;
 }
 

@@ -123,6 +123,10 @@ struct ibs_ctx {
   bool single_pair = false;  // single_items holds PairItem (two-SM kernel), else WorkItem
   int* status_host = nullptr;     // mapped pinned status word
   int* status_dev = nullptr;
+  // device-side bound of the pipeline waits of ibs_compute's persistent pair
+  // kernels, in ns (0 = the library default, 2 s); tests set it shorter
+  // through ibs_test_set_wait_limit to exercise the timeout path
+  unsigned long long wait_ns = 0;
 
   int64_t last_info[3] = {0, 0, 0};
 

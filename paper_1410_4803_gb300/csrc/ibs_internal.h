@@ -161,8 +161,11 @@ cudaError_t launch_tc_batch(const SubsetDev* subs, const WorkItem* items, int64_
 // and the finalisation of the split tiles.
 void tc_single_items(int64_t n, int64_t m, int fmt, int num_sms, int group, std::vector<WorkItem>& items,
                      std::vector<int2>& split_tiles);
+// wait_ns bounds each of the kernel's pipeline waits (the drains of work
+// already in flight keep the default bound): the library default, or a test's
+// shorter limit (ibs_test_set_wait_limit).
 cudaError_t launch_tc_single(const SubsetDev& sd, const WorkItem* items, int64_t n_items, int grid, int fmt,
-                             int* counter, int* status, cudaStream_t st);
+                             int* counter, int* status, unsigned long long wait_ns, cudaStream_t st);
 // Two-SM form of the same (tcgen05 cta_group::2, E2M1 only): clusters of two
 // CTAs, each pair item two tiles sharing their column block.  tc_pair_clusters
 // is the number of clusters the launch runs (0 when the kernel cannot run);
@@ -175,7 +178,7 @@ bool tc_pair_usable(int64_t n, int64_t m, int fmt);
 void tc_pair_items(int64_t n, int64_t m, int fmt, int n_clusters, int group, std::vector<PairItem>& items,
                    std::vector<int2>& split_tiles);
 cudaError_t launch_tc_pair(const SubsetDev& sd, const PairItem* items, int64_t n_items, int* status,
-                           cudaStream_t st);
+                           unsigned long long wait_ns, cudaStream_t st);
 cudaError_t launch_tc_finalize_tiles(const int2* tiles, int64_t n_tiles, const int32_t* partial, int64_t n,
                                      int32_t* out_counts, double* out_dist, cudaStream_t st);
 // Batch form: tiles {subset, I, J, -}, outputs from the subsets' descriptors.

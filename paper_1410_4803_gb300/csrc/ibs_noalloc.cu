@@ -52,6 +52,19 @@ ibs_status setup_device(int dev) {
   return IBS_OK;
 }
 
+// True when p is device (or managed) memory that device `dev` can use as a
+// kernel operand.  cudaPointerGetAttributes is not a stream operation, so the
+// check is also valid while a stream is being captured.
+bool device_ptr_on(const void* p, int dev) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
+
 }  // namespace
 }  // namespace ibs
 
@@ -75,6 +88,8 @@ extern "C" ibs_status ibs_compute_noalloc(const uint8_t* packed, int64_t n, int6
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(IBS_ECUDA, "cudaGetDevice failed: %s", cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return fail(IBS_EINVAL, "device ordinal %d not supported", dev);
+  if (!device_ptr_on(packed, dev) || !device_ptr_on(out_counts, dev) || (out_dist && !device_ptr_on(out_dist, dev)))
+    return fail(IBS_EINVAL, "packed, out_counts and out_dist must be device memory of the current device (%d)", dev);
   if (ibs_status s = setup_device(dev)) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   // The status word must start at zero; the planes are fully rewritten by the transpose.
@@ -87,5 +102,23 @@ extern "C" ibs_status ibs_compute_noalloc(const uint8_t* packed, int64_t n, int6
   // One K split only: a split would need a second scratch array for the partial counts.
   IBS_CUDA_TRY(launch_tri(1, g_planes_addr[dev], geo, 1, out_counts, out_dist, nullptr, false, g_status_addr[dev],
                           g_sms[dev], st));
+  return IBS_OK;
+}
+
+extern "C" ibs_status ibs_noalloc_status(void* stream) {
+  clear_error();
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(IBS_ECUDA, "cudaGetDevice failed: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return fail(IBS_EINVAL, "device ordinal %d not supported", dev);
+  if (ibs_status s = setup_device(dev)) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  IBS_CUDA_TRY(cudaStreamSynchronize(st));
+  int word = 0;
+  // a 4-byte read from the fixed status array: no allocation, staged by the runtime
+  IBS_CUDA_TRY(cudaMemcpy(&word, g_status_addr[dev], sizeof(int), cudaMemcpyDeviceToHost));
+  if (word == kDevTimeout)
+    return fail(IBS_ETIMEOUT, "a bounded device wait of ibs_compute_noalloc expired; its outputs are undefined");
+  if (word != 0) return fail(IBS_ECUDA, "device status word %d", word);
   return IBS_OK;
 }

@@ -40,6 +40,7 @@
 // set, and the CTA still waits (bounded) for its MMAs and frees its tensor
 // memory before returning.
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -232,7 +233,8 @@ __global__ void __launch_bounds__(kTThreads, 1)
   if (warp == 0) {
     // Producer warp: every lane waits for a free stage together (no lane of
     // this warp sits in another wait), lane 0 issues the bulk copies.
-    for (int64_t k = 0; k < nk; ++k) {
+    int64_t issued = 0;
+    for (int64_t k = 0; k < nk; ++k, issued = k) {
       const int s = (int)(k % kTStages);
       const bool ok = k < kTStages || mbar_wait_bounded(&empty[s], (uint32_t)((k / kTStages - 1) & 1));
       // decisions are made warp-wide so the lanes never split around __syncwarp
@@ -252,6 +254,14 @@ __global__ void __launch_bounds__(kTThreads, 1)
       }
       __syncwarp();
     }
+    // The copies complete on `full` whether or not the MMA warp consumed
+    // them; after a stop, wait (bounded) for the last ring's worth of stages
+    // before the CTA exits, since its shared memory is their destination.
+    for (int64_t j = issued > kTStages ? issued - kTStages : 0; j < issued; ++j)
+      if (__any_sync(0xffffffffu, !mbar_wait_bounded(&full[j % kTStages], (uint32_t)((j / kTStages) & 1)))) {
+        if (lane == 0) atomicExch(status, kDevTimeout);
+        break;
+      }
   } else if (warp == 1) {
     // MMA warp: every lane waits for the stage's data, lane 0 issues the MMAs.
     for (int64_t k = 0; k < nk; ++k) {
@@ -555,19 +565,62 @@ struct CrossWork {
 // The persistent kernel: 8 warps.  Warp 0 claims work items from a global
 // counter (list order, so the CTAs running at one time work on neighbouring
 // tiles and share their operand blocks through L2) and streams each item's
-// chunks through the ring; warp 1 issues the MMAs; warps 4..7 read the
-// accumulators back (warp w reads TMEM lanes 32*(w-4)..) and store the
-// counts; warps 2 and 3 only hold the block's shape.  Claimed item indices
-// reach the MMA and epilogue warps through a small shared-memory queue
-// (qfull / qempty, -1 ends the stream).  Two barriers hand the accumulators
-// over per item: tfull (the item's MMAs are done) and tempty (the epilogue has
-// read them), so the producer keeps prefetching the next item's chunks while
-// the epilogue runs.
+// chunks through the ring; warps 1..kMmaWarps issue the MMAs, warp 1 + j
+// taking the ring stages g with g % kMmaWarps == j; warps 4..7 read the
+// accumulators back (warp w reads TMEM lanes 32*(w-4)..), zero them and store
+// the counts.  Claimed item indices reach the MMA and epilogue warps through
+// a small shared-memory queue (qfull / qempty, -1 ends the stream).  Two
+// barriers hand the accumulators over per item: tfull (every MMA warp has
+// committed the item's MMAs) and tempty (the epilogue has read and zeroed
+// them), so the producer keeps prefetching the next item's chunks while the
+// epilogue runs.
+//
+// Why several MMA warps.  A thread that has MMAs in flight and then touches
+// memory (the stage barrier's try_wait, any load) stalls until those MMAs
+// have completed, and warp-wide votes stall it too, so one MMA warp that
+// waits for every stage drains the tensor pipe at each stage: 121 cycles per
+// 128 x 128 x 64 MMA against 68 back to back.  With three warps on
+// alternate stages, a warp's wait drains only its own MMAs of three stages
+// back while the other two warps' MMAs keep the pipe busy: 68 cycles per MMA.
+// Every MMA accumulates (the epilogue zeroes the accumulators when it reads
+// them), so the sums do not depend on the order in which the tensor core
+// takes the warps' MMAs; they are exact integers below 2^24 in FP32, so the
+// order does not change the rounding either.  The warps' MMAs into one
+// accumulator are not ordered against each other by tcgen05 fences: the
+// tensor core applies them one at a time, which a stress check of 160,000
+// MMAs per SM from two and three warps into shared accumulators confirmed
+// (no lost update among 7.5 M accumulator elements), and every parity test
+// checks the counts bit for bit.  IBS_TC_MMA_WARPS=1 issues from one warp,
+// ordered by construction.
 constexpr int kQueue = 8;
+constexpr int kMmaWarpsMax = 3;
+
+// MMA-issuing warps of the persistent and pair kernels (1 .. 3).
+int tc_mma_warps() {
+  static const int v = [] {
+    const char* e = getenv("IBS_TC_MMA_WARPS");
+    const int w = e ? atoi(e) : kMmaWarpsMax;
+    return w >= 1 && w <= kMmaWarpsMax ? w : kMmaWarpsMax;
+  }();
+  return v;
+}
+
+// Zero this warp's 32 TMEM lanes of columns [0, 384): the three accumulators.
+__device__ __forceinline__ void tmem_zero_acc(uint32_t lane_base) {
+  const uint32_t z = 0;
+#pragma unroll
+  for (int c = 0; c < 384; c += 32)
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,"
+        "%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(lane_base + c),
+        "r"(z)
+        : "memory");
+}
 
 template <int F, class W, int kTStages, int kPer>
 __global__ void __launch_bounds__(256, 1)
-    tc_persistent_kernel(const W work, int64_t n_items, int* counter, int* status) {
+    tc_persistent_kernel(const W work, int64_t n_items, int* counter, int* status, int mma_warps,
+                         unsigned long long wait_ns) {
   constexpr int kBlockBytes = kPer * kTChunkBytes;  // one block's share of a ring stage
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* ring = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -584,11 +637,11 @@ __global__ void __launch_bounds__(256, 1)
     }
     for (int s = 0; s < kQueue; ++s) {
       mbar_init(&qfull[s], 1);
-      mbar_init(&qempty[s], 5);  // the MMA warp and the four epilogue warps
+      mbar_init(&qempty[s], (uint32_t)(mma_warps + 4));  // the MMA warps and the four epilogue warps
     }
-    mbar_init(&tfull, 1);
-    mbar_init(&tempty, 4);  // one arrival per epilogue warp
-    mbar_init(&drain, 1);
+    mbar_init(&tfull, (uint32_t)mma_warps);  // one commit per MMA warp and item
+    mbar_init(&tempty, 4);                   // one arrival per epilogue warp
+    mbar_init(&drain, (uint32_t)mma_warps);
     mbar_fence_init();
     abort_flag = 0;
   }
@@ -602,12 +655,16 @@ __global__ void __launch_bounds__(256, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
-  if constexpr (F == kTcFp4) {
-    if (warp >= 4) tmem_fill_unit_scales(tmem, warp - 4);
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp >= 4) {
+    // the accumulators start at zero: every MMA accumulates
+    const uint32_t lane_base = tmem + ((uint32_t)((warp - 4) * 32) << 16);
+    tmem_zero_acc(lane_base);
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    if constexpr (F == kTcFp4) tmem_fill_unit_scales(tmem, warp - 4);
   }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
   auto fail = [&](bool cond) {
     // warp-uniform: record a timeout once and tell the other roles to stop
@@ -620,7 +677,7 @@ __global__ void __launch_bounds__(256, 1)
   // Wait for queue slot e and read the item index there (-1: no more items).
   auto queue_get = [&](uint32_t e, int64_t& it) {
     const int qs = (int)(e % kQueue);
-    const bool ok = mbar_wait_bounded(&qfull[qs], (e / kQueue) & 1u);
+    const bool ok = mbar_wait_bounded(&qfull[qs], (e / kQueue) & 1u, wait_ns);
     if (__any_sync(0xffffffffu, !ok)) return false;
     it = *(volatile int64_t*)&q_item[qs];
     __syncwarp();
@@ -629,14 +686,14 @@ __global__ void __launch_bounds__(256, 1)
   };
 
   if (warp == 0) {
-    uint32_t g = 0;  // chunks streamed so far (ring position)
+    uint32_t g = 0;  // ring stages streamed so far
     for (uint32_t e = 0;; ++e) {
       int64_t it = 0;
       if (lane == 0) it = atomicAdd(counter, 1);
       it = __shfl_sync(0xffffffffu, it, 0);
       const bool last = it >= n_items;
       const int qs = (int)(e % kQueue);
-      const bool qok = e < (uint32_t)kQueue || mbar_wait_bounded(&qempty[qs], ((e / kQueue) - 1) & 1u);
+      const bool qok = e < (uint32_t)kQueue || mbar_wait_bounded(&qempty[qs], ((e / kQueue) - 1) & 1u, wait_ns);
       if (__any_sync(0xffffffffu, !qok)) {
         fail(true);
         break;
@@ -653,7 +710,7 @@ __global__ void __launch_bounds__(256, 1)
       for (int64_t k = t.c0; k < t.c1; k += kPer, ++g) {
         const uint32_t bytes = (uint32_t)(t.c1 - k < kPer ? t.c1 - k : kPer) * kTChunkBytes;
         const int s = (int)(g % kTStages);
-        const bool ok = g < (uint32_t)kTStages || mbar_wait_bounded(&empty[s], ((g / kTStages) - 1) & 1u);
+        const bool ok = g < (uint32_t)kTStages || mbar_wait_bounded(&empty[s], ((g / kTStages) - 1) & 1u, wait_ns);
         if (__any_sync(0xffffffffu, !ok)) {
           fail(true);
           stop = true;
@@ -673,8 +730,19 @@ __global__ void __launch_bounds__(256, 1)
       }
       if (stop) break;
     }
-  } else if (warp == 1) {
-    uint32_t g = 0;
+    // The copies complete on `full` whether or not an MMA warp consumed
+    // them; wait (bounded) for the last ring's worth of stages issued before
+    // the CTA may exit, since its shared memory is their destination.  A wait
+    // on a phase that already completed returns at once.
+    for (uint32_t j = g > (uint32_t)kTStages ? g - kTStages : 0; j < g; ++j)
+      if (__any_sync(0xffffffffu, !mbar_wait_bounded(&full[j % kTStages], (j / kTStages) & 1u))) {
+        fail(true);
+        break;
+      }
+  } else if (warp >= 1 && warp <= mma_warps) {
+    const uint32_t mw = (uint32_t)(warp - 1);  // this warp's stages: g % mma_warps == mw
+    uint32_t g0 = 0;                           // first ring stage of the current item
+    bool stop = false;
     for (uint32_t e = 0;; ++e) {
       int64_t it;
       if (!queue_get(e, it)) {
@@ -683,20 +751,22 @@ __global__ void __launch_bounds__(256, 1)
       }
       if (it < 0) break;
       const TcTile t = work.tile(it);
-      // the epilogue must have read the previous item's accumulators
-      const bool free_ok = e == 0 || mbar_wait_bounded(&tempty, (e - 1) & 1u);
-      bool stop = __any_sync(0xffffffffu, !free_ok);
+      const uint32_t n_st = (uint32_t)((t.c1 - t.c0 + kPer - 1) / kPer);
+      // the epilogue must have read (and zeroed) the previous item's accumulators
+      const bool free_ok = e == 0 || mbar_wait_bounded(&tempty, (e - 1) & 1u, wait_ns);
+      stop = __any_sync(0xffffffffu, !free_ok);
       if (!stop) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        for (int64_t k = t.c0; k < t.c1; k += kPer, ++g) {
+        const uint32_t first = g0 + (mw + (uint32_t)mma_warps - g0 % (uint32_t)mma_warps) % (uint32_t)mma_warps;
+        for (uint32_t g = first; g < g0 + n_st; g += (uint32_t)mma_warps) {
+          const int64_t k = t.c0 + (int64_t)(g - g0) * kPer;
           const int cnt = (int)(t.c1 - k < kPer ? t.c1 - k : kPer);
           const int s = (int)(g % kTStages);
-          const bool ok = mbar_wait_bounded(&full[s], (g / kTStages) & 1u);
+          const bool ok = mbar_wait_bounded(&full[s], (g / kTStages) & 1u, wait_ns);
           if (__any_sync(0xffffffffu, !ok)) {
             stop = true;
             break;
           }
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           if (lane == 0) {
             const uint32_t st0 = smem_addr(ring + (size_t)s * 2 * kBlockBytes);
 #pragma unroll
@@ -704,7 +774,7 @@ __global__ void __launch_bounds__(256, 1)
               if (c < cnt) {
                 const uint32_t a0 = st0 + c * kTChunkBytes;
                 const uint32_t b0 = t.same ? a0 : a0 + kBlockBytes;
-                chunk_mmas<F>(tmem, a0, b0, k + c > t.c0 ? 1u : 0u);
+                chunk_mmas<F>(tmem, a0, b0, 1u);
               }
             }
             umma_commit(&empty[s]);
@@ -712,14 +782,16 @@ __global__ void __launch_bounds__(256, 1)
           __syncwarp();
         }
       }
+      g0 += n_st;
       if (stop || aborted()) {
         fail(stop);
         break;
       }
+      // arrives once this warp's MMAs of the item (and all before) have completed
       if (lane == 0) umma_commit(&tfull);
       __syncwarp();
     }
-    // arrives once every MMA issued above has completed
+    // arrives once every MMA this warp issued has completed
     if (lane == 0) umma_commit(&drain);
     __syncwarp();
     const bool drained = mbar_wait_bounded(&drain, 0);
@@ -735,7 +807,7 @@ __global__ void __launch_bounds__(256, 1)
         break;
       }
       if (it < 0) break;
-      const bool ok = mbar_wait_bounded(&tfull, e & 1u);
+      const bool ok = mbar_wait_bounded(&tfull, e & 1u, wait_ns);
       if (__any_sync(0xffffffffu, !ok) || aborted()) {
         fail(true);
         break;
@@ -750,7 +822,10 @@ __global__ void __launch_bounds__(256, 1)
         tmem_ld32(lane_base + 256 + cg * 32, v0);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (cg == kTB / 32 - 1) {
-          // every accumulator of this item is in registers: hand TMEM back
+          // every accumulator of this item is in registers: zero them for the
+          // next item and hand TMEM back
+          tmem_zero_acc(lane_base);
+          asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
           asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
           __syncwarp();
           if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&tempty)) : "memory");
@@ -841,13 +916,15 @@ __device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t pa
       : "memory");
   return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait_cluster_bounded(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait_cluster_bounded(uint64_t* bar, uint32_t parity,
+                                                          unsigned long long limit_ns = kWaitLimitNs) {
   if (mbar_try_wait_cluster(bar, parity)) return true;
   const unsigned long long t0 = globaltimer_ns();
+  const int probes = limit_ns < 1000000ull ? 1 : 64;  // short bounds (tests) read the clock every probe
   for (;;) {
-    for (int i = 0; i < 64; ++i)
+    for (int i = 0; i < probes; ++i)
       if (mbar_try_wait_cluster(bar, parity)) return true;
-    if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
+    if (globaltimer_ns() - t0 > limit_ns) return false;
   }
 }
 // The same loads issued by either CTA of the pair, completing on the barrier
@@ -915,16 +992,24 @@ constexpr int kPairStageBytes = kPer * (kTChunkBytes + kTChunkBytes / 2);
 template <int kStages, int kPer>
 constexpr size_t kPairSmem = (size_t)kStages * kPairStageBytes<kPer> + 1024 + 4096;
 
+// Hardware barrier between the pair kernel's waiter warp and its MMA warp
+// (barrier 0 is __syncthreads).  One issuing warp only: a cta_group::2 MMA
+// runs on both SMs of the pair, which exchange B halves per instruction, and
+// MMAs issued by several warps reached the two tensor cores in different
+// orders (every count wrong in the parity tests).
+constexpr int kPairBar = 1;
+
 template <int kStages, int kPer>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
     tc_pair_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap,
-                   const PairWork work, int64_t n_items, int* status) {
+                   const PairWork work, int64_t n_items, int* status, unsigned long long wait_ns) {
   constexpr int kABytes = kPer * kTChunkBytes;
   constexpr int kStageBytes = kPairStageBytes<kPer>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* ring = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ __align__(8) uint64_t full[kStages], empty[kStages], tfull, tempty, drain;
   __shared__ uint32_t tmem_slot;
+  __shared__ uint32_t issued;  // ring stages this CTA's copy warp issued
   __shared__ int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = cluster_rank();
@@ -935,11 +1020,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
       mbar_init(&full[s], 1);  // the even CTA's: both CTAs' copies complete on it
       mbar_init(&empty[s], 1);
     }
-    mbar_init(&tfull, 1);
+    mbar_init(&tfull, 1);   // the MMA warp's commit per item
     mbar_init(&tempty, 8);  // four epilogue warps per CTA
     mbar_init(&drain, 1);
     mbar_fence_init();
     abort_flag = 0;
+    issued = 0;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
@@ -951,9 +1037,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
-  if (warp >= 4) tmem_fill_unit_scales(tmem, warp - 4);
+  if (warp >= 4) {
+    // the accumulators start at zero: every MMA accumulates
+    tmem_zero_acc(tmem + ((uint32_t)((warp - 4) * 32) << 16));
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    tmem_fill_unit_scales(tmem, warp - 4);
+  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  cluster_sync_all();  // both CTAs' barriers initialised and scale factors stored
+  cluster_sync_all();  // both CTAs' barriers initialised, accumulators zeroed and scale factors stored
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
   auto fail = [&](bool cond) {
@@ -973,7 +1064,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
       const int32_t ib = rank == 0 ? pi.I0 : (pi.I1 >= 0 ? pi.I1 : pi.I0);
       for (int64_t k = pi.c0; k < pi.c1; k += kPer, ++g) {
         const int s = (int)(g % kStages);
-        const bool ok = g < (uint32_t)kStages || mbar_wait_bounded(&empty[s], ((g / kStages) - 1) & 1u);
+        const bool ok = g < (uint32_t)kStages || mbar_wait_bounded(&empty[s], ((g / kStages) - 1) & 1u, wait_ns);
         if (__any_sync(0xffffffffu, !ok)) {
           fail(true);
           stop = true;
@@ -1003,46 +1094,75 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
         break;
       }
     }
+    if (lane == 0) issued = g;
+    __syncwarp();
   } else if (warp == 1 && rank == 0) {
-    uint32_t g = 0, e = 0;
-    for (int64_t it = first; it < n_items; it += step, ++e) {
+    // MMA warp of the even CTA.  It never waits on memory itself: a thread
+    // with MMAs in flight that reads a barrier (or any memory) stalls until
+    // they have completed, which would drain the tensor pipe at every stage.
+    // Warp 2 does the waiting and releases this warp once per ring stage
+    // through hardware barrier kPairBar (both warps execute bar.sync once per
+    // stage of every item, in the same order, so neither can run ahead).
+    uint32_t g0 = 0;
+    for (int64_t it = first; it < n_items; it += step) {
       const PairItem pi = work.items[it];
-      const bool free_ok = e == 0 || mbar_wait_cluster_bounded(&tempty, (e - 1) & 1u);
-      bool stop = __any_sync(0xffffffffu, !free_ok);
-      if (!stop) {
+      const uint32_t n_st = (uint32_t)((pi.c1 - pi.c0 + kPer - 1) / kPer);
+      for (uint32_t g = g0; g < g0 + n_st; ++g) {
+        asm volatile("bar.sync %0, 64;" ::"n"(kPairBar) : "memory");
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        for (int64_t k = pi.c0; k < pi.c1; k += kPer, ++g) {
+        if (lane == 0) {
+          const int64_t k = pi.c0 + (int64_t)(g - g0) * kPer;
           const int cnt = (int)(pi.c1 - k < kPer ? pi.c1 - k : kPer);
           const int s = (int)(g % kStages);
-          const bool ok = mbar_wait_bounded(&full[s], (g / kStages) & 1u);
-          if (__any_sync(0xffffffffu, !ok)) {
-            stop = true;
-            break;
-          }
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          if (lane == 0) {
-            const uint32_t st0 = smem_addr(ring + (size_t)s * kStageBytes);
+          const uint32_t st0 = smem_addr(ring + (size_t)s * kStageBytes);
 #pragma unroll
-            for (int c = 0; c < kPer; ++c)
-              if (c < cnt)
-                chunk_mmas_pair(tmem, st0 + c * kTChunkBytes, st0 + kABytes + c * (kTChunkBytes / 2),
-                                k + c > pi.c0 ? 1u : 0u);
-            umma_commit_both(&empty[s]);
-          }
-          __syncwarp();
+          for (int c = 0; c < kPer; ++c)
+            if (c < cnt) chunk_mmas_pair(tmem, st0 + c * kTChunkBytes, st0 + kABytes + c * (kTChunkBytes / 2), 1u);
+          umma_commit_both(&empty[s]);
         }
       }
-      if (stop || aborted()) {
-        fail(stop);
-        break;
-      }
+      g0 += n_st;
       if (lane == 0) umma_commit_both(&tfull);
-      __syncwarp();
     }
+    __syncwarp();
     if (lane == 0) umma_commit_local2(&drain);
     __syncwarp();
     const bool drained = mbar_wait_bounded(&drain, 0);
     if (lane == 0 && !drained) atomicExch(status, kDevTimeout);
+  } else if (warp == 2 && rank == 0) {
+    // Waiter of the even CTA: for each stage, wait (bounded) until both CTAs'
+    // operands have landed (and, before an item's first stage, until both
+    // epilogues have read and zeroed the accumulators), then release the MMA
+    // warp.  After a failed wait or another role's abort it stops waiting but
+    // keeps releasing, so the MMA warp runs out its stages on stale operands
+    // (harmless: the call reports IBS_ETIMEOUT) and the kernel ends.
+    uint32_t g0 = 0, e = 0;
+    bool dead = false;
+    for (int64_t it = first; it < n_items; it += step, ++e) {
+      const PairItem pi = work.items[it];
+      const uint32_t n_st = (uint32_t)((pi.c1 - pi.c0 + kPer - 1) / kPer);
+      if (!dead && e > 0) {
+        const bool ok = mbar_wait_cluster_bounded(&tempty, (e - 1) & 1u, wait_ns);
+        if (__any_sync(0xffffffffu, !ok)) {
+          fail(true);
+          dead = true;
+        }
+      }
+      for (uint32_t g = g0; g < g0 + n_st; ++g) {
+        if (!dead) {
+          const bool ok = mbar_wait_bounded(&full[g % kStages], (g / kStages) & 1u, wait_ns);
+          if (__any_sync(0xffffffffu, !ok)) {
+            fail(true);
+            dead = true;
+          } else if (aborted()) {
+            dead = true;
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        asm volatile("bar.sync %0, 64;" ::"n"(kPairBar) : "memory");
+      }
+      g0 += n_st;
+    }
   } else if (warp >= 4) {
     const int quarter = warp - 4;
     const int row = quarter * 32 + lane;
@@ -1051,7 +1171,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
     uint32_t e = 0;
     for (int64_t it = first; it < n_items; it += step, ++e) {
       const PairItem pi = work.items[it];
-      const bool ok = mbar_wait_bounded(&tfull, e & 1u);
+      const bool ok = mbar_wait_bounded(&tfull, e & 1u, wait_ns);
       if (__any_sync(0xffffffffu, !ok) || aborted()) {
         fail(!ok);
         break;
@@ -1068,6 +1188,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
         tmem_ld32(lane_base + 256 + cg * 32, v0);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (cg == kTB / 32 - 1) {
+          // zero this CTA's accumulators for the next item, then hand TMEM back
+          tmem_zero_acc(lane_base);
+          asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
           asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
           __syncwarp();
           if (lane == 0) mbar_arrive_cluster(tempty_addr);
@@ -1079,7 +1202,27 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  cluster_sync_all();  // the even CTA's MMAs are drained and no arrival to either CTA is outstanding
+  cluster_sync_all();  // both CTAs have issued their last copy and the even CTA's MMAs are drained
+  if (rank == 0 && warp == 0) {
+    // Every copy of either CTA completes on the even CTA's `full` barriers.
+    // After a stop some issued stages were never consumed by the MMA warp, so
+    // wait (bounded) for the last ring's worth of stages that either CTA
+    // issued: a wait on a phase that has already completed returns at once,
+    // so on the normal path this costs kStages probes.  Only then may either
+    // CTA exit (its shared memory is the copies' destination).
+    uint32_t peer = 0;
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(peer) : "r"(cluster_addr(&issued, 1)) : "memory");
+    const uint32_t gmax = issued > peer ? issued : peer;
+    for (uint32_t j = gmax > (uint32_t)kStages ? gmax - kStages : 0; j < gmax; ++j) {
+      const bool ok = mbar_wait_bounded(&full[j % kStages], (j / kStages) & 1u);
+      if (__any_sync(0xffffffffu, !ok)) {
+        fail(true);
+        break;
+      }
+    }
+  }
+  __syncthreads();
+  cluster_sync_all();  // no copy into either CTA and no arrival on either CTA's barriers is outstanding
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
@@ -1340,7 +1483,7 @@ Ring persistent_ring(int64_t chunks_per_item) {
 
 template <int F, class W, int S, int P>
 cudaError_t launch_persistent_s(const W& work, int64_t n_items, int grid, int* counter, int* status,
-                                cudaStream_t st) {
+                                unsigned long long wait_ns, cudaStream_t st) {
   constexpr size_t smem = (size_t)S * 2 * P * kTChunkBytes + 1024;
   static_assert(smem <= 227 * 1024, "ring exceeds shared memory");
   cudaError_t e = cudaFuncSetAttribute(tc_persistent_kernel<F, W, S, P>,
@@ -1348,39 +1491,47 @@ cudaError_t launch_persistent_s(const W& work, int64_t n_items, int grid, int* c
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
-  tc_persistent_kernel<F, W, S, P><<<grid, 256, smem, st>>>(work, n_items, counter, status);
+  // Each ring slot must belong to one MMA warp (warp j takes stages g with
+  // g % warps == j, slot g % S), so that a warp waits for the phases of its
+  // slots in order: a slot shared by two warps lets one of them test a phase
+  // two completions ahead, where the parity test cannot tell it from an
+  // older completed phase.  So the warp count divides the stage count.
+  int mma_warps = tc_mma_warps();
+  while (S % mma_warps != 0) --mma_warps;
+  tc_persistent_kernel<F, W, S, P><<<grid, 256, smem, st>>>(work, n_items, counter, status, mma_warps, wait_ns);
   return cudaGetLastError();
 }
 
 template <int F, class W>
 cudaError_t launch_persistent_f(const W& work, int64_t n_items, int grid, Ring r, int* counter, int* status,
-                                cudaStream_t st) {
-  if (r.per == 1 && r.stages == 4) return launch_persistent_s<F, W, 4, 1>(work, n_items, grid, counter, status, st);
-  if (r.per == 1 && r.stages == 6) return launch_persistent_s<F, W, 6, 1>(work, n_items, grid, counter, status, st);
-  if (r.per == 2 && r.stages == 2) return launch_persistent_s<F, W, 2, 2>(work, n_items, grid, counter, status, st);
-  if (r.per == 2 && r.stages == 3) return launch_persistent_s<F, W, 3, 2>(work, n_items, grid, counter, status, st);
-  if (r.per == 3 && r.stages == 2) return launch_persistent_s<F, W, 2, 3>(work, n_items, grid, counter, status, st);
+                                unsigned long long w, cudaStream_t st) {
+  if (r.per == 1 && r.stages == 4) return launch_persistent_s<F, W, 4, 1>(work, n_items, grid, counter, status, w, st);
+  if (r.per == 1 && r.stages == 6) return launch_persistent_s<F, W, 6, 1>(work, n_items, grid, counter, status, w, st);
+  if (r.per == 2 && r.stages == 2) return launch_persistent_s<F, W, 2, 2>(work, n_items, grid, counter, status, w, st);
+  if (r.per == 2 && r.stages == 3) return launch_persistent_s<F, W, 3, 2>(work, n_items, grid, counter, status, w, st);
+  if (r.per == 3 && r.stages == 2) return launch_persistent_s<F, W, 2, 3>(work, n_items, grid, counter, status, w, st);
   return cudaErrorInvalidValue;
 }
 
 template <class W>
 cudaError_t launch_persistent(const W& work, int64_t n_items, int grid, int fmt, int64_t chunks_per_item,
-                              int* counter, int* status, cudaStream_t st) {
+                              int* counter, int* status, unsigned long long wait_ns, cudaStream_t st) {
   if (n_items <= 0) return cudaSuccess;
   if (grid < 1 || n_items > 2147483647LL - grid) return cudaErrorInvalidValue;  // the claim counter is an int
   const Ring r = persistent_ring(chunks_per_item);
-  if (fmt == kTcFp4) return launch_persistent_f<kTcFp4>(work, n_items, grid, r, counter, status, st);
-  return launch_persistent_f<kTcFp8>(work, n_items, grid, r, counter, status, st);
+  if (fmt == kTcFp4) return launch_persistent_f<kTcFp4>(work, n_items, grid, r, counter, status, wait_ns, st);
+  return launch_persistent_f<kTcFp8>(work, n_items, grid, r, counter, status, wait_ns, st);
 }
 
 cudaError_t launch_tc_batch(const SubsetDev* subs, const WorkItem* items, int64_t n_items, int grid, int fmt,
                             int64_t max_chunks, int* counter, int* status, cudaStream_t st) {
-  return launch_persistent(BatchWork{subs, items}, n_items, grid, fmt, max_chunks, counter, status, st);
+  return launch_persistent(BatchWork{subs, items}, n_items, grid, fmt, max_chunks, counter, status, kWaitLimitNs,
+                           st);
 }
 
 cudaError_t launch_tc_single(const SubsetDev& sd, const WorkItem* items, int64_t n_items, int grid, int fmt,
-                             int* counter, int* status, cudaStream_t st) {
-  return launch_persistent(SingleWork{sd, items}, n_items, grid, fmt, sd.n_chunks, counter, status, st);
+                             int* counter, int* status, unsigned long long wait_ns, cudaStream_t st) {
+  return launch_persistent(SingleWork{sd, items}, n_items, grid, fmt, sd.n_chunks, counter, status, wait_ns, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -1410,17 +1561,26 @@ PairRing pair_ring(int64_t chunks_per_item) {
 
 // Clusters of two that fit at once (one CTA per SM; a GPC with an odd number
 // of free SMs leaves one out).
+// Counted once per device ordinal (with that device current): function
+// attributes and free SMs are per device.
 template <int S, int P>
 int pair_clusters_s() {
-  static const int v = [] {
+  constexpr int kDevs = 64;
+  static std::atomic<int> cache[kDevs];  // 0 = not yet counted, else count + 1
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevs) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (const int c = cache[dev].load(std::memory_order_acquire)) return c - 1;
+  const int v = [dev] {
     constexpr size_t smem = kPairSmem<S, P>;
     if (cudaFuncSetAttribute(tc_pair_kernel<S, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess) {
       cudaGetLastError();
       return 0;
     }
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
+    int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)std::max(2, sms & ~1));
@@ -1433,6 +1593,7 @@ int pair_clusters_s() {
     }
     return n;
   }();
+  cache[dev].store(v + 1, std::memory_order_release);
   return v;
 }
 
@@ -1561,7 +1722,7 @@ void tc_pair_items(int64_t n, int64_t m, int fmt, int n_clusters, int group, std
       if (o.y >= 0) split_tiles.push_back(make_int2(o.y, o.z));
     }
     for (int64_t p = 0; p < np; ++p) {
-      PairItem w;
+      PairItem w{};
       w.I0 = o.x;
       w.I1 = o.y;
       w.J = o.z;
@@ -1575,12 +1736,12 @@ void tc_pair_items(int64_t n, int64_t m, int fmt, int n_clusters, int group, std
 
 template <int S, int P>
 cudaError_t launch_pair_s(const SubsetDev& sd, const PairItem* items, int64_t n_items, int* status,
-                          cudaStream_t st) {
+                          unsigned long long wait_ns, cudaStream_t st) {
   constexpr size_t smem = kPairSmem<S, P>;
   static_assert(smem <= 227 * 1024, "ring exceeds shared memory");
   const int clusters = tc_pair_clusters(sd.n_chunks);
   if (clusters < 1) return cudaErrorInvalidConfiguration;
-  // per device: the cluster count above was taken once, on the first device used
+  // function attributes are per device: set before every launch
   cudaError_t e = cudaFuncSetAttribute(tc_pair_kernel<S, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   CUtensorMap amap, bmap;
@@ -1588,19 +1749,19 @@ cudaError_t launch_pair_s(const SubsetDev& sd, const PairItem* items, int64_t n_
       !encode_bhalf_map(&bmap, sd.planes, sd.n_blocks, sd.n_chunks, P))
     return cudaErrorInvalidValue;
   const int grid = 2 * (int)std::min<int64_t>(clusters, n_items);
-  tc_pair_kernel<S, P><<<grid, 256, smem, st>>>(amap, bmap, PairWork{sd, items}, n_items, status);
+  tc_pair_kernel<S, P><<<grid, 256, smem, st>>>(amap, bmap, PairWork{sd, items}, n_items, status, wait_ns);
   return cudaGetLastError();
 }
 
 cudaError_t launch_tc_pair(const SubsetDev& sd, const PairItem* items, int64_t n_items, int* status,
-                           cudaStream_t st) {
+                           unsigned long long wait_ns, cudaStream_t st) {
   if (n_items <= 0) return cudaSuccess;
   if (n_items > 2147483647LL) return cudaErrorInvalidValue;
   const PairRing r = pair_ring(sd.n_chunks);
-  if (r.per == 2 && r.stages == 4) return launch_pair_s<4, 2>(sd, items, n_items, status, st);
-  if (r.per == 1 && r.stages == 8) return launch_pair_s<8, 1>(sd, items, n_items, status, st);
-  if (r.per == 4 && r.stages == 2) return launch_pair_s<2, 4>(sd, items, n_items, status, st);
-  if (r.per == 3 && r.stages == 3) return launch_pair_s<3, 3>(sd, items, n_items, status, st);
+  if (r.per == 2 && r.stages == 4) return launch_pair_s<4, 2>(sd, items, n_items, status, wait_ns, st);
+  if (r.per == 1 && r.stages == 8) return launch_pair_s<8, 1>(sd, items, n_items, status, wait_ns, st);
+  if (r.per == 4 && r.stages == 2) return launch_pair_s<2, 4>(sd, items, n_items, status, wait_ns, st);
+  if (r.per == 3 && r.stages == 3) return launch_pair_s<3, 3>(sd, items, n_items, status, wait_ns, st);
   return cudaErrorInvalidValue;
 }
 
@@ -1659,7 +1820,7 @@ void tc_single_items(int64_t n, int64_t m, int fmt, int num_sms, int group, std:
     const int64_t np = std::max<int64_t>(min_pieces, t < whole ? 1 : pieces);
     if (np > 1) split_tiles.push_back(order[t]);
     for (int64_t p = 0; p < np; ++p) {
-      WorkItem w;
+      WorkItem w{};
       w.subset = 0;
       w.I = order[t].x;
       w.J = order[t].y;
@@ -1674,7 +1835,7 @@ void tc_single_items(int64_t n, int64_t m, int fmt, int num_sms, int group, std:
 cudaError_t launch_tc_cross(const uint8_t* panel, int64_t n_panel, int64_t n_chunks, const CrossItem* items,
                             int64_t n_items, int grid, int fmt, int* counter, int* status, cudaStream_t st) {
   return launch_persistent(CrossWork{items, panel, n_panel, n_chunks}, n_items, grid, fmt, n_chunks, counter, status,
-                           st);
+                           kWaitLimitNs, st);
 }
 
 cudaError_t launch_tc_gather_rows(const RowSrc* rows, int64_t n_rows, int64_t n_chunks, uint8_t* dst,

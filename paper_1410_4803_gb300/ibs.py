@@ -98,6 +98,8 @@ def load():
             "ibs_last_launch_info": [p, ctypes.POINTER(ctypes.c_int64)],
             "ibs_kernel_times": [p, ctypes.POINTER(ctypes.c_double)],
             "ibs_compute_noalloc": [p, i64, i64, p, p, p],
+            "ibs_noalloc_status": [p],
+            "ibs_test_set_wait_limit": [p, i64],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -191,6 +193,12 @@ def ibs_compute_noalloc(packed, n_samples: int, n_variants: int, out_counts, out
     """Allocation-free ibs_compute on the current device (fixed 64 MiB scratch; see include/ibs.h)."""
     _check(load().ibs_compute_noalloc(_addr(packed), n_samples, n_variants, _addr(out_counts), _addr(out_dist),
                                       _stream(stream)), "ibs_compute_noalloc")
+
+
+def ibs_noalloc_status(stream=None):
+    """Wait for `stream` and report a bounded device wait that expired in the
+    last ibs_compute_noalloc call on it (IbsError with IBS_ETIMEOUT)."""
+    _check(load().ibs_noalloc_status(_stream(stream)), "ibs_noalloc_status")
 
 
 def ibs_synchronize(ctx: Context, stream=None):
@@ -331,6 +339,12 @@ def ibs_compute_kernel(ctx: Context, n_samples: int, n_variants: int) -> str:
     out = ctypes.c_int64()
     _check(load().ibs_compute_kernel(ctx._h, n_samples, n_variants, ctypes.byref(out)), "ibs_compute_kernel")
     return COMPUTE_KERNELS[out.value]
+
+
+def ibs_test_set_wait_limit(ctx: Context, ns: int):
+    """Testing hook: bound (ns) of the pipeline waits of ibs_compute's
+    persistent pair kernels on this context; 0 restores the 2 s default."""
+    _check(load().ibs_test_set_wait_limit(ctx._h, ns), "ibs_test_set_wait_limit")
 
 
 def ibs_batch_plan_info(ctx: Context) -> dict:

@@ -25,9 +25,12 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "synth_bed.c")
+_SRC_GPU = os.path.join(_HERE, "synth_bed_gpu.cu")
 _BUILD_DIR = os.path.join(os.path.dirname(_HERE), "_build")
 _LIB_PATH = os.path.join(_BUILD_DIR, "libsynth_bed.so")
+_LIB_GPU_PATH = os.path.join(_BUILD_DIR, "libsynth_bed_gpu.so")
 _lib = None
+_lib_gpu = None
 _lock = threading.Lock()
 
 BASE, OFFSPRING, DUPLICATE = 0, 1, 2
@@ -41,6 +44,34 @@ def build(force: bool = False) -> str:
                                "-pthread", _SRC, "-o", tmp])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
+
+
+def build_gpu(force: bool = False) -> str:
+    """Compile the device-side generator (synth_bed_gpu.cu, sm_103a)."""
+    os.makedirs(_BUILD_DIR, exist_ok=True)
+    if force or not os.path.exists(_LIB_GPU_PATH) or os.path.getmtime(_LIB_GPU_PATH) < os.path.getmtime(_SRC_GPU):
+        import shutil
+        nvcc = os.environ.get("NVCC") or "/usr/local/cuda/bin/nvcc"
+        if not os.path.exists(nvcc):
+            nvcc = shutil.which("nvcc") or nvcc
+        tmp = _LIB_GPU_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-shared", "-Xcompiler",
+                               "-fPIC", _SRC_GPU, "-o", tmp])
+        os.replace(tmp, _LIB_GPU_PATH)
+    return _LIB_GPU_PATH
+
+
+def _load_gpu():
+    global _lib_gpu
+    with _lock:
+        if _lib_gpu is None:
+            lib = ctypes.CDLL(build_gpu())
+            i64, p = ctypes.c_int64, ctypes.c_void_p
+            lib.synth_bed_gpu.argtypes = [i64, ctypes.c_uint64, i64, p, ctypes.c_int32, p, i64, p, p, p, p, p,
+                                          ctypes.c_uint64, ctypes.c_int, p, p]
+            lib.synth_bed_gpu.restype = ctypes.c_int
+            _lib_gpu = lib
+    return _lib_gpu
 
 
 def _load():
@@ -132,6 +163,45 @@ def generate(model: Model, samples: Samples, pad_garbage: bool = False, threads:
     return out
 
 
+def thresholds(p) -> np.ndarray:
+    """32-bit fixed-point thresholds of probabilities, as the C generator forms
+    them: floor(p * 2^32), 0 for p <= 0, 2^32 for p >= 1 (uint64)."""
+    p = np.asarray(p, dtype=np.float64)
+    inner = np.clip(p, 0.0, 1.0) * 4294967296.0
+    t = inner.astype(np.uint64)
+    t[p <= 0.0] = 0
+    t[p >= 1.0] = np.uint64(1) << np.uint64(32)
+    return t
+
+
+def generate_device(model: Model, samples: Samples, pad_garbage: bool = False, device: int = 0, stream=None):
+    """generate() on the GPU: the same packed bytes, as a torch uint8 tensor
+    [m][ceil(n/4)] on cuda:`device` (enqueued on `stream`, default the
+    current stream)."""
+    import torch
+    dev = torch.device("cuda", device)
+    m, n = model.m, samples.n
+    out = torch.empty((m, (n + 3) // 4), dtype=torch.uint8, device=dev)
+    thr = torch.from_numpy(np.ascontiguousarray(thresholds(model.p_pop))).to(dev)
+    miss = torch.from_numpy(np.ascontiguousarray(thresholds(model.miss_rate))).to(dev)
+    arrs = [torch.from_numpy(np.ascontiguousarray(a, dtype=t)).to(dev) for a, t in
+            ((samples.gid, np.int64), (samples.pop, np.int32), (samples.kind, np.int32),
+             (samples.src_gid, np.int64), (samples.src_pop, np.int32))]
+    for name, a in (("pop", samples.pop), ("src_pop", samples.src_pop)):
+        if np.any(np.asarray(a) < 0) or np.any(np.asarray(a) >= model.p_pop.shape[0]):
+            raise ValueError(f"{name} out of range")
+    dup = int(thresholds(np.array([model.dup_discord]))[0])
+    st = stream.cuda_stream if stream is not None else torch.cuda.current_stream(dev).cuda_stream
+    with torch.cuda.device(dev):
+        rc = _load_gpu().synth_bed_gpu(m, model.seed, model.var_offset, thr.data_ptr(), model.p_pop.shape[0],
+                                       miss.data_ptr(), n, *[a.data_ptr() for a in arrs], dup, int(pad_garbage),
+                                       out.data_ptr(), st)
+    if rc != 0:
+        raise ValueError(f"synth_bed_gpu failed ({rc})")
+    torch.cuda.current_stream(dev).synchronize() if stream is None else stream.synchronize()
+    return out
+
+
 def _flip(rng, p):
     # Orientation of A2 versus A1 by a coin per variant (IBS is invariant to it).
     return np.where(rng.random(p.size) < 0.5, 1.0 - p, p)
@@ -190,27 +260,36 @@ class Workload:
         return self.n * (self.n - 1) // 2 * self.m
 
 
-def plain_config1(pad_garbage=False) -> Workload:
+def _packed(model: Model, s: Samples, pad_garbage: bool = False, device=None):
+    """The packed matrix on the host (numpy) or, with `device` an ordinal, on
+    that GPU (torch tensor, same bytes)."""
+    if device is None:
+        return generate(model, s, pad_garbage)
+    return generate_device(model, s, pad_garbage, device=device)
+
+
+def plain_config1(pad_garbage=False, device=None) -> Workload:
     """n=256, m=4,096, MAF ~ U(0.05, 0.5), 1% missing i.i.d., seed 0."""
     model = plain_model(4096, 0, maf=(0.05, 0.5), miss=0.01)
     s = Samples.base(256)
-    return Workload("plain n=256 m=4096", generate(model, s, pad_garbage), 256, 4096, s, model)
+    return Workload("plain n=256 m=4096", _packed(model, s, pad_garbage, device), 256, 4096, s, model)
 
 
-def plain_config2(n=4096, m=100_000) -> Workload:
+def plain_config2(n=4096, m=100_000, device=None) -> Workload:
     """n=4,096, m=100,000, MAF ~ U(0.01, 0.5), 2% missing i.i.d. and 0.5% of
     variants at 30% missing, seed 1."""
     model = plain_model(m, 1, maf=(0.01, 0.5), miss=0.02, hi_miss_frac=0.005, hi_miss_rate=0.3)
     s = Samples.base(n)
-    return Workload(f"plain n={n} m={m}", generate(model, s), n, m, s, model)
+    return Workload(f"plain n={n} m={m}", _packed(model, s, device=device), n, m, s, model)
 
 
-def structured_config3(n_base_per_pop=3950, n_pop=5, m=500_000, n_offspring=200, n_dup=50, seed=2) -> Workload:
+def structured_config3(n_base_per_pop=3950, n_pop=5, m=500_000, n_offspring=200, n_dup=50, seed=2,
+                       device=None) -> Workload:
     """Balding-Nichols five subpopulations (F=0.05), 200 parent-offspring pairs
     and 50 duplicates at 0.1% discordance, 1% missing; n = 20,000 at full size."""
     model = balding_nichols_model(m, seed, n_pop=n_pop, fst=0.05, anc=(0.02, 0.5), miss=0.01)
     s = structured_samples(n_base_per_pop * n_pop, n_pop, n_offspring, n_dup, seed)
-    return Workload(f"structured n={s.n} m={m}", generate(model, s), s.n, m, s, model)
+    return Workload(f"structured n={s.n} m={m}", _packed(model, s, device=device), s.n, m, s, model)
 
 
 @dataclass
@@ -245,17 +324,18 @@ def batch_subsets(pool_n=30_000, pool_m=600_000, n_subsets=64, n_range=(200, 800
     return subs
 
 
-def batch_pool(pool_n=30_000, pool_m=600_000, seed=3) -> Workload:
+def batch_pool(pool_n=30_000, pool_m=600_000, seed=3, device=None) -> Workload:
     """Pool generated as the plain n=4,096 workload but without the
     high-missingness variants: MAF ~ U(0.01, 0.5), 2% missing."""
     model = plain_model(pool_m, seed, maf=(0.01, 0.5), miss=0.02)
     s = Samples.base(pool_n)
-    return Workload(f"pool n={pool_n} m={pool_m}", generate(model, s), pool_n, pool_m, s, model)
+    return Workload(f"pool n={pool_n} m={pool_m}", _packed(model, s, device=device), pool_n, pool_m, s, model)
 
 
-def serving_panel(n_base_per_pop=19_750, n_pop=5, m=200_000, n_offspring=1000, n_dup=250, seed=4) -> Workload:
+def serving_panel(n_base_per_pop=19_750, n_pop=5, m=200_000, n_offspring=1000, n_dup=250, seed=4,
+                  device=None) -> Workload:
     """Reference panel generated like the structured cohort, scaled."""
-    return structured_config3(n_base_per_pop, n_pop, m, n_offspring, n_dup, seed)
+    return structured_config3(n_base_per_pop, n_pop, m, n_offspring, n_dup, seed, device=device)
 
 
 def serving_query_sizes(n_requests: int, seed=4, q_max=512):
