@@ -223,6 +223,18 @@ def grm_rows(G: np.ndarray, rows, threads: int = 0) -> np.ndarray:
     return out
 
 
+def dist_from_counts(counts: np.ndarray) -> np.ndarray:
+    """The oracle's distance (IBS1 + 2*IBS0) / (2*N) from count quadruples
+    [..., 4] = (IBS0, IBS1, IBS2, N): one IEEE float64 division of exact
+    integers, as ibs_oracle.c forms it, NaN where N == 0."""
+    c = np.asarray(counts)
+    num = c[..., 1].astype(np.float64) + 2.0 * c[..., 0].astype(np.float64)
+    den = 2.0 * c[..., 3].astype(np.float64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        d = num / den
+    return np.where(c[..., 3] == 0, np.nan, d)
+
+
 def topk(dist_row: np.ndarray, k: int):
     """k nearest panel samples by distance: ascending distance, ties by ascending
     index, NaN ranked after every finite value, padded with (-1, NaN)."""

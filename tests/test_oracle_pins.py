@@ -241,3 +241,16 @@ def test_topk_rule():
     assert np.isnan(dist[5]) and np.isnan(dist[6]) and dist[0] == 0.1
     idx, _ = oracle.topk(d, 2)
     assert idx.tolist() == [2, 4]
+
+
+def test_dist_from_counts_equals_the_c_oracle_bit_for_bit():
+    # the numpy restatement used by the large GPU checks must give exactly the
+    # C oracle's doubles, NaN included
+    rng = np.random.default_rng(31)
+    codes = _random_codes(rng, 37, 300, miss=0.3)
+    codes[5] = 1  # a sample with no calls: N = 0 against everyone
+    counts, dist = oracle.ibs_triangle(pack_codes(codes), 37, 300)
+    got = oracle.dist_from_counts(counts)
+    assert np.array_equal(np.isnan(got), np.isnan(dist))
+    ok = ~np.isnan(dist)
+    assert np.array_equal(got[ok].view(np.uint64), dist[ok].view(np.uint64))
