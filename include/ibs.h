@@ -324,7 +324,7 @@ ibs_status ibs_kernel_info(ibs_ctx* ctx, int64_t out[4]);
  * two-SM kernel (clusters of two CTAs, tcgen05 cta_group::2), 4 tensor core
  * with one CTA per tile (square output).  The two-SM kernel runs for E2M1
  * operands, triangle output and 129 or more samples when the matrix has at
- * least 262,144 variants (4,096 chunks of 64), where it is the faster one;
+ * least 65,536 variants (1,024 chunks of 64), where it is the faster one;
  * IBS_TC_PAIR=1 in the environment selects it for every size, IBS_TC_PAIR=0
  * never.  Host only, no device work; IBS_EINVAL for sizes ibs_compute
  * refuses or out == NULL. */

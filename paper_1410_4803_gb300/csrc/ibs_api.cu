@@ -580,6 +580,44 @@ ibs_status plan_build(ibs_ctx* ctx, BatchPlan& plan, const std::vector<SubsetSha
   plan.q_item_off = subset_item_off;
   plan.q_chunks.clear();
   for (int64_t q : plan.order) plan.q_chunks.push_back(item_geom(shapes[(size_t)q], mode).nc);
+  plan.q_pair_off.assign(plan.order.size(), -1);
+  plan.q_pair_n.assign(plan.order.size(), 0);
+  plan.n_pitems = 0;
+  plan.pair_max_chunks = 0;
+  std::vector<PairItem> p2_items;
+  if (tc && split_policy >= 2) {
+    // Policy 2: each subset on the kernel ibs_compute picks for its shape:
+    // the two-SM kernel over its own pair work list (tail wave split over K)
+    // where it applies, else its one-SM items built above.  Policies 3, 4:
+    // every subset's own pair work list, concatenated in processing order
+    // for one launch; a subset's tail pieces keep the clusters on that
+    // subset's blocks together, as its own launch would.  Before the partial
+    // buffers are sized: a pair list may split tiles the one-SM list does not.
+    std::vector<PairItem> own;
+    std::vector<int2> own_split;
+    for (size_t q = 0; q < plan.order.size(); ++q) {
+      const size_t k = (size_t)plan.order[q];
+      if (split_policy == 2 && !tc_pair_usable(shapes[k].n, shapes[k].m, tc_fmt_of(mode))) continue;
+      const ItemGeom ig = item_geom(shapes[k], mode);
+      tc_pair_items(shapes[k].n, shapes[k].m, tc_fmt_of(mode), tc_pair_clusters(ig.nc), kTcBatchGroup, own,
+                    own_split);
+      plan.q_pair_off[q] = (int64_t)p2_items.size();
+      plan.q_pair_n[q] = (int64_t)own.size();
+      plan.pair_max_chunks = std::max(plan.pair_max_chunks, ig.nc);
+      for (PairItem w : own) {
+        w.subset = (int32_t)k;
+        p2_items.push_back(w);
+      }
+      // this subset's split tiles are the pair list's, not the one-SM list's
+      split_tiles.erase(std::remove_if(split_tiles.begin(), split_tiles.end(),
+                                       [&](const int4& t) { return t.x == (int)k; }),
+                        split_tiles.end());
+      for (const int2& t : own_split) split_tiles.push_back(make_int4((int)k, t.x, t.y, 0));
+      split[k] = own_split.empty() ? 1 : 2;
+    }
+    plan.n_pitems = (int64_t)p2_items.size();
+    plan.n_units = 0;
+  }
   plan.n_split_tiles = (int64_t)split_tiles.size();
   plan.n_items = (int64_t)items.size();
   if (plan.grid > plan.n_items) plan.grid = (int)std::max<int64_t>(1, plan.n_items);
@@ -605,13 +643,58 @@ ibs_status plan_build(ibs_ctx* ctx, BatchPlan& plan, const std::vector<SubsetSha
   for (const auto& s : shapes) plan.total_ctas += s.g.n_chunks * ((s.g.n_blocks + 1) / 2);
   if (tc) {
     // the tensor-core form gathers straight into operand planes: no bit planes
+    // (each subset's planes start on a 16 KiB block-chunk boundary, so that
+    // one tensor map over the whole buffer addresses every subset)
     size_t tb = 0;
     plan.tc_offsets.resize(shapes.size());
     plan.tc_ctas = 0;
+    constexpr size_t kBc = 16384;
     for (size_t k = 0; k < shapes.size(); ++k) {
       plan.tc_offsets[k] = (int64_t)tb;
-      tb += (tc_planes_bytes(shapes[k].n, shapes[k].m, tc_fmt_of(mode)) + 1023) / 1024 * 1024;
+      tb += (tc_planes_bytes(shapes[k].n, shapes[k].m, tc_fmt_of(mode)) + kBc - 1) / kBc * kBc;
       plan.tc_ctas += tc_gather_ctas(shapes[k].n, item_geom(shapes[k], mode).nc);
+    }
+    plan.tc_block_chunks = (int64_t)(tb / kBc);
+    if (split_policy == 2) {
+      std::vector<int32_t> zero(shapes.size(), 0);
+      if (ibs_status s = ensure_buf(ctx, plan.pitems, sizeof(PairItem) * std::max<size_t>(1, p2_items.size()))) return s;
+      if (ibs_status s = ensure_buf(ctx, plan.units, sizeof(int4))) return s;
+      if (ibs_status s = ensure_buf(ctx, plan.unit_counter, 256)) return s;
+      if (ibs_status s = ensure_buf(ctx, plan.ready, sizeof(int32_t) * shapes.size())) return s;
+      if (ibs_status s = ensure_buf(ctx, plan.need, sizeof(int32_t) * shapes.size())) return s;
+      if (!p2_items.empty())
+        IBS_CUDA_TRY(
+            cudaMemcpy(plan.pitems.p, p2_items.data(), sizeof(PairItem) * p2_items.size(), cudaMemcpyHostToDevice));
+      IBS_CUDA_TRY(cudaMemcpy(plan.need.p, zero.data(), sizeof(int32_t) * zero.size(), cudaMemcpyHostToDevice));
+      IBS_CUDA_TRY(cudaMemcpy(plan.ready.p, zero.data(), sizeof(int32_t) * zero.size(), cudaMemcpyHostToDevice));
+    }
+    if (split_policy >= 3) {
+      // One launch of the two-SM kernel over the concatenated pair lists
+      // (above), and the gather units of the subsets in the same order for
+      // its epilogue warps and the side stream's gather CTAs.
+      std::vector<PairItem>& pitems = p2_items;
+      std::vector<int4> units;
+      std::vector<int32_t> need(shapes.size(), 0);
+      for (size_t q = 0; q < plan.order.size(); ++q) {
+        const size_t k = (size_t)plan.order[q];
+        const ItemGeom ig = item_geom(shapes[k], mode);
+        const int64_t groups = (ig.nc + tc_gather_chunks() - 1) / tc_gather_chunks();
+        for (int64_t cg = 0; cg < groups; ++cg)
+          for (int64_t bl = 0; bl < ig.T; ++bl) units.push_back(make_int4((int)q, (int)bl, (int)cg, (int)k));
+        need[k] = (int32_t)(groups * ig.T);
+      }
+      plan.n_split_tiles = (int64_t)split_tiles.size();
+      plan.n_pitems = (int64_t)pitems.size();
+      plan.n_units = (int64_t)units.size();
+      if (plan.n_units > 2147483647LL) return fail(IBS_EINVAL, "batch too large for the fused gather");
+      if (ibs_status s = ensure_buf(ctx, plan.pitems, sizeof(PairItem) * std::max<size_t>(1, pitems.size()))) return s;
+      if (ibs_status s = ensure_buf(ctx, plan.units, sizeof(int4) * std::max<size_t>(1, units.size()))) return s;
+      if (ibs_status s = ensure_buf(ctx, plan.unit_counter, 256)) return s;
+      if (ibs_status s = ensure_buf(ctx, plan.ready, sizeof(int32_t) * shapes.size())) return s;
+      if (ibs_status s = ensure_buf(ctx, plan.need, sizeof(int32_t) * shapes.size())) return s;
+      IBS_CUDA_TRY(cudaMemcpy(plan.pitems.p, pitems.data(), sizeof(PairItem) * pitems.size(), cudaMemcpyHostToDevice));
+      IBS_CUDA_TRY(cudaMemcpy(plan.units.p, units.data(), sizeof(int4) * units.size(), cudaMemcpyHostToDevice));
+      IBS_CUDA_TRY(cudaMemcpy(plan.need.p, need.data(), sizeof(int32_t) * need.size(), cudaMemcpyHostToDevice));
     }
     if (plan.tc_ctas > 2147483647LL) return fail(IBS_EINVAL, "batch too large for one gather launch");
     // Stages: about 10% of the comparisons first (its gather is the only one
@@ -642,7 +725,11 @@ ibs_status plan_build(ibs_ctx* ctx, BatchPlan& plan, const std::vector<SubsetSha
         while (b < 3 && acc >= bounds[b] * total) ++b;
       }
     }
-    if (plan.stage_ctas.size() > 1) {
+    if (split_policy >= 3) {
+      IBS_CUDA_TRY(cudaStreamCreateWithFlags(&plan.side, cudaStreamNonBlocking));
+      IBS_CUDA_TRY(cudaEventCreateWithFlags(&plan.fork_ev, cudaEventDisableTiming));
+      IBS_CUDA_TRY(cudaEventCreateWithFlags(&plan.join_ev, cudaEventDisableTiming));
+    } else if (plan.stage_ctas.size() > 1) {
       IBS_CUDA_TRY(cudaStreamCreateWithFlags(&plan.side, cudaStreamNonBlocking));
       plan.stage_ev.resize(plan.stage_ctas.size(), nullptr);
       for (auto& e : plan.stage_ev) IBS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -719,6 +806,7 @@ ibs_status plan_upload(ibs_ctx* ctx, BatchPlan& plan, const uint8_t* pool, int64
       sd[i].planes = reinterpret_cast<const uint32_t*>(tcp);
       sd[i].n_blocks = ig.T;
       sd[i].n_chunks = ig.nc;
+      sd[i].pad = plan.tc_offsets[i] / 16384;  // first block-chunk of the subset in the shared buffer
       tj[q].src = jobs[i].src;
       tj[q].m = shapes[i].m;
       tj[q].n = shapes[i].n;
@@ -731,7 +819,7 @@ ibs_status plan_upload(ibs_ctx* ctx, BatchPlan& plan, const uint8_t* pool, int64
     // (a counting sort over chunk-group-sized buckets), then job, block.
     std::vector<int64_t> key(k);
     for (size_t i = 0; i < k; ++i) key[i] = subs[i].var_begin;
-    if (plan.map_key != key) {
+    if (plan.split_policy < 3 && plan.map_key != key) {  // policies 3, 4 gather by their own unit list
       const int64_t span = (int64_t)tc_gather_chunks() * (tc_fmt_of(plan.mode) == kTcFp4 ? 64 : 32);
       int64_t vend = 0;
       for (size_t i = 0; i < k; ++i) vend = std::max<int64_t>(vend, subs[i].var_begin + shapes[i].m);
@@ -778,6 +866,48 @@ ibs_status plan_enqueue(ibs_ctx* ctx, BatchPlan& plan, int n_subsets, cudaStream
     const int fmt = tc_fmt_of(plan.mode);
     const TcGatherJob* jobs = static_cast<const TcGatherJob*>(plan.tc_jobs.p);
     const WorkItem* items = static_cast<const WorkItem*>(plan.items.p);
+    if (plan.split_policy >= 3) {
+      // one launch: the two-SM kernel over every subset's pair items, its
+      // epilogue warps gathering the subsets' planes from the pool as they go
+      IBS_CUDA_TRY(cudaMemsetAsync(plan.unit_counter.p, 0, sizeof(int), st));
+      IBS_CUDA_TRY(cudaMemsetAsync(plan.ready.p, 0, sizeof(int32_t) * (size_t)n_subsets, st));
+      PairBatchArgs a;
+      a.subs = static_cast<const SubsetDev*>(plan.subsets.p);
+      a.items = static_cast<const PairItem*>(plan.pitems.p);
+      a.n_items = plan.n_pitems;
+      a.jobs = jobs;
+      a.units = static_cast<const int4*>(plan.units.p);
+      a.n_units = plan.n_units;
+      a.unit_counter = static_cast<int*>(plan.unit_counter.p);
+      a.ready = static_cast<int*>(plan.ready.p);
+      a.need = static_cast<const int*>(plan.need.p);
+      a.planes = plan.tc_planes.p;
+      a.block_chunks = plan.tc_block_chunks;
+      a.max_chunks = plan.pair_max_chunks;
+      if (plan.split_policy == 4) {
+        // policy 4: every unit gathered ahead, at full occupancy, then the
+        // pair launch (whose gate then opens at once)
+        IBS_CUDA_TRY(launch_tc_gather_units(jobs, a.units, a.n_units, a.unit_counter, a.ready, fmt,
+                                            8 * ctx->num_sms, ctx->status_dev, st));
+        IBS_CUDA_TRY(launch_tc_pair_batch(a, ctx->status_dev, kWaitLimitNs, st));
+      } else {
+        // policy 3: the pair launch first, then, on the side stream, persistent
+        // gather CTAs that run beside it (two per SM fit next to a pair CTA)
+        // and claim units from the same list as its epilogue warps
+        IBS_CUDA_TRY(cudaEventRecord(plan.fork_ev, st));
+        IBS_CUDA_TRY(launch_tc_pair_batch(a, ctx->status_dev, kWaitLimitNs, st));
+        IBS_CUDA_TRY(cudaStreamWaitEvent(plan.side, plan.fork_ev, 0));
+        IBS_CUDA_TRY(launch_tc_gather_units(jobs, a.units, a.n_units, a.unit_counter, a.ready, fmt,
+                                            2 * ctx->num_sms, ctx->status_dev, plan.side));
+        IBS_CUDA_TRY(cudaEventRecord(plan.join_ev, plan.side));
+        IBS_CUDA_TRY(cudaStreamWaitEvent(st, plan.join_ev, 0));
+      }
+      if (plan.n_split_tiles > 0)
+        IBS_CUDA_TRY(launch_tc_finalize_batch_tiles(static_cast<const SubsetDev*>(plan.subsets.p),
+                                                    static_cast<const int4*>(plan.split_tiles.p), plan.n_split_tiles,
+                                                    st));
+      return IBS_OK;
+    }
     const int G = (int)plan.stage_ctas.size();
     auto gather = [&](int g, cudaStream_t s) {
       return launch_tc_gather(jobs, static_cast<const int4*>(plan.gather_map.p) + plan.stage_map_off[g],
@@ -796,8 +926,26 @@ ibs_status plan_enqueue(ibs_ctx* ctx, BatchPlan& plan, int n_subsets, cudaStream
       }
       if (g > 0) IBS_CUDA_TRY(cudaStreamWaitEvent(st, plan.stage_ev[g], 0));  // joins the side stream
       if (plan.split_policy == 2) {
-        // one launch per subset of the stage, over its own work list
+        // one launch per subset of the stage, over its own work list, on the
+        // kernel ibs_compute would pick for its shape
         for (int64_t q = plan.stage_job_off[g]; q < plan.stage_job_off[g + 1]; ++q) {
+          if (plan.q_pair_off[(size_t)q] >= 0) {
+            PairBatchArgs a;
+            a.subs = static_cast<const SubsetDev*>(plan.subsets.p);
+            a.items = static_cast<const PairItem*>(plan.pitems.p) + plan.q_pair_off[(size_t)q];
+            a.n_items = plan.q_pair_n[(size_t)q];
+            a.jobs = jobs;
+            a.units = static_cast<const int4*>(plan.units.p);
+            a.n_units = 0;  // gathered by the stage's gather launch
+            a.unit_counter = static_cast<int*>(plan.unit_counter.p);
+            a.ready = static_cast<int*>(plan.ready.p);
+            a.need = static_cast<const int*>(plan.need.p);  // all zero: nothing to wait for
+            a.planes = plan.tc_planes.p;
+            a.block_chunks = plan.tc_block_chunks;
+            a.max_chunks = plan.q_chunks[(size_t)q];
+            IBS_CUDA_TRY(launch_tc_pair_batch(a, ctx->status_dev, kWaitLimitNs, st));
+            continue;
+          }
           const int64_t n_items = plan.q_item_off[q + 1] - plan.q_item_off[q];
           IBS_CUDA_TRY(launch_tc_batch(static_cast<const SubsetDev*>(plan.subsets.p), items + plan.q_item_off[q],
                                        n_items, (int)std::min<int64_t>(plan.grid, n_items), fmt, plan.q_chunks[q],
@@ -835,6 +983,9 @@ void plan_free(ibs_ctx* ctx, BatchPlan& plan) {
   for (auto& e : plan.stage_ev)
     if (e) cudaEventDestroy(e);
   plan.stage_ev.clear();
+  if (plan.fork_ev) cudaEventDestroy(plan.fork_ev);
+  if (plan.join_ev) cudaEventDestroy(plan.join_ev);
+  plan.fork_ev = plan.join_ev = nullptr;
   if (plan.side) cudaStreamDestroy(plan.side);
   plan.side = nullptr;
   if (plan.exec) cudaGraphExecDestroy(plan.exec);
@@ -842,7 +993,8 @@ void plan_free(ibs_ctx* ctx, BatchPlan& plan) {
   plan.exec = nullptr;
   plan.graph = nullptr;
   for (DevBuf* b : {&plan.planes, &plan.partial, &plan.subsets, &plan.jobs, &plan.items, &plan.split_ids,
-                    &plan.counter, &plan.tc_planes, &plan.tc_jobs, &plan.split_tiles, &plan.gather_map})
+                    &plan.counter, &plan.tc_planes, &plan.tc_jobs, &plan.split_tiles, &plan.gather_map, &plan.pitems,
+                    &plan.units, &plan.unit_counter, &plan.ready, &plan.need})
     free_buf(ctx, *b);
 }
 
@@ -921,9 +1073,17 @@ extern "C" ibs_status ibs_compute_batch(ibs_ctx* ctx, const uint8_t* pool, int64
     const std::string tk = tune_key(ctx, shapes) + (tc ? "_tc" : "");
     int mode = forced >= 0 ? forced : (tc ? kBatchModeTc : ctx->default_mode), policy = 0;
     auto te = ctx->tune.find(tk);
-    // IBS_BATCH_POLICY=0|1|2 fixes the split policy (2: tensor-core modes only)
+    // Policy 3 (one launch of the two-SM kernel, gather fused in) needs E2M1
+    // operands and clusters of two.
+    int64_t max_nc = 0;
+    for (const auto& sh : shapes) max_nc = std::max<int64_t>(max_nc, tc_chunks(sh.m, tc_format_for(ctx)));
+    const bool pair_ok = tc && tc_format_for(ctx) == kTcFp4 && tc_pair_clusters(max_nc) > 0;
+    // IBS_BATCH_POLICY=0|1|2|3 fixes the split policy (2, 3: tensor-core modes only)
     const char* pe = getenv("IBS_BATCH_POLICY");
-    const int fixed_policy = pe && (atoi(pe) == 0 || atoi(pe) == 1 || (atoi(pe) == 2 && tc)) ? atoi(pe) : -1;
+    const int fixed_policy =
+        pe && (atoi(pe) == 0 || atoi(pe) == 1 || (atoi(pe) == 2 && tc) || ((atoi(pe) == 3 || atoi(pe) == 4) && pair_ok))
+            ? atoi(pe)
+            : -1;
     if (fixed_policy >= 0) {
       policy = fixed_policy;
     } else if (te != ctx->tune.end()) {
@@ -934,7 +1094,7 @@ extern "C" ibs_status ibs_compute_batch(ibs_ctx* ctx, const uint8_t* pool, int64
       for (int cm = 0; cm <= kBatchModeTc + kTcFp4; ++cm) {
         if (forced >= 0 && cm != forced) continue;
         if (is_tc_mode(cm) != tc) continue;
-        for (int cp = 0; cp < (is_tc_mode(cm) ? 3 : 2); ++cp) {
+        for (int cp = 0; cp < (is_tc_mode(cm) ? (pair_ok && tc_fmt_of(cm) == kTcFp4 ? 5 : 3) : 2); ++cp) {
           BatchPlan trial;
           if (ibs_status s = plan_build(ctx, trial, shapes, cm, cp)) {
             plan_free(ctx, trial);
@@ -1002,6 +1162,7 @@ extern "C" ibs_status ibs_compute_batch(ibs_ctx* ctx, const uint8_t* pool, int64
   if (ibs_status s = plan_upload(ctx, plan, pool, pool_n, subs, shapes, st)) return s;
   IBS_CUDA_TRY(cudaGraphLaunch(plan.exec, st));
   ctx->last_info[0] = !is_tc_mode(plan.mode) ? 3 + (plan.n_split > 0 ? 1 : 0)
+                      : plan.split_policy >= 3 ? 2 + (plan.n_split_tiles > 0 ? 1 : 0)
                       : plan.split_policy == 2
                           ? (int64_t)plan.stage_ctas.size() + n_subsets + (plan.n_split_tiles > 0 ? 1 : 0)
                           : 2 * (int64_t)plan.stage_ctas.size() + (plan.n_split > 0 ? 1 : 0);

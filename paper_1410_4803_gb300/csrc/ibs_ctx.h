@@ -69,8 +69,16 @@ struct BatchPlan {
   std::vector<int64_t> stage_map_off, map_key;
   DevBuf split_tiles;
   int64_t n_split_tiles = 0;
+  // split policy 3 (E2M1): every subset's pair items in one launch of the
+  // two-SM kernel, the gather fused in (gather units, per-subset readiness)
+  DevBuf pitems, units, unit_counter, ready, need;
+  int64_t n_pitems = 0, n_units = 0, pair_max_chunks = 0, tc_block_chunks = 0;
+  // split policy 2: subsets that ibs_compute would run on the two-SM kernel
+  // take its pair work list (q_pair_off/q_pair_n into pitems, -1 = one-SM)
+  std::vector<int64_t> q_pair_off, q_pair_n;
   cudaStream_t side = nullptr;
   std::vector<cudaEvent_t> stage_ev;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;  // policy 3: the side stream's gather
   int64_t n_items = 0, total_ctas = 0, max_split_pairs = 0, tc_ctas = 0;
   int n_split = 0;
   int mode = 0, split_policy = 0, grid = 0;

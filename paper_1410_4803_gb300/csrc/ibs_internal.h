@@ -65,7 +65,9 @@ struct WorkItem {
 struct PairItem {
   int32_t I0, I1, J;
   int32_t c0, c1;
-  int32_t split;  // 1 when the tiles are split over K (accumulate into partial)
+  int32_t split;   // 1 when the tiles are split over K (accumulate into partial)
+  int32_t subset;  // batched launches: the subset the tiles belong to (0 for one matrix)
+  int32_t pad;
 };
 
 // Per-subset plane-build job for the batched gather-transpose.
@@ -179,6 +181,34 @@ void tc_pair_items(int64_t n, int64_t m, int fmt, int n_clusters, int group, std
                    std::vector<int2>& split_tiles);
 cudaError_t launch_tc_pair(const SubsetDev& sd, const PairItem* items, int64_t n_items, int* status,
                            unsigned long long wait_ns, cudaStream_t st);
+// Pair items {I0, I1, J} of a T x T block triangle in the grouped order
+// (bands of `group` block rows, rounded up to even).
+void tc_pair_order(int64_t T, int group, std::vector<int4>& order);
+// Batched subsets through the pair kernel in one launch, the gather fused in
+// (PairBatchWork in ibs_tc.cu): the subsets' planes share one buffer of
+// block_chunks 16 KiB block-chunks (SubsetDev::pad = a subset's first),
+// units {job, sample block, chunk group, subset} are gathered by the
+// epilogue warps, ready/need count them per subset, max_chunks is the
+// longest item (it picks the ring).
+struct PairBatchArgs {
+  const SubsetDev* subs;
+  const PairItem* items;
+  int64_t n_items;
+  const TcGatherJob* jobs;
+  const int4* units;
+  int64_t n_units;
+  int* unit_counter;
+  int* ready;
+  const int* need;
+  const void* planes;
+  int64_t block_chunks;
+  int64_t max_chunks;
+};
+cudaError_t launch_tc_pair_batch(const PairBatchArgs& a, int* status, unsigned long long wait_ns, cudaStream_t st);
+// Gather units of a PairBatchArgs list by `ctas` persistent CTAs (run beside
+// the pair launch on another stream; both claim from unit_counter).
+cudaError_t launch_tc_gather_units(const TcGatherJob* jobs, const int4* units, int64_t n_units, int* unit_counter,
+                                   int* ready, int fmt, int ctas, int* status, cudaStream_t st);
 cudaError_t launch_tc_finalize_tiles(const int2* tiles, int64_t n_tiles, const int32_t* partial, int64_t n,
                                      int32_t* out_counts, double* out_dist, cudaStream_t st);
 // Batch form: tiles {subset, I, J, -}, outputs from the subsets' descriptors.

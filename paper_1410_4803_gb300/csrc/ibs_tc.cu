@@ -359,18 +359,12 @@ __global__ void __launch_bounds__(kTThreads, 1)
 // status word reports it.
 constexpr int kGatherChunks = 8;
 
-// CTA blockIdx.x takes the (job, sample block, chunk group) of map[blockIdx.x]:
-// the host orders a stage's CTAs by the pool variant they start at, so that
-// subsets whose windows overlap read the same pool rows at about the same
-// time and share them through L2.
+// One gather work unit: sample block b of job j over chunk group cg, thread
+// r (0..127) = sample r of the block.  Used by the standalone gather kernel
+// and, fused, by the two-SM kernel's epilogue warps.
 template <int F>
-__global__ void __launch_bounds__(kTB) tc_gather_kernel(const TcGatherJob* __restrict__ jobs,
-                                                        const int4* __restrict__ map, int* status) {
+__device__ __forceinline__ void gather_unit(const TcGatherJob& j, int64_t b, int64_t cg, int r, int* status) {
   constexpr int K = kMarkers<F>;
-  const int4 e = map[blockIdx.x];  // {job, sample block, chunk group, -}
-  const TcGatherJob j = jobs[e.x];
-  const int64_t b = e.y, cg = e.z;
-  const int r = threadIdx.x;
   const int64_t s = b * kTB + r;
   int64_t ps = -1;
   if (s < j.n) {
@@ -416,6 +410,47 @@ __global__ void __launch_bounds__(kTB) tc_gather_kernel(const TcGatherJob* __res
       }
     }
   }
+}
+
+// Gather units claimed from a shared list (the batched pair launch's units,
+// also claimed by its epilogue warps): each CTA takes units until none are
+// left and counts every finished unit in ready[subset].  At most 64 registers
+// a thread (launch bound), so that two of these CTAs fit on an SM beside a
+// pair CTA and the two kernels overlap.
+template <int F>
+__global__ void __launch_bounds__(kTB, 8)
+    tc_gather_units_kernel(const TcGatherJob* __restrict__ jobs, const int4* __restrict__ units, int64_t n_units,
+                           int* unit_counter, int* ready, int* status) {
+  __shared__ int64_t s_u;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int64_t u = atomicAdd(unit_counter, 1);
+      s_u = u < n_units ? u : -1;
+    }
+    __syncthreads();
+    const int64_t u = s_u;
+    __syncthreads();  // everyone has read s_u
+    if (u < 0) return;
+    const int4 un = units[u];  // {job, sample block, chunk group, subset}
+    gather_unit<F>(jobs[un.x], un.y, un.z, threadIdx.x, status);
+    asm volatile("fence.proxy.async.global;" ::: "memory");  // plain stores, read later by TMA
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(ready + un.w, 1);
+    }
+  }
+}
+
+// CTA blockIdx.x takes the (job, sample block, chunk group) of map[blockIdx.x]:
+// the host orders a stage's CTAs by the pool variant they start at, so that
+// subsets whose windows overlap read the same pool rows at about the same
+// time and share them through L2.
+template <int F>
+__global__ void __launch_bounds__(kTB) tc_gather_kernel(const TcGatherJob* __restrict__ jobs,
+                                                        const int4* __restrict__ map, int* status) {
+  const int4 e = map[blockIdx.x];  // {job, sample block, chunk group, -}
+  gather_unit<F>(jobs[e.x], e.y, e.z, threadIdx.x, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -918,11 +953,25 @@ __device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t pa
 }
 __device__ __forceinline__ bool mbar_wait_cluster_bounded(uint64_t* bar, uint32_t parity,
                                                           unsigned long long limit_ns = kWaitLimitNs) {
+  if (limit_ns < 1000000ull) {  // short bounds (tests): non-blocking probes, clock read after each
+    const unsigned long long t0 = globaltimer_ns();
+    for (;;) {
+      uint32_t ok;
+      asm volatile(
+          "{\n\t.reg .pred p;\n\t"
+          "mbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+          "selp.u32 %0, 1, 0, p;\n\t}"
+          : "=r"(ok)
+          : "r"(smem_addr(bar)), "r"(parity)
+          : "memory");
+      if (ok) return true;
+      if (globaltimer_ns() - t0 > limit_ns) return false;
+    }
+  }
   if (mbar_try_wait_cluster(bar, parity)) return true;
   const unsigned long long t0 = globaltimer_ns();
-  const int probes = limit_ns < 1000000ull ? 1 : 64;  // short bounds (tests) read the clock every probe
   for (;;) {
-    for (int i = 0; i < probes; ++i)
+    for (int i = 0; i < 64; ++i)
       if (mbar_try_wait_cluster(bar, parity)) return true;
     if (globaltimer_ns() - t0 > limit_ns) return false;
   }
@@ -980,17 +1029,61 @@ __device__ __forceinline__ void chunk_mmas_pair(uint32_t tmem, uint32_t a0, uint
   umma_pair(tmem + 256, umma_desc(a0 + 3 * kTileBytes), umma_desc(b0 + 2 * kHalf), 1u, sf);   // + R Q^T
 }
 
+// Work of the pair kernel.  One matrix: the subset travels in the kernel
+// parameters and its planes start at block-chunk 0 of the tensor maps.
 struct PairWork {
   SubsetDev sd;
   const PairItem* items;
+  static constexpr bool kFused = false;
+  __device__ SubsetDev sub(int32_t) const { return sd; }
+  __device__ static int64_t base(const SubsetDev&) { return 0; }
 };
 
+// Batched subsets with the gather fused in: the subsets' operand planes share
+// one buffer (SubsetDev::pad = the block-chunk index of a subset's block 0,
+// chunk 0 in it), and the epilogue warps, which are idle while an item's
+// MMAs run, gather the planes from the pool in units {job, sample block,
+// chunk group, subset} (the standalone gather kernel's CTAs).  ready[k]
+// counts the finished units of subset k; the copy warps start an item only
+// once ready[k] == need[k].
+struct PairBatchWork {
+  const SubsetDev* subs;
+  const PairItem* items;
+  const TcGatherJob* jobs;
+  const int4* units;
+  int64_t n_units;
+  int* unit_counter;
+  int* ready;
+  const int* need;
+  static constexpr bool kFused = true;
+  __device__ SubsetDev sub(int32_t k) const { return subs[k]; }
+  __device__ static int64_t base(const SubsetDev& s) { return s.pad; }
+};
+
+// Wait until *counter >= need (another CTA's gather units; bounded).
+__device__ __forceinline__ bool wait_ready(const int* counter, int need, unsigned long long limit_ns) {
+  const unsigned long long t0 = globaltimer_ns();
+  for (unsigned ns = 32;; ns = ns < 1024 ? 2 * ns : ns) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(counter) : "memory");
+    if (v >= need) return true;
+    if (globaltimer_ns() - t0 > limit_ns) return false;
+    __nanosleep(ns);
+  }
+}
+
+// Hardware barrier of the pair kernel's four epilogue warps (the fused gather's lock step).
+constexpr int kEpiBar = 2;
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync %0, 128;" ::"n"(kEpiBar) : "memory"); }
+
 // Shared memory of one ring stage: kPer chunks of the A block, then kPer
-// chunks of the B half; 4 KiB of slack after the ring.
+// chunks of the B half (the A box is exactly kPer x 16 KiB, the B-half box
+// kPer x 8 KiB); 1 KiB for aligning the ring.  Nothing more, so that two
+// gather CTAs fit on an SM beside a pair CTA in the batched launch.
 template <int kPer>
 constexpr int kPairStageBytes = kPer * (kTChunkBytes + kTChunkBytes / 2);
 template <int kStages, int kPer>
-constexpr size_t kPairSmem = (size_t)kStages * kPairStageBytes<kPer> + 1024 + 4096;
+constexpr size_t kPairSmem = (size_t)kStages * kPairStageBytes<kPer> + 1024;
 
 // Hardware barrier between the pair kernel's waiter warp and its MMA warp
 // (barrier 0 is __syncthreads).  One issuing warp only: a cta_group::2 MMA
@@ -999,10 +1092,10 @@ constexpr size_t kPairSmem = (size_t)kStages * kPairStageBytes<kPer> + 1024 + 40
 // orders (every count wrong in the parity tests).
 constexpr int kPairBar = 1;
 
-template <int kStages, int kPer>
+template <class PW, int kStages, int kPer>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
     tc_pair_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap,
-                   const PairWork work, int64_t n_items, int* status, unsigned long long wait_ns) {
+                   const PW work, int64_t n_items, int* status, unsigned long long wait_ns) {
   constexpr int kABytes = kPer * kTChunkBytes;
   constexpr int kStageBytes = kPairStageBytes<kPer>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -1011,10 +1104,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
   __shared__ uint32_t tmem_slot;
   __shared__ uint32_t issued;  // ring stages this CTA's copy warp issued
   __shared__ int abort_flag;
+  __shared__ int64_t s_dec;    // fused gather: the epilogue warps' broadcast decision
+  __shared__ int s_ok;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = cluster_rank();
   const int64_t first = cluster_index(), step = cluster_total();
-  const int64_t nc = work.sd.n_chunks;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full[s], 1);  // the even CTA's: both CTAs' copies complete on it
@@ -1062,6 +1156,22 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
     for (int64_t it = first; it < n_items && !stop; it += step) {
       const PairItem pi = work.items[it];
       const int32_t ib = rank == 0 ? pi.I0 : (pi.I1 >= 0 ? pi.I1 : pi.I0);
+      const SubsetDev sd = work.sub(pi.subset);
+      const int64_t nc = sd.n_chunks, bc0 = PW::base(sd);
+      if constexpr (PW::kFused) {
+        // the subset's planes must be gathered before its copies start;
+        // the proxy fence orders the gather's plain stores before the TMA reads
+        bool ok = true;
+        if (lane == 0) {
+          ok = wait_ready(work.ready + pi.subset, work.need[pi.subset], wait_ns);
+          asm volatile("fence.proxy.async.global;" ::: "memory");
+        }
+        if (__any_sync(0xffffffffu, !ok)) {
+          fail(true);
+          stop = true;
+          break;
+        }
+      }
       for (int64_t k = pi.c0; k < pi.c1; k += kPer, ++g) {
         const int s = (int)(g % kStages);
         const bool ok = g < (uint32_t)kStages || mbar_wait_bounded(&empty[s], ((g / kStages) - 1) & 1u, wait_ns);
@@ -1080,8 +1190,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
           uint8_t* dst = ring + (size_t)s * kStageBytes;
           const uint32_t bar = full0 + (uint32_t)s * 8u;
           if (rank == 0) mbar_arrive_expect_tx(&full[s], 2u * kStageBytes);
-          tma_load_3d_pair(dst, &amap, 0, 0, (int)((int64_t)ib * nc + k), bar);
-          tma_load_4d_pair(dst + kABytes, &bmap, 0, (int)rank, 0, (int)((int64_t)pi.J * nc + k), bar);
+          tma_load_3d_pair(dst, &amap, 0, 0, (int)(bc0 + (int64_t)ib * nc + k), bar);
+          tma_load_4d_pair(dst + kABytes, &bmap, 0, (int)rank, 0, (int)(bc0 + (int64_t)pi.J * nc + k), bar);
         }
         __syncwarp();
       }
@@ -1168,18 +1278,62 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
     const int row = quarter * 32 + lane;
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
     const uint32_t tempty_addr = cluster_addr(&tempty, 0);
+    // Fused gather (batched subsets): one gather unit at a time by all four
+    // epilogue warps (thread `row` = sample row of the unit's block), chosen
+    // by row 0 and broadcast through shared memory; the warps move in lock
+    // step on barrier kEpiBar, so every branch below is taken by all of them.
+    // (generic lambdas: their bodies exist only for the fused work type)
+    auto gather_step = [&](const auto& w, int64_t u) {
+      const int4 un = w.units[u];  // {job, sample block, chunk group, subset}
+      gather_unit<kTcFp4>(w.jobs[un.x], un.y, un.z, row, status);
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+      epi_sync();  // every row of the unit is written
+      if (row == 0) {
+        __threadfence();
+        atomicAdd(w.ready + un.w, 1);
+      }
+    };
+    auto claim = [&](const auto& w) -> int64_t {
+      const int64_t u = atomicAdd(w.unit_counter, 1);
+      return u < w.n_units ? u : -1;
+    };
     uint32_t e = 0;
     for (int64_t it = first; it < n_items; it += step, ++e) {
       const PairItem pi = work.items[it];
-      const bool ok = mbar_wait_bounded(&tfull, e & 1u, wait_ns);
-      if (__any_sync(0xffffffffu, !ok) || aborted()) {
-        fail(!ok);
-        break;
+      bool ok = true;
+      if constexpr (PW::kFused) {
+        // gather while the item's MMAs run; then wait (bounded) for them
+        for (;;) {
+          if (row == 0) s_dec = mbar_test_wait(&tfull, e & 1u) ? -1 : claim(work);
+          epi_sync();
+          const int64_t d = s_dec;
+          epi_sync();  // everyone has read s_dec
+          if (d < 0) break;
+          gather_step(work, d);
+        }
+        if (row == 0) s_ok = mbar_wait_bounded(&tfull, e & 1u, wait_ns) && *(volatile int*)&abort_flag == 0;
+        epi_sync();
+        ok = s_ok != 0;
+        epi_sync();
+        if (!ok) {
+          if (row == 0 && *(volatile int*)&abort_flag == 0) {
+            atomicExch(status, kDevTimeout);
+            atomicExch(&abort_flag, 1);
+          }
+          break;  // all four warps together
+        }
+      } else {
+        ok = mbar_wait_bounded(&tfull, e & 1u, wait_ns);
+        if (__any_sync(0xffffffffu, !ok) || aborted()) {
+          fail(!ok);
+          break;
+        }
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int32_t ib = rank == 0 ? pi.I0 : pi.I1;
-      const TriEpi ep{ib >= 0 ? (int64_t)ib * kTB + row : work.sd.n, (int64_t)pi.J * kTB, work.sd.n,
-                      work.sd.out_counts, work.sd.out_dist, work.sd.partial, pi.split != 0};
+      const SubsetDev sd = work.sub(pi.subset);
+      const TriEpi ep{ib >= 0 ? (int64_t)ib * kTB + row : sd.n, (int64_t)pi.J * kTB, sd.n, sd.out_counts,
+                      sd.out_dist, sd.partial, pi.split != 0};
 #pragma unroll 1
       for (int cg = 0; cg < kTB / 32; ++cg) {
         uint32_t vn[32], vu[32], v0[32];
@@ -1198,6 +1352,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
         ep.store(cg, vn, vu, v0);
       }
       ep.finish();
+    }
+    if constexpr (PW::kFused) {
+      // this CTA's items are done (or stopped): gather units are left for the
+      // other CTAs' items, so keep taking them while any remain
+      for (;;) {
+        if (row == 0) s_dec = *(volatile int*)&abort_flag != 0 ? -1 : claim(work);
+        epi_sync();
+        const int64_t d = s_dec;
+        epi_sync();
+        if (d < 0) break;
+        gather_step(work, d);
+      }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1575,7 +1741,7 @@ int pair_clusters_s() {
   if (const int c = cache[dev].load(std::memory_order_acquire)) return c - 1;
   const int v = [dev] {
     constexpr size_t smem = kPairSmem<S, P>;
-    if (cudaFuncSetAttribute(tc_pair_kernel<S, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    if (cudaFuncSetAttribute(tc_pair_kernel<PairWork, S, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess) {
       cudaGetLastError();
       return 0;
@@ -1587,7 +1753,7 @@ int pair_clusters_s() {
     cfg.blockDim = dim3(256);
     cfg.dynamicSmemBytes = smem;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, tc_pair_kernel<S, P>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, tc_pair_kernel<PairWork, S, P>, &cfg) != cudaSuccess) {
       cudaGetLastError();
       return 0;
     }
@@ -1653,10 +1819,15 @@ bool encode_bhalf_map(CUtensorMap* map, const void* planes, int64_t nb, int64_t 
 }
 
 // IBS_TC_PAIR=1: the pair kernel wherever it can run; 0: never; unset: for
-// items of at least kLongK chunks, where the one-SM kernel's CTAs drift apart
-// along K and miss L2, and the pair's smaller L2 stream pays (n = 20,000,
-// m = 500,000: 156 ms against 198 ms; n = 4,096, m = 100,000: 1.50 ms
-// against 1.38 ms).
+// matrices of at least kPairMinChunks chunks.  Each SM of a pair takes 24 KiB
+// of operands per chunk instead of 32 KiB, and operand ingest (TMA, about
+// 65-75 B/clk per SM) bounds both kernels; below about a thousand chunks the
+// pair's per-item overheads cost more than that saves.  Measured pair kernel
+// against one-SM kernel: n = 4,096, m = 10,000: 0.313 against 0.286 ms; m =
+// 50,000 (n = 1,024): 0.096 against 0.094 ms; m = 100,000: 1.334 against
+// 1.449 ms; n = 8,000, m = 200,000: 9.05 against 12.52 ms.
+constexpr int64_t kPairMinChunks = 1024;
+
 int tc_pair_mode() {
   static const int v = [] {
     const char* e = getenv("IBS_TC_PAIR");
@@ -1670,7 +1841,7 @@ int tc_pair_mode() {
 bool tc_pair_usable(int64_t n, int64_t m, int fmt) {
   if (tc_pair_mode() < 0 || fmt != kTcFp4) return false;
   const int64_t nb = (n + kTB - 1) / kTB, nc = tc_chunks(m, fmt);
-  if (tc_pair_mode() == 0 && nc < kLongK) return false;
+  if (tc_pair_mode() == 0 && nc < kPairMinChunks) return false;
   if (nb < 2 || nb * nc + 8 > 2147483647LL) return false;  // the tensor map's chunk coordinate is an int
   if (!encode_tiled_fn()) return false;
   return tc_pair_clusters(nc) > 0;
@@ -1681,13 +1852,9 @@ bool tc_pair_usable(int64_t n, int64_t m, int fmt) {
 // rows (I, I+1) of a column as one item, a lone row where I+1 is past the band
 // or the diagonal).  The clusters take items round-robin, so the items of the
 // final partial wave are split over K where that shortens the tail.
-void tc_pair_items(int64_t n, int64_t m, int fmt, int n_clusters, int group, std::vector<PairItem>& items,
-                   std::vector<int2>& split_tiles) {
-  items.clear();
-  split_tiles.clear();
-  const int64_t T = (n + kTB - 1) / kTB, nc = tc_chunks(m, fmt);
+void tc_pair_order(int64_t T, int group, std::vector<int4>& order) {
+  order.clear();
   const int64_t G = group + (group & 1);
-  std::vector<int4> order;  // {I0, I1, J, -}
   for (int64_t g0 = 0; g0 < T; g0 += G) {
     const int64_t g1 = g0 + G < T ? g0 + G : T;
     for (int64_t J = g0; J < T; ++J)
@@ -1696,6 +1863,15 @@ void tc_pair_items(int64_t n, int64_t m, int fmt, int n_clusters, int group, std
         order.push_back(make_int4((int)I, (int)I1, (int)J, 0));
       }
   }
+}
+
+void tc_pair_items(int64_t n, int64_t m, int fmt, int n_clusters, int group, std::vector<PairItem>& items,
+                   std::vector<int2>& split_tiles) {
+  items.clear();
+  split_tiles.clear();
+  const int64_t T = (n + kTB - 1) / kTB, nc = tc_chunks(m, fmt);
+  std::vector<int4> order;  // {I0, I1, J, -}
+  tc_pair_order(T, group, order);
   const int64_t W = (int64_t)order.size(), C = std::max(1, n_clusters);
   int64_t whole = W, pieces = 1;
   if (W < C) {
@@ -1734,23 +1910,46 @@ void tc_pair_items(int64_t n, int64_t m, int fmt, int n_clusters, int group, std
   }
 }
 
+template <class PW, int S, int P>
+cudaError_t launch_pair_w(const PW& work, const void* planes, int64_t block_chunks, int64_t chunks_per_item,
+                          int64_t n_items, int* status, unsigned long long wait_ns, cudaStream_t st) {
+  constexpr size_t smem = kPairSmem<S, P>;
+  static_assert(smem <= 227 * 1024, "ring exceeds shared memory");
+  const int clusters = tc_pair_clusters(chunks_per_item);
+  if (clusters < 1) return cudaErrorInvalidConfiguration;
+  // function attributes are per device: set before every launch
+  cudaError_t e =
+      cudaFuncSetAttribute(tc_pair_kernel<PW, S, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  CUtensorMap amap, bmap;
+  if (!encode_a_map(&amap, planes, 1, block_chunks, P) || !encode_bhalf_map(&bmap, planes, 1, block_chunks, P))
+    return cudaErrorInvalidValue;
+  const int grid = 2 * (int)std::min<int64_t>(clusters, n_items);
+  tc_pair_kernel<PW, S, P><<<grid, 256, smem, st>>>(amap, bmap, work, n_items, status, wait_ns);
+  return cudaGetLastError();
+}
+
 template <int S, int P>
 cudaError_t launch_pair_s(const SubsetDev& sd, const PairItem* items, int64_t n_items, int* status,
                           unsigned long long wait_ns, cudaStream_t st) {
-  constexpr size_t smem = kPairSmem<S, P>;
-  static_assert(smem <= 227 * 1024, "ring exceeds shared memory");
-  const int clusters = tc_pair_clusters(sd.n_chunks);
-  if (clusters < 1) return cudaErrorInvalidConfiguration;
-  // function attributes are per device: set before every launch
-  cudaError_t e = cudaFuncSetAttribute(tc_pair_kernel<S, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  CUtensorMap amap, bmap;
-  if (!encode_a_map(&amap, sd.planes, sd.n_blocks, sd.n_chunks, P) ||
-      !encode_bhalf_map(&bmap, sd.planes, sd.n_blocks, sd.n_chunks, P))
-    return cudaErrorInvalidValue;
-  const int grid = 2 * (int)std::min<int64_t>(clusters, n_items);
-  tc_pair_kernel<S, P><<<grid, 256, smem, st>>>(amap, bmap, PairWork{sd, items}, n_items, status, wait_ns);
-  return cudaGetLastError();
+  return launch_pair_w<PairWork, S, P>(PairWork{sd, items}, sd.planes, sd.n_blocks * sd.n_chunks, sd.n_chunks,
+                                       n_items, status, wait_ns, st);
+}
+
+cudaError_t launch_tc_pair_batch(const PairBatchArgs& a, int* status, unsigned long long wait_ns, cudaStream_t st) {
+  if (a.n_items <= 0) return cudaSuccess;
+  if (a.n_items > 2147483647LL || a.block_chunks + 8 > 2147483647LL) return cudaErrorInvalidValue;
+  const PairBatchWork w{a.subs, a.items, a.jobs, a.units, a.n_units, a.unit_counter, a.ready, a.need};
+  const PairRing r = pair_ring(a.max_chunks);
+  if (r.per == 2 && r.stages == 4)
+    return launch_pair_w<PairBatchWork, 4, 2>(w, a.planes, a.block_chunks, a.max_chunks, a.n_items, status, wait_ns, st);
+  if (r.per == 1 && r.stages == 8)
+    return launch_pair_w<PairBatchWork, 8, 1>(w, a.planes, a.block_chunks, a.max_chunks, a.n_items, status, wait_ns, st);
+  if (r.per == 4 && r.stages == 2)
+    return launch_pair_w<PairBatchWork, 2, 4>(w, a.planes, a.block_chunks, a.max_chunks, a.n_items, status, wait_ns, st);
+  if (r.per == 3 && r.stages == 3)
+    return launch_pair_w<PairBatchWork, 3, 3>(w, a.planes, a.block_chunks, a.max_chunks, a.n_items, status, wait_ns, st);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_tc_pair(const SubsetDev& sd, const PairItem* items, int64_t n_items, int* status,
@@ -1785,6 +1984,16 @@ cudaError_t launch_tc_finalize_batch_tiles(const SubsetDev* subs, const int4* ti
 }
 
 int tc_gather_chunks() { return kGatherChunks; }
+
+cudaError_t launch_tc_gather_units(const TcGatherJob* jobs, const int4* units, int64_t n_units, int* unit_counter,
+                                   int* ready, int fmt, int ctas, int* status, cudaStream_t st) {
+  if (n_units <= 0 || ctas <= 0) return cudaSuccess;
+  if (fmt == kTcFp4)
+    tc_gather_units_kernel<kTcFp4><<<ctas, kTB, 0, st>>>(jobs, units, n_units, unit_counter, ready, status);
+  else
+    tc_gather_units_kernel<kTcFp8><<<ctas, kTB, 0, st>>>(jobs, units, n_units, unit_counter, ready, status);
+  return cudaGetLastError();
+}
 
 int64_t tc_gather_ctas(int64_t n, int64_t nc) {
   return (n + kTB - 1) / kTB * ((nc + kGatherChunks - 1) / kGatherChunks);

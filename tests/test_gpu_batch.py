@@ -125,7 +125,7 @@ def test_batch_split_items(pool, flags_name):
         (c, d), = _run_batch(ctx, w, subs, torch.from_numpy(w.packed).cuda())
         # tensor-core modes may also pick the per-subset launches (policy 2),
         # which split this subset's few tiles over K as ibs_compute does
-        assert ibs.ibs_batch_plan_info(ctx)["split_policy"] in ((1, 2) if "TC" in flags_name else (1,))
+        assert ibs.ibs_batch_plan_info(ctx)["split_policy"] in ((1, 2, 3) if "TC" in flags_name else (1,))
         idx, vb, vl = subs[0]
         G = oracle.unpack_subset(w.packed, w.n, w.m, idx, vb, vl)
         oc, od, _ = oracle.ibs_triangle_from_codes(G)
@@ -135,16 +135,20 @@ def test_batch_split_items(pool, flags_name):
         ibs.ibs_shutdown(ctx)
 
 
-@pytest.mark.parametrize("policy", [0, 1, 2])
+@pytest.mark.parametrize("policy", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("fmt", ["IBS_TC_FP8", "IBS_TC_FP4"])
 def test_batch_each_policy(pool, policy, fmt, monkeypatch):
     """Every split policy of the tensor-core batch, fixed by IBS_BATCH_POLICY:
     0 whole tiles in one launch per stage, 1 K-split large subsets, 2 one
     launch per subset over its own work list (small subsets and tail waves
-    split over K, split tiles finalised from the subset descriptors).  Counts
-    equal the oracle for all twelve subsets, twice (graph replay)."""
+    split over K, split tiles finalised from the subset descriptors), 3 (E2M1
+    only) one launch of the two-SM kernel over every subset's pair items with
+    the gather fused into its epilogue warps.  Counts equal the oracle for all
+    twelve subsets, twice (graph replay)."""
     import torch
     from paper_1410_4803_gb300 import ibs
+    if policy >= 3 and fmt != "IBS_TC_FP4":
+        pytest.skip("the two-SM kernel takes E2M1 operands only")
     monkeypatch.setenv("IBS_BATCH_POLICY", str(policy))
     w, codes = pool
     rng = np.random.default_rng(9)

@@ -2,7 +2,7 @@
 on for every size with IBS_TC_PAIR=1: bit-exact counts and distances within
 1e-12 against the oracle.  The switch is read once per process, so each case
 runs in a child process.  Also the default choice (ibs_compute_kernel): the
-pair kernel for 262,144 or more variants, the one-SM kernel otherwise.
+pair kernel for 65,536 or more variants, the one-SM kernel otherwise.
 Shapes: two blocks with a ragged marker tail, a lone diagonal tile per column
 pair, garbage in the padding bits, every tile split over K (fewer pair items
 than clusters), and whole waves plus an unsplit tail; every ring variant."""
@@ -75,8 +75,9 @@ def test_default_kernel_choice(mode):
     from paper_1410_4803_gb300 import ibs
     tc4, tc8 = ibs.IBS_KERNEL_TC | ibs.IBS_TC_FP4, ibs.IBS_KERNEL_TC | ibs.IBS_TC_FP8
     long_k = "tc-pair" if mode == "auto" else "tc-persistent"
-    want = [(tc4, 4096, 100_000, "tc-persistent"), (tc4, 20_000, 500_000, long_k), (tc4, 300, 262_144, long_k),
-            (tc4, 300, 262_080, "tc-persistent"), (tc4, 128, 500_000, "tc-persistent"),
+    want = [(tc4, 4096, 100_000, long_k), (tc4, 20_000, 500_000, long_k), (tc4, 300, 65_536, long_k),
+            (tc4, 300, 65_472, "tc-persistent"), (tc4, 4096, 30_000, "tc-persistent"),
+            (tc4, 128, 500_000, "tc-persistent"),
             (tc8, 20_000, 500_000, "tc-persistent"), (tc4 | ibs.IBS_OUT_SQUARE, 20_000, 500_000, "tc-tile"),
             (ibs.IBS_KERNEL_CSA, 20_000, 500_000, "popc-csa")]
     env = {k: v for k, v in os.environ.items() if k not in ("IBS_TC_PAIR", "IBS_TC_TILE_KERNEL")}

@@ -38,7 +38,7 @@ def test_serving_mix_equals_alone_and_oracle(panel, kernel):
     try:
         ibs.ibs_panel_load(ctx, torch.from_numpy(w.packed).cuda(), w.n, w.m)
         # The first request is large enough that its work spans several engine
-        # steps (a step holds about 16 waves of 64 x 64 tiles, or 4 waves of
+        # steps (a step holds about 16 waves of 64 x 64 tiles, or 8 waves of
         # the tensor-core form's 128 x 128 tiles), so the small requests
         # submitted right after it join while it is still running.
         sizes = [2048, 1, 64, 65, 3, 150, 17, 128, 2, 90, 33, 7, 129]
@@ -52,7 +52,9 @@ def test_serving_mix_equals_alone_and_oracle(panel, kernel):
                    for q, _, _ in reqs]
         ids = [None] * len(reqs)
         errors = []
-        # the large request first, then the others from three threads while it runs
+        # the large request first, then half of the others at once from this
+        # thread (they join while it is still on the GPU: the engine takes
+        # several steps over it), the rest from three threads at the same time
         ids[0] = ibs.ibs_query(ctx, reqs[0][1], reqs[0][0], k, *results[0])
 
         def submit(slot_list):
@@ -64,7 +66,8 @@ def test_serving_mix_equals_alone_and_oracle(panel, kernel):
                 errors.append(e)
 
         rest = list(range(1, len(reqs)))
-        threads = [threading.Thread(target=submit, args=(rest[j::3],)) for j in range(3)]
+        submit(rest[::2])
+        threads = [threading.Thread(target=submit, args=(rest[1::2][j::3],)) for j in range(3)]
         for t in threads:
             t.start()
         for t in threads:

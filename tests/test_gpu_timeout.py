@@ -4,10 +4,11 @@ Failure handling of the pair kernels: every wait on a pipeline barrier is
 bounded by %globaltimer; when one runs out the kernel records IBS_ETIMEOUT in
 the context's status word, stops issuing work, waits (with the full bound)
 for the copies and MMAs it already issued, frees its tensor memory and
-returns.  The test sets a 1 us bound through the test hook, far shorter than
-an item's MMAs take (m = 200,000 markers: 3,125 chunks per tile, split into
-pieces of about 60 chunks), so the epilogue's wait for the accumulators runs
-out; ibs_synchronize must then
+returns.  The test sets a 1 ns bound through the test hook, so the first
+wait that is not already over (an operand stage, the accumulators) runs out,
+in the one-SM persistent kernel and in the two-SM kernel (whose waiter warp
+then stops waiting but keeps releasing its MMA warp until the work list
+ends); ibs_synchronize must then
 report IBS_ETIMEOUT, and the next call on the same context with the default
 bound must be bit-exact against the oracle.  The failure is made on the
 device with a short limit only: nothing faults, traps or hangs.
@@ -26,8 +27,8 @@ def _run(ctx, packed_dev, n, m):
     return counts, dist
 
 
-@pytest.mark.parametrize("n,m", [(200, 200_000)])
-def test_short_wait_limit_reports_timeout_and_context_recovers(n, m):
+@pytest.mark.parametrize("n,m,kernel", [(200, 60_000, "tc-persistent"), (300, 200_000, "tc-pair")])
+def test_short_wait_limit_reports_timeout_and_context_recovers(n, m, kernel):
     import torch
     import oracle
     from paper_1410_4803_gb300 import ibs
@@ -36,9 +37,9 @@ def test_short_wait_limit_reports_timeout_and_context_recovers(n, m):
     packed = pack_codes(codes, garbage_rng=rng)
     ctx = ibs.ibs_init(0)
     try:
-        assert ibs.ibs_compute_kernel(ctx, n, m) == "tc-persistent"
+        assert ibs.ibs_compute_kernel(ctx, n, m) == kernel
         dev = torch.from_numpy(packed).cuda()
-        ibs.ibs_test_set_wait_limit(ctx, 1000)  # 1 us
+        ibs.ibs_test_set_wait_limit(ctx, 1)  # 1 ns: the first wait that is not already over runs out
         _run(ctx, dev, n, m)
         with pytest.raises(ibs.IbsError) as ei:
             ibs.ibs_synchronize(ctx)
