@@ -273,14 +273,29 @@ WORKLOADS = {
 }
 
 
-def make_workload(name: str, device=None):
-    """The named all-pairs workload; packed on `device` (torch) or on the host (numpy)."""
+def make_workload(name: str, device=None, samples: int = 0):
+    """The named all-pairs workload; packed on `device` (torch) or on the host
+    (numpy).  `samples` > 0 keeps the workload's recipe and marker count with
+    fewer samples (a smaller case of the same kernel items, for profiling):
+    plain takes that many samples; structured keeps its 200 offspring and 50
+    duplicates and splits the rest evenly over the five subpopulations."""
     from paper_1410_4803_gb300 import synth
     if name == "plain":
-        return synth.plain_config2(device=device)
+        return synth.plain_config2(n=samples, device=device) if samples > 0 else synth.plain_config2(device=device)
     if name == "structured":
+        if samples > 0:
+            if samples < 255:
+                raise ValueError("structured: --samples must be at least 255 (250 relatives + 5 base)")
+            return synth.structured_config3(n_base_per_pop=(samples - 250) // 5, device=device)
         return synth.structured_config3(device=device)
     raise ValueError(name)
+
+
+def workload_label(name: str, n: int, samples: int) -> str:
+    """WORKLOADS[name], with the sample count replaced for a reduced case."""
+    if samples <= 0:
+        return WORKLOADS[name]
+    return re.sub(r"n=\d+", f"n={n}", WORKLOADS[name], count=1) + " (reduced sample count, --samples)"
 
 
 def run_matrix(args, rank, world, local, name: str, full: bool = True):
@@ -298,7 +313,8 @@ def run_matrix(args, rank, world, local, name: str, full: bool = True):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     t0 = time.perf_counter()
-    w = make_workload(name, device=local)
+    samples = getattr(args, "samples", 0) if full else 0
+    w = make_workload(name, device=local, samples=samples)
     gen_s = time.perf_counter() - t0
     n, m = w.n, w.m
     comps = n * (n - 1) // 2 * m
@@ -480,7 +496,8 @@ def run_matrix(args, rank, world, local, name: str, full: bool = True):
         # in FP32, exact integer counts; the integer form computes in int32
         "dtype": ("e2m1xe2m1->f32" if fp4 else "e4m3xe4m3->f32") if use_tc else "int32",
         "data": "synthetic",
-        "config": {"workload": WORKLOADS[name], "n_samples": n, "n_variants": m, "pairs_incl_diagonal": P,
+        "config": {"workload": workload_label(name, n, samples), "n_samples": n, "n_variants": m,
+                   "pairs_incl_diagonal": P,
                    "comparisons_per_step": comps,
                    "l2": "flushed between steps (256 MiB write, outside the step events); the operand planes "
                          f"({tc_planes_gb(n, m, fp4):.1f} GB) exceed L2 many times over",
@@ -1161,6 +1178,8 @@ def main():
                     help="serving: Poisson arrival rates per second (0 = all at once)")
     ap.add_argument("--requests", type=int, default=None, help="serving: requests per rate")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--samples", type=int, default=0,
+                    help="plain/structured: a smaller case with this many samples (profiling captures)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-step-seconds", type=float, default=3.0)
     args = ap.parse_args()
@@ -1212,7 +1231,6 @@ def main():
             sv = run_serve(args, rank, world, local)
             line["served"] = sub_record(sv, ["value", "unit", "dtype", "config", "serving", "engine_stats",
                                              "exact", "clocks"])
-            line["gpu_launches"] += b.get("gpu_launches", 0) + p.get("gpu_launches", 0)
     if line is not None:
         print(json.dumps(line))
     if world > 1 and args.impl == "ours":

@@ -8,8 +8,19 @@
  * 2-bit codes are equal, IBS0 when both bits differ and IBS1 otherwise.
  * N = IBS0 + IBS1 + IBS2 is the number of jointly non-missing markers.  The
  * paper's replacement evaluates the same counts with XOR, a missing-call mask
- * and a population count over blocks of markers; this library does that on
- * sample-major bit planes with LOP3 and POPC in registers.
+ * and a population count over blocks of markers.
+ *
+ * This library's default form counts on the tensor cores instead (tcgen05,
+ * sm_103a).  Per sample and marker it writes four indicator values: V = 1 for
+ * a present call, U = +1 homozygous / -1 heterozygous, Q = 1 hom A2,
+ * R = 1 hom A1 (all 0 when missing).  Then N = V V^T, IBS0 = Q R^T + R Q^T,
+ * IBS1 = (N - U U^T) / 2 and IBS2 = N - IBS0 - IBS1.  The products are
+ * E2M1 (kind::mxf4, unit scale factors) or E4M3 (kind::f8f6f4) matrix
+ * products accumulated in FP32; every term is an integer well below 2^24, so
+ * the counts are exact.  The paper's own scheme (XOR / mask / POPC on
+ * sample-major bit planes, LOP3 and POPC in registers) is kept as the
+ * integer form, selected with IBS_KERNEL_PLAIN or IBS_KERNEL_CSA; both forms
+ * give identical counts.
  *
  * Input layout (every entry point): a variant-major packed matrix, row k =
  * ceil(n/4) bytes, sample s in bits 2*(s%4) (low) and 2*(s%4)+1 (high) of
@@ -72,13 +83,19 @@ typedef enum {
 typedef struct {
   int device;                      /* CUDA device ordinal */
   size_t workspace_bytes;          /* upper bound for library-owned device memory; 0 = no bound */
-  int flags;                       /* IBS_OUT_SQUARE, IBS_NO_DIST */
+  int flags;                       /* OR of IBS_OUT_SQUARE, IBS_NO_DIST, IBS_KERNEL_PLAIN, IBS_KERNEL_CSA,
+                                      IBS_KERNEL_TC, IBS_TC_FP8, IBS_TC_FP4, IBS_TIMING; no kernel flag =
+                                      the tensor-core form (IBS_KERNEL_TC) with E2M1 operands */
   const char* autotune_cache_path; /* JSON file for the batched-launch tuner; NULL = in-memory only */
 } ibs_config;
 
 /* Create a context on cfg->device (NULL cfg = device 0, defaults).  Allocates
  * only the small control block; workspaces grow on demand up to
- * cfg->workspace_bytes. */
+ * cfg->workspace_bytes.  (No paper passage: the context is this library's
+ * handle for its device workspaces, the batched-launch tuner and the serving
+ * engine.)  IBS_EINVAL for a bad device ordinal or for IBS_TC_FP8 together
+ * with IBS_TC_FP4; IBS_ECUDA when the device is not an sm_103a GPU or cannot
+ * be used. */
 ibs_status ibs_init(const ibs_config* cfg, ibs_ctx** out_ctx);
 
 /* Plain all-pairs IBS of one cohort (paper: the IBS matrix of
@@ -163,19 +180,32 @@ typedef struct {
  *      into a partial triangle (finalised at the end);
  *   2  one persistent launch per subset over ibs_compute's own work list
  *      (a subset with fewer tiles than SMs, and the tiles of a final partial
- *      wave, split over K; their tiles finalised at the end).
+ *      wave, split over K; their tiles finalised at the end); subsets whose
+ *      windows reach the two-SM size (see ibs_compute_kernel) run the two-SM
+ *      kernel;
+ *   3  one two-SM persistent launch over every subset's two-SM work list,
+ *      concatenated, with the gather fused: a concurrent gather kernel fills
+ *      the operand planes unit by unit and per-subset readiness counters hold
+ *      each item's copies until its planes are written;
+ *   4  as 3, with the gather units taken by the pair launch's own epilogue
+ *      warps between items (one launch after a short head start).
+ * Policies 3 and 4 need E2M1 operands and windows that the two-SM kernel
+ * takes; they are tuner candidates only then.
  * POPC form (IBS_KERNEL_PLAIN / IBS_KERNEL_CSA): one gather-transpose launch
  * and one persistent launch over all subsets (policies 0 and 1).  The launch
  * sequence is captured into a CUDA graph per batch shape and replayed; the
  * policy (and, for POPC, the kernel variant) is chosen by timing the
  * candidates on the first call of a shape, or fixed by the environment
- * variable IBS_BATCH_POLICY=0|1|2.  pool_packed is DEVICE
+ * variable IBS_BATCH_POLICY=0|1|2|3|4.  pool_packed is DEVICE
  * [pool_m][ceil(pool_n/4)].  Results are bit-identical to ibs_compute on each
  * subset alone. */
 ibs_status ibs_compute_batch(ibs_ctx* ctx, const uint8_t* pool_packed, int64_t pool_n, int64_t pool_m,
                              const ibs_subset* subsets, int n_subsets, void* stream);
 
-/* Serving.  ibs_panel_load copies a reference panel (DEVICE or HOST packed
+/* Serving (no paper passage: the serving workload of this library, a
+ * resident reference panel queried by batches of new samples; the counts and
+ * distances are the paper's, as for ibs_compute).  ibs_panel_load copies a
+ * reference panel (DEVICE or HOST packed
  * [n_variants][ceil(n_panel/4)]) into library-owned resident bit planes and
  * starts the serving engine: a host thread that admits requests by free
  * device memory and slot count and advances all admitted requests together,
@@ -183,7 +213,9 @@ ibs_status ibs_compute_batch(ibs_ctx* ctx, const uint8_t* pool_packed, int64_t p
  * are built.  Replaces any previous panel (pending requests are cancelled). */
 ibs_status ibs_panel_load(ibs_ctx* ctx, const uint8_t* panel_packed, int64_t n_panel, int64_t n_variants);
 
-/* Submit q query samples (HOST or DEVICE packed [n_variants][ceil(q/4)],
+/* Submit q query samples (no paper passage: serving workload, as above; the
+ * counts are the paper's pair counts of each query against each panel
+ * sample) (HOST or DEVICE packed [n_variants][ceil(q/4)],
  * copied before return) for counts against every panel sample plus the k
  * nearest panel samples by distance.  Non-blocking; returns a request id.
  *   out_counts    HOST or DEVICE int32 [q][n_panel][4], or NULL.
@@ -205,11 +237,13 @@ ibs_status ibs_query_sync(ibs_ctx* ctx, const uint8_t* query_packed, int64_t n_q
                           int32_t* out_topk_idx, double* out_topk_dist);
 
 /* Wait until request req_id has written its outputs (timeout_ms < 0 = no
- * limit).  Returns IBS_OK, IBS_ETIMEOUT, IBS_ECANCELLED or the request's
+ * limit; no paper passage: serving workload, as above).  Returns IBS_OK, IBS_ETIMEOUT, IBS_ECANCELLED or the request's
  * error.  A request id can be waited on successfully once.  Thread-safe. */
 ibs_status ibs_wait(ibs_ctx* ctx, uint64_t req_id, int64_t timeout_ms);
 
-/* Non-blocking completion check: IBS_OK when done, IBS_EBUSY while pending. */
+/* Non-blocking completion check (no paper passage: serving workload, as
+ * above): IBS_OK when done, IBS_EBUSY while pending, IBS_EINVAL for an
+ * unknown id, IBS_ESTATE when no panel is loaded. */
 ibs_status ibs_poll(ibs_ctx* ctx, uint64_t req_id);
 
 /* Serving-engine counters: completed requests, steps run, peak in-flight query rows. */

@@ -259,6 +259,11 @@ ibs_status ibs_compute(ibs_ctx* ctx, const uint8_t* packed, int64_t n, int64_t m
         IBS_CUDA_TRY(cudaMemcpyAsync(ctx->single_split.p, split_tiles.data(), split_tiles.size() * sizeof(int2),
                                      cudaMemcpyHostToDevice, st));
       ctx->single_n_items = (int64_t)(pair_clusters > 0 ? pitems.size() : items.size());
+      // leading unsplit pair items, in whole waves of one item per cluster
+      int64_t whole = 0;
+      while (whole < (int64_t)pitems.size() && pitems[whole].split == 0) ++whole;
+      ctx->single_clusters = pair_clusters;
+      ctx->single_n_sync = pair_clusters > 0 ? whole / pair_clusters * pair_clusters : 0;
       ctx->single_n_split = (int64_t)split_tiles.size();
       ctx->single_key = key;
     }
@@ -305,8 +310,20 @@ ibs_status ibs_compute(ibs_ctx* ctx, const uint8_t* packed, int64_t n, int64_t m
     sd.pad = 0;
     const unsigned long long wait_ns = ctx->wait_ns > 0 ? ctx->wait_ns : kWaitLimitNs;
     if (ctx->single_pair) {
+      PairSync sync;
+      const int2 ss = tc_pair_sync_setting(sd.n_chunks);
+      if (ss.x > 0 && ctx->single_n_sync > 0) {
+        sync.seg = ss.x;
+        sync.lag = ss.y;
+        sync.n_seg = (int32_t)((sd.n_chunks + ss.x - 1) / ss.x);
+        sync.n_items = ctx->single_n_sync;
+        const size_t bytes = (size_t)(ctx->single_n_sync / ctx->single_clusters) * sync.n_seg * sizeof(int);
+        if (ibs_status s = ensure_buf(ctx, ctx->single_sync, bytes)) return s;
+        IBS_CUDA_TRY(cudaMemsetAsync(ctx->single_sync.p, 0, bytes, st));
+        sync.ctr = static_cast<int*>(ctx->single_sync.p);
+      }
       IBS_CUDA_TRY(launch_tc_pair(sd, static_cast<const PairItem*>(ctx->single_items.p), ctx->single_n_items,
-                                  ctx->status_dev, wait_ns, st));
+                                  ctx->status_dev, wait_ns, st, sync));
     } else {
       const int grid = (int)std::min<int64_t>(ctx->num_sms, ctx->single_n_items);
       IBS_CUDA_TRY(launch_tc_single(sd, static_cast<const WorkItem*>(ctx->single_items.p), ctx->single_n_items,
@@ -1078,7 +1095,7 @@ extern "C" ibs_status ibs_compute_batch(ibs_ctx* ctx, const uint8_t* pool, int64
     int64_t max_nc = 0;
     for (const auto& sh : shapes) max_nc = std::max<int64_t>(max_nc, tc_chunks(sh.m, tc_format_for(ctx)));
     const bool pair_ok = tc && tc_format_for(ctx) == kTcFp4 && tc_pair_clusters(max_nc) > 0;
-    // IBS_BATCH_POLICY=0|1|2|3 fixes the split policy (2, 3: tensor-core modes only)
+    // IBS_BATCH_POLICY=0|1|2|3|4 fixes the split policy (2: tensor-core modes; 3, 4: two-SM E2M1 only)
     const char* pe = getenv("IBS_BATCH_POLICY");
     const int fixed_policy =
         pe && (atoi(pe) == 0 || atoi(pe) == 1 || (atoi(pe) == 2 && tc) || ((atoi(pe) == 3 || atoi(pe) == 4) && pair_ok))
@@ -1342,7 +1359,7 @@ extern "C" ibs_status ibs_shutdown(ibs_ctx* ctx) {
     free_buf(ctx, ctx->planes);
     free_buf(ctx, ctx->partial);
     free_buf(ctx, ctx->tile_list);
-    for (DevBuf* b : {&ctx->single_items, &ctx->single_split, &ctx->single_counter, &ctx->ld_planes, &ctx->ld_diff,
+    for (DevBuf* b : {&ctx->single_items, &ctx->single_split, &ctx->single_counter, &ctx->single_sync, &ctx->ld_planes, &ctx->ld_diff,
                       &ctx->ld_items, &ctx->ld_counter, &ctx->cluster_work, &ctx->grm_work,
                       &ctx->grm_items, &ctx->grm_splits, &ctx->grm_part, &ctx->grm_counter})
       free_buf(ctx, *b);

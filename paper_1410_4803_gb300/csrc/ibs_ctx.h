@@ -126,8 +126,10 @@ struct ibs_ctx {
   int64_t grm_n_items = 0, grm_n_splits = 0, grm_parts = 0;
   // persistent tensor-core work list of the last (n, m, format, SMs, group)
   std::vector<int64_t> single_key;
-  ibs::DevBuf single_items, single_split, single_counter;
+  ibs::DevBuf single_items, single_split, single_counter, single_sync;
   int64_t single_n_items = 0, single_n_split = 0;
+  int64_t single_n_sync = 0;  // pair items in full waves of equal length (the K-lockstep's items)
+  int single_clusters = 0;
   bool single_pair = false;  // single_items holds PairItem (two-SM kernel), else WorkItem
   int* status_host = nullptr;     // mapped pinned status word
   int* status_dev = nullptr;

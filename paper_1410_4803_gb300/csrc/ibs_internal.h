@@ -173,14 +173,28 @@ cudaError_t launch_tc_single(const SubsetDev& sd, const WorkItem* items, int64_t
 // is the number of clusters the launch runs (0 when the kernel cannot run);
 // tc_pair_usable says whether it runs for an n x m matrix (E2M1; two or more
 // blocks; within its tensor map's coordinate range; tc_pair_mode: 1 always,
-// -1 never, 0 for items of at least 4,096 chunks, from IBS_TC_PAIR).
+// -1 never, 0 for items of at least 1,024 chunks, from IBS_TC_PAIR).
 int tc_pair_mode();
 int tc_pair_clusters(int64_t chunks_per_item);
+// K-lockstep of the pair kernel's full waves (off unless IBS_TC_PAIR_SYNC=
+// seg,lag): the items [0, n_items) come in waves of one item per cluster, all
+// of equal length; the copy warp of every CTA counts each seg-chunk segment
+// it starts in ctr[wave * n_seg + segment] and, before segment s, waits
+// (bounded) until every CTA of its wave has started segment s - lag, so the
+// clusters of a wave stream nearly the same chunks at the same time.
+struct PairSync {
+  int* ctr = nullptr;
+  int32_t n_seg = 0, seg = 0, lag = 0;
+  int64_t n_items = 0;
+};
+// The lockstep setting from the environment ({seg, lag}, seg a multiple of
+// the ring's chunks per stage; {0, 0} = off).
+int2 tc_pair_sync_setting(int64_t chunks_per_item);
 bool tc_pair_usable(int64_t n, int64_t m, int fmt);
 void tc_pair_items(int64_t n, int64_t m, int fmt, int n_clusters, int group, std::vector<PairItem>& items,
                    std::vector<int2>& split_tiles);
 cudaError_t launch_tc_pair(const SubsetDev& sd, const PairItem* items, int64_t n_items, int* status,
-                           unsigned long long wait_ns, cudaStream_t st);
+                           unsigned long long wait_ns, cudaStream_t st, const PairSync& sync = PairSync{});
 // Pair items {I0, I1, J} of a T x T block triangle in the grouped order
 // (bands of `group` block rows, rounded up to even).
 void tc_pair_order(int64_t T, int group, std::vector<int4>& order);
@@ -220,6 +234,16 @@ cudaError_t launch_tc_cross(const uint8_t* panel, int64_t n_panel, int64_t n_chu
                             int64_t n_items, int grid, int fmt, int* counter, int* status, cudaStream_t st);
 cudaError_t launch_tc_gather_rows(const RowSrc* rows, int64_t n_rows, int64_t n_chunks, uint8_t* dst,
                                   cudaStream_t st);
+// Serving on the two-SM kernel (PairCrossWork in ibs_tc.cu): items {I0, I1,
+// J, 0, n_chunks} pair two 128-row blocks of the dense query planes qplanes
+// (q_blocks_cap blocks allocated) with panel block J; step row r (< n_rows)
+// writes its counts through row_out[r].  tc_pair_cross_usable: whether the
+// kernel runs for a panel of n_panel samples and n_chunks chunks (the
+// two-SM rule of tc_pair_usable).
+bool tc_pair_cross_usable(int64_t n_panel, int64_t n_chunks, int fmt);
+cudaError_t launch_tc_pair_cross(const uint8_t* panel, int64_t n_panel, int64_t n_chunks, const uint8_t* qplanes,
+                                 int64_t q_blocks_cap, int32_t* const* row_out, int64_t n_rows, const PairItem* items,
+                                 int64_t n_items, int* status, cudaStream_t st);
 int tc_block_samples();  // 128
 // LD correlation (ibs_ld.cu): operand planes of the markers (128-marker
 // blocks, 64-sample chunks, planes X, V, H), the band's work items and the

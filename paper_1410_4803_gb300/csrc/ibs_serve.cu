@@ -20,6 +20,15 @@
 // stream-ordered memory pool, so freeing them never synchronises the device.
 // At most two steps are in flight, so admission and completion are handled
 // between steps while the GPU stays busy.
+//
+// Tensor-core form: a step with two or more query blocks runs on the two-SM
+// kernel (items of two query blocks x one panel block; the faster kernel for
+// panels of at least 1,024 chunks), a step of one query block on the one-SM
+// kernel.  The step length is rounded so that its last wave of items is as
+// full as possible.  The dense query planes are gathered again only when the
+// set of admitted requests changed.  Counts bound for host memory leave the
+// device step by step on a second stream (the panel columns each step wrote),
+// so those copies overlap the following steps instead of trailing them.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -61,7 +70,7 @@ struct Request {
   DevBuf packed, planes, counts, tidx, tdist;
   size_t reserved = 0;
   int64_t blocks_done = 0;  // panel blocks processed since admission
-  cudaEvent_t done_ev = nullptr;
+  cudaEvent_t done_ev = nullptr;  // recorded on the engine's copy stream after the request's last output
   ibs_status status = IBS_OK;
   RState state = RState::Pending;
 };
@@ -108,10 +117,15 @@ class ServeEngine {
   ibs_serve_stats stats{};
   int64_t cursor = 0;  // first panel block of the next step
   int grid_ctas = 0;   // persistent cross-kernel CTAs (SMs x 2)
+  bool pair = false;   // two-SM kernel for steps of two or more query blocks
+  int clusters = 0;    // its clusters of two CTAs
+  cudaStream_t side = nullptr;  // device -> host copies of finished columns and top-k lists
+  cudaEvent_t kern_ev[2] = {nullptr, nullptr}, fin_ev[2] = {nullptr, nullptr};
+  uint64_t set_version = 1, gathered_version = 0;  // the admitted set; the set the step planes hold
   size_t fixed_bytes = 0;  // panel planes + step buffers
-  // double-buffered item arrays
+  // double-buffered item arrays (one-SM CrossItem or two-SM PairItem)
   DevBuf items_dev[2];
-  CrossItem* items_host[2] = {nullptr, nullptr};
+  uint8_t* items_host[2] = {nullptr, nullptr};
   size_t items_cap = 0;
   cudaEvent_t step_ev[2] = {nullptr, nullptr};
   int64_t step_no = 0;
@@ -230,31 +244,79 @@ class ServeEngine {
 
   int32_t* counts_ptr(Request& r) { return r.counts_on_dev ? r.user_counts : static_cast<int32_t*>(r.counts.p); }
 
-  void finish(Request& r) {
-    int32_t* cnt = counts_ptr(r);
-    int32_t* oi = r.topk_on_dev ? r.user_idx : static_cast<int32_t*>(r.tidx.p);
-    double* od = r.topk_on_dev ? r.user_dist : static_cast<double*>(r.tdist.p);
-    if (r.k > 0) launch_topk(cnt, r.q, pg.n, r.k, oi, od, stream);
-    if (!r.counts_on_dev && r.user_counts)
-      cudaMemcpyAsync(r.user_counts, r.counts.p, (size_t)r.q * pg.n * 16, cudaMemcpyDeviceToHost, stream);
-    if (!r.topk_on_dev && r.k > 0) {
-      cudaMemcpyAsync(r.user_idx, r.tidx.p, (size_t)r.q * r.k * 4, cudaMemcpyDeviceToHost, stream);
-      cudaMemcpyAsync(r.user_dist, r.tdist.p, (size_t)r.q * r.k * 8, cudaMemcpyDeviceToHost, stream);
+  // The request's counts columns [b0, b1) panel blocks, written by the step
+  // just enqueued, to its host buffer (on the copy stream, which waits for
+  // the step's kernel).
+  void copy_columns(Request& r, int64_t b0, int64_t b1) {
+    const int64_t c0 = b0 * blk, c1 = std::min<int64_t>(b1 * blk, pg.n);
+    if (c1 <= c0) return;
+    const size_t pitch = (size_t)pg.n * 16;
+    cudaMemcpy2DAsync(r.user_counts + c0 * 4, pitch, static_cast<const int32_t*>(r.counts.p) + c0 * 4, pitch,
+                      (size_t)(c1 - c0) * 16, (size_t)r.q, cudaMemcpyDeviceToHost, side);
+  }
+
+  // Top-k of the requests that saw their last panel block in this step (on
+  // the engine stream, after the step), then their top-k lists to the host
+  // and their completion events on the copy stream (after their last counts
+  // columns).
+  void finish(const std::vector<std::shared_ptr<Request>>& done, int slot) {
+    for (auto& rp : done) {
+      Request& r = *rp;
+      int32_t* oi = r.topk_on_dev ? r.user_idx : static_cast<int32_t*>(r.tidx.p);
+      double* od = r.topk_on_dev ? r.user_dist : static_cast<double*>(r.tdist.p);
+      if (r.k > 0) launch_topk(counts_ptr(r), r.q, pg.n, r.k, oi, od, stream);
     }
-    cudaEventRecord(r.done_ev, stream);
-    r.state = RState::Finishing;
+    if (!fin_ev[slot]) cudaEventCreateWithFlags(&fin_ev[slot], cudaEventDisableTiming);
+    cudaEventRecord(fin_ev[slot], stream);
+    cudaStreamWaitEvent(side, fin_ev[slot], 0);
+    for (auto& rp : done) {
+      Request& r = *rp;
+      if (!r.topk_on_dev && r.k > 0) {
+        cudaMemcpyAsync(r.user_idx, r.tidx.p, (size_t)r.q * r.k * 4, cudaMemcpyDeviceToHost, side);
+        cudaMemcpyAsync(r.user_dist, r.tdist.p, (size_t)r.q * r.k * 8, cudaMemcpyDeviceToHost, side);
+      }
+      cudaEventRecord(r.done_ev, side);
+      r.state = RState::Finishing;
+    }
   }
 
   void ensure_items(size_t n) {
     if (n <= items_cap) return;
+    const size_t each = std::max(sizeof(CrossItem), sizeof(PairItem));
     for (int s = 0; s < 2; ++s) {
       if (step_ev[s]) cudaEventSynchronize(step_ev[s]);
       if (items_dev[s].p) cudaFree(items_dev[s].p);
       if (items_host[s]) cudaFreeHost(items_host[s]);
-      cudaMalloc(&items_dev[s].p, n * sizeof(CrossItem));
-      cudaHostAlloc(reinterpret_cast<void**>(&items_host[s]), n * sizeof(CrossItem), cudaHostAllocDefault);
+      cudaMalloc(&items_dev[s].p, n * each);
+      cudaHostAlloc(reinterpret_cast<void**>(&items_host[s]), n * each, cudaHostAllocDefault);
     }
     items_cap = n;
+  }
+
+  // Step length in panel blocks for `units` item rows (query blocks, or query
+  // block pairs on the two-SM kernel) run by C persistent CTAs or clusters:
+  // about kStepWaves(Tc) waves of items, at least 1/kMinStepDiv of the panel,
+  // at most all of it; among the lengths up to one more wave, the one whose
+  // last wave is fullest (the items of a step all cost the same), the
+  // shortest of equals.
+  int64_t step_len(int64_t units, int64_t C) const {
+    units = std::max<int64_t>(1, units);
+    C = std::max<int64_t>(1, C);
+    int64_t lo = ((tc ? kStepWavesTc : kStepWaves) * C + units - 1) / units;
+    lo = std::max<int64_t>(lo, (pgeo.blocks + kMinStepDiv - 1) / kMinStepDiv);
+    lo = std::min<int64_t>(lo, pgeo.blocks);
+    const int64_t hi = std::min<int64_t>(pgeo.blocks, lo + (C + units - 1) / units);
+    int64_t best = lo;
+    double best_fill = 0.0;
+    for (int64_t L = lo; L <= hi; ++L) {
+      const int64_t n = units * L;
+      const double fill = (double)n / (double)(((n + C - 1) / C) * C);
+      if (fill > best_fill + 1e-3) {
+        best_fill = fill;
+        best = L;
+      }
+    }
+    return best;
   }
 
   // Step-level buffers: dense query planes for kMaxRows rows and the per-row
@@ -288,55 +350,99 @@ class ServeEngine {
         ++n_rows;
       }
     const int64_t qblocks = (n_rows + blk - 1) / blk;
-    // Step length: about kStepWaves waves of tiles, at least 1/kMinStepDiv of
-    // the panel, at most the whole panel.  Few rows in flight -> one step
-    // covers the whole panel (a lone request costs one launch, as on the
-    // unbatched path); many rows -> shorter steps that new requests can join
-    // between.
-    int64_t len = ((tc ? kStepWavesTc : kStepWaves) * grid_ctas + qblocks - 1) / std::max<int64_t>(1, qblocks);
-    len = std::max<int64_t>(len, (pgeo.blocks + kMinStepDiv - 1) / kMinStepDiv);
-    len = std::min<int64_t>(len, pgeo.blocks);
-    const size_t n_items = (size_t)qblocks * (size_t)len;
+    // Step length: few rows in flight -> one step covers the whole panel (a
+    // lone request costs one launch, as on the unbatched path); many rows ->
+    // shorter steps that new requests can join between.
+    const bool two_sm = pair && qblocks >= 2;
+    const int64_t units = two_sm ? (qblocks + 1) / 2 : qblocks;
+    const int64_t len = step_len(units, two_sm ? clusters : grid_ctas);
+    const size_t n_items = (size_t)units * (size_t)len;
     ensure_items(std::max<size_t>(n_items, 1));
-    CrossItem* h = items_host[slot];
     size_t t = 0;
     int32_t** outs_d = static_cast<int32_t**>(outs_dev[slot].p);
-    const size_t qblock_bytes = (size_t)pgeo.chunks * chunk_block_bytes();
-    for (int64_t k = 0; k < len; ++k) {
-      const int64_t pb = (cursor + k) % pgeo.blocks;  // wraps around the panel
-      for (int64_t b = 0; b < qblocks; ++b) {
-        CrossItem& it = h[t++];
-        it.qplanes = reinterpret_cast<const uint32_t*>(static_cast<const uint8_t*>(step_planes.p) + b * qblock_bytes);
-        it.row_out = outs_d + b * blk;
-        it.q_rows = (int32_t)std::min<int64_t>(blk, n_rows - b * blk);
-        it.pb = (int32_t)pb;
+    if (two_sm) {
+      PairItem* h = reinterpret_cast<PairItem*>(items_host[slot]);
+      for (int64_t k = 0; k < len; ++k) {
+        const int64_t pb = (cursor + k) % pgeo.blocks;  // wraps around the panel
+        for (int64_t u = 0; u < units; ++u) {
+          PairItem& it = h[t++];
+          it = PairItem{};
+          it.I0 = (int32_t)(2 * u);
+          it.I1 = 2 * u + 1 < qblocks ? (int32_t)(2 * u + 1) : -1;
+          it.J = (int32_t)pb;
+          it.c0 = 0;
+          it.c1 = (int32_t)pgeo.chunks;
+        }
+      }
+    } else {
+      CrossItem* h = reinterpret_cast<CrossItem*>(items_host[slot]);
+      const size_t qblock_bytes = (size_t)pgeo.chunks * chunk_block_bytes();
+      for (int64_t k = 0; k < len; ++k) {
+        const int64_t pb = (cursor + k) % pgeo.blocks;  // wraps around the panel
+        for (int64_t b = 0; b < qblocks; ++b) {
+          CrossItem& it = h[t++];
+          it.qplanes =
+              reinterpret_cast<const uint32_t*>(static_cast<const uint8_t*>(step_planes.p) + b * qblock_bytes);
+          it.row_out = outs_d + b * blk;
+          it.q_rows = (int32_t)std::min<int64_t>(blk, n_rows - b * blk);
+          it.pb = (int32_t)pb;
+        }
       }
     }
     if (t > 0) {
-      cudaMemcpyAsync(rows_dev[slot].p, rows_host[slot], n_rows * sizeof(RowSrc), cudaMemcpyHostToDevice, stream);
+      if (gathered_version != set_version) {
+        // the admitted set changed: pack its rows into the step planes again
+        cudaMemcpyAsync(rows_dev[slot].p, rows_host[slot], n_rows * sizeof(RowSrc), cudaMemcpyHostToDevice, stream);
+        if (tc)
+          launch_tc_gather_rows(static_cast<const RowSrc*>(rows_dev[slot].p), n_rows, pgeo.chunks,
+                                static_cast<uint8_t*>(step_planes.p), stream);
+        else
+          launch_gather_rows(static_cast<const RowSrc*>(rows_dev[slot].p), n_rows, pg.n_chunks,
+                             static_cast<uint32_t*>(step_planes.p), stream);
+        gathered_version = set_version;
+      }
       cudaMemcpyAsync(outs_dev[slot].p, outs_host[slot], n_rows * sizeof(int32_t*), cudaMemcpyHostToDevice, stream);
-      cudaMemcpyAsync(items_dev[slot].p, h, t * sizeof(CrossItem), cudaMemcpyHostToDevice, stream);
-      if (tc)
-        launch_tc_gather_rows(static_cast<const RowSrc*>(rows_dev[slot].p), n_rows, pgeo.chunks,
-                              static_cast<uint8_t*>(step_planes.p), stream);
-      else
-        launch_gather_rows(static_cast<const RowSrc*>(rows_dev[slot].p), n_rows, pg.n_chunks,
-                           static_cast<uint32_t*>(step_planes.p), stream);
-      cross(static_cast<const CrossItem*>(items_dev[slot].p), (int64_t)t, stream);
+      if (two_sm) {
+        cudaMemcpyAsync(items_dev[slot].p, items_host[slot], t * sizeof(PairItem), cudaMemcpyHostToDevice, stream);
+        launch_tc_pair_cross(static_cast<const uint8_t*>(panel_planes.p), pg.n, pgeo.chunks,
+                             static_cast<const uint8_t*>(step_planes.p), geo(kMaxRows).blocks, outs_d, n_rows,
+                             static_cast<const PairItem*>(items_dev[slot].p), (int64_t)t, ctx->status_dev, stream);
+      } else {
+        cudaMemcpyAsync(items_dev[slot].p, items_host[slot], t * sizeof(CrossItem), cudaMemcpyHostToDevice, stream);
+        cross(static_cast<const CrossItem*>(items_dev[slot].p), (int64_t)t, stream);
+      }
+      // this step's panel columns of requests whose counts go to host memory
+      bool any_host = false;
+      for (auto& r : active) any_host |= !r->counts_on_dev && r->user_counts;
+      if (any_host) {
+        if (!kern_ev[slot]) cudaEventCreateWithFlags(&kern_ev[slot], cudaEventDisableTiming);
+        cudaEventRecord(kern_ev[slot], stream);
+        cudaStreamWaitEvent(side, kern_ev[slot], 0);
+        const int64_t b0 = cursor, b1 = cursor + len;  // may wrap once
+        for (auto& r : active) {
+          if (r->counts_on_dev || !r->user_counts) continue;
+          copy_columns(*r, b0, std::min<int64_t>(b1, pgeo.blocks));
+          if (b1 > pgeo.blocks) copy_columns(*r, 0, b1 - pgeo.blocks);
+        }
+      }
     }
     cursor = (cursor + len) % pgeo.blocks;
-    std::vector<std::shared_ptr<Request>> still;
+    std::vector<std::shared_ptr<Request>> still, done;
     for (auto& r : active) {
       // A request joined at some cursor position and is done once it has seen
       // every panel block (blocks seen twice near the end are rewritten with
       // the same counts).
       r->blocks_done += len;
       if (r->blocks_done >= pgeo.blocks) {
-        finish(*r);
+        done.push_back(r);
         finishing.push_back(r);
       } else {
         still.push_back(r);
       }
+    }
+    if (!done.empty()) {
+      finish(done, slot);
+      ++set_version;
     }
     active.swap(still);
     if (!step_ev[slot]) cudaEventCreateWithFlags(&step_ev[slot], cudaEventDisableTiming);
@@ -383,6 +489,7 @@ class ServeEngine {
           if (!ok) break;
           pending.pop_front();
           active.push_back(r);
+          ++set_version;
           rows += r->q;
           stats.peak_rows = std::max<uint64_t>(stats.peak_rows, (uint64_t)rows);
         }
@@ -408,6 +515,7 @@ class ServeEngine {
     cv_work.notify_all();
     if (worker.joinable()) worker.join();
     cudaStreamSynchronize(stream);
+    if (side) cudaStreamSynchronize(side);
     std::lock_guard<std::mutex> lk(mu);
     for (auto& kv : all) {
       Request& r = *kv.second;
@@ -425,9 +533,13 @@ class ServeEngine {
       if (items_dev[s].p) cudaFree(items_dev[s].p);
       if (items_host[s]) cudaFreeHost(items_host[s]);
       if (step_ev[s]) cudaEventDestroy(step_ev[s]);
+      if (kern_ev[s]) cudaEventDestroy(kern_ev[s]);
+      if (fin_ev[s]) cudaEventDestroy(fin_ev[s]);
       items_dev[s].p = nullptr;
       items_host[s] = nullptr;
       step_ev[s] = nullptr;
+      kern_ev[s] = nullptr;
+      fin_ev[s] = nullptr;
     }
     if (panel_planes.p) free_buf(ctx, panel_planes);
     free_buf(ctx, step_planes);
@@ -441,7 +553,9 @@ class ServeEngine {
       outs_host[s] = nullptr;
     }
     if (stream) cudaStreamDestroy(stream);
+    if (side) cudaStreamDestroy(side);
     stream = nullptr;
+    side = nullptr;
   }
 };
 
@@ -476,8 +590,14 @@ ibs_status serve_panel_load(ibs_ctx* ctx, const uint8_t* panel, int64_t n_panel,
   eng->blk = eng->tc ? kTcBlock : kSB;
   eng->pgeo = eng->geo(n_panel);
   IBS_CUDA_TRY(cudaStreamCreateWithFlags(&eng->stream, cudaStreamNonBlocking));
+  if (cudaStreamCreateWithFlags(&eng->side, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    cudaStreamDestroy(eng->stream);
+    return fail(IBS_ECUDA, "copy stream could not be created");
+  }
   if (ibs_status s = ensure_buf(ctx, eng->panel_planes, eng->pgeo.bytes)) {
     cudaStreamDestroy(eng->stream);
+    cudaStreamDestroy(eng->side);
     return s;
   }
   const size_t bytes = (size_t)m * (size_t)((n_panel + 3) / 4);
@@ -488,6 +608,7 @@ ibs_status serve_panel_load(ibs_ctx* ctx, const uint8_t* panel, int64_t n_panel,
     if (e != cudaSuccess) {
       free_buf(ctx, eng->panel_planes);
       cudaStreamDestroy(eng->stream);
+      cudaStreamDestroy(eng->side);
       cudaGetLastError();
       return fail(IBS_ENOMEM, "panel staging cudaMalloc(%zu) failed", bytes);
     }
@@ -502,6 +623,9 @@ ibs_status serve_panel_load(ibs_ctx* ctx, const uint8_t* panel, int64_t n_panel,
     return st;
   }
   eng->grid_ctas = eng->tc ? ctx->num_sms : ctx->num_sms * pair_kernel_ctas_per_sm(pick_mode(ctx));
+  eng->pair = eng->tc && tc_pair_cross_usable(n_panel, eng->pgeo.chunks, eng->fmt);
+  eng->clusters = eng->pair ? tc_pair_clusters(eng->pgeo.chunks) : 0;
+  if (eng->clusters < 1) eng->pair = false;
   // Requests draw on the device's default stream-ordered pool; keep freed
   // blocks cached in it so steady-state serving does not go back to the driver.
   cudaMemPool_t mp;
@@ -666,9 +790,23 @@ ibs_status serve_query_sync(ibs_ctx* ctx, const uint8_t* q, int64_t nq, int k, i
   for (int64_t row = 0; row < nq; ++row) outs[row] = cnt + (size_t)row * pg.n * 4;
   DevBuf outs_d;
   cudaError_t ce = cudaMallocAsync(&outs_d.p, outs.size() * sizeof(int32_t*), s);
+  // the engine's kernel rule: two or more query blocks on the two-SM kernel
+  const bool two_sm = e.pair && qg.blocks >= 2;
   std::vector<CrossItem> items;
+  std::vector<PairItem> pitems;
   const size_t qblock_bytes = (size_t)qg.chunks * e.chunk_block_bytes();
-  for (int64_t pb = 0; pb < e.pgeo.blocks; ++pb)
+  for (int64_t pb = 0; pb < e.pgeo.blocks; ++pb) {
+    if (two_sm) {
+      for (int64_t u = 0; 2 * u < qg.blocks; ++u) {
+        PairItem it{};
+        it.I0 = (int32_t)(2 * u);
+        it.I1 = 2 * u + 1 < qg.blocks ? (int32_t)(2 * u + 1) : -1;
+        it.J = (int32_t)pb;
+        it.c1 = (int32_t)qg.chunks;
+        pitems.push_back(it);
+      }
+      continue;
+    }
     for (int64_t qb = 0; qb < qg.blocks; ++qb) {
       CrossItem it;
       it.qplanes = reinterpret_cast<const uint32_t*>(static_cast<const uint8_t*>(r.planes.p) + qb * qblock_bytes);
@@ -677,19 +815,26 @@ ibs_status serve_query_sync(ibs_ctx* ctx, const uint8_t* q, int64_t nq, int k, i
       it.pb = (int32_t)pb;
       items.push_back(it);
     }
+  }
+  const size_t item_bytes = two_sm ? pitems.size() * sizeof(PairItem) : items.size() * sizeof(CrossItem);
+  const void* item_src = two_sm ? static_cast<const void*>(pitems.data()) : static_cast<const void*>(items.data());
   DevBuf items_dev;
-  if (ce == cudaSuccess) ce = cudaMallocAsync(&items_dev.p, items.size() * sizeof(CrossItem), s);
+  if (ce == cudaSuccess) ce = cudaMallocAsync(&items_dev.p, item_bytes, s);
   if (ce == cudaSuccess)
     ce = cudaMemcpyAsync(outs_d.p, outs.data(), outs.size() * sizeof(int32_t*), cudaMemcpyHostToDevice, s);
   if (ce == cudaSuccess) {
     if (ptr_kind(q) == PtrKind::Device) ce = cudaMemcpyAsync(r.packed.p, q, pk, cudaMemcpyDeviceToDevice, s);
     else ce = cudaMemcpyAsync(r.packed.p, q, pk, cudaMemcpyHostToDevice, s);
   }
-  if (ce == cudaSuccess)
-    ce = cudaMemcpyAsync(items_dev.p, items.data(), items.size() * sizeof(CrossItem), cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(items_dev.p, item_src, item_bytes, cudaMemcpyHostToDevice, s);
   if (ce == cudaSuccess) ce = e.build_planes(static_cast<const uint8_t*>(r.packed.p), nq, r.planes.p, s);
   if (ce == cudaSuccess) {
-    if (e.tc)
+    if (two_sm)
+      ce = launch_tc_pair_cross(static_cast<const uint8_t*>(e.panel_planes.p), pg.n, e.pgeo.chunks,
+                                static_cast<const uint8_t*>(r.planes.p), qg.blocks,
+                                static_cast<int32_t* const*>(outs_d.p), nq,
+                                static_cast<const PairItem*>(items_dev.p), (int64_t)pitems.size(), ctx->status_dev, s);
+    else if (e.tc)
       ce = launch_tc_cross(static_cast<const uint8_t*>(e.panel_planes.p), pg.n, e.pgeo.chunks,
                            static_cast<const CrossItem*>(items_dev.p), (int64_t)items.size(),
                            (int)std::min<int64_t>(ctx->num_sms, (int64_t)items.size()), e.fmt,

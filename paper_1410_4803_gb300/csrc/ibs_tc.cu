@@ -1060,6 +1060,37 @@ struct PairBatchWork {
   __device__ static int64_t base(const SubsetDev& s) { return s.pad; }
 };
 
+// Serving on the two-SM kernel: A = two 128-row blocks of the step's dense
+// query planes (I0, I1; I1 < 0: the odd CTA loads I0 again and stores
+// nothing), B = panel block J, over all chunks.  Counts only: step row r
+// writes its 128 panel samples through its own output row row_out[r]
+// ([n_panel][4] int32), as the one-SM CrossWork does.
+struct PairCrossWork {
+  const PairItem* items;
+  int32_t* const* row_out;
+  int64_t n_rows, n_panel, n_chunks;
+  static constexpr bool kFused = false;
+  __device__ SubsetDev sub(int32_t) const {
+    SubsetDev s{};
+    s.n_chunks = n_chunks;
+    return s;
+  }
+  __device__ static int64_t base(const SubsetDev&) { return 0; }
+};
+
+// The epilogue of one CTA's tile of a pair item: triangle output for one
+// matrix or a batch of subsets, per-row output rows for serving.
+template <class PW>
+__device__ __forceinline__ TriEpi pair_epi(const PW& w, const PairItem& pi, int32_t ib, int row) {
+  const SubsetDev sd = w.sub(pi.subset);
+  return TriEpi{ib >= 0 ? (int64_t)ib * kTB + row : sd.n, (int64_t)pi.J * kTB, sd.n, sd.out_counts,
+                sd.out_dist, sd.partial, pi.split != 0};
+}
+__device__ __forceinline__ CrossWork::Epi pair_epi(const PairCrossWork& w, const PairItem& pi, int32_t ib, int row) {
+  const int64_t r = ib >= 0 ? (int64_t)ib * kTB + row : w.n_rows;
+  return {r < w.n_rows ? w.row_out[r] : nullptr, (int64_t)pi.J * kTB, w.n_panel};
+}
+
 // Wait until *counter >= need (another CTA's gather units; bounded).
 __device__ __forceinline__ bool wait_ready(const int* counter, int need, unsigned long long limit_ns) {
   const unsigned long long t0 = globaltimer_ns();
@@ -1095,7 +1126,7 @@ constexpr int kPairBar = 1;
 template <class PW, int kStages, int kPer>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
     tc_pair_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap,
-                   const PW work, int64_t n_items, int* status, unsigned long long wait_ns) {
+                   const PW work, int64_t n_items, int* status, unsigned long long wait_ns, const PairSync sync) {
   constexpr int kABytes = kPer * kTChunkBytes;
   constexpr int kStageBytes = kPairStageBytes<kPer>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -1172,7 +1203,24 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
           break;
         }
       }
+      const bool lockstep = sync.seg > 0 && it < sync.n_items;
+      int* wave_ctr = lockstep ? sync.ctr + (it / step) * sync.n_seg : nullptr;
       for (int64_t k = pi.c0; k < pi.c1; k += kPer, ++g) {
+        if (lockstep && (k - pi.c0) % sync.seg == 0) {
+          // announce this segment, then hold back until the whole wave has
+          // started the segment `lag` back (bounded; seg is a multiple of kPer)
+          const int64_t sg = (k - pi.c0) / sync.seg;
+          bool okw = true;
+          if (lane == 0) {
+            atomicAdd(wave_ctr + sg, 1);
+            if (sg >= sync.lag) okw = wait_ready(wave_ctr + sg - sync.lag, 2 * (int)step, wait_ns);
+          }
+          if (__any_sync(0xffffffffu, !okw)) {
+            fail(true);
+            stop = true;
+            break;
+          }
+        }
         const int s = (int)(g % kStages);
         const bool ok = g < (uint32_t)kStages || mbar_wait_bounded(&empty[s], ((g / kStages) - 1) & 1u, wait_ns);
         if (__any_sync(0xffffffffu, !ok)) {
@@ -1331,9 +1379,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 1)
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int32_t ib = rank == 0 ? pi.I0 : pi.I1;
-      const SubsetDev sd = work.sub(pi.subset);
-      const TriEpi ep{ib >= 0 ? (int64_t)ib * kTB + row : sd.n, (int64_t)pi.J * kTB, sd.n, sd.out_counts,
-                      sd.out_dist, sd.partial, pi.split != 0};
+      const auto ep = pair_epi(work, pi, ib, row);
 #pragma unroll 1
       for (int cg = 0; cg < kTB / 32; ++cg) {
         uint32_t vn[32], vu[32], v0[32];
@@ -1910,9 +1956,12 @@ void tc_pair_items(int64_t n, int64_t m, int fmt, int n_clusters, int group, std
   }
 }
 
+// A operands from a_planes (a_block_chunks block-chunks), B halves from
+// b_planes (b_block_chunks); the same buffer for one matrix or a batch.
 template <class PW, int S, int P>
-cudaError_t launch_pair_w(const PW& work, const void* planes, int64_t block_chunks, int64_t chunks_per_item,
-                          int64_t n_items, int* status, unsigned long long wait_ns, cudaStream_t st) {
+cudaError_t launch_pair_w(const PW& work, const void* a_planes, int64_t a_block_chunks, const void* b_planes,
+                          int64_t b_block_chunks, int64_t chunks_per_item, int64_t n_items, int* status,
+                          unsigned long long wait_ns, cudaStream_t st, const PairSync& sync = PairSync{}) {
   constexpr size_t smem = kPairSmem<S, P>;
   static_assert(smem <= 227 * 1024, "ring exceeds shared memory");
   const int clusters = tc_pair_clusters(chunks_per_item);
@@ -1922,18 +1971,18 @@ cudaError_t launch_pair_w(const PW& work, const void* planes, int64_t block_chun
       cudaFuncSetAttribute(tc_pair_kernel<PW, S, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   CUtensorMap amap, bmap;
-  if (!encode_a_map(&amap, planes, 1, block_chunks, P) || !encode_bhalf_map(&bmap, planes, 1, block_chunks, P))
+  if (!encode_a_map(&amap, a_planes, 1, a_block_chunks, P) || !encode_bhalf_map(&bmap, b_planes, 1, b_block_chunks, P))
     return cudaErrorInvalidValue;
   const int grid = 2 * (int)std::min<int64_t>(clusters, n_items);
-  tc_pair_kernel<PW, S, P><<<grid, 256, smem, st>>>(amap, bmap, work, n_items, status, wait_ns);
+  tc_pair_kernel<PW, S, P><<<grid, 256, smem, st>>>(amap, bmap, work, n_items, status, wait_ns, sync);
   return cudaGetLastError();
 }
 
 template <int S, int P>
 cudaError_t launch_pair_s(const SubsetDev& sd, const PairItem* items, int64_t n_items, int* status,
-                          unsigned long long wait_ns, cudaStream_t st) {
-  return launch_pair_w<PairWork, S, P>(PairWork{sd, items}, sd.planes, sd.n_blocks * sd.n_chunks, sd.n_chunks,
-                                       n_items, status, wait_ns, st);
+                          unsigned long long wait_ns, cudaStream_t st, const PairSync& sync) {
+  return launch_pair_w<PairWork, S, P>(PairWork{sd, items}, sd.planes, sd.n_blocks * sd.n_chunks, sd.planes,
+                                       sd.n_blocks * sd.n_chunks, sd.n_chunks, n_items, status, wait_ns, st, sync);
 }
 
 cudaError_t launch_tc_pair_batch(const PairBatchArgs& a, int* status, unsigned long long wait_ns, cudaStream_t st) {
@@ -1942,25 +1991,75 @@ cudaError_t launch_tc_pair_batch(const PairBatchArgs& a, int* status, unsigned l
   const PairBatchWork w{a.subs, a.items, a.jobs, a.units, a.n_units, a.unit_counter, a.ready, a.need};
   const PairRing r = pair_ring(a.max_chunks);
   if (r.per == 2 && r.stages == 4)
-    return launch_pair_w<PairBatchWork, 4, 2>(w, a.planes, a.block_chunks, a.max_chunks, a.n_items, status, wait_ns, st);
+    return launch_pair_w<PairBatchWork, 4, 2>(w, a.planes, a.block_chunks, a.planes, a.block_chunks, a.max_chunks,
+                                                a.n_items, status, wait_ns, st);
   if (r.per == 1 && r.stages == 8)
-    return launch_pair_w<PairBatchWork, 8, 1>(w, a.planes, a.block_chunks, a.max_chunks, a.n_items, status, wait_ns, st);
+    return launch_pair_w<PairBatchWork, 8, 1>(w, a.planes, a.block_chunks, a.planes, a.block_chunks, a.max_chunks,
+                                                a.n_items, status, wait_ns, st);
   if (r.per == 4 && r.stages == 2)
-    return launch_pair_w<PairBatchWork, 2, 4>(w, a.planes, a.block_chunks, a.max_chunks, a.n_items, status, wait_ns, st);
+    return launch_pair_w<PairBatchWork, 2, 4>(w, a.planes, a.block_chunks, a.planes, a.block_chunks, a.max_chunks,
+                                                a.n_items, status, wait_ns, st);
   if (r.per == 3 && r.stages == 3)
-    return launch_pair_w<PairBatchWork, 3, 3>(w, a.planes, a.block_chunks, a.max_chunks, a.n_items, status, wait_ns, st);
+    return launch_pair_w<PairBatchWork, 3, 3>(w, a.planes, a.block_chunks, a.planes, a.block_chunks, a.max_chunks,
+                                                a.n_items, status, wait_ns, st);
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_tc_pair(const SubsetDev& sd, const PairItem* items, int64_t n_items, int* status,
-                           unsigned long long wait_ns, cudaStream_t st) {
+                           unsigned long long wait_ns, cudaStream_t st, const PairSync& sync) {
   if (n_items <= 0) return cudaSuccess;
   if (n_items > 2147483647LL) return cudaErrorInvalidValue;
   const PairRing r = pair_ring(sd.n_chunks);
-  if (r.per == 2 && r.stages == 4) return launch_pair_s<4, 2>(sd, items, n_items, status, wait_ns, st);
-  if (r.per == 1 && r.stages == 8) return launch_pair_s<8, 1>(sd, items, n_items, status, wait_ns, st);
-  if (r.per == 4 && r.stages == 2) return launch_pair_s<2, 4>(sd, items, n_items, status, wait_ns, st);
-  if (r.per == 3 && r.stages == 3) return launch_pair_s<3, 3>(sd, items, n_items, status, wait_ns, st);
+  if (r.per == 2 && r.stages == 4) return launch_pair_s<4, 2>(sd, items, n_items, status, wait_ns, st, sync);
+  if (r.per == 1 && r.stages == 8) return launch_pair_s<8, 1>(sd, items, n_items, status, wait_ns, st, sync);
+  if (r.per == 4 && r.stages == 2) return launch_pair_s<2, 4>(sd, items, n_items, status, wait_ns, st, sync);
+  if (r.per == 3 && r.stages == 3) return launch_pair_s<3, 3>(sd, items, n_items, status, wait_ns, st, sync);
+  return cudaErrorInvalidValue;
+}
+
+int2 tc_pair_sync_setting(int64_t chunks_per_item) {
+  static const int2 v = [] {
+    int seg = 0, lag = 0;
+    if (const char* e = getenv("IBS_TC_PAIR_SYNC"))
+      if (sscanf(e, "%d,%d", &seg, &lag) != 2) seg = lag = 0;
+    // a segment must exceed the ring (partners then stay within one segment
+    // of each other) and lag >= 2, which keeps the least advanced CTA and its
+    // partner free of waits: the lockstep cannot deadlock
+    if (seg < 16 || seg > 65536 || lag < 2 || lag > 1024) seg = lag = 0;
+    return make_int2(seg, lag);
+  }();
+  if (v.x == 0) return v;
+  const int per = pair_ring(chunks_per_item).per;
+  return make_int2((v.x + per - 1) / per * per, v.y);
+}
+
+bool tc_pair_cross_usable(int64_t n_panel, int64_t n_chunks, int fmt) {
+  if (tc_pair_mode() < 0 || fmt != kTcFp4) return false;
+  if (tc_pair_mode() == 0 && n_chunks < kPairMinChunks) return false;
+  const int64_t pb = (n_panel + kTB - 1) / kTB;
+  if (pb * n_chunks + 8 > 2147483647LL) return false;  // the tensor map's chunk coordinate is an int
+  if (!encode_tiled_fn()) return false;
+  return tc_pair_clusters(n_chunks) > 0;
+}
+
+cudaError_t launch_tc_pair_cross(const uint8_t* panel, int64_t n_panel, int64_t n_chunks, const uint8_t* qplanes,
+                                 int64_t q_blocks_cap, int32_t* const* row_out, int64_t n_rows, const PairItem* items,
+                                 int64_t n_items, int* status, cudaStream_t st) {
+  if (n_items <= 0) return cudaSuccess;
+  const int64_t pb = (n_panel + kTB - 1) / kTB;
+  if (n_items > 2147483647LL || q_blocks_cap * n_chunks + 8 > 2147483647LL || pb * n_chunks + 8 > 2147483647LL)
+    return cudaErrorInvalidValue;
+  const PairCrossWork w{items, row_out, n_rows, n_panel, n_chunks};
+  const PairRing r = pair_ring(n_chunks);
+  const int64_t qa = q_blocks_cap * n_chunks, pa = pb * n_chunks;
+  if (r.per == 2 && r.stages == 4)
+    return launch_pair_w<PairCrossWork, 4, 2>(w, qplanes, qa, panel, pa, n_chunks, n_items, status, kWaitLimitNs, st);
+  if (r.per == 1 && r.stages == 8)
+    return launch_pair_w<PairCrossWork, 8, 1>(w, qplanes, qa, panel, pa, n_chunks, n_items, status, kWaitLimitNs, st);
+  if (r.per == 4 && r.stages == 2)
+    return launch_pair_w<PairCrossWork, 2, 4>(w, qplanes, qa, panel, pa, n_chunks, n_items, status, kWaitLimitNs, st);
+  if (r.per == 3 && r.stages == 3)
+    return launch_pair_w<PairCrossWork, 3, 3>(w, qplanes, qa, panel, pa, n_chunks, n_items, status, kWaitLimitNs, st);
   return cudaErrorInvalidValue;
 }
 

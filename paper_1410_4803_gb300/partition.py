@@ -3,15 +3,20 @@
 The paper splits a sample x sample matrix across processes with
 `--parallel k K`, each run computing 1/K of the matrix and the pieces being
 concatenated ("Multicore and cluster parallelism", "Memory efficiency").  The
-GPU equivalent: the 64 x 64 pair tiles of the upper triangle, in row-major
-order, are cut into contiguous ranges of whole tile rows with near-equal work
-(row I holds T - I tiles).  Each rank needs the planes of its rows and of all
+GPU equivalent: the pair tiles of the upper triangle, in row-major order, are
+cut into contiguous ranges of whole tile rows with near-equal work (row I
+holds T - I tiles).  Each rank needs the planes of its rows and of all
 columns to its right; the ranks' outputs are disjoint, so no reduction is
 needed.  This module is host logic only.
+
+The default tile is the tensor-core kernels' 128-sample block (the operand
+planes' block), so a rank's range never splits a block; the integer (POPC)
+form works on 64-sample blocks and takes ``tile=TILE_POPC``.
 """
 from __future__ import annotations
 
-TILE = 64
+TILE = 128      # sample block of the tensor-core operand planes (default form)
+TILE_POPC = 64  # sample block of the integer form's bit planes
 
 
 def n_tiles(n: int, tile: int = TILE) -> int:

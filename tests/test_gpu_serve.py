@@ -209,3 +209,71 @@ def test_shutdown_cancels_pending(panel):
         t.join(timeout=60)
     assert len(statuses) == len(rids)
     assert all(s in (ibs.IBS_OK, ibs.IBS_ECANCELLED) for s in statuses)
+
+
+SERVE_TWO_SM = r"""
+import sys
+import numpy as np
+import torch
+sys.path.insert(0, {tests!r}); sys.path.insert(0, {root!r})
+import oracle
+from helpers import pack_codes, random_codes
+from paper_1410_4803_gb300 import ibs
+rng = np.random.default_rng(5)
+n_panel, m, k = 5999, 2100, 8  # 47 panel blocks (ragged), 33 chunks (ragged), padding garbage
+pcodes = random_codes(rng, n_panel, m, miss=0.03)
+pp = pack_codes(pcodes, garbage_rng=np.random.default_rng(3))
+ctx = ibs.ibs_init(0, flags=ibs.IBS_KERNEL_TC | ibs.IBS_TC_FP4)
+ibs.ibs_panel_load(ctx, torch.from_numpy(pp).cuda(), n_panel, m)
+# 4,096 rows in all: odd and even numbers of 128-row blocks, a lone row, a
+# request that spans several steps
+sizes = [2900, 1, 130, 300, 129, 64, 77, 495]
+reqs = []
+for i, q in enumerate(sizes):
+    qc = random_codes(np.random.default_rng(100 + i), q, m, miss=0.03)
+    reqs.append((q, qc, pack_codes(qc, garbage_rng=np.random.default_rng(200 + i))))
+outs = [(torch.empty((q, n_panel, 4), dtype=torch.int32).pin_memory(), torch.empty((q, k), dtype=torch.int32).pin_memory(),
+         torch.empty((q, k), dtype=torch.float64).pin_memory()) for q, _, _ in reqs]
+ids = [ibs.ibs_query(ctx, qp, q, k, *o) for (q, _, qp), o in zip(reqs, outs)]
+for rid in ids:
+    ibs.ibs_wait(ctx, rid, timeout_ms=120000)
+st = ibs.ibs_serve_stats_get(ctx)
+assert st["requests_done"] == len(sizes), st
+for i, ((q, qc, qp), (oc, oi, od)) in enumerate(zip(reqs, outs)):
+    ac = torch.empty((q, n_panel, 4), dtype=torch.int32).pin_memory()
+    ai = torch.empty((q, k), dtype=torch.int32).pin_memory()
+    ad = torch.empty((q, k), dtype=torch.float64).pin_memory()
+    ibs.ibs_query_sync(ctx, qp, q, k, ac, ai, ad)
+    assert (oc.numpy() == ac.numpy()).all(), f"request {{i}}: engine and unbatched counts differ"
+    assert (oi.numpy() == ai.numpy()).all()
+    rows = np.arange(q) if q <= 512 else np.linspace(0, q - 1, 64).astype(np.int64)
+    wc, wd = oracle.ibs_block(qc, pcodes, rows=rows)
+    bad = np.flatnonzero((oc.numpy()[rows] != wc).any(axis=(1, 2)))
+    assert bad.size == 0, f"request {{i}} (q={{q}}): rows {{rows[bad[:4]]}} differ from the oracle"
+    for t, r in enumerate(rows):
+        ti, td = oracle.topk(wd[t], k)
+        assert (oi.numpy()[r] == ti).all(), f"request {{i}} row {{r}}: top-k differs"
+        fin = ~np.isnan(td)
+        assert (np.isnan(od.numpy()[r]) == ~fin).all()
+        assert np.allclose(od.numpy()[r][fin], td[fin], rtol=1e-12, atol=0)
+    print(f"ok q={{q}}")
+ibs.ibs_shutdown(ctx)
+"""
+
+
+def test_serving_two_sm_kernel_matches_oracle():
+    """The engine's steps and the unbatched path on the two-SM kernel (forced
+    on for this small panel with IBS_TC_PAIR=1; the switch is read once per
+    process, so the case runs in a child): items of two query blocks x one
+    panel block, a lone last block when the step's block count is odd, steps
+    of one block on the one-SM kernel, counts columns copied to host memory
+    step by step."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = SERVE_TWO_SM.format(tests=os.path.join(root, "tests"), root=root)
+    env = dict(os.environ, IBS_TC_PAIR="1")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.count("ok q=") == 8, r.stdout

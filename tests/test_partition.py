@@ -10,11 +10,21 @@ import pytest
 from paper_1410_4803_gb300 import partition
 
 
-@pytest.mark.parametrize("n", [1, 63, 64, 65, 500, 4096, 20000])
+def test_default_tile_is_the_tensor_core_block():
+    assert partition.TILE == 128 and partition.TILE_POPC == 64
+    # a rank boundary falls on a 128-sample block edge
+    for world in (2, 3, 8):
+        for rank in range(world):
+            r0, r1 = partition.pair_rows(20000, rank, world)
+            assert r0 % 128 == 0 and (r1 % 128 == 0 or r1 == 20000)
+
+
+@pytest.mark.parametrize("n", [1, 63, 64, 65, 127, 128, 129, 500, 4096, 20000])
 @pytest.mark.parametrize("world", [1, 2, 3, 8])
-def test_ranges_cover_triangle(n, world):
-    T = partition.n_tiles(n)
-    ranges = partition.partition_tiles(n, world)
+@pytest.mark.parametrize("tile", [partition.TILE, partition.TILE_POPC])
+def test_ranges_cover_triangle(n, world, tile):
+    T = partition.n_tiles(n, tile)
+    ranges = partition.partition_tiles(n, world, tile)
     assert ranges[0][0] == 0 and ranges[-1][1] == T * (T + 1) // 2
     for (a, b), (c, d) in zip(ranges, ranges[1:]):
         assert b == c and a <= b
