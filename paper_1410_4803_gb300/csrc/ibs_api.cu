@@ -234,7 +234,7 @@ ibs_status ibs_compute(ibs_ctx* ctx, const uint8_t* packed, int64_t n, int64_t m
   int splits = 1;
   if (persistent) {
     // the two-SM kernel where it applies (E2M1, at least two blocks, items of
-    // at least 4,096 chunks unless IBS_TC_PAIR says otherwise); its work list
+    // at least 1,024 chunks unless IBS_TC_PAIR says otherwise); its work list
     // depends on how many clusters of two fit at once
     const int pair_clusters = tc_pair_usable(n, m, fmt) ? tc_pair_clusters(tc_chunks(m, fmt)) : 0;
     const std::vector<int64_t> key = {n, m, fmt, ctx->num_sms, group, pair_clusters};
@@ -599,6 +599,8 @@ ibs_status plan_build(ibs_ctx* ctx, BatchPlan& plan, const std::vector<SubsetSha
   for (int64_t q : plan.order) plan.q_chunks.push_back(item_geom(shapes[(size_t)q], mode).nc);
   plan.q_pair_off.assign(plan.order.size(), -1);
   plan.q_pair_n.assign(plan.order.size(), 0);
+  plan.q_pair_sync.assign(plan.order.size(), 0);
+  plan.pair_sync_bytes = 0;
   plan.n_pitems = 0;
   plan.pair_max_chunks = 0;
   std::vector<PairItem> p2_items;
@@ -620,6 +622,18 @@ ibs_status plan_build(ibs_ctx* ctx, BatchPlan& plan, const std::vector<SubsetSha
                     own_split);
       plan.q_pair_off[q] = (int64_t)p2_items.size();
       plan.q_pair_n[q] = (int64_t)own.size();
+      {
+        // its own launch (policy 2) keeps its leading whole waves in K-lockstep
+        const int C = tc_pair_clusters(ig.nc);
+        const int2 ss = tc_pair_sync_setting(ig.nc);
+        int64_t whole = 0;
+        while (whole < (int64_t)own.size() && own[(size_t)whole].split == 0) ++whole;
+        if (split_policy == 2 && ss.x > 0 && C > 0 && whole >= C) {
+          plan.q_pair_sync[q] = whole / C * C;
+          plan.pair_sync_bytes = std::max(plan.pair_sync_bytes,
+                                          (size_t)(whole / C) * (size_t)((ig.nc + ss.x - 1) / ss.x) * sizeof(int));
+        }
+      }
       plan.pair_max_chunks = std::max(plan.pair_max_chunks, ig.nc);
       for (PairItem w : own) {
         w.subset = (int32_t)k;
@@ -675,6 +689,8 @@ ibs_status plan_build(ibs_ctx* ctx, BatchPlan& plan, const std::vector<SubsetSha
     if (split_policy == 2) {
       std::vector<int32_t> zero(shapes.size(), 0);
       if (ibs_status s = ensure_buf(ctx, plan.pitems, sizeof(PairItem) * std::max<size_t>(1, p2_items.size()))) return s;
+      if (plan.pair_sync_bytes > 0)
+        if (ibs_status s = ensure_buf(ctx, plan.pair_sync, plan.pair_sync_bytes)) return s;
       if (ibs_status s = ensure_buf(ctx, plan.units, sizeof(int4))) return s;
       if (ibs_status s = ensure_buf(ctx, plan.unit_counter, 256)) return s;
       if (ibs_status s = ensure_buf(ctx, plan.ready, sizeof(int32_t) * shapes.size())) return s;
@@ -960,6 +976,18 @@ ibs_status plan_enqueue(ibs_ctx* ctx, BatchPlan& plan, int n_subsets, cudaStream
             a.planes = plan.tc_planes.p;
             a.block_chunks = plan.tc_block_chunks;
             a.max_chunks = plan.q_chunks[(size_t)q];
+            if (plan.q_pair_sync[(size_t)q] > 0) {
+              const int2 ss = tc_pair_sync_setting(a.max_chunks);
+              a.sync.seg = ss.x;
+              a.sync.lag = ss.y;
+              a.sync.n_seg = (int32_t)((a.max_chunks + ss.x - 1) / ss.x);
+              a.sync.n_items = plan.q_pair_sync[(size_t)q];
+              a.sync.ctr = static_cast<int*>(plan.pair_sync.p);
+              IBS_CUDA_TRY(cudaMemsetAsync(plan.pair_sync.p, 0,
+                                           (size_t)(a.sync.n_items / tc_pair_clusters(a.max_chunks)) * a.sync.n_seg *
+                                               sizeof(int),
+                                           st));
+            }
             IBS_CUDA_TRY(launch_tc_pair_batch(a, ctx->status_dev, kWaitLimitNs, st));
             continue;
           }
@@ -1011,7 +1039,7 @@ void plan_free(ibs_ctx* ctx, BatchPlan& plan) {
   plan.graph = nullptr;
   for (DevBuf* b : {&plan.planes, &plan.partial, &plan.subsets, &plan.jobs, &plan.items, &plan.split_ids,
                     &plan.counter, &plan.tc_planes, &plan.tc_jobs, &plan.split_tiles, &plan.gather_map, &plan.pitems,
-                    &plan.units, &plan.unit_counter, &plan.ready, &plan.need})
+                    &plan.units, &plan.unit_counter, &plan.ready, &plan.need, &plan.pair_sync})
     free_buf(ctx, *b);
 }
 

@@ -76,6 +76,11 @@ struct BatchPlan {
   // split policy 2: subsets that ibs_compute would run on the two-SM kernel
   // take its pair work list (q_pair_off/q_pair_n into pitems, -1 = one-SM)
   std::vector<int64_t> q_pair_off, q_pair_n;
+  // ... and their K-lockstep: items in whole waves per position (0 = none),
+  // one counter buffer for the largest, zeroed before each launch
+  std::vector<int64_t> q_pair_sync;
+  DevBuf pair_sync;
+  size_t pair_sync_bytes = 0;
   cudaStream_t side = nullptr;
   std::vector<cudaEvent_t> stage_ev;
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;  // policy 3: the side stream's gather

@@ -176,8 +176,8 @@ cudaError_t launch_tc_single(const SubsetDev& sd, const WorkItem* items, int64_t
 // -1 never, 0 for items of at least 1,024 chunks, from IBS_TC_PAIR).
 int tc_pair_mode();
 int tc_pair_clusters(int64_t chunks_per_item);
-// K-lockstep of the pair kernel's full waves (off unless IBS_TC_PAIR_SYNC=
-// seg,lag): the items [0, n_items) come in waves of one item per cluster, all
+// K-lockstep of the pair kernel's full waves (the default; IBS_TC_PAIR_SYNC=
+// seg,lag or off): the items [0, n_items) come in waves of one item per cluster, all
 // of equal length; the copy warp of every CTA counts each seg-chunk segment
 // it starts in ctr[wave * n_seg + segment] and, before segment s, waits
 // (bounded) until every CTA of its wave has started segment s - lag, so the
@@ -217,6 +217,7 @@ struct PairBatchArgs {
   const void* planes;
   int64_t block_chunks;
   int64_t max_chunks;
+  PairSync sync;  // K-lockstep of the launch's whole waves (policy 2), or off
 };
 cudaError_t launch_tc_pair_batch(const PairBatchArgs& a, int* status, unsigned long long wait_ns, cudaStream_t st);
 // Gather units of a PairBatchArgs list by `ctas` persistent CTAs (run beside
@@ -243,7 +244,7 @@ cudaError_t launch_tc_gather_rows(const RowSrc* rows, int64_t n_rows, int64_t n_
 bool tc_pair_cross_usable(int64_t n_panel, int64_t n_chunks, int fmt);
 cudaError_t launch_tc_pair_cross(const uint8_t* panel, int64_t n_panel, int64_t n_chunks, const uint8_t* qplanes,
                                  int64_t q_blocks_cap, int32_t* const* row_out, int64_t n_rows, const PairItem* items,
-                                 int64_t n_items, int* status, cudaStream_t st);
+                                 int64_t n_items, int* status, cudaStream_t st, const PairSync& sync = PairSync{});
 int tc_block_samples();  // 128
 // LD correlation (ibs_ld.cu): operand planes of the markers (128-marker
 // blocks, 64-sample chunks, planes X, V, H), the band's work items and the

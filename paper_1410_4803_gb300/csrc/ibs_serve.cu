@@ -119,6 +119,7 @@ class ServeEngine {
   int grid_ctas = 0;   // persistent cross-kernel CTAs (SMs x 2)
   bool pair = false;   // two-SM kernel for steps of two or more query blocks
   int clusters = 0;    // its clusters of two CTAs
+  DevBuf sync_ctr;     // the two-SM kernel's K-lockstep counters of a step
   cudaStream_t side = nullptr;  // device -> host copies of finished columns and top-k lists
   cudaEvent_t kern_ev[2] = {nullptr, nullptr}, fin_ev[2] = {nullptr, nullptr};
   uint64_t set_version = 1, gathered_version = 0;  // the admitted set; the set the step planes hold
@@ -293,6 +294,26 @@ class ServeEngine {
     items_cap = n;
   }
 
+  // K-lockstep of a two-SM launch of n_items equal items (whole waves of one
+  // item per cluster take part); counters zeroed on stream s.  Off (an empty
+  // PairSync) when the setting is off or the counters cannot be had.
+  PairSync pair_sync(int64_t n_items, DevBuf& ctr, bool library_buf, cudaStream_t s) {
+    PairSync ps;
+    const int2 ss = tc_pair_sync_setting(pgeo.chunks);
+    const int64_t waves = n_items / std::max(1, clusters);
+    if (ss.x <= 0 || waves < 1) return ps;
+    const int32_t n_seg = (int32_t)((pgeo.chunks + ss.x - 1) / ss.x);
+    const size_t bytes = (size_t)waves * n_seg * sizeof(int);
+    if (library_buf ? ensure_buf(ctx, ctr, bytes) != IBS_OK : alloc(ctr, bytes, s) != IBS_OK) return ps;
+    if (cudaMemsetAsync(ctr.p, 0, bytes, s) != cudaSuccess) return ps;
+    ps.ctr = static_cast<int*>(ctr.p);
+    ps.seg = ss.x;
+    ps.lag = ss.y;
+    ps.n_seg = n_seg;
+    ps.n_items = waves * clusters;
+    return ps;
+  }
+
   // Step length in panel blocks for `units` item rows (query blocks, or query
   // block pairs on the two-SM kernel) run by C persistent CTAs or clusters:
   // about kStepWaves(Tc) waves of items, at least 1/kMinStepDiv of the panel,
@@ -406,7 +427,8 @@ class ServeEngine {
         cudaMemcpyAsync(items_dev[slot].p, items_host[slot], t * sizeof(PairItem), cudaMemcpyHostToDevice, stream);
         launch_tc_pair_cross(static_cast<const uint8_t*>(panel_planes.p), pg.n, pgeo.chunks,
                              static_cast<const uint8_t*>(step_planes.p), geo(kMaxRows).blocks, outs_d, n_rows,
-                             static_cast<const PairItem*>(items_dev[slot].p), (int64_t)t, ctx->status_dev, stream);
+                             static_cast<const PairItem*>(items_dev[slot].p), (int64_t)t, ctx->status_dev, stream,
+                             pair_sync((int64_t)t, sync_ctr, true, stream));
       } else {
         cudaMemcpyAsync(items_dev[slot].p, items_host[slot], t * sizeof(CrossItem), cudaMemcpyHostToDevice, stream);
         cross(static_cast<const CrossItem*>(items_dev[slot].p), (int64_t)t, stream);
@@ -544,6 +566,7 @@ class ServeEngine {
     if (panel_planes.p) free_buf(ctx, panel_planes);
     free_buf(ctx, step_planes);
     free_buf(ctx, counter);
+    free_buf(ctx, sync_ctr);
     for (int s = 0; s < 2; ++s) {
       free_buf(ctx, rows_dev[s]);
       free_buf(ctx, outs_dev[s]);
@@ -626,6 +649,20 @@ ibs_status serve_panel_load(ibs_ctx* ctx, const uint8_t* panel, int64_t n_panel,
   eng->pair = eng->tc && tc_pair_cross_usable(n_panel, eng->pgeo.chunks, eng->fmt);
   eng->clusters = eng->pair ? tc_pair_clusters(eng->pgeo.chunks) : 0;
   if (eng->clusters < 1) eng->pair = false;
+  if (eng->pair) {
+    // lockstep counters for the largest step (all 4,096 rows, every panel
+    // block), so that a step never grows them while earlier steps run
+    const int2 ss = tc_pair_sync_setting(eng->pgeo.chunks);
+    const int64_t max_items = (eng->geo(kMaxRows).blocks + 1) / 2 * eng->pgeo.blocks;
+    if (ss.x > 0) {
+      const size_t bytes =
+          (size_t)(max_items / eng->clusters + 1) * (size_t)((eng->pgeo.chunks + ss.x - 1) / ss.x) * sizeof(int);
+      if (ibs_status st = ensure_buf(ctx, eng->sync_ctr, bytes)) {
+        eng->shutdown();
+        return st;
+      }
+    }
+  }
   // Requests draw on the device's default stream-ordered pool; keep freed
   // blocks cached in it so steady-state serving does not go back to the driver.
   cudaMemPool_t mp;
@@ -818,7 +855,7 @@ ibs_status serve_query_sync(ibs_ctx* ctx, const uint8_t* q, int64_t nq, int k, i
   }
   const size_t item_bytes = two_sm ? pitems.size() * sizeof(PairItem) : items.size() * sizeof(CrossItem);
   const void* item_src = two_sm ? static_cast<const void*>(pitems.data()) : static_cast<const void*>(items.data());
-  DevBuf items_dev;
+  DevBuf items_dev, sync_d;
   if (ce == cudaSuccess) ce = cudaMallocAsync(&items_dev.p, item_bytes, s);
   if (ce == cudaSuccess)
     ce = cudaMemcpyAsync(outs_d.p, outs.data(), outs.size() * sizeof(int32_t*), cudaMemcpyHostToDevice, s);
@@ -833,7 +870,8 @@ ibs_status serve_query_sync(ibs_ctx* ctx, const uint8_t* q, int64_t nq, int k, i
       ce = launch_tc_pair_cross(static_cast<const uint8_t*>(e.panel_planes.p), pg.n, e.pgeo.chunks,
                                 static_cast<const uint8_t*>(r.planes.p), qg.blocks,
                                 static_cast<int32_t* const*>(outs_d.p), nq,
-                                static_cast<const PairItem*>(items_dev.p), (int64_t)pitems.size(), ctx->status_dev, s);
+                                static_cast<const PairItem*>(items_dev.p), (int64_t)pitems.size(), ctx->status_dev, s,
+                                e.pair_sync((int64_t)pitems.size(), sync_d, false, s));
     else if (e.tc)
       ce = launch_tc_cross(static_cast<const uint8_t*>(e.panel_planes.p), pg.n, e.pgeo.chunks,
                            static_cast<const CrossItem*>(items_dev.p), (int64_t)items.size(),
@@ -852,6 +890,7 @@ ibs_status serve_query_sync(ibs_ctx* ctx, const uint8_t* q, int64_t nq, int k, i
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(od, r.tdist.p, (size_t)nq * k * 8, cudaMemcpyDeviceToHost, s);
   }
   if (items_dev.p) cudaFreeAsync(items_dev.p, s);
+  if (sync_d.p) cudaFreeAsync(sync_d.p, s);
   if (outs_d.p) cudaFreeAsync(outs_d.p, s);
   if (counter.p) cudaFreeAsync(counter.p, s);
   e.release(r, s);
