@@ -754,7 +754,15 @@ def run_serve(args, rank, world, local):
 
     torch.cuda.set_device(local)
     t0 = time.perf_counter()
-    panel = synth.serving_panel(device=local)
+    samples = getattr(args, "samples", 0)
+    if samples > 0:
+        # a smaller panel for profiling captures: the same recipe and markers,
+        # its 1,000 offspring and 250 duplicates, fewer base samples
+        if samples < 1255:
+            raise ValueError("serve: --samples must be at least 1,255 (1,250 relatives + 5 base)")
+        panel = synth.serving_panel(n_base_per_pop=(samples - 1250) // 5, device=local)
+    else:
+        panel = synth.serving_panel(device=local)
     gen_s = time.perf_counter() - t0
     n_payload = 48
     sizes = synth.serving_query_sizes(n_payload)
@@ -769,7 +777,9 @@ def run_serve(args, rank, world, local):
     load_s = time.perf_counter() - t
     # oracle spot check later: two query rows against 4,096 evenly spaced panel samples
     check_cols = np.linspace(0, panel.n - 1, 4096).astype(np.int64)
-    panel_host = panel.packed.cpu().numpy()
+    # the oracle check's panel samples only (a 4,096-sample .bed matrix, 205 MB), taken on the device
+    check_packed = subset_packed_device(panel.packed, torch.from_numpy(check_cols).to(panel.packed.device), 0,
+                                        panel.m).cpu().numpy()
     panel.packed = None  # the library holds its own planes of the panel
     torch.cuda.empty_cache()
 
@@ -817,11 +827,51 @@ def run_serve(args, rank, world, local):
         return {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
                 "mean_ms": float(lat.mean() * 1e3), "throughput": total / span, "requests": len(arrivals)}
 
-    # warm-up both paths
+    # warm-up both paths (the exactness checks run after the timed runs, so
+    # that the CPU oracle does not run just before them)
     run_engine([0.0] * 4)
     run_plain([0.0] * 2)
-    # exactness: a few requests, engine vs plain, bit for bit
+    rng = np.random.default_rng(4)
+    results = []
+    clk = ClockSampler(local)
+    clk.start()
+    for lam in args.rates:
+        n_req = args.requests
+        if lam > 0:
+            arrivals = list(np.cumsum(rng.exponential(1.0 / lam, n_req)))
+        else:
+            arrivals = [0.0] * n_req  # saturation: everything arrives at once
+        eng = summarize(arrivals, run_engine(arrivals))
+        pln = summarize(arrivals, run_plain(arrivals))
+        results.append({"lambda_per_s": lam if lam > 0 else "saturation", "engine": eng, "plain": pln})
+    clocks = clk.stop()
+    # Context for the saturation figures, which depend on the host: the
+    # device -> host rate into these pinned request buffers (it varied between
+    # processes on the same kind of box), and the engine at saturation with
+    # device-resident outputs (no host copies at all).
+    host_flat = bufs[0][0].view(-1)
+    probe = torch.empty(host_flat.numel(), dtype=torch.int32, device=local)
+    for _ in range(2):
+        host_flat.copy_(probe)
+    torch.cuda.synchronize(local)
+    t = time.perf_counter()
+    for _ in range(3):
+        host_flat.copy_(probe)
+    torch.cuda.synchronize(local)
+    host_gbs = 3 * probe.numel() * 4 / (time.perf_counter() - t) / 1e9
+    del probe
+    dev_bufs = [(torch.empty((int(q), panel.n, 4), dtype=torch.int32, device=local),
+                 torch.empty((int(q), k), dtype=torch.int32, device=local),
+                 torch.empty((int(q), k), dtype=torch.float64, device=local)) for q in sizes]
+    host_bufs, bufs = bufs, dev_bufs
+    run_engine([0.0] * n_payload)  # first use of the device buffers
+    dev_sat = summarize([0.0] * n_payload, run_engine([0.0] * n_payload))
+    bufs = host_bufs
+    del dev_bufs
+    # exactness: a few requests, engine vs plain, bit for bit; the first
+    # request's first and last rows against the oracle on 4,096 panel samples
     exact = True
+    oracle_ok = False
     for p in range(3):
         q = int(sizes[p])
         a = [torch.empty((q, panel.n, 4), dtype=torch.int32).pin_memory(),
@@ -837,24 +887,10 @@ def run_serve(args, rank, world, local):
             import oracle
             qrows = np.array([0, q - 1], dtype=np.int64)
             GQ = oracle.unpack_subset(payloads[0], q, panel.m, qrows, 0, panel.m)
-            GP = oracle.unpack_subset(panel_host, panel.n, panel.m, check_cols, 0, panel.m)
+            GP = oracle.unpack(check_packed, check_cols.size, panel.m)
             want_c, _ = oracle.ibs_block(GQ, GP)
             oracle_ok = bool(np.array_equal(a[0].numpy()[qrows][:, check_cols], want_c))
-    del panel_host
-    rng = np.random.default_rng(4)
-    results = []
-    clk = ClockSampler(local)
-    clk.start()
-    for lam in args.rates:
-        n_req = args.requests
-        if lam > 0:
-            arrivals = list(np.cumsum(rng.exponential(1.0 / lam, n_req)))
-        else:
-            arrivals = [0.0] * n_req  # saturation: everything arrives at once
-        eng = summarize(arrivals, run_engine(arrivals))
-        pln = summarize(arrivals, run_plain(arrivals))
-        results.append({"lambda_per_s": lam if lam > 0 else "saturation", "engine": eng, "plain": pln})
-    clocks = clk.stop()
+    del check_packed
     stats = ibs.ibs_serve_stats_get(ctx)
     dtype_s = kernel_dtype(ibs, ctx)
     ibs.ibs_shutdown(ctx)
@@ -869,6 +905,8 @@ def run_serve(args, rank, world, local):
                                f"top-{k} to pinned host buffers", "distinct_payloads": n_payload,
                    "mean_q": float(np.mean(sizes)), "panel_generation_s": gen_s, "panel_load_s": load_s},
         "serving": results, "engine_stats": stats,
+        "host_context": {"d2h_gbs_into_request_buffers": host_gbs,
+                         "engine_saturation_device_outputs": dev_sat},
         "exact": {"engine_equals_plain": bool(exact),
                   "oracle_two_query_rows_x_4096_panel_samples": oracle_ok},
         "clocks": clocks,
@@ -1179,7 +1217,7 @@ def main():
     ap.add_argument("--requests", type=int, default=None, help="serving: requests per rate")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--samples", type=int, default=0,
-                    help="plain/structured: a smaller case with this many samples (profiling captures)")
+                    help="plain/structured/serve: a smaller case with this many samples (profiling captures)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-step-seconds", type=float, default=3.0)
     args = ap.parse_args()
@@ -1230,7 +1268,7 @@ def main():
                 args.requests = 48
             sv = run_serve(args, rank, world, local)
             line["served"] = sub_record(sv, ["value", "unit", "dtype", "config", "serving", "engine_stats",
-                                             "exact", "clocks"])
+                                             "host_context", "exact", "clocks"])
     if line is not None:
         print(json.dumps(line))
     if world > 1 and args.impl == "ours":

@@ -119,6 +119,16 @@ cudaError_t launch_cross(int mode, const uint32_t* panel_planes, int64_t n_panel
                          cudaStream_t st);
 cudaError_t launch_gather_rows(const RowSrc* rows, int64_t n_rows, int64_t n_chunks, uint32_t* dst,
                                cudaStream_t st);
+// Top-k of many query rows in one launch (rows of any requests, 1 <= k <= 64
+// each): counts [n_panel][4] of the row -> out_idx [k], out_dist [k].
+struct TopkRow {
+  const int32_t* counts;
+  int32_t* out_idx;
+  double* out_dist;
+  int32_t k;
+  int32_t pad;
+};
+cudaError_t launch_topk_rows(const TopkRow* rows, int64_t n_rows, int64_t n_panel, cudaStream_t st);
 cudaError_t launch_topk(const int32_t* counts, int64_t q, int64_t n_panel, int k, int32_t* out_idx,
                         double* out_dist, cudaStream_t st);
 int pair_kernel_ctas_per_sm(int mode);

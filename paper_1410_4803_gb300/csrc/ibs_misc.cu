@@ -22,11 +22,10 @@ __device__ __forceinline__ bool key_less(uint64_t ka, int ia, uint64_t kb, int i
   return ka < kb || (ka == kb && ia < ib);
 }
 
-__global__ void __launch_bounds__(kTopkThreads)
-    topk_kernel(const int32_t* __restrict__ counts, int64_t n_panel, int k, int32_t* __restrict__ out_idx,
-                double* __restrict__ out_dist) {
-  const int64_t row = blockIdx.x;
-  const int4* c = reinterpret_cast<const int4*>(counts) + row * n_panel;
+// One row's k nearest panel samples (one CTA of kTopkThreads threads):
+// counts c[n_panel] -> out_idx[k], out_dist[k].
+__device__ __forceinline__ void topk_row(const int4* __restrict__ c, int64_t n_panel, int k,
+                                         int32_t* __restrict__ out_idx, double* __restrict__ out_dist) {
   uint64_t key[kTopkMax];
   int idx[kTopkMax];
 #pragma unroll
@@ -43,6 +42,18 @@ __global__ void __launch_bounds__(kTopkThreads)
     if (q.w == 0) {
       kk = kNanKey;
     } else {
+      // Cheap exact reject once the list is full of finite keys: the two
+      // integer-to-FP32 conversions and the FP32 division are each correctly
+      // rounded, so the FP32 quotient f is within 3 * 2^-24 (relative) of the
+      // rational r.  If f > t (1 + 2^-20), with t the list's k-th key, then
+      // r > t, and the double key (r rounded, a monotone map) is >= t: it
+      // would not be inserted (strict comparison below).  Only the others pay
+      // the FP64 division.
+      const uint64_t last = key[k - 1];
+      if (last < kNanKey) {
+        const float f = __fdiv_rn((float)(q.y + 2 * q.x), (float)(2 * q.w));
+        if ((double)f > __longlong_as_double((long long)last) * (1.0 + 0x1p-20)) continue;
+      }
       const double d = (double)(q.y + 2 * q.x) / (2.0 * (double)q.w);
       kk = (uint64_t)__double_as_longlong(d);
     }
@@ -102,8 +113,8 @@ __global__ void __launch_bounds__(kTopkThreads)
           bt = wt[w];
         }
       const bool pad = bk == kPadKey;
-      out_idx[row * k + r] = pad ? -1 : bi;
-      out_dist[row * k + r] =
+      out_idx[r] = pad ? -1 : bi;
+      out_dist[r] =
           (pad || bk == kNanKey) ? __longlong_as_double(0x7ff8000000000000LL) : __longlong_as_double((long long)bk);
       winner = pad ? -1 : bt;
     }
@@ -111,6 +122,21 @@ __global__ void __launch_bounds__(kTopkThreads)
     if (threadIdx.x == winner) ++head;
     __syncthreads();
   }
+}
+
+// One request: row r of counts [q][n_panel] -> out_idx/out_dist [q][k].
+__global__ void __launch_bounds__(kTopkThreads)
+    topk_kernel(const int32_t* __restrict__ counts, int64_t n_panel, int k, int32_t* __restrict__ out_idx,
+                double* __restrict__ out_dist) {
+  const int64_t row = blockIdx.x;
+  topk_row(reinterpret_cast<const int4*>(counts) + row * n_panel, n_panel, k, out_idx + row * k,
+           out_dist + row * k);
+}
+
+// Many requests in one launch: CTA r takes row list entry r.
+__global__ void __launch_bounds__(kTopkThreads) topk_rows_kernel(const TopkRow* __restrict__ rows, int64_t n_panel) {
+  const TopkRow t = rows[blockIdx.x];
+  topk_row(reinterpret_cast<const int4*>(t.counts), n_panel, t.k, t.out_idx, t.out_dist);
 }
 
 // ---------------------------------------------------------------------------
@@ -199,6 +225,13 @@ cudaError_t launch_topk(const int32_t* counts, int64_t q, int64_t n_panel, int k
   if (q <= 0 || k <= 0) return cudaSuccess;
   if (k > kTopkMax || q > 2147483647LL) return cudaErrorInvalidValue;
   topk_kernel<<<(unsigned)q, kTopkThreads, 0, st>>>(counts, n_panel, k, out_idx, out_dist);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_topk_rows(const TopkRow* rows, int64_t n_rows, int64_t n_panel, cudaStream_t st) {
+  if (n_rows <= 0) return cudaSuccess;
+  if (n_rows > 2147483647LL) return cudaErrorInvalidValue;
+  topk_rows_kernel<<<(unsigned)n_rows, kTopkThreads, 0, st>>>(rows, n_panel);
   return cudaGetLastError();
 }
 

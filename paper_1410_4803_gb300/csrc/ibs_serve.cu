@@ -120,6 +120,8 @@ class ServeEngine {
   bool pair = false;   // two-SM kernel for steps of two or more query blocks
   int clusters = 0;    // its clusters of two CTAs
   DevBuf sync_ctr;     // the two-SM kernel's K-lockstep counters of a step
+  DevBuf topk_dev[2];  // row lists of a step's finishing requests (one top-k launch)
+  TopkRow* topk_host[2] = {nullptr, nullptr};
   cudaStream_t side = nullptr;  // device -> host copies of finished columns and top-k lists
   cudaEvent_t kern_ev[2] = {nullptr, nullptr}, fin_ev[2] = {nullptr, nullptr};
   uint64_t set_version = 1, gathered_version = 0;  // the admitted set; the set the step planes hold
@@ -261,11 +263,21 @@ class ServeEngine {
   // and their completion events on the copy stream (after their last counts
   // columns).
   void finish(const std::vector<std::shared_ptr<Request>>& done, int slot) {
+    // every row of every finishing request in one launch (at most kMaxRows
+    // rows: the admitted set never holds more)
+    int64_t n = 0;
     for (auto& rp : done) {
       Request& r = *rp;
+      if (r.k <= 0) continue;
       int32_t* oi = r.topk_on_dev ? r.user_idx : static_cast<int32_t*>(r.tidx.p);
       double* od = r.topk_on_dev ? r.user_dist : static_cast<double*>(r.tdist.p);
-      if (r.k > 0) launch_topk(counts_ptr(r), r.q, pg.n, r.k, oi, od, stream);
+      const int32_t* cnt = counts_ptr(r);
+      for (int64_t row = 0; row < r.q && n < kMaxRows; ++row, ++n)
+        topk_host[slot][n] = TopkRow{cnt + (size_t)row * pg.n * 4, oi + row * r.k, od + row * r.k, r.k, 0};
+    }
+    if (n > 0) {
+      cudaMemcpyAsync(topk_dev[slot].p, topk_host[slot], (size_t)n * sizeof(TopkRow), cudaMemcpyHostToDevice, stream);
+      launch_topk_rows(static_cast<const TopkRow*>(topk_dev[slot].p), n, pg.n, stream);
     }
     if (!fin_ev[slot]) cudaEventCreateWithFlags(&fin_ev[slot], cudaEventDisableTiming);
     cudaEventRecord(fin_ev[slot], stream);
@@ -346,6 +358,10 @@ class ServeEngine {
     if (ibs_status s = ensure_buf(ctx, step_planes, geo(kMaxRows).bytes)) return s;
     if (ibs_status s = ensure_buf(ctx, counter, 256)) return s;
     for (int s = 0; s < 2; ++s) {
+      if (ibs_status e = ensure_buf(ctx, topk_dev[s], kMaxRows * sizeof(TopkRow))) return e;
+      if (cudaHostAlloc(reinterpret_cast<void**>(&topk_host[s]), kMaxRows * sizeof(TopkRow), cudaHostAllocDefault) !=
+          cudaSuccess)
+        return fail(IBS_ENOMEM, "pinned top-k tables could not be allocated");
       if (ibs_status e = ensure_buf(ctx, rows_dev[s], kMaxRows * sizeof(RowSrc))) return e;
       if (ibs_status e = ensure_buf(ctx, outs_dev[s], kMaxRows * sizeof(int32_t*))) return e;
       if (cudaHostAlloc(reinterpret_cast<void**>(&rows_host[s]), kMaxRows * sizeof(RowSrc), cudaHostAllocDefault) !=
@@ -568,6 +584,9 @@ class ServeEngine {
     free_buf(ctx, counter);
     free_buf(ctx, sync_ctr);
     for (int s = 0; s < 2; ++s) {
+      free_buf(ctx, topk_dev[s]);
+      if (topk_host[s]) cudaFreeHost(topk_host[s]);
+      topk_host[s] = nullptr;
       free_buf(ctx, rows_dev[s]);
       free_buf(ctx, outs_dev[s]);
       if (rows_host[s]) cudaFreeHost(rows_host[s]);
