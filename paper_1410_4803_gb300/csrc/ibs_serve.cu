@@ -28,7 +28,8 @@
 // full as possible.  The dense query planes are gathered again only when the
 // set of admitted requests changed.  Counts bound for host memory leave the
 // device step by step on a second stream (the panel columns each step wrote),
-// so those copies overlap the following steps instead of trailing them.
+// so those copies overlap the following steps instead of trailing them.  The
+// top-k of all requests that finish in a step runs as one launch.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
