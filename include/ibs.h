@@ -130,7 +130,10 @@ ibs_status ibs_compute_sz(ibs_ctx* ctx, const uint8_t* packed, size_t packed_byt
  * those of ibs_compute (upper triangle, out_dist optional), on the CURRENT
  * device.  Inputs whose planes exceed the scratch, i.e. when
  * ceil(n/64) * ceil(ceil(m/32)/12) * 12288 > 64 MiB (for example n = 4096 with
- * m > 32,640), are rejected with IBS_EINVAL.  The first call on a device looks
+ * m > 32,640), are rejected with IBS_EINVAL.  Small triangles split the
+ * marker axis as ibs_compute does when their partial counts (16 bytes per
+ * pair) fit in the scratch beside the planes; otherwise they run unsplit.  The
+ * first call on a device looks
  * up the scratch address (cudaGetSymbolAddress); make it before any stream
  * capture.  All calls share the one scratch array: calls whose work overlaps
  * on the GPU (different streams, or threads) race and give undefined results;

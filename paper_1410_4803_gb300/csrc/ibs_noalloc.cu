@@ -99,9 +99,20 @@ extern "C" ibs_status ibs_compute_noalloc(const uint8_t* packed, int64_t n, int6
   src.row_bytes = (n + 3) / 4;
   src.n_src = n;
   IBS_CUDA_TRY(launch_planes(src, n, m, geo, g_planes_addr[dev], g_status_addr[dev], st));
-  // One K split only: a split would need a second scratch array for the partial counts.
-  IBS_CUDA_TRY(launch_tri(1, g_planes_addr[dev], geo, 1, out_counts, out_dist, nullptr, false, g_status_addr[dev],
-                          g_sms[dev], st));
+  // Small triangles (fewer tiles than two waves) split the marker axis as
+  // ibs_compute does; their partial counts ([P][4] int32, zeroed here) sit in
+  // the same scratch after the planes when both fit, else one split runs.
+  const int64_t tiles = geo.n_blocks * (geo.n_blocks + 1) / 2;
+  int splits = tri_splits_for(tiles, geo.n_chunks, g_sms[dev]);
+  const size_t planes_bytes = (geo.bytes() + 255) / 256 * 256;
+  const size_t partial_bytes = (size_t)(n * (n + 1) / 2) * 16;
+  if (splits > 1 && planes_bytes + partial_bytes > kNoAllocScratchBytes) splits = 1;
+  int32_t* partial =
+      splits > 1 ? reinterpret_cast<int32_t*>(reinterpret_cast<uint8_t*>(g_planes_addr[dev]) + planes_bytes) : nullptr;
+  if (partial) IBS_CUDA_TRY(cudaMemsetAsync(partial, 0, partial_bytes, st));
+  IBS_CUDA_TRY(launch_tri(1, g_planes_addr[dev], geo, splits, out_counts, out_dist, partial, false,
+                          g_status_addr[dev], g_sms[dev], st));
+  if (partial) IBS_CUDA_TRY(launch_finalize(partial, n, out_counts, out_dist, false, st));
   return IBS_OK;
 }
 

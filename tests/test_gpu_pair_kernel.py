@@ -5,7 +5,9 @@ runs in a child process.  Also the default choice (ibs_compute_kernel): the
 pair kernel for 65,536 or more variants, the one-SM kernel otherwise.
 Shapes: two blocks with a ragged marker tail, a lone diagonal tile per column
 pair, garbage in the padding bits, every tile split over K (fewer pair items
-than clusters), and whole waves plus an unsplit tail; every ring variant."""
+than clusters), and whole waves plus an unsplit tail; every ring variant.
+The K-lockstep of full waves with 16-chunk segments (lag 2 and 3), so that its
+bounded waits run many times per item."""
 import os
 import subprocess
 import sys
@@ -86,3 +88,20 @@ def test_default_kernel_choice(mode):
     r = subprocess.run([sys.executable, "-c", CHOICE.format(root=ROOT, want=want)], env=env, capture_output=True,
                        text=True, timeout=300)
     assert r.returncode == 0 and "ok" in r.stdout, r.stdout + r.stderr
+
+
+# K-lockstep of full waves with short segments, so that the bounded waits run
+# many times per item: shapes with at least one full wave of pair items (76
+# clusters; 2,200 samples = 18 blocks = 90 pair items) and hundreds of chunks,
+# plus a shape whose items are all in the split tail (no lockstep).
+SYNC_SHAPES = [(2200, 20_000, 0.02, True), (2500, 9_001, 0.05, False), (700, 30_000, 0.02, False)]
+
+
+@pytest.mark.parametrize("sync", ["16,2", "16,3"])
+def test_pair_kernel_lockstep_matches_oracle(sync):
+    code = CHILD.format(tests=os.path.join(ROOT, "tests"), root=ROOT, seed=12, shapes=SYNC_SHAPES)
+    env = dict(os.environ, IBS_TC_PAIR="1", IBS_TC_PAIR_SYNC=sync)
+    env.pop("IBS_TC_PAIR_RING", None)
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.count("ok n=") == len(SYNC_SHAPES)

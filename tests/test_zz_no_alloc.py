@@ -10,8 +10,11 @@ The test calls it through the C ABI twice in a row, on two different inputs,
 and compares each result with the regular entry point, ibs_compute, and with
 the CPU oracle: counts bit for bit and distances within 1e-12 relative error.
 The second input is smaller than the first, so stale scratch contents from the
-first call would show up as wrong counts.  After each call the status query
-(ibs_noalloc_status) must report that no bounded device wait expired.
+first call would show up as wrong counts.  Both are small triangles whose
+marker axis is split (partial counts in the scratch after the planes); the
+third wants a split but its partial counts do not fit beside its planes, so it
+runs unsplit.  After each call the status query (ibs_noalloc_status) must
+report that no bounded device wait expired.
 """
 import numpy as np
 import pytest
@@ -51,7 +54,9 @@ def _regular(packed_np, n, m):
 def test_noalloc_matches_ibs_compute_on_two_calls():
     import oracle
     rng = np.random.default_rng(2024)
-    cases = [(1000, 20000), (333, 5001)]  # the second call is smaller than the first
+    # 16 blocks (5 splits), 6 blocks (14 splits, the second call smaller than the
+    # first), 32 blocks with 41 MB of planes + 32 MB of partial counts (unsplit)
+    cases = [(1000, 20000), (333, 5001), (2000, 40000)]
     for n, m in cases:
         packed = pack_codes(random_codes(rng, n, m, miss=0.04), garbage_rng=rng)
         got_c, got_d = _noalloc(packed, n, m)
