@@ -191,15 +191,20 @@ typedef struct {
  *      the operand planes unit by unit and per-subset readiness counters hold
  *      each item's copies until its planes are written;
  *   4  as 3, with the gather units taken by the pair launch's own epilogue
- *      warps between items (one launch after a short head start).
- * Policies 3 and 4 need E2M1 operands and windows that the two-SM kernel
- * takes; they are tuner candidates only then.
+ *      warps between items (one launch after a short head start);
+ *   5  policy 2's launches, gathered without gather stages: the epilogue
+ *      warps of each two-SM launch gather the planes of the subsets after
+ *      it (through the next two-SM subset) while its items' MMAs run; a
+ *      subset that no earlier launch gathered gets a gather launch of its
+ *      own.
+ * Policies 3 to 5 need E2M1 operands and the two-SM kernel; they are tuner
+ * candidates only then.
  * POPC form (IBS_KERNEL_PLAIN / IBS_KERNEL_CSA): one gather-transpose launch
  * and one persistent launch over all subsets (policies 0 and 1).  The launch
  * sequence is captured into a CUDA graph per batch shape and replayed; the
  * policy (and, for POPC, the kernel variant) is chosen by timing the
  * candidates on the first call of a shape, or fixed by the environment
- * variable IBS_BATCH_POLICY=0|1|2|3|4.  pool_packed is DEVICE
+ * variable IBS_BATCH_POLICY=0|1|2|3|4|5.  pool_packed is DEVICE
  * [pool_m][ceil(pool_n/4)].  Results are bit-identical to ibs_compute on each
  * subset alone. */
 ibs_status ibs_compute_batch(ibs_ctx* ctx, const uint8_t* pool_packed, int64_t pool_n, int64_t pool_m,

@@ -515,7 +515,7 @@ void build_items(const std::vector<SubsetShape>& shapes, int mode, int split_pol
     for (size_t k : order) {
       const ItemGeom ig = item_geom(shapes[k], mode);
       if (item_off_out) item_off_out->push_back((int64_t)items.size());
-      if (split_policy == 2) {
+      if (split_policy == 2 || split_policy == 5) {
         std::vector<WorkItem> own;
         std::vector<int2> own_split;
         tc_single_items(shapes[k].n, shapes[k].m, tc_fmt_of(mode), grid, kTcBatchGroup, own, own_split);
@@ -616,7 +616,8 @@ ibs_status plan_build(ibs_ctx* ctx, BatchPlan& plan, const std::vector<SubsetSha
     std::vector<int2> own_split;
     for (size_t q = 0; q < plan.order.size(); ++q) {
       const size_t k = (size_t)plan.order[q];
-      if (split_policy == 2 && !tc_pair_usable(shapes[k].n, shapes[k].m, tc_fmt_of(mode))) continue;
+      if ((split_policy == 2 || split_policy == 5) && !tc_pair_usable(shapes[k].n, shapes[k].m, tc_fmt_of(mode)))
+        continue;
       const ItemGeom ig = item_geom(shapes[k], mode);
       tc_pair_items(shapes[k].n, shapes[k].m, tc_fmt_of(mode), tc_pair_clusters(ig.nc), kTcBatchGroup, own,
                     own_split);
@@ -628,7 +629,7 @@ ibs_status plan_build(ibs_ctx* ctx, BatchPlan& plan, const std::vector<SubsetSha
         const int2 ss = tc_pair_sync_setting(ig.nc);
         int64_t whole = 0;
         while (whole < (int64_t)own.size() && own[(size_t)whole].split == 0) ++whole;
-        if (split_policy == 2 && ss.x > 0 && C > 0 && whole >= C) {
+        if ((split_policy == 2 || split_policy == 5) && ss.x > 0 && C > 0 && whole >= C) {
           plan.q_pair_sync[q] = whole / C * C;
           plan.pair_sync_bytes = std::max(plan.pair_sync_bytes,
                                           (size_t)(whole / C) * (size_t)((ig.nc + ss.x - 1) / ss.x) * sizeof(int));
@@ -686,13 +687,16 @@ ibs_status plan_build(ibs_ctx* ctx, BatchPlan& plan, const std::vector<SubsetSha
       plan.tc_ctas += tc_gather_ctas(shapes[k].n, item_geom(shapes[k], mode).nc);
     }
     plan.tc_block_chunks = (int64_t)(tb / kBc);
-    if (split_policy == 2) {
+    if (split_policy == 2 || split_policy == 5) {
       std::vector<int32_t> zero(shapes.size(), 0);
       if (ibs_status s = ensure_buf(ctx, plan.pitems, sizeof(PairItem) * std::max<size_t>(1, p2_items.size()))) return s;
       if (plan.pair_sync_bytes > 0)
         if (ibs_status s = ensure_buf(ctx, plan.pair_sync, plan.pair_sync_bytes)) return s;
       if (ibs_status s = ensure_buf(ctx, plan.units, sizeof(int4))) return s;
-      if (ibs_status s = ensure_buf(ctx, plan.unit_counter, 256)) return s;
+      // policy 5: two unit counters per subset position (its own gather launch, and the fused gather
+      // of the two-SM launch that runs it)
+      if (ibs_status s = ensure_buf(ctx, plan.unit_counter, std::max<size_t>(256, 8 * (plan.order.size() + 1))))
+        return s;
       if (ibs_status s = ensure_buf(ctx, plan.ready, sizeof(int32_t) * shapes.size())) return s;
       if (ibs_status s = ensure_buf(ctx, plan.need, sizeof(int32_t) * shapes.size())) return s;
       if (!p2_items.empty())
@@ -701,7 +705,28 @@ ibs_status plan_build(ibs_ctx* ctx, BatchPlan& plan, const std::vector<SubsetSha
       IBS_CUDA_TRY(cudaMemcpy(plan.need.p, zero.data(), sizeof(int32_t) * zero.size(), cudaMemcpyHostToDevice));
       IBS_CUDA_TRY(cudaMemcpy(plan.ready.p, zero.data(), sizeof(int32_t) * zero.size(), cudaMemcpyHostToDevice));
     }
-    if (split_policy >= 3) {
+    if (split_policy == 5) {
+      // Policy 5: policy 2's launches; the gather units of every subset in
+      // processing order (q_unit_off per position), taken by the epilogue
+      // warps of the two-SM launch before them, or by a gather launch of
+      // their own.  No copy waits on readiness (need stays zero): stream
+      // order has every subset gathered before its launch.
+      std::vector<int4> units;
+      plan.q_unit_off.assign(1, 0);
+      for (size_t q = 0; q < plan.order.size(); ++q) {
+        const size_t k = (size_t)plan.order[q];
+        const ItemGeom ig = item_geom(shapes[k], mode);
+        const int64_t groups = (ig.nc + tc_gather_chunks() - 1) / tc_gather_chunks();
+        for (int64_t cg = 0; cg < groups; ++cg)
+          for (int64_t bl = 0; bl < ig.T; ++bl) units.push_back(make_int4((int)q, (int)bl, (int)cg, (int)k));
+        plan.q_unit_off.push_back((int64_t)units.size());
+      }
+      plan.n_units = (int64_t)units.size();
+      if (plan.n_units > 2147483647LL) return fail(IBS_EINVAL, "batch too large for the fused gather");
+      if (ibs_status s = ensure_buf(ctx, plan.units, sizeof(int4) * std::max<size_t>(1, units.size()))) return s;
+      IBS_CUDA_TRY(cudaMemcpy(plan.units.p, units.data(), sizeof(int4) * units.size(), cudaMemcpyHostToDevice));
+    }
+    if (split_policy == 3 || split_policy == 4) {
       // One launch of the two-SM kernel over the concatenated pair lists
       // (above), and the gather units of the subsets in the same order for
       // its epilogue warps and the side stream's gather CTAs.
@@ -758,7 +783,7 @@ ibs_status plan_build(ibs_ctx* ctx, BatchPlan& plan, const std::vector<SubsetSha
         while (b < 3 && acc >= bounds[b] * total) ++b;
       }
     }
-    if (split_policy >= 3) {
+    if (split_policy == 3 || split_policy == 4) {
       IBS_CUDA_TRY(cudaStreamCreateWithFlags(&plan.side, cudaStreamNonBlocking));
       IBS_CUDA_TRY(cudaEventCreateWithFlags(&plan.fork_ev, cudaEventDisableTiming));
       IBS_CUDA_TRY(cudaEventCreateWithFlags(&plan.join_ev, cudaEventDisableTiming));
@@ -852,7 +877,7 @@ ibs_status plan_upload(ibs_ctx* ctx, BatchPlan& plan, const uint8_t* pool, int64
     // (a counting sort over chunk-group-sized buckets), then job, block.
     std::vector<int64_t> key(k);
     for (size_t i = 0; i < k; ++i) key[i] = subs[i].var_begin;
-    if (plan.split_policy < 3 && plan.map_key != key) {  // policies 3, 4 gather by their own unit list
+    if (plan.split_policy < 3 && plan.map_key != key) {  // policies 3-5 gather by their own unit list
       const int64_t span = (int64_t)tc_gather_chunks() * (tc_fmt_of(plan.mode) == kTcFp4 ? 64 : 32);
       int64_t vend = 0;
       for (size_t i = 0; i < k; ++i) vend = std::max<int64_t>(vend, subs[i].var_begin + shapes[i].m);
@@ -899,6 +924,67 @@ ibs_status plan_enqueue(ibs_ctx* ctx, BatchPlan& plan, int n_subsets, cudaStream
     const int fmt = tc_fmt_of(plan.mode);
     const TcGatherJob* jobs = static_cast<const TcGatherJob*>(plan.tc_jobs.p);
     const WorkItem* items = static_cast<const WorkItem*>(plan.items.p);
+    if (plan.split_policy == 5) {
+      // One launch per subset, as policy 2.  The epilogue warps of each
+      // two-SM launch gather the planes of the subsets after it, up to and
+      // including the next two-SM subset, while its items' MMAs run; a subset
+      // that no earlier launch gathered gets a gather launch first.
+      const int64_t Q = (int64_t)plan.order.size();
+      const int4* units = static_cast<const int4*>(plan.units.p);
+      int* ctr = static_cast<int*>(plan.unit_counter.p);  // [2 q]: own gather, [2 q + 1]: fused in launch q
+      IBS_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(int) * 2 * (size_t)(Q + 1), st));
+      int64_t gathered_upto = 0;  // positions [0, gathered_upto) are (being) gathered
+      for (int64_t q = 0; q < Q; ++q) {
+        if (gathered_upto <= q) {
+          IBS_CUDA_TRY(launch_tc_gather_units(jobs, units + plan.q_unit_off[(size_t)q],
+                                              plan.q_unit_off[(size_t)q + 1] - plan.q_unit_off[(size_t)q],
+                                              ctr + 2 * q, static_cast<int*>(plan.ready.p), fmt, 8 * ctx->num_sms,
+                                              ctx->status_dev, st));
+          gathered_upto = q + 1;
+        }
+        if (plan.q_pair_off[(size_t)q] >= 0) {
+          int64_t r = q + 1;
+          while (r < Q && plan.q_pair_off[(size_t)r] < 0) ++r;
+          const int64_t end = std::min<int64_t>(r + 1, Q);  // exclusive: through the next two-SM subset
+          PairBatchArgs a;
+          a.subs = static_cast<const SubsetDev*>(plan.subsets.p);
+          a.items = static_cast<const PairItem*>(plan.pitems.p) + plan.q_pair_off[(size_t)q];
+          a.n_items = plan.q_pair_n[(size_t)q];
+          a.jobs = jobs;
+          a.units = units + plan.q_unit_off[(size_t)gathered_upto];
+          a.n_units = end > gathered_upto ? plan.q_unit_off[(size_t)end] - plan.q_unit_off[(size_t)gathered_upto] : 0;
+          a.unit_counter = ctr + 2 * q + 1;
+          a.ready = static_cast<int*>(plan.ready.p);
+          a.need = static_cast<const int*>(plan.need.p);  // all zero: nothing to wait for
+          a.planes = plan.tc_planes.p;
+          a.block_chunks = plan.tc_block_chunks;
+          a.max_chunks = plan.q_chunks[(size_t)q];
+          if (plan.q_pair_sync[(size_t)q] > 0) {
+            const int2 ss = tc_pair_sync_setting(a.max_chunks);
+            a.sync.seg = ss.x;
+            a.sync.lag = ss.y;
+            a.sync.n_seg = (int32_t)((a.max_chunks + ss.x - 1) / ss.x);
+            a.sync.n_items = plan.q_pair_sync[(size_t)q];
+            a.sync.ctr = static_cast<int*>(plan.pair_sync.p);
+            IBS_CUDA_TRY(cudaMemsetAsync(plan.pair_sync.p, 0,
+                                         (size_t)(a.sync.n_items / tc_pair_clusters(a.max_chunks)) * a.sync.n_seg *
+                                             sizeof(int),
+                                         st));
+          }
+          IBS_CUDA_TRY(launch_tc_pair_batch(a, ctx->status_dev, kWaitLimitNs, st));
+          gathered_upto = std::max(gathered_upto, end);
+          continue;
+        }
+        const int64_t n_items = plan.q_item_off[q + 1] - plan.q_item_off[q];
+        IBS_CUDA_TRY(launch_tc_batch(static_cast<const SubsetDev*>(plan.subsets.p), items + plan.q_item_off[q],
+                                     n_items, (int)std::min<int64_t>(plan.grid, n_items), fmt, plan.q_chunks[q],
+                                     static_cast<int*>(plan.counter.p), ctx->status_dev, st));
+      }
+      IBS_CUDA_TRY(launch_tc_finalize_batch_tiles(static_cast<const SubsetDev*>(plan.subsets.p),
+                                                  static_cast<const int4*>(plan.split_tiles.p), plan.n_split_tiles,
+                                                  st));
+      return IBS_OK;
+    }
     if (plan.split_policy >= 3) {
       // one launch: the two-SM kernel over every subset's pair items, its
       // epilogue warps gathering the subsets' planes from the pool as they go
@@ -1123,12 +1209,12 @@ extern "C" ibs_status ibs_compute_batch(ibs_ctx* ctx, const uint8_t* pool, int64
     int64_t max_nc = 0;
     for (const auto& sh : shapes) max_nc = std::max<int64_t>(max_nc, tc_chunks(sh.m, tc_format_for(ctx)));
     const bool pair_ok = tc && tc_format_for(ctx) == kTcFp4 && tc_pair_clusters(max_nc) > 0;
-    // IBS_BATCH_POLICY=0|1|2|3|4 fixes the split policy (2: tensor-core modes; 3, 4: two-SM E2M1 only)
+    // IBS_BATCH_POLICY=0..5 fixes the split policy (2: tensor-core modes; 3-5: two-SM E2M1 only)
     const char* pe = getenv("IBS_BATCH_POLICY");
-    const int fixed_policy =
-        pe && (atoi(pe) == 0 || atoi(pe) == 1 || (atoi(pe) == 2 && tc) || ((atoi(pe) == 3 || atoi(pe) == 4) && pair_ok))
-            ? atoi(pe)
-            : -1;
+    const int fixed_policy = pe && (atoi(pe) == 0 || atoi(pe) == 1 || (atoi(pe) == 2 && tc) ||
+                                    ((atoi(pe) == 3 || atoi(pe) == 4 || atoi(pe) == 5) && pair_ok))
+                                 ? atoi(pe)
+                                 : -1;
     if (fixed_policy >= 0) {
       policy = fixed_policy;
     } else if (te != ctx->tune.end()) {
@@ -1139,7 +1225,7 @@ extern "C" ibs_status ibs_compute_batch(ibs_ctx* ctx, const uint8_t* pool, int64
       for (int cm = 0; cm <= kBatchModeTc + kTcFp4; ++cm) {
         if (forced >= 0 && cm != forced) continue;
         if (is_tc_mode(cm) != tc) continue;
-        for (int cp = 0; cp < (is_tc_mode(cm) ? (pair_ok && tc_fmt_of(cm) == kTcFp4 ? 5 : 3) : 2); ++cp) {
+        for (int cp = 0; cp < (is_tc_mode(cm) ? (pair_ok && tc_fmt_of(cm) == kTcFp4 ? 6 : 3) : 2); ++cp) {
           BatchPlan trial;
           if (ibs_status s = plan_build(ctx, trial, shapes, cm, cp)) {
             plan_free(ctx, trial);
@@ -1206,7 +1292,23 @@ extern "C" ibs_status ibs_compute_batch(ibs_ctx* ctx, const uint8_t* pool, int64
   BatchPlan& plan = *it->second;
   if (ibs_status s = plan_upload(ctx, plan, pool, pool_n, subs, shapes, st)) return s;
   IBS_CUDA_TRY(cudaGraphLaunch(plan.exec, st));
+  int64_t own_gathers = 0;  // policy 5: subsets no two-SM launch gathered
+  if (plan.split_policy == 5) {
+    int64_t upto = 0;
+    for (int64_t q = 0; q < (int64_t)plan.order.size(); ++q) {
+      if (upto <= q) {
+        ++own_gathers;
+        upto = q + 1;
+      }
+      if (plan.q_pair_off[(size_t)q] >= 0) {
+        int64_t r = q + 1;
+        while (r < (int64_t)plan.order.size() && plan.q_pair_off[(size_t)r] < 0) ++r;
+        upto = std::max<int64_t>(upto, std::min<int64_t>(r + 1, (int64_t)plan.order.size()));
+      }
+    }
+  }
   ctx->last_info[0] = !is_tc_mode(plan.mode) ? 3 + (plan.n_split > 0 ? 1 : 0)
+                      : plan.split_policy == 5 ? own_gathers + n_subsets + (plan.n_split_tiles > 0 ? 1 : 0)
                       : plan.split_policy >= 3 ? 2 + (plan.n_split_tiles > 0 ? 1 : 0)
                       : plan.split_policy == 2
                           ? (int64_t)plan.stage_ctas.size() + n_subsets + (plan.n_split_tiles > 0 ? 1 : 0)

@@ -79,6 +79,8 @@ struct BatchPlan {
   // ... and their K-lockstep: items in whole waves per position (0 = none),
   // one counter buffer for the largest, zeroed before each launch
   std::vector<int64_t> q_pair_sync;
+  // split policy 5: gather units per position of `order` (offsets into units)
+  std::vector<int64_t> q_unit_off;
   DevBuf pair_sync;
   size_t pair_sync_bytes = 0;
   cudaStream_t side = nullptr;

@@ -135,16 +135,19 @@ def test_batch_split_items(pool, flags_name):
         ibs.ibs_shutdown(ctx)
 
 
-@pytest.mark.parametrize("policy", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("policy", [0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("fmt", ["IBS_TC_FP8", "IBS_TC_FP4"])
 def test_batch_each_policy(pool, policy, fmt, monkeypatch):
     """Every split policy of the tensor-core batch, fixed by IBS_BATCH_POLICY:
     0 whole tiles in one launch per stage, 1 K-split large subsets, 2 one
     launch per subset over its own work list (small subsets and tail waves
-    split over K, split tiles finalised from the subset descriptors), 3 (E2M1
-    only) one launch of the two-SM kernel over every subset's pair items with
-    the gather fused into its epilogue warps.  Counts equal the oracle for all
-    twelve subsets, twice (graph replay)."""
+    split over K, split tiles finalised from the subset descriptors), 3 and 4
+    (E2M1 only) one launch of the two-SM kernel over every subset's pair items
+    with the gather fused in, 5 (E2M1 only) policy 2's launches with each
+    two-SM launch's epilogue warps gathering the following subsets (here every
+    window is under the two-SM size, so each subset gets its own gather
+    launch; the fused form is tested in a child below).  Counts equal the
+    oracle for all twelve subsets, twice (graph replay)."""
     import torch
     from paper_1410_4803_gb300 import ibs
     if policy >= 3 and fmt != "IBS_TC_FP4":
@@ -231,3 +234,50 @@ def test_batch_windows_move_between_calls(pool):
                 assert_dist_close(d, od)
     finally:
         ibs.ibs_shutdown(ctx)
+
+
+POLICY5_CHILD = r"""
+import sys
+import numpy as np
+sys.path.insert(0, {tests!r}); sys.path.insert(0, {root!r})
+import torch
+import oracle
+from helpers import assert_dist_close
+from test_gpu_batch import _flags, _make_subsets, _run_batch
+from paper_1410_4803_gb300 import ibs, synth
+w = synth.batch_pool(pool_n=1500, pool_m=30000, seed=11)
+subs = _make_subsets(np.random.default_rng(9), w.n, w.m)
+ctx = ibs.ibs_init(0, flags=_flags(ibs, "IBS_KERNEL_TC|IBS_TC_FP4"))
+dev = torch.from_numpy(w.packed).cuda()
+first = _run_batch(ctx, w, subs, dev)
+second = _run_batch(ctx, w, subs, dev)
+assert ibs.ibs_batch_plan_info(ctx)["split_policy"] == 5
+launches = ibs.ibs_last_launch_info(ctx)["launches"]
+for (idx, vb, vl), (c1, d1), (c2, d2) in zip(subs, first, second):
+    G = oracle.unpack_subset(w.packed, w.n, w.m, idx, vb, vl)
+    oc, od, _ = oracle.ibs_triangle_from_codes(G)
+    assert (c1 == oc).all(), f"n={{idx.size}} window={{vb}}+{{vl}}"
+    assert (c2 == oc).all()
+    assert_dist_close(d1, od)
+    np.testing.assert_array_equal(d1, d2)
+ibs.ibs_shutdown(ctx)
+print("ok", launches)
+"""
+
+
+def test_batch_policy5_fused_gather():
+    """Policy 5 with the two-SM kernel forced on for every subset of two or
+    more blocks (IBS_TC_PAIR=1, read once per process: a child): the order
+    mixes two-SM subsets, whose epilogue warps gather the planes of the
+    subsets after them, and one-SM subsets (n <= 128), which the preceding
+    two-SM launch gathers; the first subset gets a gather launch of its own.
+    Counts equal the oracle for all twelve subsets, twice (graph replay)."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = POLICY5_CHILD.format(tests=os.path.join(root, "tests"), root=root)
+    env = dict(os.environ, IBS_TC_PAIR="1", IBS_BATCH_POLICY="5")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "ok" in r.stdout, r.stdout
