@@ -277,3 +277,36 @@ def test_serving_two_sm_kernel_matches_oracle():
     r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
     assert r.returncode == 0, r.stdout + r.stderr
     assert r.stdout.count("ok q=") == 8, r.stdout
+
+
+def test_serving_requests_at_the_row_limit():
+    """Three 4,096-row requests submitted at once: each fills the engine's
+    4,096 admission slots, so they are admitted one after another while the
+    others wait.  Every result equals the unbatched path and the oracle."""
+    import torch
+    from paper_1410_4803_gb300 import ibs
+    from helpers import pack_codes, random_codes
+    rng = np.random.default_rng(31)
+    n_panel, m, q, k = 300, 700, 4096, 4
+    pcodes = random_codes(rng, n_panel, m)
+    ctx = ibs.ibs_init(0)
+    try:
+        ibs.ibs_panel_load(ctx, pack_codes(pcodes), n_panel, m)
+        reqs = []
+        for i in range(3):
+            qc = random_codes(np.random.default_rng(40 + i), q, m)
+            out = (_pinned((q, n_panel, 4), torch.int32), _pinned((q, k), torch.int32), _pinned((q, k), torch.float64))
+            reqs.append((qc, pack_codes(qc), out))
+        ids = [ibs.ibs_query(ctx, qp, q, k, *out) for _, qp, out in reqs]
+        for rid in ids:
+            ibs.ibs_wait(ctx, rid, timeout_ms=120000)
+        for qc, qp, (oc, oi, od) in reqs:
+            ac, ai, ad = _pinned((q, n_panel, 4), torch.int32), _pinned((q, k), torch.int32), _pinned((q, k), torch.float64)
+            ibs.ibs_query_sync(ctx, qp, q, k, ac, ai, ad)
+            assert (oc.numpy() == ac.numpy()).all()
+            assert (oi.numpy() == ai.numpy()).all()
+            rows = np.arange(0, q, 97)
+            wc, _ = oracle.ibs_block(qc, pcodes, rows=rows)
+            assert (oc.numpy()[rows] == wc).all()
+    finally:
+        ibs.ibs_shutdown(ctx)
