@@ -61,8 +61,12 @@ constexpr int kGrmQueue = 8;
 constexpr int kGrmSeg = 8;                               // chunks per numerator segment
 static_assert(kGrmSeg % kGrmPad == 0, "a ring stage never straddles two segments");
 constexpr int kGrmEpiWarps = 8;
-constexpr int kGrmThreads = (kGrmEpiWarps + 2) * 32;
-constexpr int kGrmCopyWarp = kGrmEpiWarps, kGrmMmaWarp = kGrmEpiWarps + 1;
+constexpr int kGrmThreads = (kGrmEpiWarps + 3) * 32;
+constexpr int kGrmCopyWarp = kGrmEpiWarps, kGrmMmaWarp = kGrmEpiWarps + 1, kGrmWaitWarp = kGrmEpiWarps + 2;
+// Hardware barrier between the waiter warp and the MMA warp (barrier 0 is
+// __syncthreads): both execute bar.sync once per item hand-over and once per
+// ring stage, in the same order.
+constexpr int kGrmBar = 1;
 constexpr uint32_t kColNum = 0, kColCnt = 256, kColHi = 384;
 
 // FP16 x FP16 -> F32 (kind::f16): D format F32 (bit 4), A and B formats F16
@@ -264,6 +268,7 @@ __global__ void __launch_bounds__(kGrmThreads, 1) tc_grm_kernel(const GrmArgs ar
   __shared__ __align__(8) uint64_t seg_full[2], seg_free[2], cnt_free, drain;
   __shared__ __align__(8) uint64_t qfull[kGrmQueue], qempty[kGrmQueue];
   __shared__ int64_t q_item[kGrmQueue];
+  __shared__ int64_t s_item[2];  // the waiter's hand-over of items to the MMA warp
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -368,41 +373,27 @@ __global__ void __launch_bounds__(kGrmThreads, 1) tc_grm_kernel(const GrmArgs ar
       if (stop) break;
     }
   } else if (warp == kGrmMmaWarp) {
+    // MMA warp.  It never waits on memory itself: a thread with MMAs in flight
+    // that polls a barrier or loads from memory stalls until they complete,
+    // which would drain the tensor pipe at every ring stage.  The waiter warp
+    // takes the items from the queue and does every wait; it hands each item
+    // over through s_item and releases this warp once per stage through
+    // hardware barrier kGrmBar.
     uint32_t g = 0, gs = 0;
-    bool stop = false;
-    for (uint32_t e = 0; !stop; ++e) {
-      int64_t it;
-      if (!queue_get(e, it)) {
-        fail(true);
-        break;
-      }
+    for (uint32_t e = 0;; ++e) {
+      asm volatile("bar.sync %0, 64;" ::"n"(kGrmBar) : "memory");
+      const int64_t it = *(volatile int64_t*)&s_item[e & 1u];
       if (it < 0) break;
       const GrmItem t = args.items[it];
       const bool same = t.I == t.J;
       const int64_t q1 = t.c1 / kPer;
-      for (int64_t q = t.c0 / kPer; q < q1 && !stop; ++q, ++g) {
+      for (int64_t q = t.c0 / kPer; q < q1; ++q, ++g) {
         const int64_t k0 = q * kPer, r0 = k0 - t.c0;  // r0: chunks into the item
         const uint32_t b = gs & 1u;
         const bool seg_end = (r0 + kPer) % kGrmSeg == 0 || q == q1 - 1;
-        if (r0 % kGrmSeg == 0) {
-          // the numerator bank is free once the epilogue has read the segment
-          // two back; the previous tile's count must be read before the first
-          // count MMA of this one
-          bool ok = gs < 2 || mbar_wait_bounded(&seg_free[b], ((gs >> 1) - 1) & 1u);
-          if (ok && r0 == 0 && e > 0) ok = mbar_wait_bounded(&cnt_free, (e - 1) & 1u);
-          if (__any_sync(0xffffffffu, !ok)) {
-            stop = true;
-            break;
-          }
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        }
-        const int s = (int)(g % kGrmStages);
-        const bool ok = mbar_wait_bounded(&full[s], (g / kGrmStages) & 1u);
-        if (__any_sync(0xffffffffu, !ok)) {
-          stop = true;
-          break;
-        }
+        asm volatile("bar.sync %0, 64;" ::"n"(kGrmBar) : "memory");
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int s = (int)(g % kGrmStages);
         if (lane == 0) {
           const uint32_t st0 = smem_addr(ring + (size_t)s * 2 * kBlockBytes);
           const uint32_t num = tmem + kColNum + 128u * b;
@@ -426,15 +417,58 @@ __global__ void __launch_bounds__(kGrmThreads, 1) tc_grm_kernel(const GrmArgs ar
         __syncwarp();
         if (seg_end) ++gs;
       }
-      if (stop || aborted()) {
-        fail(stop);
-        break;
-      }
     }
     if (lane == 0) umma_commit(&drain);
     __syncwarp();
     const bool drained = mbar_wait_bounded(&drain, 0);
     if (lane == 0 && !drained) atomicExch(status, kDevTimeout);
+  } else if (warp == kGrmWaitWarp) {
+    // Waiter: for each item from the queue, hand it over; then for each ring
+    // stage wait (bounded) until its operands have landed and, at a segment's
+    // start, until the epilogue has freed that numerator bank (the segment
+    // two back) and, at a tile's start, has read the previous tile's count;
+    // then release the MMA warp.  After a failed wait or another role's abort
+    // it stops waiting but keeps releasing the current item's stages (the MMA
+    // warp runs them out on stale operands; the call reports IBS_ETIMEOUT),
+    // then hands over the end (-1).
+    uint32_t g = 0, gs = 0;
+    bool dead = false;
+    for (uint32_t e = 0;; ++e) {
+      int64_t it = -1;
+      if (!dead && !queue_get(e, it)) {
+        fail(true);
+        dead = true;
+      }
+      if (dead) it = -1;
+      if (lane == 0) s_item[e & 1u] = it;
+      __syncwarp();
+      asm volatile("bar.sync %0, 64;" ::"n"(kGrmBar) : "memory");
+      if (it < 0) break;
+      const GrmItem t = args.items[it];
+      const int64_t q1 = t.c1 / kPer;
+      for (int64_t q = t.c0 / kPer; q < q1; ++q, ++g) {
+        const int64_t k0 = q * kPer, r0 = k0 - t.c0;
+        const uint32_t b = gs & 1u;
+        const bool seg_end = (r0 + kPer) % kGrmSeg == 0 || q == q1 - 1;
+        if (!dead) {
+          bool ok = true;
+          if (r0 % kGrmSeg == 0) {
+            ok = gs < 2 || mbar_wait_bounded(&seg_free[b], ((gs >> 1) - 1) & 1u);
+            if (ok && r0 == 0 && e > 0) ok = mbar_wait_bounded(&cnt_free, (e - 1) & 1u);
+          }
+          if (ok) ok = mbar_wait_bounded(&full[(int)(g % kGrmStages)], (g / kGrmStages) & 1u);
+          if (__any_sync(0xffffffffu, !ok)) {
+            fail(true);
+            dead = true;
+          } else if (aborted()) {
+            dead = true;
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        asm volatile("bar.sync %0, 64;" ::"n"(kGrmBar) : "memory");
+        if (seg_end) ++gs;
+      }
+    }
   } else if (warp < kGrmEpiWarps) {
     const int quarter = warp & 3, half = warp >> 2;
     const int row = quarter * 32 + lane;
