@@ -198,7 +198,9 @@ typedef struct {
  *      subset that no earlier launch gathered gets a gather launch of its
  *      own.
  * Policies 3 to 5 need E2M1 operands and the two-SM kernel; they are tuner
- * candidates only then.
+ * candidates only then.  The tuner also tries policy 2 with the two-SM
+ * kernel from 2,048 or 4,096 chunks on, or for no subset (the tile shape per
+ * window size class; ibs_batch_plan_info reports the choice).
  * POPC form (IBS_KERNEL_PLAIN / IBS_KERNEL_CSA): one gather-transpose launch
  * and one persistent launch over all subsets (policies 0 and 1).  The launch
  * sequence is captured into a CUDA graph per batch shape and replayed; the
@@ -286,9 +288,11 @@ ibs_status ibs_probe_mma(ibs_ctx* ctx, double out[2]);
 
 /* The largest cached batched-launch plan: out[0] = kernel mode (0 plain,
  * 1 carry-save 2 CTAs/SM, 2 carry-save 1 CTA/SM, 3 tensor core E4M3, 4 tensor
- * core E2M1), out[1] =
- * split policy, out[2] = work items, out[3] = grid. */
-ibs_status ibs_batch_plan_info(ibs_ctx* ctx, int64_t out[4]);
+ * core E2M1), out[1] = split policy, out[2] = work items, out[3] = grid,
+ * out[4] = the two-SM size class of policies 2 and 5 in chunks (subsets of
+ * at least that many chunks run the two-SM kernel; 2^40 = none; chosen by
+ * the tuner among 1,024, 2,048, 4,096 and none for policy 2). */
+ibs_status ibs_batch_plan_info(ibs_ctx* ctx, int64_t out[5]);
 
 /* With IBS_TIMING: wait for the recorded events and return the summed device
  * time in ms of each kernel of all ibs_compute calls since the last query:

@@ -186,9 +186,14 @@ ibs_status ibs_init(const ibs_config* cfg, ibs_ctx** out_ctx) {
     while (std::getline(f, line)) {
       char key[512];
       TuneEntry t;
-      if (sscanf(line.c_str(), "{\"key\": \"%511[^\"]\", \"mode\": %d, \"split\": %d, \"ms\": %lf}", key, &t.mode,
-                 &t.split_policy, &t.ms) == 4)
+      long long pm = 1024;
+      const int got = sscanf(line.c_str(),
+                             "{\"key\": \"%511[^\"]\", \"mode\": %d, \"split\": %d, \"ms\": %lf, \"pair_min\": %lld}", key,
+                             &t.mode, &t.split_policy, &t.ms, &pm);
+      if (got >= 4) {  // entries written before the size class was tuned lack pair_min
+        t.pair_min = pm;
         ctx->tune[key] = t;
+      }
     }
   }
   *out_ctx = ctx;
@@ -583,9 +588,10 @@ std::string tune_key(const ibs_ctx* ctx, const std::vector<SubsetShape>& shapes)
 }
 
 ibs_status plan_build(ibs_ctx* ctx, BatchPlan& plan, const std::vector<SubsetShape>& shapes, int mode,
-                      int split_policy) {
+                      int split_policy, int64_t pair_min = 1024) {
   plan.mode = mode;
   plan.split_policy = split_policy;
+  plan.pair_min_chunks = pair_min;
   const bool tc = is_tc_mode(mode);
   plan.grid = ctx->num_sms * (tc ? 1 : pair_kernel_ctas_per_sm(mode));
   std::vector<WorkItem> items;
@@ -616,8 +622,10 @@ ibs_status plan_build(ibs_ctx* ctx, BatchPlan& plan, const std::vector<SubsetSha
     std::vector<int2> own_split;
     for (size_t q = 0; q < plan.order.size(); ++q) {
       const size_t k = (size_t)plan.order[q];
-      if ((split_policy == 2 || split_policy == 5) && !tc_pair_usable(shapes[k].n, shapes[k].m, tc_fmt_of(mode)))
-        continue;
+      if ((split_policy == 2 || split_policy == 5) &&
+          (!tc_pair_usable(shapes[k].n, shapes[k].m, tc_fmt_of(mode)) ||
+           (tc_pair_mode() == 0 && item_geom(shapes[k], mode).nc < pair_min)))
+        continue;  // this subset's size class runs on the one-SM kernel
       const ItemGeom ig = item_geom(shapes[k], mode);
       tc_pair_items(shapes[k].n, shapes[k].m, tc_fmt_of(mode), tc_pair_clusters(ig.nc), kTcBatchGroup, own,
                     own_split);
@@ -1134,7 +1142,7 @@ void save_tune(const ibs_ctx* ctx) {
   std::ofstream f(ctx->tune_path, std::ios::trunc);
   for (const auto& kv : ctx->tune)
     f << "{\"key\": \"" << kv.first << "\", \"mode\": " << kv.second.mode << ", \"split\": " << kv.second.split_policy
-      << ", \"ms\": " << kv.second.ms << "}\n";
+      << ", \"ms\": " << kv.second.ms << ", \"pair_min\": " << kv.second.pair_min << "}\n";
 }
 
 }  // namespace
@@ -1203,6 +1211,7 @@ extern "C" ibs_status ibs_compute_batch(ibs_ctx* ctx, const uint8_t* pool, int64
     // Choose mode and split policy: cached tuning result, or measure the candidates now.
     const std::string tk = tune_key(ctx, shapes) + (tc ? "_tc" : "");
     int mode = forced >= 0 ? forced : (tc ? kBatchModeTc : ctx->default_mode), policy = 0;
+    int64_t pair_min = 1024;  // the two-SM size class of policies 2 and 5
     auto te = ctx->tune.find(tk);
     // Policy 3 (one launch of the two-SM kernel, gather fused in) needs E2M1
     // operands and clusters of two.
@@ -1220,14 +1229,32 @@ extern "C" ibs_status ibs_compute_batch(ibs_ctx* ctx, const uint8_t* pool, int64
     } else if (te != ctx->tune.end()) {
       if (forced < 0) mode = te->second.mode;
       policy = te->second.split_policy;
+      pair_min = te->second.pair_min;
     } else if (!getenv("IBS_NO_AUTOTUNE")) {
       double best = 1e30;
+      // candidates: (mode, policy, size class); policy 2 of the E2M1 mode is
+      // also tried with the two-SM kernel from 2,048 or 4,096 chunks on, or
+      // not at all (its default is ibs_compute's rule, 1,024 chunks)
+      struct Cand {
+        int mode, policy;
+        int64_t pair_min;
+      };
+      std::vector<Cand> cands;
       for (int cm = 0; cm <= kBatchModeTc + kTcFp4; ++cm) {
         if (forced >= 0 && cm != forced) continue;
         if (is_tc_mode(cm) != tc) continue;
-        for (int cp = 0; cp < (is_tc_mode(cm) ? (pair_ok && tc_fmt_of(cm) == kTcFp4 ? 6 : 3) : 2); ++cp) {
+        const bool fp4_pair = pair_ok && tc_fmt_of(cm) == kTcFp4;
+        for (int cp = 0; cp < (is_tc_mode(cm) ? (fp4_pair ? 6 : 3) : 2); ++cp) {
+          cands.push_back({cm, cp, 1024});
+          if (cp == 2 && fp4_pair && tc_pair_mode() == 0)
+            for (int64_t pm : {(int64_t)2048, (int64_t)4096, (int64_t)1 << 40}) cands.push_back({cm, cp, pm});
+        }
+      }
+      for (const Cand& c : cands) {
+        const int cm = c.mode, cp = c.policy;
+        {
           BatchPlan trial;
-          if (ibs_status s = plan_build(ctx, trial, shapes, cm, cp)) {
+          if (ibs_status s = plan_build(ctx, trial, shapes, cm, cp, c.pair_min)) {
             plan_free(ctx, trial);
             return s;
           }
@@ -1251,19 +1278,21 @@ extern "C" ibs_status ibs_compute_batch(ibs_ctx* ctx, const uint8_t* pool, int64
             best = ms;
             mode = cm;
             policy = cp;
+            pair_min = c.pair_min;
           }
         }
       }
       TuneEntry t;
       t.mode = mode;
       t.split_policy = policy;
+      t.pair_min = pair_min;
       t.ms = best;
       ctx->tune[tk] = t;
       save_tune(ctx);
     }
     auto plan = std::make_unique<BatchPlan>();
     plan->shape_key = key;
-    if (ibs_status s = plan_build(ctx, *plan, shapes, mode, policy)) {
+    if (ibs_status s = plan_build(ctx, *plan, shapes, mode, policy, pair_min)) {
       plan_free(ctx, *plan);
       return s;
     }
@@ -1461,7 +1490,7 @@ extern "C" ibs_status ibs_compute_kernel(ibs_ctx* ctx, int64_t n, int64_t m, int
   return IBS_OK;
 }
 
-extern "C" ibs_status ibs_batch_plan_info(ibs_ctx* ctx, int64_t out[4]) {
+extern "C" ibs_status ibs_batch_plan_info(ibs_ctx* ctx, int64_t out[5]) {
   clear_error();
   if (ibs_status s = check_ctx(ctx)) return s;
   if (!out) return fail(IBS_EINVAL, "out is NULL");
@@ -1474,6 +1503,7 @@ extern "C" ibs_status ibs_batch_plan_info(ibs_ctx* ctx, int64_t out[4]) {
   out[1] = best->split_policy;
   out[2] = best->n_items;
   out[3] = best->grid;
+  out[4] = best->pair_min_chunks;
   return IBS_OK;
 }
 

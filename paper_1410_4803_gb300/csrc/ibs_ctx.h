@@ -89,6 +89,9 @@ struct BatchPlan {
   int64_t n_items = 0, total_ctas = 0, max_split_pairs = 0, tc_ctas = 0;
   int n_split = 0;
   int mode = 0, split_policy = 0, grid = 0;
+  // policies 2 and 5: subsets of at least this many chunks (and that the
+  // two-SM kernel takes) run on it, the rest on the one-SM kernel; tuned
+  int64_t pair_min_chunks = 1024;
   std::vector<int64_t> plane_offsets;   // bytes into planes
   std::vector<int64_t> tc_offsets;      // bytes into tc_planes (mode 3)
   std::vector<int64_t> partial_offsets; // bytes into partial, -1 if not split
@@ -99,6 +102,7 @@ struct BatchPlan {
 
 struct TuneEntry {
   int mode = -1;
+  int64_t pair_min = 1024;  // the tuned two-SM size class (chunks) of policies 2 and 5
   int split_policy = 0;
   double ms = 0;
 };

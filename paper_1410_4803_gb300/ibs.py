@@ -348,9 +348,9 @@ def ibs_test_set_wait_limit(ctx: Context, ns: int):
 
 
 def ibs_batch_plan_info(ctx: Context) -> dict:
-    out = (ctypes.c_int64 * 4)()
+    out = (ctypes.c_int64 * 5)()
     _check(load().ibs_batch_plan_info(ctx._h, out), "ibs_batch_plan_info")
-    return {"mode": out[0], "split_policy": out[1], "items": out[2], "grid": out[3]}
+    return {"mode": out[0], "split_policy": out[1], "items": out[2], "grid": out[3], "pair_min_chunks": out[4]}
 
 
 # ---------------------------------------------------------------------------
