@@ -58,9 +58,12 @@ constexpr int kLdStages = 3;
 constexpr size_t kLdSmem = (size_t)kLdStages * kLdStageBytes + 1024;
 constexpr int kLdN = 64;                             // B rows (markers) per item
 constexpr int kLdQueue = 8;
-// warps 0 (copies), 1 (MMAs), 2-3 idle, 4..11 epilogue: two warps per TMEM lane
+// warps 0 (copies), 1 (MMAs), 2 (the MMA warp's waits), 3 idle, 4..11 epilogue: two warps per TMEM lane
 // quarter, each reading 32 of the item's 64 accumulator columns
 constexpr int kLdEpiWarps = 8;
+// Hardware barrier between the waiter warp (2) and the MMA warp (1); barrier
+// 0 is __syncthreads.
+constexpr int kLdBar = 1;
 constexpr int kLdThreads = (4 + kLdEpiWarps) * 32;
 
 // Even bits of a 64-bit word packed into 32 bits (bit 2i -> bit i).
@@ -196,6 +199,7 @@ __global__ void __launch_bounds__(kLdThreads, 1) tc_ld_kernel(const LdArgs args)
   __shared__ __align__(8) uint64_t full[kLdStages], empty[kLdStages], tfull, tempty, drain;
   __shared__ __align__(8) uint64_t qfull[kLdQueue], qempty[kLdQueue];
   __shared__ int64_t q_item[kLdQueue];
+  __shared__ int64_t s_item[2];  // the waiter's hand-over of items to the MMA warp
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -207,7 +211,7 @@ __global__ void __launch_bounds__(kLdThreads, 1) tc_ld_kernel(const LdArgs args)
     }
     for (int s = 0; s < kLdQueue; ++s) {
       mbar_init(&qfull[s], 1);
-      mbar_init(&qempty[s], 1 + kLdEpiWarps);  // the MMA warp and the epilogue warps
+      mbar_init(&qempty[s], 1 + kLdEpiWarps);  // the waiter warp and the epilogue warps
     }
     mbar_init(&tfull, 1);
     mbar_init(&tempty, kLdEpiWarps);
@@ -296,51 +300,42 @@ __global__ void __launch_bounds__(kLdThreads, 1) tc_ld_kernel(const LdArgs args)
       if (stop) break;
     }
   } else if (warp == 1) {
+    // MMA warp.  It never waits on memory itself: a thread with MMAs in flight
+    // that polls a barrier or loads from memory stalls until they complete,
+    // which would drain the tensor pipe at every ring stage.  Warp 2 takes the
+    // items from the queue and does every wait; it hands each item over
+    // through s_item and releases this warp once per stage through hardware
+    // barrier kLdBar (both warps execute bar.sync once per hand-over and once
+    // per stage, in the same order; every item covers all chunks).
     uint32_t g = 0;
     const uint32_t sf = tmem + kSfCol;
     for (uint32_t e = 0;; ++e) {
-      int64_t it;
-      if (!queue_get(e, it)) {
-        fail(true);
-        break;
-      }
+      asm volatile("bar.sync %0, 64;" ::"n"(kLdBar) : "memory");
+      const int64_t it = *(volatile int64_t*)&s_item[e & 1u];
       if (it < 0) break;
-      const bool free_ok = e == 0 || mbar_wait_bounded(&tempty, (e - 1) & 1u);
-      bool stop = __any_sync(0xffffffffu, !free_ok);
-      if (!stop) {
+      for (int64_t k0 = 0; k0 < nk; k0 += kLdPer, ++g) {
+        asm volatile("bar.sync %0, 64;" ::"n"(kLdBar) : "memory");
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        for (int64_t k0 = 0; k0 < nk; k0 += kLdPer, ++g) {
-          const int s = (int)(g % kLdStages);
-          const bool ok = mbar_wait_bounded(&full[s], (g / kLdStages) & 1u);
-          if (__any_sync(0xffffffffu, !ok)) {
-            stop = true;
-            break;
-          }
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          if (lane == 0) {
-            const uint32_t st0 = smem_addr(ring + (size_t)s * kLdStageBytes);
+        const int s = (int)(g % kLdStages);
+        if (lane == 0) {
+          const uint32_t st0 = smem_addr(ring + (size_t)s * kLdStageBytes);
 #pragma unroll
-            for (int c = 0; c < kLdPer; ++c) {
-              const uint32_t a0 = st0 + c * kLdChunkBytes, b0 = st0 + kLdPer * kLdChunkBytes + c * kLdHalfChunkBytes;
-              const uint64_t aX = umma_desc(a0), aV = umma_desc(a0 + kTileBytes), aH = umma_desc(a0 + 2 * kTileBytes);
-              const uint64_t bX = umma_desc(b0), bV = umma_desc(b0 + kLdHalfBytes),
-                             bH = umma_desc(b0 + 2 * kLdHalfBytes);
-              const uint32_t acc = k0 + c > 0 ? 1u : 0u;
-              umma<kTcFp4, kLdN>(tmem + 0 * kLdN, aV, bV, acc, sf);  // N
-              umma<kTcFp4, kLdN>(tmem + 1 * kLdN, aX, bV, acc, sf);  // Sx
-              umma<kTcFp4, kLdN>(tmem + 2 * kLdN, aV, bX, acc, sf);  // Sy
-              umma<kTcFp4, kLdN>(tmem + 3 * kLdN, aH, bV, acc, sf);  // Sxx
-              umma<kTcFp4, kLdN>(tmem + 4 * kLdN, aV, bH, acc, sf);  // Syy
-              umma<kTcFp4, kLdN>(tmem + 5 * kLdN, aX, bX, acc, sf);  // Sxy
-            }
-            umma_commit(&empty[s]);
+          for (int c = 0; c < kLdPer; ++c) {
+            const uint32_t a0 = st0 + c * kLdChunkBytes, b0 = st0 + kLdPer * kLdChunkBytes + c * kLdHalfChunkBytes;
+            const uint64_t aX = umma_desc(a0), aV = umma_desc(a0 + kTileBytes), aH = umma_desc(a0 + 2 * kTileBytes);
+            const uint64_t bX = umma_desc(b0), bV = umma_desc(b0 + kLdHalfBytes),
+                           bH = umma_desc(b0 + 2 * kLdHalfBytes);
+            const uint32_t acc = k0 + c > 0 ? 1u : 0u;
+            umma<kTcFp4, kLdN>(tmem + 0 * kLdN, aV, bV, acc, sf);  // N
+            umma<kTcFp4, kLdN>(tmem + 1 * kLdN, aX, bV, acc, sf);  // Sx
+            umma<kTcFp4, kLdN>(tmem + 2 * kLdN, aV, bX, acc, sf);  // Sy
+            umma<kTcFp4, kLdN>(tmem + 3 * kLdN, aH, bV, acc, sf);  // Sxx
+            umma<kTcFp4, kLdN>(tmem + 4 * kLdN, aV, bH, acc, sf);  // Syy
+            umma<kTcFp4, kLdN>(tmem + 5 * kLdN, aX, bX, acc, sf);  // Sxy
           }
-          __syncwarp();
+          umma_commit(&empty[s]);
         }
-      }
-      if (stop || aborted()) {
-        fail(stop);
-        break;
+        __syncwarp();
       }
       if (lane == 0) umma_commit(&tfull);
       __syncwarp();
@@ -349,6 +344,42 @@ __global__ void __launch_bounds__(kLdThreads, 1) tc_ld_kernel(const LdArgs args)
     __syncwarp();
     const bool drained = mbar_wait_bounded(&drain, 0);
     if (lane == 0 && !drained) atomicExch(status, kDevTimeout);
+  } else if (warp == 2) {
+    // Waiter: for each item from the queue, hand it over; before its first
+    // stage wait (bounded) until the epilogue has read the previous item's
+    // accumulators, and before each stage until its operands have landed;
+    // then release the MMA warp.  After a failed wait or another role's abort
+    // it stops waiting but keeps releasing the current item's stages (the MMA
+    // warp runs them out on stale operands; the call reports IBS_ETIMEOUT),
+    // then hands over the end (-1).
+    uint32_t g = 0;
+    bool dead = false;
+    for (uint32_t e = 0;; ++e) {
+      int64_t it = -1;
+      if (!dead && !queue_get(e, it)) {
+        fail(true);
+        dead = true;
+      }
+      if (dead) it = -1;
+      if (lane == 0) s_item[e & 1u] = it;
+      __syncwarp();
+      asm volatile("bar.sync %0, 64;" ::"n"(kLdBar) : "memory");
+      if (it < 0) break;
+      for (int64_t k0 = 0; k0 < nk; k0 += kLdPer, ++g) {
+        if (!dead) {
+          bool ok = k0 > 0 || e == 0 || mbar_wait_bounded(&tempty, (e - 1) & 1u);
+          if (ok) ok = mbar_wait_bounded(&full[(int)(g % kLdStages)], (g / kLdStages) & 1u);
+          if (__any_sync(0xffffffffu, !ok)) {
+            fail(true);
+            dead = true;
+          } else if (aborted()) {
+            dead = true;
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        asm volatile("bar.sync %0, 64;" ::"n"(kLdBar) : "memory");
+      }
+    }
   } else if (warp >= 4) {
     const int quarter = warp & 3, colhalf = (warp - 4) >> 2;
     const int row = quarter * 32 + lane;
